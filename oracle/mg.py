@@ -1,0 +1,402 @@
+"""Plain FP64 multigrid for 2D Poisson with red-black or standard coarsening.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring). Parity of the CUDA library
+is measured against this module; the library never calls it.
+
+What is computed, and where the paper defines it (Liu & Henshaw, "Multigrid with
+nonstandard coarsening", arXiv:2008.03885):
+
+* Problem: -Laplace u = f on the unit square, homogeneous Dirichlet data, N cells
+  per side (h = 1/N, N a power of two), unknowns = interior nodes (Sec. 2.1).
+* Fine operators: the 5-point second-order Laplacian, Eq. (L_h_2), and the wide
+  9-point fourth-order one, Eq. (L_h_2d_4o). Next to the boundary the fourth-order
+  stencil reaches one node outside; that ghost is closed by odd reflection
+  u(-x) = -u(x) (the paper analyses infinite or periodic grids and is silent here).
+* Coarse grids: standard coarsening H = 2h (Eq. G_H_d) or red-black coarsening
+  (Sec. 4.3, Eq. G_r2, Fig. "redBlackCoarseLevelGrids"): level 2m is an axis grid
+  of spacing 2^m h, level 2m+1 is the set of black points (i+j even) of level 2m,
+  a rotated grid of spacing 2^m sqrt(2) h. Coarsening stops at an axis grid with
+  n_min cells per side.
+* Transfers: red-black coarsening uses Eq. (transfer_r2) in each fine level's own
+  frame: interpolation 1/4 ]. 1 .; 1 4 1; . 1 .[ and restriction R = 1/2 P^T;
+  standard coarsening uses bilinear interpolation and full weighting R = 1/4 P^T,
+  Eq. (transfer_2d). Both are assembled here as explicit sparse matrices.
+* Coarse operators (Sec. 2.3 notation, Sec. 4.4): non-Galerkin = the 5-point
+  stencil on the coarse grid with spacing H (Eq. L_H_2d; for fourth order this is
+  nG^(2)); Galerkin = the recursion L_{l+1} = R L_l P, Eq. (L_G_l), formed here by
+  an explicit sparse product; for a fourth-order fine level the recursion starts
+  from the second-order L_h^(2), Eq. (L_H_2G_2d), i.e. G^(2); "true high" starts it
+  from the fourth-order L_h itself; G1 = the first-generation Galerkin stencil
+  Eq. (L_G1) on every coarse level; Gn = Galerkin on level 1, non-Galerkin below.
+* Smoother: red-black relaxation S = S^B S^R, Eq. (S_rb), red = (i+j) odd on axis
+  grids; on a rotated grid the colour is the parity of k1+k2 in the rotated frame,
+  which is the parity of i. Within one colour every point is updated from the
+  values at the start of the half-sweep (Jacobi within a colour); for the 5-point
+  stencil this is exactly red-black Gauss-Seidel (Sec. 4.2, S^GS = S^J).
+  Weighted Jacobi, S = I - omega h^2/(2d) L_h (Sec. 5.3), is the other option.
+* Cycle: the gamma-cycle MG(f; maxIters) of Sec. 2.2 (Algorithm "MG"): pre-smooth,
+  residual, restrict, recurse (zero initial guess, Eq. L_H_approx) or solve exactly
+  on the coarsest level, interpolate, correct, post-smooth.
+
+Floating-point evaluation order (so that any implementation following the same
+order reproduces every iterate bit for bit): each operator application
+y_p = sum_q a_pq x_q sums its nonzeros in increasing column order of a row-major
+(j, then i) numbering of the level's unknowns, starting from the first product,
+every product rounded separately (no fused multiply-add); coefficients are exact
+dyadic weights w times one scale s per level (a_pq = fl(w_pq * s)); a relaxation
+is u + r * fl(omega / a_pp) with r = f - (A u); a correction is u + (P v).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+
+REDBLACK = "redblack"
+STANDARD = "standard"
+
+NONGALERKIN = "nongalerkin"
+GALERKIN = "galerkin"
+G1 = "g1"
+GN = "gn"
+TRUE_HIGH = "galerkin_true_high"
+
+# Stencils in a level's own frame, as {(a, b): weight}; a along the frame's first
+# axis, b along its second. Scales are applied separately.
+FIVE_POINT = {(0, 0): 4.0, (-1, 0): -1.0, (1, 0): -1.0, (0, -1): -1.0, (0, 1): -1.0}  # Eq. L_h_2
+FOURTH_ORDER = {  # Eq. L_h_2d_4o, times 12 h^2
+    (0, 0): 60.0,
+    (-1, 0): -16.0, (1, 0): -16.0, (0, -1): -16.0, (0, 1): -16.0,
+    (-2, 0): 1.0, (2, 0): 1.0, (0, -2): 1.0, (0, 2): 1.0,
+}
+FIRST_GALERKIN = {  # Eq. L_G1 / Eq. L_2h_G, times H^2
+    (0, 0): 3.0,
+    (-1, 0): -0.5, (1, 0): -0.5, (0, -1): -0.5, (0, 1): -0.5,
+    (-1, -1): -0.25, (1, -1): -0.25, (-1, 1): -0.25, (1, 1): -0.25,
+}
+
+
+def fold(t: np.ndarray, n: int):
+    """Odd-periodic reflection of lattice coordinate t into [0, n].
+
+    Returns (t', sign, on_boundary). The odd extension of a grid function that
+    vanishes on x = 0 and x = n has period 2n and flips sign at each reflection.
+    """
+    m = np.mod(t, 2 * n)
+    sign = np.where(m <= n, 1.0, -1.0)
+    tp = np.where(m <= n, m, 2 * n - m)
+    return tp, sign, (tp == 0) | (tp == n)
+
+
+@dataclass
+class Level:
+    kind: str  # "axis" or "rot"
+    n: int  # cells per side of the lattice the level's points live on
+    h2: float  # squared grid spacing of this level (in the level's own frame)
+    pi: np.ndarray = field(repr=False, default=None)  # unknowns' lattice i
+    pj: np.ndarray = field(repr=False, default=None)  # unknowns' lattice j
+    index: np.ndarray = field(repr=False, default=None)  # (n+1, n+1) -> unknown or -1
+    red: np.ndarray = field(repr=False, default=None)  # colour mask over unknowns
+    W: sp.csr_matrix = field(repr=False, default=None)  # dyadic weights
+    s: float = 1.0  # scale: A = fl(W * s)
+    A: sp.csr_matrix = field(repr=False, default=None)
+
+    @property
+    def size(self) -> int:
+        return int(self.pi.size)
+
+    def frame(self, a: int, b: int):
+        """Own-frame stencil offset -> lattice offset (dx, dy).
+
+        Rotated frame: k1 = (i - j)/2, k2 = (i + j)/2 (r = U x, Eq. G_r2), so the
+        frame offset (a, b) is the lattice offset (a + b, b - a).
+        """
+        return (a, b) if self.kind == "axis" else (a + b, b - a)
+
+
+def _make_level(kind: str, n: int, h2: float) -> Level:
+    jj, ii = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+    pi, pj = ii.ravel(), jj.ravel()  # row-major: j major, i minor
+    if kind == "rot":
+        keep = (pi + pj) % 2 == 0
+        pi, pj = pi[keep], pj[keep]
+    index = -np.ones((n + 1, n + 1), dtype=np.int64)
+    index[pj, pi] = np.arange(pi.size)
+    red = ((pi + pj) % 2 == 1) if kind == "axis" else (pi % 2 == 1)
+    return Level(kind=kind, n=n, h2=h2, pi=pi, pj=pj, index=index, red=red)
+
+
+def level_shapes(n: int, coarsening: str, n_min: int = 2, max_levels: int | None = None):
+    """(kind, lattice n, h^2 / h0^2) of every level, finest first."""
+    shapes = [("axis", n, 1.0)]
+    while True:
+        kind, m, r2 = shapes[-1]
+        if max_levels is not None and len(shapes) >= max_levels:
+            break
+        if kind == "axis" and m <= n_min:
+            break
+        if coarsening == REDBLACK:
+            shapes.append(("rot", m, 2.0 * r2) if kind == "axis" else ("axis", m // 2, 2.0 * r2))
+        else:
+            shapes.append(("axis", m // 2, 4.0 * r2))
+    return shapes
+
+
+def stencil_weights(level: Level, stencil: dict, factor: float) -> sp.csr_matrix:
+    """Dirichlet matrix of an own-frame stencil (times `factor`) with odd-reflection ghosts."""
+    n = level.n
+    rows, cols, vals = [], [], []
+    for (a, b), w in stencil.items():
+        dx, dy = level.frame(a, b)
+        ti, si, bi = fold(level.pi + dx, n)
+        tj, sj, bj = fold(level.pj + dy, n)
+        keep = ~(bi | bj)
+        rows.append(np.nonzero(keep)[0])
+        cols.append(level.index[tj[keep], ti[keep]])
+        vals.append((si * sj)[keep] * (w * factor))
+    m = sp.coo_matrix(
+        (np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+        shape=(level.size, level.size),
+    ).tocsr()
+    m.sum_duplicates()
+    m.sort_indices()
+    return m
+
+
+def interpolation(fine: Level, coarse: Level, coarsening: str) -> sp.csr_matrix:
+    """Explicit interpolation P: coarse unknowns -> fine unknowns (Dirichlet)."""
+    rows, cols, vals = [], [], []
+    fi, fj = fine.pi, fine.pj
+    nf, nc = fine.n, coarse.n
+
+    def add(mask, ci, cj, w):
+        inside = mask & (ci >= 1) & (ci <= nc - 1) & (cj >= 1) & (cj <= nc - 1)
+        r = np.nonzero(inside)[0]
+        rows.append(r)
+        cols.append(coarse.index[cj[inside], ci[inside]])
+        vals.append(np.full(r.size, w))
+
+    if coarsening == REDBLACK and fine.kind == "axis":
+        # coarse = black points of the same lattice; red points average 4 axis nbrs
+        black = ~fine.red
+        add(black, fi, fj, 1.0)
+        for dx, dy in ((0, -1), (-1, 0), (1, 0), (0, 1)):
+            add(fine.red, fi + dx, fj + dy, 0.25)
+    elif coarsening == REDBLACK:
+        # rotated fine level: coarse = points with i, j even (lattice n/2)
+        black = ~fine.red
+        add(black, fi // 2, fj // 2, 1.0)
+        for dx, dy in ((-1, -1), (1, -1), (-1, 1), (1, 1)):
+            add(fine.red, (fi + dx) // 2, (fj + dy) // 2, 0.25)
+    else:
+        # bilinear, Eq. transfer_2d
+        assert nf == 2 * nc
+        for ox, wx in ((0, 1.0), (-1, 0.5), (1, 0.5)):
+            for oy, wy in ((0, 1.0), (-1, 0.5), (1, 0.5)):
+                okx = (fi % 2 == 0) if ox == 0 else (fi % 2 == 1)
+                oky = (fj % 2 == 0) if oy == 0 else (fj % 2 == 1)
+                add(okx & oky, (fi + ox) // 2, (fj + oy) // 2, wx * wy)
+    m = sp.coo_matrix(
+        (np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+        shape=(fine.size, coarse.size),
+    ).tocsr()
+    m.sum_duplicates()
+    m.sort_indices()
+    return m
+
+
+class Ell:
+    """A CSR matrix as padded rows with sorted columns, applied in column order."""
+
+    def __init__(self, m: sp.csr_matrix):
+        m = m.tocsr()
+        m.sort_indices()
+        nrow = m.shape[0]
+        counts = np.diff(m.indptr)
+        width = int(counts.max()) if nrow else 0
+        self.shape = m.shape
+        self.cols = np.zeros((width, nrow), dtype=np.int64)
+        self.vals = np.zeros((width, nrow))
+        self.cols[:, :] = np.minimum(np.arange(nrow), max(m.shape[1] - 1, 0))[None, :]
+        row_of = np.repeat(np.arange(nrow), counts)
+        pos = np.arange(m.nnz) - np.repeat(m.indptr[:-1], counts)
+        self.cols[pos, row_of] = m.indices
+        self.vals[pos, row_of] = m.data
+        self.width = width
+
+    def __matmul__(self, x: np.ndarray) -> np.ndarray:
+        if self.width == 0:
+            return np.zeros(self.shape[0])
+        y = self.vals[0] * x[self.cols[0]]
+        for k in range(1, self.width):
+            y = y + self.vals[k] * x[self.cols[k]]
+        return y
+
+
+@dataclass
+class Options:
+    omega: float = 1.0
+    nu1: int = 1
+    nu2: int = 1
+    gamma: int = 1
+    smoother: str = "rb"  # "rb" or "jacobi"
+    n_min: int = 2
+    max_levels: int | None = None
+
+
+class Oracle:
+    """Multigrid hierarchy over explicit sparse matrices (FP64)."""
+
+    def __init__(self, n: int, order: int = 2, coarsening: str = REDBLACK,
+                 coarse_op: str = GALERKIN, options: Options | None = None):
+        assert n >= 2 and (n & (n - 1)) == 0, "N must be a power of two"
+        assert order in (2, 4)
+        self.n, self.order, self.coarsening, self.coarse_op = n, order, coarsening, coarse_op
+        self.opt = options or Options()
+        h = 1.0 / n
+        self.levels = [_make_level(k, m, r2) for k, m, r2 in
+                       level_shapes(n, coarsening, self.opt.n_min, self.opt.max_levels)]
+        self.P, self.R = [], []
+        for l in range(len(self.levels) - 1):
+            P = interpolation(self.levels[l], self.levels[l + 1], coarsening)
+            R = (P.T * (0.5 if coarsening == REDBLACK else 0.25)).tocsr()
+            R.sort_indices()
+            self.P.append(P)
+            self.R.append(R)
+
+        s2 = 1.0 / (h * h)  # scale of operators derived from L_h^(2)
+        s4 = 1.0 / (12.0 * h * h)  # scale of operators derived from L_h^(4)
+        L0 = self.levels[0]
+        if order == 2:
+            L0.W, L0.s = stencil_weights(L0, FIVE_POINT, 1.0), s2
+            base_W, base_s = L0.W, s2
+        else:
+            L0.W, L0.s = stencil_weights(L0, FOURTH_ORDER, 1.0), s4
+            if coarse_op == TRUE_HIGH:
+                base_W, base_s = L0.W, s4
+            else:
+                base_W, base_s = stencil_weights(L0, FIVE_POINT, 1.0), s2  # L_h^(2)
+        gal_W = base_W
+        for l in range(1, len(self.levels)):
+            lev = self.levels[l]
+            gal_W = (self.R[l - 1] @ gal_W @ self.P[l - 1]).tocsr()
+            gal_W.sort_indices()
+            hh = lev.h2  # (h_l / h_0)^2
+            if coarse_op in (GALERKIN, TRUE_HIGH) or (coarse_op == GN and l == 1):
+                lev.W, lev.s = gal_W, base_s
+            elif coarse_op == G1:
+                lev.W, lev.s = stencil_weights(lev, FIRST_GALERKIN, 1.0 / hh), s2
+            else:  # non-Galerkin 5-point with spacing H = h_l
+                lev.W, lev.s = stencil_weights(lev, FIVE_POINT, 1.0 / hh), s2
+        for lev in self.levels:
+            lev.A = (lev.W * lev.s).tocsr()  # elementwise fl(w * s)
+            lev.A.sort_indices()
+        self._A = [Ell(lev.A) for lev in self.levels]
+        self._P = [Ell(P) for P in self.P]
+        self._R = [Ell(R) for R in self.R]
+        self.wd = [self.opt.omega / lev.A.diagonal() for lev in self.levels]
+        last = self.levels[-1]
+        self._coarse_dense = last.A.toarray()
+
+    # ---- grid <-> vector -------------------------------------------------
+    def to_vec(self, grid: np.ndarray, level: int = 0) -> np.ndarray:
+        lev = self.levels[level]
+        return np.ascontiguousarray(grid[lev.pj, lev.pi], dtype=np.float64)
+
+    def to_grid(self, v: np.ndarray, level: int = 0) -> np.ndarray:
+        lev = self.levels[level]
+        g = np.zeros((lev.n + 1, lev.n + 1))
+        g[lev.pj, lev.pi] = v
+        return g
+
+    @property
+    def lmax(self) -> int:
+        return len(self.levels) - 1
+
+    # ---- level operations ------------------------------------------------
+    def apply(self, l: int, u: np.ndarray) -> np.ndarray:
+        return self._A[l] @ u
+
+    def residual(self, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
+        return f - self._A[l] @ u
+
+    def restrict(self, l: int, d: np.ndarray) -> np.ndarray:
+        return self._R[l] @ d
+
+    def prolong(self, l: int, v: np.ndarray) -> np.ndarray:
+        return self._P[l] @ v
+
+    def half_sweep(self, l: int, u: np.ndarray, f: np.ndarray, red: bool) -> np.ndarray:
+        mask = self.levels[l].red if red else ~self.levels[l].red
+        r = f - self._A[l] @ u
+        return np.where(mask, u + r * self.wd[l], u)
+
+    def smooth(self, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
+        if self.opt.smoother == "jacobi":
+            r = f - self._A[l] @ u
+            return u + r * self.wd[l]
+        u = self.half_sweep(l, u, f, red=True)
+        return self.half_sweep(l, u, f, red=False)
+
+    def coarse_solve(self, d: np.ndarray) -> np.ndarray:
+        if d.size == 1:
+            return d / self._coarse_dense[0, 0]
+        return np.linalg.solve(self._coarse_dense, d)
+
+    def cycle_level(self, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
+        o = self.opt
+        for _ in range(o.nu1):
+            u = self.smooth(l, u, f)
+        d = f - self._A[l] @ u
+        fc = self._R[l] @ d
+        if l + 1 == self.lmax:
+            uc = self.coarse_solve(fc)
+        else:
+            uc = np.zeros_like(fc)
+            for _ in range(o.gamma):
+                uc = self.cycle_level(l + 1, uc, fc)
+        u = u + self._P[l] @ uc
+        for _ in range(o.nu2):
+            u = self.smooth(l, u, f)
+        return u
+
+    def cycle(self, u: np.ndarray, f: np.ndarray) -> np.ndarray:
+        if self.lmax == 0:
+            return self.coarse_solve(f)
+        return self.cycle_level(0, u, f)
+
+    def rel_residual(self, u: np.ndarray, f: np.ndarray) -> float:
+        d = f - self._A[0] @ u
+        return math.sqrt(float(np.dot(d, d))) / math.sqrt(float(np.dot(f, f)))
+
+    def solve(self, f: np.ndarray, u: np.ndarray | None = None, rtol: float = 1e-10,
+              max_cycles: int = 50, fixed_cycles: bool = False):
+        """Cycle until ||f - A u|| / ||f|| < rtol (or max_cycles); return (u, history)."""
+        u = np.zeros_like(f) if u is None else u.copy()
+        hist = [self.rel_residual(u, f)]
+        for _ in range(max_cycles):
+            if not fixed_cycles and hist[-1] < rtol:
+                break
+            u = self.cycle(u, f)
+            hist.append(self.rel_residual(u, f))
+        return u, hist
+
+    def direct(self, f: np.ndarray) -> np.ndarray:
+        """Sparse direct solution of A_0 u = f (a check, not part of the cycle)."""
+        import scipy.sparse.linalg as spla
+        return spla.spsolve(self.levels[0].A.tocsc(), f)
+
+
+def work_units(oracle: Oracle) -> float:
+    """Work units of one cycle: sum over levels of (nu1 + nu2 + 1) sweeps weighted by
+    the level's share of fine points, plus the transfers (Sec. 4.4 estimate form)."""
+    o = oracle.opt
+    n0 = oracle.levels[0].size
+    wu = 0.0
+    visits = 1
+    for l, lev in enumerate(oracle.levels[:-1]):
+        wu += visits * (o.nu1 + o.nu2 + 2) * lev.size / n0
+        visits *= o.gamma if l + 1 < oracle.lmax else 1
+    return wu

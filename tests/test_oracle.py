@@ -1,0 +1,326 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks a printed stencil or
+number, a closed form, a theorem, an exact algebraic identity or brute force.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import synth
+from oracle import lfa
+from oracle.mg import (G1, GALERKIN, GN, NONGALERKIN, REDBLACK, STANDARD, TRUE_HIGH,
+                       Options, Oracle)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return json.load(fh)
+
+
+def row_stencil(lev, A, i, j):
+    """{(dx, dy): value} of the row of unknown (i, j) of an explicit level matrix."""
+    p = lev.index[j, i]
+    row = A.getrow(p)
+    return {(int(lev.pi[q] - i), int(lev.pj[q] - j)): float(v) for q, v in zip(row.indices, row.data)}
+
+
+def printed(entry):
+    """Printed stencil -> {(a, b): weight}, a along +x (columns), b along +y (rows)."""
+    w = np.array(entry["weights"], dtype=float)
+    r = w.shape[0] // 2
+    out = {}
+    for row in range(w.shape[0]):
+        for col in range(w.shape[1]):
+            if w[row, col] != 0:
+                out[(col - r, r - row)] = w[row, col]
+    return out
+
+
+# ---------------------------------------------------------------- fine operators
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("n", [8, 32])
+def test_fine_operator_matches_printed_stencil(order, n):
+    st = golden("paper_stencils.json")["L_h_2" if order == 2 else "L_h_2d_4o"]
+    o = Oracle(n, order, REDBLACK, GALERKIN)
+    lev = o.levels[0]
+    c = n // 2
+    row = row_stencil(lev, lev.A, c, c)
+    denom = 1.0 if order == 2 else 12.0
+    want = {k: v * n * n / denom for k, v in printed(st).items()}
+    assert set(row) == set(want)
+    for k in want:
+        assert row[k] == pytest.approx(want[k], rel=1e-15)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("k,l", [(1, 1), (3, 5), (7, 2), (15, 15)])
+def test_sine_modes_are_eigenvectors_with_paper_symbol(order, k, l):
+    """sin(k pi x) sin(l pi y) is an exact eigenvector of the Dirichlet operator (odd
+    reflection closure) with eigenvalue = the paper's symbol at theta = (k pi h, l pi h)."""
+    n = 16
+    o = Oracle(n, order, REDBLACK, GALERKIN)
+    v = o.to_vec(synth.rhs_single_mode(n, k, l))
+    t1, t2 = k * math.pi / n, l * math.pi / n
+    lam = lfa.symbol_L2(t1, t2, 1.0 / n) if order == 2 else lfa.symbol_L4(t1, t2, 1.0 / n)
+    Av = o.apply(0, v)
+    assert np.max(np.abs(Av - lam * v)) <= 1e-12 * lam * np.max(np.abs(v))
+
+
+@pytest.mark.parametrize("order,expected", [(2, 4.0), (4, 16.0)])
+def test_manufactured_solution_convergence_order(order, expected):
+    """Discretisation error of u = sin(pi x) sin(pi y) falls at order 2 / 4 (Sec. 2.3)."""
+    errs = []
+    for n in (16, 32, 64):
+        o = Oracle(n, order, REDBLACK, GALERKIN)
+        x = np.arange(n + 1) / n
+        U = np.outer(np.sin(math.pi * x), np.sin(math.pi * x))
+        F = 2 * math.pi ** 2 * U
+        u = o.direct(o.to_vec(F))
+        errs.append(np.max(np.abs(u - o.to_vec(U))))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert ratios[-1] == pytest.approx(expected, rel=0.05)
+
+
+# ---------------------------------------------------------------- coarse operators
+def test_first_galerkin_rbc_equals_printed_L_G1():
+    """R L_h P on the first red-black coarse level is Eq. (L_G1), in the rotated frame."""
+    st = printed(golden("paper_stencils.json")["L_G1"])
+    n = 32
+    o = Oracle(n, 2, REDBLACK, GALERKIN)
+    lev = o.levels[1]
+    row = row_stencil(lev, lev.A, 16, 16)
+    H2 = 2.0 / (n * n)
+    want = {}
+    for (a, b), w in st.items():
+        dx, dy = a + b, b - a  # rotated frame -> lattice
+        want[(dx, dy)] = w / (4.0 * H2)
+    assert row == pytest.approx(want, rel=1e-15)
+
+
+def test_first_galerkin_sc_equals_printed_L_2h_G():
+    st = printed(golden("paper_stencils.json")["L_2h_G"])
+    n = 32
+    o = Oracle(n, 2, STANDARD, GALERKIN)
+    lev = o.levels[1]
+    row = row_stencil(lev, lev.A, 8, 8)
+    H2 = 4.0 / (n * n)
+    assert row == pytest.approx({k: w / (4.0 * H2) for k, w in st.items()}, rel=1e-15)
+
+
+def test_transfers_match_printed_stencils():
+    g = golden("paper_stencils.json")
+    n = 16
+    o = Oracle(n, 2, REDBLACK, GALERKIN)
+    lev0, lev1 = o.levels[0], o.levels[1]
+    c = lev1.index[8, 8]
+    row = o.R[0].getrow(c)
+    got = {(int(lev0.pi[q] - 8), int(lev0.pj[q] - 8)): v for q, v in zip(row.indices, row.data)}
+    assert got == pytest.approx({k: w / 8 for k, w in printed(g["restriction_rb"]).items()})
+    os_ = Oracle(n, 2, STANDARD, GALERKIN)
+    c = os_.levels[1].index[4, 4]
+    row = os_.R[0].getrow(c)
+    got = {(int(lev0.pi[q] - 8), int(lev0.pj[q] - 8)): v for q, v in zip(row.indices, row.data)}
+    assert got == pytest.approx({k: w / 16 for k, w in printed(g["restriction_std"]).items()})
+    # interpolation = adjoint: P = 2 R^T (red-black), 4 R^T (standard)
+    assert abs(o.P[0] - 2 * o.R[0].T).max() == 0
+    assert abs(os_.P[0] - 4 * os_.R[0].T).max() == 0
+
+
+@pytest.mark.parametrize("coarsening", [REDBLACK, STANDARD])
+@pytest.mark.parametrize("op", [NONGALERKIN, GALERKIN, G1, GN, TRUE_HIGH])
+@pytest.mark.parametrize("order", [2, 4])
+def test_level_operators_symmetric_positive_definite(coarsening, op, order):
+    o = Oracle(16, order, coarsening, op)
+    for lev in o.levels:
+        A = lev.A.toarray()
+        assert np.array_equal(A, A.T)
+        assert np.linalg.eigvalsh(A).min() > 0
+
+
+def _convolve(a, b):
+    out = {}
+    for (x1, y1), w1 in a.items():
+        for (x2, y2), w2 in b.items():
+            k = (x1 + x2, y1 + y2)
+            out[k] = out.get(k, 0.0) + w1 * w2
+    return {k: v for k, v in out.items() if v != 0.0}
+
+
+def test_multilevel_galerkin_interior_rows_equal_infinite_grid_stencil_product():
+    """Away from the boundary the sparse R A P row equals the convolution R * A * P of
+    the infinite-grid stencils (brute force on the lattice), on every level."""
+    n = 64
+    o = Oracle(n, 2, REDBLACK, GALERKIN)
+    A = {(0, 0): 4.0, (1, 0): -1.0, (-1, 0): -1.0, (0, 1): -1.0, (0, -1): -1.0}
+    for l in range(1, 5):
+        fine, lev = o.levels[l - 1], o.levels[l]
+        if fine.kind == "axis":
+            Pst = {(0, 0): 1.0, (1, 0): 0.25, (-1, 0): 0.25, (0, 1): 0.25, (0, -1): 0.25}
+            scale = 1  # coarse lattice = fine lattice
+        else:
+            Pst = {(0, 0): 1.0, (1, 1): 0.25, (-1, 1): 0.25, (1, -1): 0.25, (-1, -1): 0.25}
+            scale = 2
+        Rst = {k: 0.5 * v for k, v in Pst.items()}
+        full = _convolve(_convolve(Rst, A), Pst)
+        # keep offsets that land on coarse points, express in coarse lattice units
+        A = {(dx // scale, dy // scale): v for (dx, dy), v in full.items()
+             if dx % scale == 0 and dy % scale == 0 and (fine.kind == "rot" or (dx + dy) % 2 == 0)}
+        c = lev.n // 2
+        row = row_stencil(lev, lev.W, c, c)
+        assert row == pytest.approx(A, rel=0, abs=0), l
+
+
+def test_red_black_reduction_schur_complement_is_twice_galerkin():
+    """Eliminating the red unknowns of the 5-point Dirichlet matrix gives 2 R A P
+    (Sec. 4.5, red-black reduction / total reduction: S_H = 8 h^2 L_H, S_h = h^2 L_h)."""
+    n = 16
+    o = Oracle(n, 2, REDBLACK, GALERKIN)
+    lev = o.levels[0]
+    A = lev.A.toarray()
+    red, blk = lev.red, ~lev.red
+    Arr, Arb, Abr, Abb = A[np.ix_(red, red)], A[np.ix_(red, blk)], A[np.ix_(blk, red)], A[np.ix_(blk, blk)]
+    assert np.array_equal(Arr, np.diag(np.diag(Arr)))
+    S = Abb - Abr @ np.diag(1.0 / np.diag(Arr)) @ Arb
+    # black unknowns of level 0 in row-major order are exactly level 1's unknowns
+    assert np.array_equal(lev.pi[blk], o.levels[1].pi) and np.array_equal(lev.pj[blk], o.levels[1].pj)
+    assert np.array_equal(S, 2.0 * o.levels[1].A.toarray())
+
+
+# ---------------------------------------------------------------- cycles
+def test_two_level_rbc_galerkin_is_direct_solver():
+    """Theorem (Sec. 4.3): two-level RBC, Galerkin, omega = 1 converges in one cycle."""
+    ref = golden("paper_rates.json")["rbc_2level_V11_galerkin_omega1_cr"]
+    n = ref["N"]
+    for nu1, nu2 in ((1, 1), (0, 1), (2, 1)):
+        o = Oracle(n, 2, REDBLACK, GALERKIN, Options(nu1=nu1, nu2=nu2, max_levels=2))
+        f = o.to_vec(synth.rhs_normal(n, 3))
+        _, h = o.solve(f, max_cycles=1, fixed_cycles=True)
+        assert h[1] <= ref["abs_tol"] * 100  # roundoff of a 961-unknown solve
+        assert h[1] < 1e-13
+
+
+def test_two_level_rbc_not_direct_without_post_smoothing():
+    o = Oracle(32, 2, REDBLACK, GALERKIN, Options(nu1=1, nu2=0, max_levels=2))
+    f = o.to_vec(synth.rhs_normal(32, 3))
+    _, h = o.solve(f, max_cycles=1, fixed_cycles=True)
+    assert h[1] > 1e-3
+
+
+def _asymptotic_cr(o, seed=5, cycles=12):
+    f = o.to_vec(synth.rhs_normal(o.n, seed))
+    _, h = o.solve(f, max_cycles=cycles, fixed_cycles=True)
+    rates = [h[i + 1] / h[i] for i in range(len(h) - 1) if h[i + 1] > 1e-11]
+    return rates[-1]
+
+
+@pytest.mark.parametrize("omega", [0.9, 1.0, 1.1])
+def test_two_level_rbc_nongalerkin_rate_matches_lfa(omega):
+    """Measured asymptotic CR of the two-level RBC nG cycle vs the LFA of Sec. 4.3."""
+    rho = lfa.rbc_two_level_rho(omega, 1, 1, "nongalerkin")
+    o = Oracle(64, 2, REDBLACK, NONGALERKIN, Options(omega=omega, max_levels=2))
+    cr = _asymptotic_cr(o)
+    assert 0.7 * rho <= cr <= 1.1 * rho, (cr, rho)
+
+
+def test_lfa_galerkin_omega1_is_zero_and_positive_otherwise():
+    assert lfa.rbc_two_level_rho(1.0, 1, 1, "galerkin") < 1e-13
+    assert lfa.rbc_two_level_rho(0.9, 1, 1, "galerkin") > 1e-3
+
+
+def test_jacobi_optimal_parameters_printed_values():
+    g = golden("paper_rates.json")
+    w, mu = lfa.jacobi_optimal(2.0, 2)
+    assert w == pytest.approx(g["jacobi_r2_omega_star"]["value"], abs=1e-12)
+    assert mu == pytest.approx(g["jacobi_r2_mu_star"]["value"], abs=1e-12)
+    # brute-force sup over the high frequencies agrees with the closed form
+    assert lfa.jacobi_smoothing_factor(w, 2.0, 2) == pytest.approx(mu, abs=2e-3)
+
+
+def test_jacobi_smoother_two_level_rate_near_smoothing_factor():
+    """omega*-Jacobi, nu = 2, standard coarsening: CR is of the order of mu*^nu."""
+    w, mu = lfa.jacobi_optimal(2.0, 2)
+    o = Oracle(64, 2, STANDARD, GALERKIN, Options(omega=w, smoother="jacobi", max_levels=2))
+    cr = _asymptotic_cr(o)
+    assert cr <= 1.05 * mu ** 2
+
+
+def _best_over_omega(make, omegas):
+    return min(_asymptotic_cr(make(w)) for w in omegas)
+
+
+def test_three_level_rbc_printed_rates():
+    g = golden("paper_rates.json")
+    omegas = [0.95, 0.97, 1.0, 1.03]
+    for key, gamma in (("rbc_3level_V11_best_cr", 1), ("rbc_3level_W11_best_cr", 2)):
+        ref = g[key]
+        cr = _best_over_omega(lambda w: Oracle(ref["N"], 2, REDBLACK, GALERKIN,
+                                               Options(omega=w, gamma=gamma, max_levels=3)), omegas)
+        lo, hi = ref["band"]
+        assert lo * ref["value"] <= cr <= hi * ref["value"], (key, cr)
+    ref = g["sc_2level_V11_cr"]
+    cr = _asymptotic_cr(Oracle(ref["N"], 2, STANDARD, GALERKIN, Options(max_levels=2)))
+    lo, hi = ref["band"]
+    assert lo * ref["value"] <= cr <= hi * ref["value"], cr
+
+
+def test_multilevel_printed_ecr():
+    g = golden("paper_rates.json")
+    nu = 2
+    omegas = [1.0, 1.1, 1.2]
+    ref = g["rbc_7level_V11_ecr"]
+    cr = _best_over_omega(lambda w: Oracle(ref["N"], 2, REDBLACK, GALERKIN, Options(omega=w, max_levels=7)), omegas)
+    ecr = cr ** (1.0 / (2 * (nu + 2)))
+    assert ref["band"][0] * ref["value"] <= ecr <= ref["band"][1] * ref["value"], ecr
+    ref = g["rbc_7level_W11_ecr"]
+    cr = _asymptotic_cr(Oracle(ref["N"], 2, REDBLACK, GALERKIN, Options(gamma=2, max_levels=7)), cycles=6)
+    ecr = cr ** (1.0 / (6 * (nu + 2)))
+    assert ref["band"][0] * ref["value"] <= ecr <= ref["band"][1] * ref["value"], ecr
+    ref = g["sc_4level_V11_ecr"]
+    cr = _best_over_omega(lambda w: Oracle(ref["N"], 2, STANDARD, GALERKIN, Options(omega=w, max_levels=4)), omegas)
+    ecr = cr ** (1.0 / (4.0 / 3.0 * (nu + 2)))
+    assert ref["band"][0] * ref["value"] <= ecr <= ref["band"][1] * ref["value"], ecr
+
+
+def test_converged_multilevel_solution_equals_direct_solve():
+    for order, co, op in ((2, REDBLACK, GALERKIN), (4, REDBLACK, NONGALERKIN), (4, STANDARD, GALERKIN)):
+        o = Oracle(32, order, co, op, Options(nu1=2 if order == 4 else 1))
+        f = o.to_vec(synth.rhs_normal(32, 7))
+        u, h = o.solve(f, rtol=1e-13, max_cycles=40)
+        ud = o.direct(f)
+        assert np.max(np.abs(u - ud)) <= 1e-11 * np.max(np.abs(ud))
+
+
+def test_converged_solution_equals_closed_form_for_sine_rhs():
+    """For f = sin(k pi x) sin(l pi y) the discrete solution is f / symbol."""
+    n, k, l = 64, 3, 7
+    for order in (2, 4):
+        o = Oracle(n, order, REDBLACK, GALERKIN, Options(nu1=2, nu2=1))
+        f = o.to_vec(synth.rhs_single_mode(n, k, l))
+        t1, t2 = k * math.pi / n, l * math.pi / n
+        lam = lfa.symbol_L2(t1, t2, 1.0 / n) if order == 2 else lfa.symbol_L4(t1, t2, 1.0 / n)
+        u, _ = o.solve(f, rtol=1e-14, max_cycles=30)
+        assert np.max(np.abs(u - f / lam)) <= 1e-12 * np.max(np.abs(f / lam))
+
+
+def test_level_sizes_red_black():
+    o = Oracle(64, 2, REDBLACK, GALERKIN)
+    assert [lev.size for lev in o.levels] == [3969, 1985, 961, 481, 225, 113, 49, 25, 9, 5, 1]
+    o = Oracle(64, 2, STANDARD, GALERKIN)
+    assert [lev.size for lev in o.levels] == [3969, 961, 225, 49, 9, 1]
+
+
+def test_red_points_have_black_neighbours_only_for_five_point():
+    """Red-black colouring of each level: the 5-point (own frame) stencil couples
+    only points of different colour (Sec. 3.1 / Sec. 4.3)."""
+    o = Oracle(32, 2, REDBLACK, NONGALERKIN)
+    for lev in o.levels:
+        A = lev.A.tocoo()
+        off = A.row != A.col
+        assert np.all(lev.red[A.row[off]] != lev.red[A.col[off]])
