@@ -1,0 +1,185 @@
+/*
+ * nsmg.h — C ABI of the GB300 multigrid library for 2D Poisson problems with
+ * nonstandard (red-black, "rotated-grid") or standard coarsening.
+ *
+ * Method: Liu & Henshaw, "Multigrid with nonstandard coarsening",
+ * arXiv:2008.03885. The problem statement is Sec. 2.1 (L_h u_h = f_h); the
+ * fine operators are Eq. (L_h_2) and Eq. (L_h_2d_4o) (Sec. 2.3); coarse grids
+ * are standard coarsening H = 2h (Eq. G_H_d) or red-black coarsening H = sqrt(2) h
+ * (Sec. 4.3, Eq. G_r2), recursively (Sec. 4.4); transfers are Eq. (transfer_2d)
+ * and Eq. (transfer_r2); coarse operators are the non-Galerkin / Galerkin /
+ * G1 / Gn / G^(2) family of Sec. 2.3 and Sec. 4.4 (Eq. L_G_l); the smoother is
+ * red-black relaxation, Eq. (S_rb), or weighted Jacobi (Sec. 5.3); the cycle is
+ * the gamma-cycle of Sec. 2.2 (Algorithm "MG").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Domain: the unit square, N cells per side (N a power of two, 4 <= N <= 16384),
+ *   h = 1/N, homogeneous Dirichlet boundary values.
+ * - Grid arrays on the finest level are caller-owned DEVICE pointers to
+ *   (N+1) x (N+1) contiguous doubles, row-major with x fastest:
+ *   a[j*(N+1) + i] is the node (i h, j h). Boundary entries of f are ignored; the
+ *   boundary entries of u are set to zero by mg_cycle / mg_solve.
+ * - u is the initial guess and is overwritten with the new iterate.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   Work is enqueued on it; calls with *_out arguments synchronise the stream
+ *   before returning so that the outputs are valid.
+ * - The handle owns every hierarchy buffer (allocated with cudaMalloc at setup,
+ *   freed by mg_destroy). A handle is not thread-safe; different handles are
+ *   independent.
+ * - Errors are returned as mg_status, never by aborting. After an error other
+ *   than MG_ERR_CUDA the handle stays usable; the content of u is unspecified.
+ * - Relative residual = ||f - L_h u||_2 / ||f||_2 over interior nodes (the h^d
+ *   weight of the paper's grid norm, Sec. 2.1, cancels).
+ * - Floating-point evaluation order (precision MG_PREC_FP64, fma_contract = 0):
+ *   every operator application sums its nonzeros in increasing row-major
+ *   position of the column, each product rounded separately; relaxation is
+ *   u + r * fl(omega / a_pp) with r = f - (A u). Two implementations that follow
+ *   this order produce the same iterates bit for bit.
+ */
+#ifndef NSMG_H
+#define NSMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID = 1,       /* bad argument: size, enum, NULL pointer, level index */
+  MG_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  MG_ERR_OOM = 3,           /* device allocation failed */
+  MG_ERR_BUDGET = 4,        /* request exceeds a caller-set memory budget */
+  MG_ERR_CUDA = 5,          /* a CUDA runtime call failed; the handle must be destroyed */
+  MG_ERR_NONFINITE = 6,     /* a residual norm is NaN or Inf */
+  MG_ERR_NOT_CONVERGED = 7, /* mg_solve reached max_cycles above rtol */
+  MG_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} mg_status;
+
+typedef enum {
+  MG_COARSEN_STANDARD = 0, /* H = 2h, Eq. (G_H_d) */
+  MG_COARSEN_REDBLACK = 1  /* H = sqrt(2) h, black points of the finer level, Eq. (G_r2) */
+} mg_coarsening;
+
+typedef enum {
+  MG_OP_NONGALERKIN = 0,        /* 5-point stencil with spacing H on every coarse level
+                                   (for order 4 this is nG^(2), Eq. L_H_2d) */
+  MG_OP_GALERKIN = 1,           /* L_{l+1} = R L_l P, Eq. (L_G_l); for order 4 the
+                                   recursion starts from L_h^(2) (G^(2), Eq. L_H_2G_2d) */
+  MG_OP_GALERKIN_G1 = 2,        /* Eq. (L_G1) stencil on every coarse level (Sec. 4.4 "G1") */
+  MG_OP_GALERKIN_GN = 3,        /* Galerkin on level 1, non-Galerkin below (Sec. 4.4 "Gn") */
+  MG_OP_GALERKIN_TRUE_HIGH = 4  /* Galerkin recursion from the order-4 operator itself */
+} mg_coarse_op;
+
+typedef enum {
+  MG_SMOOTH_REDBLACK = 0, /* S = S^B S^R, Eq. (S_rb); Jacobi within a colour */
+  MG_SMOOTH_JACOBI = 1    /* weighted Jacobi, Sec. 5.3 */
+} mg_smoother;
+
+typedef enum {
+  MG_PREC_FP64 = 0,       /* every level in FP64 */
+  MG_PREC_MIXED_FP32 = 1  /* FP64 residual/update, FP32 inner cycles (iterative refinement) */
+} mg_precision;
+
+typedef struct {
+  int32_t n; /* cells per side, power of two */
+} mg_grid;
+
+typedef struct {
+  double omega;        /* relaxation parameter (default 1.0) */
+  int32_t nu1, nu2;    /* pre- and post-smoothing sweeps (default 1, 1) */
+  int32_t gamma;       /* 1 = V cycle, 2 = W cycle (default 1) */
+  int32_t smoother;    /* mg_smoother (default MG_SMOOTH_REDBLACK) */
+  int32_t n_min;       /* coarsest axis grid cells per side (default 2: one unknown) */
+  int32_t max_levels;  /* 0 = no limit */
+  int32_t precision;   /* mg_precision (default MG_PREC_FP64) */
+  int32_t fma_contract;/* 0 = separate rounding of every product (default), 1 = FMA allowed */
+  int32_t inner_cycles;/* mixed precision: FP32 cycles per refinement step (default 2) */
+} mg_options;
+
+typedef struct mg_handle mg_handle;
+
+typedef struct {
+  int32_t kind;     /* 0 = axis grid, 1 = rotated grid (black points of an axis grid) */
+  int32_t n;        /* cells per side of the lattice the level's points live on */
+  int32_t rows;     /* storage rows (n + 1) */
+  int32_t cols;     /* used storage columns: n + 1 (axis) or n/2 + 1 (rotated) */
+  int32_t pitch;    /* elements between rows */
+  int32_t unknowns; /* interior unknowns */
+  int32_t nterms;   /* interior stencil size */
+} mg_level_info;
+/* Storage of a level: a rows x pitch array of the level's precision. Axis
+   grid: element [j*pitch + i] is lattice node (i, j). Rotated grid: only nodes
+   with i + j even exist; node (i, j) is element [j*pitch + (i >> 1)]. */
+
+/* Fill *opt with the defaults listed in mg_options. */
+void mg_default_options(mg_options* opt);
+
+/* Build a hierarchy (Sec. 2.2 components 1-4 for the chosen coarsening and
+   coarse operators). order is 2 (Eq. L_h_2) or 4 (Eq. L_h_2d_4o). opt may be
+   NULL (defaults). On success *out owns device memory until mg_destroy.
+   Errors: MG_ERR_INVALID (n not a power of two in [4, 16384], bad enum, out NULL),
+   MG_ERR_UNSUPPORTED, MG_ERR_OOM, MG_ERR_CUDA. */
+mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening,
+                   mg_coarse_op coarse_op, const mg_options* opt, mg_handle** out);
+
+/* One gamma-cycle (Algorithm "MG" of Sec. 2.2 with maxIters = 1) on device
+   arrays u (in/out) and f. If rel_res_out is not NULL the stream is
+   synchronised and the relative residual after the cycle is stored there.
+   Precision MG_PREC_MIXED_FP32: one refinement step (FP64 residual, inner FP32
+   cycles, FP64 update). */
+mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out, void* stream);
+
+/* Cycle until the relative residual is below rtol or max_cycles cycles ran
+   (the while-test of Algorithm "MG", read as "repeat while above tol").
+   history_out (may be NULL) receives max_cycles + 1 doubles: entry 0 is the
+   initial relative residual, entry k the one after cycle k; entries after the
+   last cycle are left unchanged. cycles_out (may be NULL) receives the number
+   of cycles run. Returns MG_ERR_NOT_CONVERGED if rtol was not reached,
+   MG_ERR_NONFINITE on a NaN/Inf residual, MG_ERR_INVALID if f is zero. */
+mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int max_cycles,
+                   int* cycles_out, double* history_out, void* stream);
+
+/* Release every buffer of the handle (NULL is accepted). */
+mg_status mg_destroy(mg_handle* h);
+
+/* Static text for a status code. */
+const char* mg_status_string(mg_status s);
+
+/* Device bytes mg_setup would allocate for these arguments (0 if invalid). */
+size_t mg_workspace_bytes(const mg_grid* grid, int order, mg_coarsening coarsening,
+                          mg_coarse_op coarse_op, const mg_options* opt);
+
+/* Number of levels (finest = 0, coarsest = mg_num_levels - 1), or -1. */
+int mg_num_levels(const mg_handle* h);
+
+/* Layout of level `level`. */
+mg_status mg_get_level_info(const mg_handle* h, int level, mg_level_info* out);
+
+/* ---- single steps of the cycle on caller buffers in a level's storage ------
+   All pointers are device pointers in the FP64 storage of the named level(s)
+   (mg_get_level_info); boundary entries are read as zero and never written. */
+
+/* out = L_l u on interior nodes. */
+mg_status mg_level_apply(mg_handle* h, int level, const double* u, double* out, void* stream);
+/* d = f - L_l u on interior nodes (Algorithm "MG", residual step). */
+mg_status mg_level_residual(mg_handle* h, int level, const double* u, const double* f,
+                            double* d, void* stream);
+/* `sweeps` smoothing sweeps in place on u (red-black: red half-sweep then black). */
+mg_status mg_level_smooth(mg_handle* h, int level, double* u, const double* f, int sweeps,
+                          void* stream);
+/* f_coarse = R d_fine, R from level `level` to level + 1 (Eq. transfer_r2 / transfer_2d). */
+mg_status mg_level_restrict(mg_handle* h, int level, const double* d_fine, double* f_coarse,
+                            void* stream);
+/* u_fine += P v_coarse, P from level + 1 to level `level`. */
+mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const double* v_coarse,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSMG_H */

@@ -1,0 +1,232 @@
+"""Python binding of libnsmg.so, the GB300 multigrid library (nonstandard coarsening).
+
+Argument marshalling only: every step of the multigrid cycle runs in the CUDA
+kernels of the library. Device arrays are torch CUDA tensors (FP64, contiguous);
+streams are torch CUDA streams. The functions keep the C ABI's names
+(include/nsmg.h) and raise `MGError` on a non-zero status.
+
+There is no CPU fallback: importing this package loads the compiled library
+and fails loudly if it has not been built (`python -c "import __graft_entry__ as
+g; g.build()"`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnsmg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libnsmg.so is not built ({LIB_PATH} missing); run the package build first")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- enums (mirror include/nsmg.h) ------------------------------------------
+MG_OK, MG_ERR_INVALID, MG_ERR_UNSUPPORTED, MG_ERR_OOM, MG_ERR_BUDGET, MG_ERR_CUDA, \
+    MG_ERR_NONFINITE, MG_ERR_NOT_CONVERGED, MG_ERR_TIMEOUT = range(9)
+MG_COARSEN_STANDARD, MG_COARSEN_REDBLACK = 0, 1
+MG_OP_NONGALERKIN, MG_OP_GALERKIN, MG_OP_GALERKIN_G1, MG_OP_GALERKIN_GN, MG_OP_GALERKIN_TRUE_HIGH = range(5)
+MG_SMOOTH_REDBLACK, MG_SMOOTH_JACOBI = 0, 1
+MG_PREC_FP64, MG_PREC_MIXED_FP32 = 0, 1
+
+COARSENING = {"standard": MG_COARSEN_STANDARD, "redblack": MG_COARSEN_REDBLACK}
+COARSE_OP = {"nongalerkin": MG_OP_NONGALERKIN, "galerkin": MG_OP_GALERKIN, "g1": MG_OP_GALERKIN_G1,
+             "gn": MG_OP_GALERKIN_GN, "galerkin_true_high": MG_OP_GALERKIN_TRUE_HIGH}
+
+
+class mg_grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32)]
+
+
+class mg_options(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
+                ("gamma", ctypes.c_int32), ("smoother", ctypes.c_int32), ("n_min", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32)]
+
+
+class mg_level_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("cols", ctypes.c_int32), ("pitch", ctypes.c_int32), ("unknowns", ctypes.c_int32),
+                ("nterms", ctypes.c_int32)]
+
+
+_vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+
+_lib.mg_default_options.argtypes = [ctypes.POINTER(mg_options)]
+_lib.mg_default_options.restype = None
+_lib.mg_setup.argtypes = [ctypes.POINTER(mg_grid), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                          ctypes.POINTER(mg_options), ctypes.POINTER(_vp)]
+_lib.mg_cycle.argtypes = [_vp, _vp, _vp, _dp, _vp]
+_lib.mg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip, _dp, _vp]
+_lib.mg_destroy.argtypes = [_vp]
+_lib.mg_status_string.argtypes = [ctypes.c_int]
+_lib.mg_status_string.restype = ctypes.c_char_p
+_lib.mg_workspace_bytes.argtypes = [ctypes.POINTER(mg_grid), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(mg_options)]
+_lib.mg_workspace_bytes.restype = ctypes.c_size_t
+_lib.mg_num_levels.argtypes = [_vp]
+_lib.mg_get_level_info.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(mg_level_info)]
+_lib.mg_level_apply.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+_lib.mg_level_residual.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.mg_level_smooth.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]
+_lib.mg_level_restrict.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+_lib.mg_level_prolong_add.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
+for _name in ("mg_setup", "mg_cycle", "mg_solve", "mg_destroy", "mg_get_level_info", "mg_level_apply",
+              "mg_level_residual", "mg_level_smooth", "mg_level_restrict", "mg_level_prolong_add"):
+    getattr(_lib, _name).restype = ctypes.c_int
+_lib.mg_num_levels.restype = ctypes.c_int
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib.mg_status_string(status).decode()} (status {status})")
+
+
+def _check(status: int, what: str):
+    if status != MG_OK:
+        raise MGError(status, what)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a torch CUDA tensor (contiguous); ints pass through."""
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def mg_default_options(**overrides) -> mg_options:
+    o = mg_options()
+    _lib.mg_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def mg_workspace_bytes(n: int, order: int = 2, coarsening="redblack", coarse_op="galerkin", **opts) -> int:
+    g = mg_grid(n)
+    o = mg_default_options(**opts)
+    return int(_lib.mg_workspace_bytes(ctypes.byref(g), order, COARSENING.get(coarsening, coarsening),
+                                       COARSE_OP.get(coarse_op, coarse_op), ctypes.byref(o)))
+
+
+class Handle:
+    """Owns an mg_handle; freed by close() or garbage collection."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            _lib.mg_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def mg_setup(n: int, order: int = 2, coarsening="redblack", coarse_op="galerkin", **opts) -> Handle:
+    g = mg_grid(n)
+    o = mg_default_options(**opts)
+    out = _vp()
+    _check(_lib.mg_setup(ctypes.byref(g), order, COARSENING.get(coarsening, coarsening),
+                         COARSE_OP.get(coarse_op, coarse_op), ctypes.byref(o), ctypes.byref(out)), "mg_setup")
+    return Handle(out.value)
+
+
+def mg_destroy(h: Handle):
+    h.close()
+
+
+def mg_cycle(h: Handle, u, f, stream=None) -> float:
+    rr = ctypes.c_double()
+    _check(_lib.mg_cycle(h.ptr, _ptr(u), _ptr(f), ctypes.byref(rr), _stream(stream)), "mg_cycle")
+    return rr.value
+
+
+def mg_solve(h: Handle, u, f, rtol: float = 1e-10, max_cycles: int = 50, stream=None,
+             raise_not_converged: bool = True):
+    """Returns (cycles, history list of relative residuals)."""
+    hist = (ctypes.c_double * (max_cycles + 1))()
+    cyc = ctypes.c_int()
+    st = _lib.mg_solve(h.ptr, _ptr(u), _ptr(f), rtol, max_cycles, ctypes.byref(cyc), hist, _stream(stream))
+    if st != MG_OK and not (st == MG_ERR_NOT_CONVERGED and not raise_not_converged):
+        raise MGError(st, "mg_solve")
+    return cyc.value, [hist[k] for k in range(cyc.value + 1)]
+
+
+def mg_num_levels(h: Handle) -> int:
+    return _lib.mg_num_levels(h.ptr)
+
+
+def mg_get_level_info(h: Handle, level: int) -> mg_level_info:
+    info = mg_level_info()
+    _check(_lib.mg_get_level_info(h.ptr, level, ctypes.byref(info)), "mg_get_level_info")
+    return info
+
+
+def mg_level_apply(h: Handle, level: int, u, out, stream=None):
+    _check(_lib.mg_level_apply(h.ptr, level, _ptr(u), _ptr(out), _stream(stream)), "mg_level_apply")
+
+
+def mg_level_residual(h: Handle, level: int, u, f, d, stream=None):
+    _check(_lib.mg_level_residual(h.ptr, level, _ptr(u), _ptr(f), _ptr(d), _stream(stream)), "mg_level_residual")
+
+
+def mg_level_smooth(h: Handle, level: int, u, f, sweeps: int = 1, stream=None):
+    _check(_lib.mg_level_smooth(h.ptr, level, _ptr(u), _ptr(f), sweeps, _stream(stream)), "mg_level_smooth")
+
+
+def mg_level_restrict(h: Handle, level: int, d_fine, f_coarse, stream=None):
+    _check(_lib.mg_level_restrict(h.ptr, level, _ptr(d_fine), _ptr(f_coarse), _stream(stream)), "mg_level_restrict")
+
+
+def mg_level_prolong_add(h: Handle, level: int, u_fine, v_coarse, stream=None):
+    _check(_lib.mg_level_prolong_add(h.ptr, level, _ptr(u_fine), _ptr(v_coarse), _stream(stream)),
+           "mg_level_prolong_add")
+
+
+def level_array(h: Handle, level: int, device="cuda"):
+    """A zeroed FP64 torch tensor in the storage layout of `level` (rows x pitch)."""
+    import torch
+    info = mg_get_level_info(h, level)
+    return torch.zeros((info.rows, info.pitch), dtype=torch.float64, device=device)
+
+
+def level_nodes(h: Handle, level: int):
+    """(i, j, row, col) numpy index arrays of the level's interior nodes in row-major
+    (j, then i) order, with their storage row/column."""
+    import numpy as np
+    info = mg_get_level_info(h, level)
+    n = info.n
+    jj, ii = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+    i, j = ii.ravel(), jj.ravel()
+    if info.kind == 1:
+        keep = (i + j) % 2 == 0
+        i, j = i[keep], j[keep]
+        col = i >> 1
+    else:
+        col = i
+    return i, j, j, col

@@ -1,0 +1,667 @@
+// Host side of the library: level layout, stencil calculus for the coarse
+// operators, boundary classes, device buffers, and the cycle / solve drivers
+// behind the C ABI declared in include/nsmg.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/nsmg.h"
+#include "kernels.h"
+
+using namespace nsmg;
+
+namespace {
+
+// ---------------------------------------------------------------- stencils
+// A stencil on a level's lattice: (dy, dx) -> exact dyadic weight. Keying by
+// (dy, dx) makes iteration order the evaluation order of the ABI.
+using Key = std::pair<int, int>;
+using Stencil = std::map<Key, double>;
+
+void put(Stencil& s, int dx, int dy, double w) {
+  if (w == 0.0) return;
+  s[Key(dy, dx)] += w;
+  if (s[Key(dy, dx)] == 0.0) s.erase(Key(dy, dx));
+}
+
+// Own-frame offset (a, b) -> lattice offset. A rotated level's frame has
+// k1 = (i - j)/2, k2 = (i + j)/2 (Sec. 4.3, Eq. G_r2), so (a, b) -> (a + b, b - a).
+Key frame(int kind, int a, int b) { return kind == kRot ? Key(b - a, a + b) : Key(b, a); }
+
+Stencil from_frame(int kind, const std::vector<std::pair<Key, double>>& st, double factor) {
+  Stencil s;
+  for (const auto& t : st) {
+    const Key k = frame(kind, t.first.first, t.first.second);  // (dy, dx)
+    put(s, k.second, k.first, t.second * factor);
+  }
+  return s;
+}
+
+// Own-frame stencils as ((a, b), weight).
+const std::vector<std::pair<Key, double>> kFivePoint = {  // Eq. (L_h_2) times h^2
+    {{0, 0}, 4.0}, {{-1, 0}, -1.0}, {{1, 0}, -1.0}, {{0, -1}, -1.0}, {{0, 1}, -1.0}};
+const std::vector<std::pair<Key, double>> kFourthOrder = {  // Eq. (L_h_2d_4o) times 12 h^2
+    {{0, 0}, 60.0}, {{-1, 0}, -16.0}, {{1, 0}, -16.0}, {{0, -1}, -16.0}, {{0, 1}, -16.0},
+    {{-2, 0}, 1.0}, {{2, 0}, 1.0}, {{0, -2}, 1.0}, {{0, 2}, 1.0}};
+const std::vector<std::pair<Key, double>> kFirstGalerkin = {  // Eq. (L_G1) times H^2
+    {{0, 0}, 3.0}, {{-1, 0}, -0.5}, {{1, 0}, -0.5}, {{0, -1}, -0.5}, {{0, 1}, -0.5},
+    {{-1, -1}, -0.25}, {{1, -1}, -0.25}, {{-1, 1}, -0.25}, {{1, 1}, -0.25}};
+
+// Interpolation weights from a coarse node at fine-lattice position (0, 0) to fine
+// offsets (dx, dy) (Eq. transfer_r2 in the fine level's own frame; Eq. transfer_2d).
+std::vector<std::pair<Key, double>> interp_stencil(int transfer) {
+  if (transfer == kRbAxisToRot)
+    return {{{0, 0}, 1.0}, {{1, 0}, 0.25}, {{-1, 0}, 0.25}, {{0, 1}, 0.25}, {{0, -1}, 0.25}};
+  if (transfer == kRbRotToAxis)
+    return {{{0, 0}, 1.0}, {{1, 1}, 0.25}, {{-1, 1}, 0.25}, {{1, -1}, 0.25}, {{-1, -1}, 0.25}};
+  std::vector<std::pair<Key, double>> p;
+  const double w1[3] = {0.5, 1.0, 0.5};
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) p.push_back({{dx, dy}, w1[dx + 1] * w1[dy + 1]});
+  return p;
+}
+
+int radius(const Stencil& s, bool x) {
+  int r = 0;
+  for (const auto& t : s) r = std::max(r, std::abs(x ? t.first.second : t.first.first));
+  return r;
+}
+
+// Galerkin product R W P on the infinite lattice (Eq. L_G_l): the coarse stencil of a
+// coarse node at the origin. R = 1/2 P^T (red-black) or 1/4 P^T (standard).
+Stencil galerkin(const Stencil& W, int transfer) {
+  const auto P = interp_stencil(transfer);
+  const double rscale = transfer == kStandard ? 0.25 : 0.5;
+  const int step = transfer == kRbAxisToRot ? 1 : 2;  // fine-lattice units per coarse unit
+  const int M = (std::max(radius(W, true), radius(W, false)) + 4) / step + 2;
+  Stencil out;
+  for (int b = -M; b <= M; ++b)
+    for (int a = -M; a <= M; ++a) {
+      if (transfer == kRbAxisToRot && ((a + b) & 1)) continue;  // coarse = black points
+      const int px = a * step, py = b * step;
+      // v = P e_(a,b) on the fine lattice, then (W v) at the restriction's support.
+      std::map<Key, double> v;
+      for (const auto& t : P) v[Key(py + t.first.second, px + t.first.first)] += t.second;
+      double g = 0.0;
+      for (const auto& r : P) {  // restriction support = interpolation support at origin
+        const int rx = r.first.first, ry = r.first.second;
+        double wv = 0.0;
+        for (const auto& w : W) {
+          auto it = v.find(Key(ry + w.first.first, rx + w.first.second));
+          if (it != v.end()) wv += w.second * it->second;
+        }
+        g += rscale * r.second * wv;
+      }
+      if (g != 0.0) put(out, a, b, g);
+    }
+  return out;
+}
+
+// Odd-periodic reflection of t into [0, n]; sets sign and whether it lands on a boundary line.
+int fold(int t, int n, double& sign, bool& bnd) {
+  int m = t % (2 * n);
+  if (m < 0) m += 2 * n;
+  sign = m <= n ? 1.0 : -1.0;
+  const int tp = m <= n ? m : 2 * n - m;
+  bnd = tp == 0 || tp == n;
+  return tp;
+}
+
+// Dirichlet row of node (i, j): the stencil folded by odd reflection, boundary
+// columns dropped, duplicates summed, sorted by (dy, dx).
+Stencil fold_row(const Stencil& st, int n, int i, int j) {
+  Stencil row;
+  for (const auto& t : st) {
+    double si, sj;
+    bool bi, bj;
+    const int ti = fold(i + t.first.second, n, si, bi);
+    const int tj = fold(j + t.first.first, n, sj, bj);
+    if (bi || bj) continue;
+    put(row, ti - i, tj - j, si * sj * t.second);
+  }
+  return row;
+}
+
+struct LevelShape {
+  int kind, n;
+  double hh;  // (h_l / h_0)^2
+};
+
+std::vector<LevelShape> level_shapes(int N, int coarsening, int n_min, int max_levels) {
+  std::vector<LevelShape> s{{kAxis, N, 1.0}};
+  for (;;) {
+    const LevelShape c = s.back();
+    if (max_levels > 0 && (int)s.size() >= max_levels) break;
+    if (c.kind == kAxis && c.n <= n_min) break;
+    if (coarsening == MG_COARSEN_REDBLACK)
+      s.push_back(c.kind == kAxis ? LevelShape{kRot, c.n, 2.0 * c.hh} : LevelShape{kAxis, c.n / 2, 2.0 * c.hh});
+    else
+      s.push_back({kAxis, c.n / 2, 4.0 * c.hh});
+  }
+  return s;
+}
+
+int transfer_of(int coarsening, int fine_kind) {
+  if (coarsening == MG_COARSEN_STANDARD) return kStandard;
+  return fine_kind == kAxis ? kRbAxisToRot : kRbRotToAxis;
+}
+
+// Host-side build of one level's operator description (both precisions).
+struct HostLevel {
+  LevelShape shape;
+  int rows, cols, pitch;
+  Stencil W;  // exact weights
+  double s;   // scale: coefficient = fl(w * s)
+  // boundary classes
+  int small, clsw, ncls;
+  std::vector<int2> cls;
+  std::vector<double> cls_wd;
+  std::vector<int32_t> tdx, tdy;
+  std::vector<double> tc;
+  double wd_fast = 0.0;
+  int rx = 0, ry = 0;
+  std::vector<double> c;  // fast coefficients, (dy, dx) order
+  std::vector<int> dxs, dys;
+  int64_t unknowns = 0;
+};
+
+int storage_cols(int kind, int n) { return kind == kAxis ? n + 1 : n / 2 + 1; }
+int round_pitch(int cols) { return (cols + 31) / 32 * 32; }
+
+void build_classes(HostLevel& L, double omega) {
+  const int n = L.shape.n;
+  L.rx = radius(L.W, true);
+  L.ry = radius(L.W, false);
+  for (const auto& t : L.W) {
+    L.c.push_back(t.second * L.s);
+    L.dxs.push_back(t.first.second);
+    L.dys.push_back(t.first.first);
+  }
+  L.wd_fast = omega / (L.W.at(Key(0, 0)) * L.s);
+  const int R = std::max(L.rx, L.ry);
+  L.small = (n <= 4 * R + 4) ? 1 : 0;
+  L.clsw = L.small ? n + 1 : 2 * L.rx + 1;
+  const int clsh = L.small ? n + 1 : 2 * L.ry + 1;
+  L.ncls = L.clsw * clsh;
+  L.cls.assign(L.ncls, make_int2(0, 0));
+  L.cls_wd.assign(L.ncls, 0.0);
+  auto rep = [&](int c, int r) -> int {  // representative coordinate of class c
+    if (c < r) return c;
+    if (c > r) return n - (2 * r - c);
+    return n / 2;
+  };
+  for (int cy = 0; cy < clsh; ++cy)
+    for (int cx = 0; cx < L.clsw; ++cx) {
+      const int i = L.small ? cx : rep(cx, L.rx);
+      const int j = L.small ? cy : rep(cy, L.ry);
+      const int k = cy * L.clsw + cx;
+      if (i <= 0 || i >= n || j <= 0 || j >= n) continue;
+      if (L.small && L.shape.kind == kRot && ((i + j) & 1)) continue;
+      const Stencil row = fold_row(L.W, n, i, j);
+      L.cls[k] = make_int2((int)L.tdx.size(), (int)row.size());
+      double diag = 0.0;
+      for (const auto& t : row) {
+        L.tdx.push_back(t.first.second);
+        L.tdy.push_back(t.first.first);
+        L.tc.push_back(t.second * L.s);
+        if (t.first.first == 0 && t.first.second == 0) diag = t.second * L.s;
+      }
+      L.cls_wd[k] = omega / diag;
+    }
+}
+
+template <typename T>
+LevelDev<T> to_dev(const HostLevel& L) {
+  LevelDev<T> d;
+  std::memset(&d, 0, sizeof(d));
+  d.kind = L.shape.kind;
+  d.n = L.shape.n;
+  d.rows = L.rows;
+  d.cols = L.cols;
+  d.pitch = L.pitch;
+  d.nt = (int)L.c.size();
+  d.rx = L.rx;
+  d.ry = L.ry;
+  d.small = L.small;
+  d.clsw = L.clsw;
+  d.wd = (T)L.wd_fast;
+  for (int k = 0; k < d.nt; ++k) {
+    d.c[k] = (T)L.c[k];
+    const int dx = L.dxs[k], dy = L.dys[k];
+    if (L.shape.kind == kRot) {
+      // column of (i + dx) >> 1 relative to i >> 1 for i even / odd
+      d.delta[0][k] = dy * L.pitch + (dx >= 0 ? dx / 2 : -((-dx + 1) / 2));
+      d.delta[1][k] = dy * L.pitch + ((dx + 1) >= 0 ? (dx + 1) / 2 : -((-(dx + 1) + 1) / 2));
+    } else {
+      d.delta[0][k] = d.delta[1][k] = dy * L.pitch + dx;
+    }
+  }
+  return d;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- handle
+struct mg_handle {
+  int N = 0, order = 2, coarsening = 1, coarse_op = 1;
+  mg_options opt;
+  std::vector<HostLevel> host;
+  std::vector<int> transfer;
+  std::vector<LevelPair<double>> L64;
+  std::vector<LevelPair<float>> L32;
+  std::vector<double*> u, t, f, d;  // level 0: u and f are the caller's
+  std::vector<float*> u32, t32, f32, d32;
+  double* partial = nullptr;
+  double* scalar = nullptr;      // device
+  double* hscalar = nullptr;     // pinned host
+  std::vector<void*> allocs;     // every cudaMalloc / cudaMallocHost to free
+  std::vector<void*> host_allocs;
+  int64_t coarsest_idx = 0;
+  double coarsest_a = 1.0;
+  int nblocks0 = 0;
+};
+
+namespace {
+
+#define CK(x)                                 \
+  do {                                        \
+    if ((x) != cudaSuccess) return MG_ERR_CUDA; \
+  } while (0)
+
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op, const mg_options& o) {
+  if (!grid || !pow2(grid->n) || grid->n < 4 || grid->n > 16384) return MG_ERR_INVALID;
+  if (order != 2 && order != 4) return MG_ERR_INVALID;
+  if (coarsening != MG_COARSEN_STANDARD && coarsening != MG_COARSEN_REDBLACK) return MG_ERR_INVALID;
+  if (coarse_op < MG_OP_NONGALERKIN || coarse_op > MG_OP_GALERKIN_TRUE_HIGH) return MG_ERR_INVALID;
+  if (!(o.omega > 0.0 && o.omega < 2.0) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 ||
+      o.gamma < 1 || o.gamma > 2 || (o.smoother != MG_SMOOTH_REDBLACK && o.smoother != MG_SMOOTH_JACOBI))
+    return MG_ERR_INVALID;
+  if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED_FP32) return MG_ERR_INVALID;
+  if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
+  if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
+  return MG_OK;
+}
+
+// Level operators for the chosen coarse-operator family (Sec. 2.3 notation).
+void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
+  const double hf = 1.0 / h->N;
+  const double s2 = 1.0 / (hf * hf);         // operators derived from L_h^(2)
+  const double s4 = 1.0 / (12.0 * hf * hf);  // operators derived from L_h^(4)
+  const int nl = (int)shapes.size();
+  h->host.resize(nl);
+  for (int l = 0; l < nl; ++l) h->host[l].shape = shapes[l];
+  HostLevel& L0 = h->host[0];
+  Stencil base;
+  double base_s;
+  if (h->order == 2) {
+    L0.W = from_frame(kAxis, kFivePoint, 1.0);
+    L0.s = s2;
+    base = L0.W;
+    base_s = s2;
+  } else {
+    L0.W = from_frame(kAxis, kFourthOrder, 1.0);
+    L0.s = s4;
+    if (h->coarse_op == MG_OP_GALERKIN_TRUE_HIGH) {
+      base = L0.W;
+      base_s = s4;
+    } else {
+      base = from_frame(kAxis, kFivePoint, 1.0);
+      base_s = s2;
+    }
+  }
+  Stencil gal = base;
+  for (int l = 1; l < nl; ++l) {
+    HostLevel& L = h->host[l];
+    gal = galerkin(gal, transfer_of(h->coarsening, shapes[l - 1].kind));
+    const int op = h->coarse_op;
+    if (op == MG_OP_GALERKIN || op == MG_OP_GALERKIN_TRUE_HIGH || (op == MG_OP_GALERKIN_GN && l == 1)) {
+      L.W = gal;
+      L.s = base_s;
+    } else if (op == MG_OP_GALERKIN_G1) {
+      L.W = from_frame(L.shape.kind, kFirstGalerkin, 1.0 / L.shape.hh);
+      L.s = s2;
+    } else {
+      L.W = from_frame(L.shape.kind, kFivePoint, 1.0 / L.shape.hh);
+      L.s = s2;
+    }
+  }
+  for (int l = 0; l < nl; ++l) {
+    HostLevel& L = h->host[l];
+    L.rows = L.shape.n + 1;
+    L.cols = storage_cols(L.shape.kind, L.shape.n);
+    L.pitch = l == 0 ? L.cols : round_pitch(L.cols);
+    const int64_t m = L.shape.n - 1;
+    L.unknowns = L.shape.kind == kAxis ? m * m : (m * m + 1) / 2;
+    build_classes(L, h->opt.omega);
+  }
+}
+
+size_t level_bytes(const HostLevel& L, size_t elem) { return (size_t)L.rows * L.pitch * elem; }
+
+mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+  }
+  h->allocs.push_back(*p);
+  if (cudaMemset(*p, 0, bytes) != cudaSuccess) return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+template <typename T>
+mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P) {
+  P.h = to_dev<T>(L);
+  int2* cls;
+  T* cwd;
+  int32_t *tdx, *tdy;
+  T* tc;
+  mg_status st;
+  const size_t nt = std::max<size_t>(L.tdx.size(), 1);
+  if ((st = device_alloc(h, (void**)&cls, L.cls.size() * sizeof(int2))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&cwd, L.cls_wd.size() * sizeof(T))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&tdx, nt * sizeof(int32_t))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&tdy, nt * sizeof(int32_t))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&tc, nt * sizeof(T))) != MG_OK) return st;
+  std::vector<T> wd(L.cls_wd.begin(), L.cls_wd.end()), c(L.tc.begin(), L.tc.end());
+  CK(cudaMemcpy(cls, L.cls.data(), L.cls.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(cwd, wd.data(), wd.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!L.tdx.empty()) {
+    CK(cudaMemcpy(tdx, L.tdx.data(), L.tdx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tdy, L.tdy.data(), L.tdy.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tc, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  P.h.cls = cls;
+  P.h.cls_wd = cwd;
+  P.h.tdx = tdx;
+  P.h.tdy = tdy;
+  P.h.tc = tc;
+  if ((st = device_alloc(h, (void**)&P.d, sizeof(LevelDev<T>))) != MG_OK) return st;
+  CK(cudaMemcpy(P.d, &P.h, sizeof(LevelDev<T>), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+void free_all(mg_handle* h) {
+  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->host_allocs) cudaFreeHost(p);
+  h->allocs.clear();
+  h->host_allocs.clear();
+}
+
+// ---------------------------------------------------------------- cycle
+struct Ctx {
+  mg_handle* h;
+  cudaStream_t s;
+  bool exact;
+};
+
+mg_status smooth(const Ctx& c, int l, double* U, const double* F) {
+  mg_handle* h = c.h;
+  double* T = h->t[l];
+  const auto& L = h->L64[l];
+  if (h->opt.smoother == MG_SMOOTH_REDBLACK) {
+    CK(launch_half_sweep<double>(L, c.exact, U, F, T, 1, c.s));
+    CK(launch_half_sweep<double>(L, c.exact, T, F, U, 0, c.s));
+  } else {
+    CK(launch_jacobi<double>(L, c.exact, U, F, T, c.s));
+    CK(cudaMemcpyAsync(U, T, level_bytes(h->host[l], sizeof(double)), cudaMemcpyDeviceToDevice, c.s));
+  }
+  return MG_OK;
+}
+
+mg_status cycle_level(const Ctx& c, int l, double* U, const double* F, bool zero_init) {
+  mg_handle* h = c.h;
+  const int lmax = (int)h->host.size() - 1;
+  mg_status st;
+  if (zero_init) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(double)), c.s));
+  for (int k = 0; k < h->opt.nu1; ++k)
+    if ((st = smooth(c, l, U, F)) != MG_OK) return st;
+  CK(launch_residual<double>(h->L64[l], c.exact, U, F, h->d[l], c.s));
+  CK(launch_restrict<double>(h->L64[l], h->L64[l + 1], h->transfer[l], c.exact, h->d[l], h->f[l + 1], c.s));
+  if (l + 1 == lmax) {
+    CK(launch_coarsest<double>(h->coarsest_idx, h->coarsest_a, h->f[lmax], h->u[lmax], c.s));
+  } else {
+    for (int g = 0; g < h->opt.gamma; ++g)
+      if ((st = cycle_level(c, l + 1, h->u[l + 1], h->f[l + 1], g == 0)) != MG_OK) return st;
+  }
+  CK(launch_prolong_add<double>(h->L64[l], h->L64[l + 1], h->transfer[l], c.exact, U, h->u[l + 1], c.s));
+  for (int k = 0; k < h->opt.nu2; ++k)
+    if ((st = smooth(c, l, U, F)) != MG_OK) return st;
+  return MG_OK;
+}
+
+mg_status read_scalar(mg_handle* h, cudaStream_t s, double* out) {
+  CK(cudaMemcpyAsync(h->hscalar, h->scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *out = *h->hscalar;
+  return MG_OK;
+}
+
+mg_status rel_residual(mg_handle* h, const Ctx& c, const double* U, const double* F, double fn2,
+                       double* out) {
+  CK(launch_resnorm<double>(h->L64[0], c.exact, U, F, h->partial, h->scalar, c.s));
+  double r2;
+  mg_status st = read_scalar(h, c.s, &r2);
+  if (st != MG_OK) return st;
+  *out = std::sqrt(r2) / std::sqrt(fn2);
+  if (!std::isfinite(*out)) return MG_ERR_NONFINITE;
+  return MG_OK;
+}
+
+mg_status f_norm2(mg_handle* h, cudaStream_t s, const double* F, double* out) {
+  CK(launch_sumsq<double>(h->L64[0], F, h->partial, h->scalar, s));
+  mg_status st = read_scalar(h, s, out);
+  if (st != MG_OK) return st;
+  if (!std::isfinite(*out)) return MG_ERR_NONFINITE;
+  if (*out == 0.0) return MG_ERR_INVALID;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_default_options(mg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->omega = 1.0;
+  o->nu1 = 1;
+  o->nu2 = 1;
+  o->gamma = 1;
+  o->smoother = MG_SMOOTH_REDBLACK;
+  o->n_min = 2;
+  o->max_levels = 0;
+  o->precision = MG_PREC_FP64;
+  o->fma_contract = 0;
+  o->inner_cycles = 2;
+}
+
+const char* mg_status_string(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID: return "invalid argument";
+    case MG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case MG_ERR_OOM: return "device out of memory";
+    case MG_ERR_BUDGET: return "memory budget exceeded";
+    case MG_ERR_CUDA: return "CUDA runtime error";
+    case MG_ERR_NONFINITE: return "non-finite residual";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+size_t mg_workspace_bytes(const mg_grid* grid, int order, mg_coarsening coarsening,
+                          mg_coarse_op coarse_op, const mg_options* opt) {
+  mg_options o;
+  if (opt) o = *opt; else mg_default_options(&o);
+  if (validate(grid, order, coarsening, coarse_op, o) != MG_OK) return 0;
+  const auto shapes = level_shapes(grid->n, coarsening, o.n_min, o.max_levels);
+  size_t bytes = 0;
+  for (size_t l = 0; l < shapes.size(); ++l) {
+    const size_t rows = shapes[l].n + 1;
+    const size_t cols = storage_cols(shapes[l].kind, shapes[l].n);
+    const size_t pitch = l == 0 ? cols : round_pitch((int)cols);
+    const size_t arrays = l == 0 ? 2 : 4;
+    bytes += arrays * rows * pitch * sizeof(double);
+    if (o.precision == MG_PREC_MIXED_FP32) bytes += 4 * rows * pitch * sizeof(float);
+  }
+  return bytes;
+}
+
+mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_coarse_op coarse_op,
+                   const mg_options* opt, mg_handle** out) {
+  if (!out) return MG_ERR_INVALID;
+  *out = nullptr;
+  mg_options o;
+  if (opt) o = *opt; else mg_default_options(&o);
+  mg_status st = validate(grid, order, coarsening, coarse_op, o);
+  if (st != MG_OK) return st;
+  if (o.precision != MG_PREC_FP64) return MG_ERR_UNSUPPORTED;
+  mg_handle* h = new (std::nothrow) mg_handle();
+  if (!h) return MG_ERR_OOM;
+  h->N = grid->n;
+  h->order = order;
+  h->coarsening = coarsening;
+  h->coarse_op = coarse_op;
+  h->opt = o;
+  const auto shapes = level_shapes(h->N, coarsening, o.n_min, o.max_levels);
+  build_operators(h, shapes);
+  const int nl = (int)shapes.size();
+  for (int l = 0; l + 1 < nl; ++l) h->transfer.push_back(transfer_of(coarsening, shapes[l].kind));
+  for (const auto& L : h->host)
+    if (L.c.size() > (size_t)kMaxTerms) { delete h; return MG_ERR_UNSUPPORTED; }
+  h->L64.resize(nl);
+  h->u.assign(nl, nullptr);
+  h->t.assign(nl, nullptr);
+  h->f.assign(nl, nullptr);
+  h->d.assign(nl, nullptr);
+  auto fail = [&](mg_status s) { free_all(h); delete h; return s; };
+  for (int l = 0; l < nl; ++l) {
+    if ((st = upload_level<double>(h, h->host[l], h->L64[l])) != MG_OK) return fail(st);
+    const size_t b = level_bytes(h->host[l], sizeof(double));
+    if (l > 0) {
+      if ((st = device_alloc(h, (void**)&h->u[l], b)) != MG_OK) return fail(st);
+      if ((st = device_alloc(h, (void**)&h->f[l], b)) != MG_OK) return fail(st);
+    }
+    if ((st = device_alloc(h, (void**)&h->t[l], b)) != MG_OK) return fail(st);
+    if ((st = device_alloc(h, (void**)&h->d[l], b)) != MG_OK) return fail(st);
+  }
+  h->nblocks0 = resnorm_blocks<double>(h->L64[0]);
+  if ((st = device_alloc(h, (void**)&h->partial, h->nblocks0 * sizeof(double))) != MG_OK) return fail(st);
+  if ((st = device_alloc(h, (void**)&h->scalar, 64)) != MG_OK) return fail(st);
+  if (cudaMallocHost((void**)&h->hscalar, 64) != cudaSuccess) return fail(MG_ERR_CUDA);
+  h->host_allocs.push_back(h->hscalar);
+  // coarsest level: one unknown at lattice node (1, 1)
+  const HostLevel& C = h->host.back();
+  if (C.unknowns != 1) return fail(MG_ERR_UNSUPPORTED);
+  h->coarsest_idx = (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
+  const Stencil row = fold_row(C.W, C.shape.n, 1, 1);
+  h->coarsest_a = row.at(Key(0, 0)) * C.s;
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(MG_ERR_CUDA);
+  *out = h;
+  return MG_OK;
+}
+
+mg_status mg_destroy(mg_handle* h) {
+  if (!h) return MG_OK;
+  free_all(h);
+  delete h;
+  return MG_OK;
+}
+
+int mg_num_levels(const mg_handle* h) { return h ? (int)h->host.size() : -1; }
+
+mg_status mg_get_level_info(const mg_handle* h, int level, mg_level_info* out) {
+  if (!h || !out || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
+  const HostLevel& L = h->host[level];
+  out->kind = L.shape.kind;
+  out->n = L.shape.n;
+  out->rows = L.rows;
+  out->cols = L.cols;
+  out->pitch = L.pitch;
+  out->unknowns = (int32_t)L.unknowns;
+  out->nterms = (int32_t)L.c.size();
+  return MG_OK;
+}
+
+mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out, void* stream) {
+  if (!h || !u || !f) return MG_ERR_INVALID;
+  Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
+  CK(launch_zero_boundary<double>(h->L64[0], u, c.s));
+  mg_status st = cycle_level(c, 0, u, f, false);
+  if (st != MG_OK) return st;
+  if (rel_res_out) {
+    double fn2;
+    if ((st = f_norm2(h, c.s, f, &fn2)) != MG_OK) return st;
+    return rel_residual(h, c, u, f, fn2, rel_res_out);
+  }
+  return MG_OK;
+}
+
+mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int max_cycles,
+                   int* cycles_out, double* history_out, void* stream) {
+  if (!h || !u || !f || max_cycles < 0 || !(rtol >= 0.0)) return MG_ERR_INVALID;
+  Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
+  CK(launch_zero_boundary<double>(h->L64[0], u, c.s));
+  double fn2, rr;
+  mg_status st = f_norm2(h, c.s, f, &fn2);
+  if (st != MG_OK) return st;
+  if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
+  if (history_out) history_out[0] = rr;
+  int k = 0;
+  while (k < max_cycles && rr >= rtol) {
+    if ((st = cycle_level(c, 0, u, f, false)) != MG_OK) return st;
+    ++k;
+    if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
+    if (history_out) history_out[k] = rr;
+  }
+  if (cycles_out) *cycles_out = k;
+  return rr < rtol ? MG_OK : MG_ERR_NOT_CONVERGED;
+}
+
+mg_status mg_level_apply(mg_handle* h, int level, const double* u, double* out, void* stream) {
+  if (!h || !u || !out || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
+  CK(launch_apply<double>(h->L64[level], h->opt.fma_contract == 0, u, out, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_level_residual(mg_handle* h, int level, const double* u, const double* f, double* d,
+                            void* stream) {
+  if (!h || !u || !f || !d || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
+  CK(launch_residual<double>(h->L64[level], h->opt.fma_contract == 0, u, f, d, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_level_smooth(mg_handle* h, int level, double* u, const double* f, int sweeps, void* stream) {
+  if (!h || !u || !f || sweeps < 0 || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
+  Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
+  for (int k = 0; k < sweeps; ++k) {
+    mg_status st = smooth(c, level, u, f);
+    if (st != MG_OK) return st;
+  }
+  return MG_OK;
+}
+
+mg_status mg_level_restrict(mg_handle* h, int level, const double* d_fine, double* f_coarse, void* stream) {
+  if (!h || !d_fine || !f_coarse || level < 0 || level + 1 >= (int)h->host.size()) return MG_ERR_INVALID;
+  CK(launch_restrict<double>(h->L64[level], h->L64[level + 1], h->transfer[level], h->opt.fma_contract == 0,
+                             d_fine, f_coarse, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const double* v_coarse, void* stream) {
+  if (!h || !u_fine || !v_coarse || level < 0 || level + 1 >= (int)h->host.size()) return MG_ERR_INVALID;
+  CK(launch_prolong_add<double>(h->L64[level], h->L64[level + 1], h->transfer[level], h->opt.fma_contract == 0,
+                                u_fine, v_coarse, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// Launch wrappers for the multigrid kernels (kernels.cu). Every wrapper enqueues
+// on `s` and returns the launch status.
+#pragma once
+
+#include "levels.h"
+
+namespace nsmg {
+
+// Host copy + device copy of a level description.
+template <typename T>
+struct LevelPair {
+  LevelDev<T> h;            // host copy (launch geometry, scalars)
+  LevelDev<T>* d = nullptr;  // device copy (read by kernels)
+};
+
+template <typename T>
+cudaError_t launch_half_sweep(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout,
+                              int red, cudaStream_t s);
+template <typename T>
+cudaError_t launch_jacobi(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const LevelPair<T>& L, bool exact, const T* u, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
+                            const T* d, T* fc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer,
+                               bool exact, T* uf, const T* vc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarsest(int64_t idx, T a, const T* f, T* u, cudaStream_t s);
+
+// Sum of squares of d = f - L u over interior nodes of an axis level, in FP64:
+// per-block partial sums into `partial` (size >= resnorm_blocks(L)), then one
+// block adds the partials in a fixed order into *out. Deterministic.
+template <typename T>
+int resnorm_blocks(const LevelPair<T>& L);
+template <typename T>
+cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const T* f,
+                           double* partial, double* out, cudaStream_t s);
+// Sum of squares of f over interior nodes (same reduction order).
+template <typename T>
+cudaError_t launch_sumsq(const LevelPair<T>& L, const T* f, double* partial, double* out,
+                         cudaStream_t s);
+
+// Zero the boundary entries of an axis-level array.
+template <typename T>
+cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s);
+
+}  // namespace nsmg

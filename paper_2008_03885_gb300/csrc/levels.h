@@ -1,0 +1,48 @@
+// Internal types shared by the host hierarchy code and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace nsmg {
+
+constexpr int kMaxTerms = 64;  // largest interior stencil a level may carry
+
+enum Kind : int32_t { kAxis = 0, kRot = 1 };
+
+// Grid transfer between level l (fine) and l + 1 (coarse).
+enum Transfer : int32_t {
+  kRbAxisToRot = 0,  // axis fine grid -> its black points (same lattice)
+  kRbRotToAxis = 1,  // rotated fine grid -> points with i, j even (lattice n/2)
+  kStandard = 2      // axis n -> axis n/2, bilinear / full weighting
+};
+
+// Device-resident description of one level in precision T.
+//
+// Points live on an integer lattice (i, j), 0 <= i, j <= n. Axis levels hold every
+// node; rotated levels hold nodes with i + j even and store node (i, j) at column
+// i >> 1. Interior nodes are the unknowns; boundary entries of every array are 0.
+//
+// The operator is a constant stencil (dx, dy, c) sorted by (dy, dx) for nodes whose
+// stencil stays inside [0, n]^2 ("fast" nodes: rx <= i <= n - rx, ry <= j <= n - ry).
+// Other nodes use a per-class merged term list: the stencil folded by odd
+// reflection at the boundary lines, duplicate columns summed, boundary columns
+// dropped, sorted by (dy, dx). A class is (cx, cy):
+//   small levels: cx = i, cy = j (table (n+1) x (n+1));
+//   otherwise: cx = i for i < rx, 2 rx - (n - i) for i > n - rx, rx in between.
+template <typename T>
+struct LevelDev {
+  int32_t kind, n, rows, cols, pitch;
+  int32_t nt, rx, ry;
+  int32_t small, clsw;
+  T wd;                       // omega / a_pp at fast nodes
+  T c[kMaxTerms];             // fast-node coefficients
+  int32_t delta[2][kMaxTerms];  // storage offsets of the fast terms for i even / odd
+  const int2* cls;            // per class: (first term, term count)
+  const T* cls_wd;            // per class: omega / a_pp
+  const int32_t* tdx;         // merged terms
+  const int32_t* tdy;
+  const T* tc;
+};
+
+}  // namespace nsmg

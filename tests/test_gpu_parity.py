@@ -1,0 +1,196 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 with fma_contract = 0 follows the same evaluation order as the oracle, so
+single steps and whole iterates are compared bit for bit; residual norms differ
+only by the order of the final sum of squares, and per-cycle relative residual
+histories must agree to 1e-12 relative.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle.mg import (G1, GALERKIN, GN, NONGALERKIN, REDBLACK, STANDARD, TRUE_HIGH,
+                       Options, Oracle)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU machines skip the module
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2008_03885_gb300 as mg  # noqa: E402
+
+HIST_RTOL = 1e-12
+
+ALL_CONFIGS = [(order, co, op) for order in (2, 4) for co in (REDBLACK, STANDARD)
+               for op in (NONGALERKIN, GALERKIN, G1, GN, TRUE_HIGH)]
+
+
+def to_dev(h, level, vec):
+    i, j, row, col = mg.level_nodes(h, level)
+    a = mg.level_array(h, level)
+    a[torch.as_tensor(row), torch.as_tensor(col)] = torch.as_tensor(vec, dtype=torch.float64).cuda()
+    return a
+
+
+def from_dev(h, level, a):
+    i, j, row, col = mg.level_nodes(h, level)
+    return a.cpu().numpy()[row, col]
+
+
+def check_order_matches(h, o):
+    for l in range(mg.mg_num_levels(h)):
+        i, j, _, _ = mg.level_nodes(h, l)
+        assert np.array_equal(i, o.levels[l].pi) and np.array_equal(j, o.levels[l].pj)
+
+
+def rng_vec(seed, n):
+    return synth.uniform_pm1(seed, n)
+
+
+@pytest.mark.parametrize("order,co,op", ALL_CONFIGS)
+@pytest.mark.parametrize("n", [64, 128])
+def test_level_steps_bitwise(order, co, op, n):
+    if n == 128 and op in (G1, GN):
+        pytest.skip("covered at n=64")
+    o = Oracle(n, order, co, op)
+    h = mg.mg_setup(n, order, co, op)
+    try:
+        assert mg.mg_num_levels(h) == len(o.levels)
+        check_order_matches(h, o)
+        for l, lev in enumerate(o.levels):
+            m = lev.size
+            u = rng_vec(1000 + l, m) * 3.0
+            f = rng_vec(2000 + l, m) * 1e3
+            du, df = to_dev(h, l, u), to_dev(h, l, f)
+            out = mg.level_array(h, l)
+            mg.mg_level_apply(h, l, du, out)
+            assert np.array_equal(from_dev(h, l, out), o.apply(l, u)), ("apply", l)
+            mg.mg_level_residual(h, l, du, df, out)
+            assert np.array_equal(from_dev(h, l, out), o.residual(l, u, f)), ("residual", l)
+            us = du.clone()
+            mg.mg_level_smooth(h, l, us, df, 2)
+            ref = o.smooth(l, o.smooth(l, u, f), f)
+            assert np.array_equal(from_dev(h, l, us), ref), ("smooth", l)
+            if l + 1 < len(o.levels):
+                fc = mg.level_array(h, l + 1)
+                mg.mg_level_restrict(h, l, df, fc)
+                assert np.array_equal(from_dev(h, l + 1, fc), o.restrict(l, f)), ("restrict", l)
+                v = rng_vec(3000 + l, o.levels[l + 1].size)
+                dv = to_dev(h, l + 1, v)
+                uu = du.clone()
+                mg.mg_level_prolong_add(h, l, uu, dv)
+                assert np.array_equal(from_dev(h, l, uu), u + o.prolong(l, v)), ("prolong", l)
+        torch.cuda.synchronize()
+    finally:
+        h.close()
+
+
+def run_pair(n, order, co, op, F, cycles, **opts):
+    o = Oracle(n, order, co, op, Options(**{k: v for k, v in opts.items() if k in ("omega", "nu1", "nu2", "gamma", "smoother")}))
+    uo, ho = o.solve(o.to_vec(F), max_cycles=cycles, fixed_cycles=True)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    mgopts = dict(opts)
+    if mgopts.get("smoother") == "jacobi":
+        mgopts["smoother"] = mg.MG_SMOOTH_JACOBI
+    h = mg.mg_setup(n, order, co, op, **mgopts)
+    try:
+        k, hg = mg.mg_solve(h, u, f, rtol=0.0, max_cycles=cycles, raise_not_converged=False)
+    finally:
+        h.close()
+    assert k == cycles
+    ug = u.cpu().numpy()[o.levels[0].pj, o.levels[0].pi]
+    return np.array(hg), np.array(ho), ug, uo
+
+
+def test_config_a_history_matches_oracle():
+    """65x65, order 2, RBC, Galerkin, V(1,1), omega = 1, 15 cycles."""
+    n = 64
+    F = synth.rhs_manufactured_noise(n, seed=0)
+    hg, ho, ug, uo = run_pair(n, 2, REDBLACK, GALERKIN, F, 15)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)
+    assert ho[-1] < 1e-12
+
+
+@pytest.mark.parametrize("order,co,op", ALL_CONFIGS)
+def test_cycle_histories_match_oracle(order, co, op):
+    n = 128
+    F = synth.rhs_sine_modes(n, seed=1, n_modes=16, kmax=64) + 0.1 * synth.rhs_normal(n, seed=2)
+    nu1 = 2 if order == 4 else 1
+    omega = 1.1 if (order == 4 and co == STANDARD) else 1.0
+    hg, ho, ug, uo = run_pair(n, order, co, op, F, 10, nu1=nu1, omega=omega)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)
+
+
+@pytest.mark.parametrize("opts", [dict(gamma=2), dict(nu1=0, nu2=2), dict(omega=0.9, nu1=3, nu2=2),
+                                  dict(smoother="jacobi", omega=0.8, nu1=2, nu2=2)])
+def test_cycle_variants_match_oracle(opts):
+    n = 64
+    F = synth.rhs_normal(n, seed=4)
+    co = STANDARD if opts.get("smoother") == "jacobi" else REDBLACK
+    hg, ho, ug, uo = run_pair(n, 2, co, GALERKIN, F, 8, **opts)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32])
+def test_small_grids_match_oracle(n):
+    for order, co, op in ((2, REDBLACK, GALERKIN), (4, REDBLACK, TRUE_HIGH), (4, STANDARD, G1)):
+        F = synth.rhs_normal(n, seed=n)
+        hg, ho, ug, uo = run_pair(n, order, co, op, F, 5)
+        assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+        assert np.array_equal(ug, uo)
+
+
+def test_solve_reaches_tolerance_and_reports_history():
+    n = 256
+    F = synth.rhs_sine_modes(n, seed=0)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    h = mg.mg_setup(n, 4, "redblack", "galerkin", nu1=2, nu2=1)
+    try:
+        k, hist = mg.mg_solve(h, u, f, rtol=1e-10, max_cycles=40)
+    finally:
+        h.close()
+    assert hist[-1] < 1e-10 and all(hist[i + 1] < hist[i] for i in range(k))
+
+
+def test_boundary_of_u_is_reset_and_f_boundary_ignored():
+    n = 32
+    F = synth.rhs_normal(n, seed=9)
+    F2 = F.copy()
+    F2[0, :] = 5.0
+    F2[:, -1] = -7.0
+    outs = []
+    for FF, u0 in ((F, 0.0), (F2, 3.0)):
+        f = torch.tensor(FF, dtype=torch.float64, device="cuda")
+        u = torch.full_like(f, u0)
+        u[1:-1, 1:-1] = 0.0
+        h = mg.mg_setup(n, 2)
+        try:
+            mg.mg_solve(h, u, f, rtol=0.0, max_cycles=3, raise_not_converged=False)
+        finally:
+            h.close()
+        outs.append(u.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.all(outs[1][0, :] == 0) and np.all(outs[1][:, -1] == 0)
+
+
+def test_zero_rhs_and_nonfinite_rhs_are_reported():
+    n = 16
+    h = mg.mg_setup(n, 2)
+    try:
+        f = torch.zeros((n + 1, n + 1), dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(f)
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_solve(h, u, f)
+        assert e.value.status == mg.MG_ERR_INVALID
+        f[3, 4] = float("nan")
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_solve(h, u, f)
+        assert e.value.status == mg.MG_ERR_NONFINITE
+    finally:
+        h.close()
