@@ -1,0 +1,361 @@
+"""Benchmark: time to 1e-10 relative residual of nonstandard-coarsening multigrid.
+
+Workload (one step): 2D Poisson, fourth-order 9-point Laplacian on 4097 x 4097
+nodes (N = 4096), FP64, right-hand side = 16 seeded sin(k pi x) sin(l pi y)
+modes (k, l uniform in 1..64, amplitudes N(0,1)), red-black coarsening down to a
+3 x 3 grid, Galerkin coarse operators built from the second-order operator
+(G^(2)), V(2,1) cycles with red-black smoothing, solved from u = 0 until
+||f - L u|| / ||f|| < 1e-10. The non-Galerkin and standard-coarsening runs of
+the same workload are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-10 rel. residual and HBM GB/s, mixed vs FP64; p50/p99 served latency"
+N = 4096
+ORDER = 4
+RTOL = 1e-10
+NU1, NU2 = 2, 1
+SEED = 0
+WORKLOAD = ("2D Poisson -Lap u = f, 4th-order 9-point Laplacian, 4097x4097 nodes (N=4096), FP64; "
+            "f = 16 seeded sin*sin modes (freq 1-64, N(0,1) amplitudes); red-black coarsening to 3x3, "
+            "Galerkin G^(2) coarse operators, V(2,1) red-black smoothing, omega=1, solve from u=0 to 1e-10")
+
+# FP64 ALU peak for non-fused FP64 operations: GB300 FP64 1.25 TFLOP/s counts an FMA as
+# two flops, i.e. 0.625 T FP64 instructions/s; a kernel that rounds every product
+# separately issues one instruction per flop.
+FP64_SEPARATE_OP_PEAK_TFLOPS = 0.625
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(cycles_to_tol: int, n_sample: int = 2048):
+    """Time one V(2,1) cycle of the oracle on an (n_sample+1)^2 grid of the same workload
+    and scale it to the full grid and the cycle count: a bounded CPU baseline."""
+    import synth
+    from oracle.mg import GALERKIN, REDBLACK, Options, Oracle
+    import numpy as np
+    o = Oracle(n_sample, ORDER, REDBLACK, GALERKIN, Options(nu1=NU1, nu2=NU2))
+    f = o.to_vec(synth.rhs_sine_modes(n_sample, SEED))
+    t0 = time.perf_counter()
+    o.cycle(np.zeros_like(f), f)
+    dt = time.perf_counter() - t0
+    scale = (N - 1) ** 2 / (n_sample - 1) ** 2
+    return dt * scale * cycles_to_tol * 1e3, dt
+
+
+def oracle_cycles_to_tol(n_small: int = 256) -> int:
+    """Cycles the oracle needs for this workload on a small grid (the count is
+    nearly independent of the grid size for multigrid)."""
+    import synth
+    from oracle.mg import GALERKIN, REDBLACK, Options, Oracle
+    o = Oracle(n_small, ORDER, REDBLACK, GALERKIN, Options(nu1=NU1, nu2=NU2))
+    _, hist = o.solve(o.to_vec(synth.rhs_sine_modes(n_small, SEED)), rtol=RTOL, max_cycles=60)
+    return len(hist) - 1
+
+
+def run_reference(args, ws, rank):
+    """The FP64 oracle on the host cores, each step one bounded sample (see oracle_sample)."""
+    if rank != 0:
+        return
+    cycles = oracle_cycles_to_tol()
+    vals = []
+    for k in range(args.warmup + args.steps):
+        v, _ = oracle_sample(cycles, args.ref_n)
+        if k >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    sample = (f"one V(2,1) cycle of the oracle on a {args.ref_n + 1}^2 grid of the same workload, "
+              f"scaled by the point ratio to 4097^2 and by {cycles} cycles to 1e-10 (the oracle's count on 257^2)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    import paper_2008_03885_gb300 as mg
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    F = synth.rhs_sine_modes(N, SEED)
+    f_host = torch.from_numpy(F).pin_memory()
+    u_host = torch.zeros_like(f_host).pin_memory()
+    f = f_host.to(dev)
+    u = torch.zeros_like(f)
+    bytes_grid = f.numel() * 8
+
+    def solve(h, uu, ff):
+        uu.zero_()
+        k, hist = mg.mg_solve(h, uu, ff, rtol=RTOL, max_cycles=60)
+        return k, hist
+
+    h = mg.mg_setup(N, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2)
+    for _ in range(args.warmup):
+        cycles, hist = solve(h, u, f)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, device time via events on the launching stream
+    mg.mg_reset_counters(h)
+    mg.mg_set_timing(h, True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            cycles, hist = solve(h, u, f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = max_over_ranks(ws, ms)
+    launches, ncyc = mg.mg_get_counters(h)
+    kt = {k: mg.mg_get_timing(h, k) for k in range(5)}
+    mg.mg_set_timing(h, False)
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    barrier(ws)
+    torch.cuda.synchronize()
+    u_out = torch.empty_like(u_host).pin_memory()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        f.copy_(f_host, non_blocking=True)
+        u.copy_(u_host, non_blocking=True)
+        mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)
+        u_out.copy_(u, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ws, e2.elapsed_time(e3) / args.steps)
+    final_rr = hist[-1]
+
+    # ---- variants of the same workload (one timed solve each after one warm-up)
+    variants = {}
+    if not args.quick:
+        for name, co, op, omega in (("redblack_nongalerkin", "redblack", "nongalerkin", 1.0),
+                                    ("standard_galerkin_omega1.1", "standard", "galerkin", 1.1)):
+            hv = mg.mg_setup(N, ORDER, co, op, nu1=NU1, nu2=NU2, omega=omega)
+            solve(hv, u, f)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kv, hv_hist = solve(hv, u, f)
+            b.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = {"ms": a.elapsed_time(b), "cycles": kv, "final_rel_res": hv_hist[-1],
+                              "cr_last": hv_hist[-1] / hv_hist[-2] if kv > 1 else None}
+            hv.close()
+    h.close()
+
+    # ---- roofline of the dominant kernel (finest-level red-black half-sweep)
+    sm_ms, sm_n = kt[mg.MG_KERNEL_SMOOTH]
+    per_launch_ms = sm_ms / max(sm_n, 1)
+    pts = (N - 1) ** 2
+    flops_per_launch = pts / 2 * 20  # 9 mul + 8 add + sub + mul + add per updated node
+    bytes_per_launch = 3 * (N + 1) ** 2 * 8  # read u, f; write u (whole grid)
+    achieved_tflops = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    hbm_peak, peak_kind = load_peaks()
+    achieved_gbs = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    total_kernel_ms = sum(v[0] for v in kt.values())
+    out = {
+        "metric": METRIC, "value": ms_max, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N, "order": ORDER, "coarsening": "redblack",
+                   "coarse_op": "galerkin (G^(2))", "cycle": f"V({NU1},{NU2})", "omega": 1.0, "rtol": RTOL,
+                   "cycles_to_tol": cycles, "final_rel_res": final_rr, "fma_contract": 0,
+                   "l2": "inputs larger than L2: f alone is 134 MB and the hierarchy ~1.1 GB per solve",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_SEPARATE_OP_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_SEPARATE_OP_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_half_sweep<double, exact> on level 0",
+                     "per_launch_ms": per_launch_ms, "launches": sm_n,
+                     "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak,
+                     "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
+                     "peak_kind": "FP64 1.25 TFLOP/s nominal counted per separately rounded op",
+                     "share_of_finest_level_kernel_time": sm_ms / total_kernel_ms if total_kernel_ms else None},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * bytes_grid, "d2h_bytes_per_step": bytes_grid},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "variants": variants,
+        "kernel_ms_per_step": {name: kt[k][0] / args.steps for k, name in
+                               enumerate(("smooth", "residual", "restrict", "prolong", "norm"))},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, dt = oracle_sample(cycles, args.ref_n)
+        out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
+                               "sample": f"one V(2,1) cycle of the oracle on a {args.ref_n + 1}^2 grid "
+                                         f"({dt:.2f} s), scaled by the point ratio to 4097^2 and by "
+                                         f"{cycles} cycles to 1e-10"}
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_profile_case(args):
+    """A few finest-level kernels of the bench workload, for ncu captures: 4 smoothing
+    sweeps, 2 residuals, 2 restrictions, 2 interpolations on level 0."""
+    import torch
+    import paper_2008_03885_gb300 as mg
+    import synth
+    n = args.profile_n
+    F = synth.rhs_sine_modes(n, SEED)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    d = torch.zeros_like(f)
+    h = mg.mg_setup(n, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2)
+    fc = mg.level_array(h, 1)
+    for _ in range(2):
+        mg.mg_level_smooth(h, 0, u, f, 2)
+        mg.mg_level_residual(h, 0, u, f, d)
+        mg.mg_level_restrict(h, 0, d, fc)
+        mg.mg_level_prolong_add(h, 0, u, fc)
+    torch.cuda.synchronize()
+    h.close()
+    print(json.dumps({"profile_case": n, "ok": True}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-n", type=int, default=2048)
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true", help="run a few finest-level kernels (ncu)")
+    ap.add_argument("--profile-n", type=int, default=4096)
+    args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -178,6 +178,32 @@ mg_status mg_level_restrict(mg_handle* h, int level, const double* d_fine, doubl
 mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const double* v_coarse,
                                void* stream);
 
+/* ---- instrumentation --------------------------------------------------------
+   Counters of kernel launches and cycles made through the handle, and optional
+   CUDA-event timing of the finest level's kernels (recorded on the stream the
+   kernels are launched on). Not part of the paper's method. */
+typedef struct {
+  int64_t launches; /* kernels launched by the library since the last reset */
+  int64_t cycles;   /* multigrid cycles run since the last reset */
+} mg_counters;
+
+typedef enum {
+  MG_KERNEL_SMOOTH = 0,   /* finest-level smoothing sweeps */
+  MG_KERNEL_RESIDUAL = 1, /* finest-level residual */
+  MG_KERNEL_RESTRICT = 2, /* restriction from the finest level */
+  MG_KERNEL_PROLONG = 3,  /* interpolation + correction into the finest level */
+  MG_KERNEL_NORM = 4,     /* residual-norm reduction */
+  MG_KERNEL_CLASSES = 5
+} mg_kernel_class;
+
+mg_status mg_get_counters(const mg_handle* h, mg_counters* out);
+mg_status mg_reset_counters(mg_handle* h);
+/* enable != 0: record a CUDA event pair around every finest-level launch. */
+mg_status mg_set_timing(mg_handle* h, int enable);
+/* Total device milliseconds and launch count of a kernel class since timing was
+   enabled or last read (waits for the recorded events; resets the class). */
+mg_status mg_get_timing(mg_handle* h, int kernel_class, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,10 +73,21 @@ _lib.mg_level_residual.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
 _lib.mg_level_smooth.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp]
 _lib.mg_level_restrict.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
 _lib.mg_level_prolong_add.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp]
-for _name in ("mg_setup", "mg_cycle", "mg_solve", "mg_destroy", "mg_get_level_info", "mg_level_apply",
+_lib.mg_get_counters.argtypes = [_vp, _vp]
+_lib.mg_reset_counters.argtypes = [_vp]
+_lib.mg_set_timing.argtypes = [_vp, ctypes.c_int]
+_lib.mg_get_timing.argtypes = [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64)]
+for _name in ("mg_get_counters", "mg_reset_counters", "mg_set_timing", "mg_get_timing", "mg_setup", "mg_cycle", "mg_solve", "mg_destroy", "mg_get_level_info", "mg_level_apply",
               "mg_level_residual", "mg_level_smooth", "mg_level_restrict", "mg_level_prolong_add"):
     getattr(_lib, _name).restype = ctypes.c_int
 _lib.mg_num_levels.restype = ctypes.c_int
+
+
+MG_KERNEL_SMOOTH, MG_KERNEL_RESIDUAL, MG_KERNEL_RESTRICT, MG_KERNEL_PROLONG, MG_KERNEL_NORM = range(5)
+
+
+class mg_counters(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("cycles", ctypes.c_int64)]
 
 
 class MGError(RuntimeError):
@@ -230,3 +241,26 @@ def level_nodes(h: Handle, level: int):
     else:
         col = i
     return i, j, j, col
+
+
+def mg_get_counters(h: Handle):
+    """(kernel launches, cycles) since the last reset."""
+    c = mg_counters()
+    _check(_lib.mg_get_counters(h.ptr, ctypes.byref(c)), "mg_get_counters")
+    return c.launches, c.cycles
+
+
+def mg_reset_counters(h: Handle):
+    _check(_lib.mg_reset_counters(h.ptr), "mg_reset_counters")
+
+
+def mg_set_timing(h: Handle, enable: bool = True):
+    _check(_lib.mg_set_timing(h.ptr, int(bool(enable))), "mg_set_timing")
+
+
+def mg_get_timing(h: Handle, kernel_class: int):
+    """(total device ms, launches) of a finest-level kernel class since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib.mg_get_timing(h.ptr, kernel_class, ctypes.byref(ms), ctypes.byref(n)), "mg_get_timing")
+    return ms.value, n.value

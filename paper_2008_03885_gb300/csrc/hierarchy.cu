@@ -246,24 +246,42 @@ LevelDev<T> to_dev(const HostLevel& L) {
 }  // namespace
 
 // ---------------------------------------------------------------- handle
+// Device hierarchy in one precision.
+template <typename T>
+struct Hier {
+  std::vector<LevelPair<T>> L;
+  std::vector<T*> u, t, f, d;  // FP64 level 0: u and f are the caller's
+  int64_t coarsest_idx = 0;
+  T coarsest_a = T(1);
+};
+
 struct mg_handle {
   int N = 0, order = 2, coarsening = 1, coarse_op = 1;
   mg_options opt;
   std::vector<HostLevel> host;
   std::vector<int> transfer;
-  std::vector<LevelPair<double>> L64;
-  std::vector<LevelPair<float>> L32;
-  std::vector<double*> u, t, f, d;  // level 0: u and f are the caller's
-  std::vector<float*> u32, t32, f32, d32;
+  Hier<double> h64;
+  Hier<float> h32;  // mixed precision: inner cycles (level 0 = scaled residual / correction)
   double* partial = nullptr;
   double* scalar = nullptr;      // device
   double* hscalar = nullptr;     // pinned host
   std::vector<void*> allocs;     // every cudaMalloc / cudaMallocHost to free
   std::vector<void*> host_allocs;
-  int64_t coarsest_idx = 0;
-  double coarsest_a = 1.0;
   int nblocks0 = 0;
+  double ir_scale = 0.0;  // mixed precision: scale of the next refinement residual (0 = unset)
+  // instrumentation
+  int64_t launches = 0, cycles = 0;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[MG_KERNEL_CLASSES];
+  size_t ev_used[MG_KERNEL_CLASSES] = {};
 };
+
+template <typename T>
+Hier<T>& hier(mg_handle* h);
+template <>
+Hier<double>& hier<double>(mg_handle* h) { return h->h64; }
+template <>
+Hier<float>& hier<float>(mg_handle* h) { return h->h32; }
 
 namespace {
 
@@ -271,6 +289,37 @@ namespace {
   do {                                        \
     if ((x) != cudaSuccess) return MG_ERR_CUDA; \
   } while (0)
+
+// Launch `nk` kernels through `expr`, counting them.
+#define LAUNCH(h, nk, expr)                       \
+  do {                                            \
+    (h)->launches += (nk);                        \
+    if ((expr) != cudaSuccess) return MG_ERR_CUDA; \
+  } while (0)
+
+// CUDA-event bracket around finest-level launches of one kernel class.
+struct Bracket {
+  mg_handle* h;
+  int cls;
+  cudaStream_t s;
+  bool on;
+  Bracket(mg_handle* h_, int level, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_), on(h_->timing && level == 0) {
+    if (!on) return;
+    auto& v = h->ev[cls];
+    if (h->ev_used[cls] == v.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      v.push_back({a, b});
+    }
+    cudaEventRecord(v[h->ev_used[cls]].first, s);
+  }
+  ~Bracket() {
+    if (!on) return;
+    cudaEventRecord(h->ev[cls][h->ev_used[cls]].second, s);
+    ++h->ev_used[cls];
+  }
+};
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -283,6 +332,7 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
       o.gamma < 1 || o.gamma > 2 || (o.smoother != MG_SMOOTH_REDBLACK && o.smoother != MG_SMOOTH_JACOBI))
     return MG_ERR_INVALID;
   if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED_FP32) return MG_ERR_INVALID;
+  if (o.precision == MG_PREC_MIXED_FP32 && (o.inner_cycles < 1 || o.inner_cycles > 64)) return MG_ERR_INVALID;
   if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
   if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
   return MG_OK;
@@ -389,6 +439,11 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P) {
 }
 
 void free_all(mg_handle* h) {
+  for (auto& v : h->ev)
+    for (auto& e : v) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
   for (void* p : h->allocs) cudaFree(p);
   for (void* p : h->host_allocs) cudaFreeHost(p);
   h->allocs.clear();
@@ -402,38 +457,56 @@ struct Ctx {
   bool exact;
 };
 
-mg_status smooth(const Ctx& c, int l, double* U, const double* F) {
+template <typename T>
+mg_status smooth(const Ctx& c, int l, T* U, const T* F) {
   mg_handle* h = c.h;
-  double* T = h->t[l];
-  const auto& L = h->L64[l];
+  Hier<T>& H = hier<T>(h);
+  T* Tb = H.t[l];
+  const auto& L = H.L[l];
   if (h->opt.smoother == MG_SMOOTH_REDBLACK) {
-    CK(launch_half_sweep<double>(L, c.exact, U, F, T, 1, c.s));
-    CK(launch_half_sweep<double>(L, c.exact, T, F, U, 0, c.s));
+    {
+      Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+      LAUNCH(h, 1, launch_half_sweep<T>(L, c.exact, U, F, Tb, 1, c.s));
+    }
+    Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+    LAUNCH(h, 1, launch_half_sweep<T>(L, c.exact, Tb, F, U, 0, c.s));
   } else {
-    CK(launch_jacobi<double>(L, c.exact, U, F, T, c.s));
-    CK(cudaMemcpyAsync(U, T, level_bytes(h->host[l], sizeof(double)), cudaMemcpyDeviceToDevice, c.s));
+    Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+    LAUNCH(h, 1, launch_jacobi<T>(L, c.exact, U, F, Tb, c.s));
+    CK(cudaMemcpyAsync(U, Tb, level_bytes(h->host[l], sizeof(T)), cudaMemcpyDeviceToDevice, c.s));
   }
   return MG_OK;
 }
 
-mg_status cycle_level(const Ctx& c, int l, double* U, const double* F, bool zero_init) {
+template <typename T>
+mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
   mg_handle* h = c.h;
+  Hier<T>& H = hier<T>(h);
   const int lmax = (int)h->host.size() - 1;
   mg_status st;
-  if (zero_init) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(double)), c.s));
+  if (zero_init) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
   for (int k = 0; k < h->opt.nu1; ++k)
-    if ((st = smooth(c, l, U, F)) != MG_OK) return st;
-  CK(launch_residual<double>(h->L64[l], c.exact, U, F, h->d[l], c.s));
-  CK(launch_restrict<double>(h->L64[l], h->L64[l + 1], h->transfer[l], c.exact, h->d[l], h->f[l + 1], c.s));
+    if ((st = smooth<T>(c, l, U, F)) != MG_OK) return st;
+  {
+    Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
+    LAUNCH(h, 1, launch_residual<T>(H.L[l], c.exact, U, F, H.d[l], c.s));
+  }
+  {
+    Bracket b(h, l, MG_KERNEL_RESTRICT, c.s);
+    LAUNCH(h, 1, launch_restrict<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, H.d[l], H.f[l + 1], c.s));
+  }
   if (l + 1 == lmax) {
-    CK(launch_coarsest<double>(h->coarsest_idx, h->coarsest_a, h->f[lmax], h->u[lmax], c.s));
+    LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.f[lmax], H.u[lmax], c.s));
   } else {
     for (int g = 0; g < h->opt.gamma; ++g)
-      if ((st = cycle_level(c, l + 1, h->u[l + 1], h->f[l + 1], g == 0)) != MG_OK) return st;
+      if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0)) != MG_OK) return st;
   }
-  CK(launch_prolong_add<double>(h->L64[l], h->L64[l + 1], h->transfer[l], c.exact, U, h->u[l + 1], c.s));
+  {
+    Bracket b(h, l, MG_KERNEL_PROLONG, c.s);
+    LAUNCH(h, 1, launch_prolong_add<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, U, H.u[l + 1], c.s));
+  }
   for (int k = 0; k < h->opt.nu2; ++k)
-    if ((st = smooth(c, l, U, F)) != MG_OK) return st;
+    if ((st = smooth<T>(c, l, U, F)) != MG_OK) return st;
   return MG_OK;
 }
 
@@ -446,7 +519,10 @@ mg_status read_scalar(mg_handle* h, cudaStream_t s, double* out) {
 
 mg_status rel_residual(mg_handle* h, const Ctx& c, const double* U, const double* F, double fn2,
                        double* out) {
-  CK(launch_resnorm<double>(h->L64[0], c.exact, U, F, h->partial, h->scalar, c.s));
+  {
+    Bracket b(h, 0, MG_KERNEL_NORM, c.s);
+    LAUNCH(h, 2, launch_resnorm<double>(h->h64.L[0], c.exact, U, F, h->partial, h->scalar, c.s));
+  }
   double r2;
   mg_status st = read_scalar(h, c.s, &r2);
   if (st != MG_OK) return st;
@@ -456,11 +532,67 @@ mg_status rel_residual(mg_handle* h, const Ctx& c, const double* U, const double
 }
 
 mg_status f_norm2(mg_handle* h, cudaStream_t s, const double* F, double* out) {
-  CK(launch_sumsq<double>(h->L64[0], F, h->partial, h->scalar, s));
+  LAUNCH(h, 2, launch_sumsq<double>(h->h64.L[0], F, h->partial, h->scalar, s));
   mg_status st = read_scalar(h, s, out);
   if (st != MG_OK) return st;
   if (!std::isfinite(*out)) return MG_ERR_NONFINITE;
   if (*out == 0.0) return MG_ERR_INVALID;
+  return MG_OK;
+}
+
+// Level descriptors and buffers of one precision. With caller_level0 the finest
+// level's u and f are the caller's arrays (FP64 path); otherwise all four arrays are
+// allocated (FP32 inner hierarchy of the mixed-precision path).
+template <typename T>
+mg_status alloc_hier(mg_handle* h, bool caller_level0) {
+  Hier<T>& H = hier<T>(h);
+  const int nl = (int)h->host.size();
+  H.L.resize(nl);
+  H.u.assign(nl, nullptr);
+  H.t.assign(nl, nullptr);
+  H.f.assign(nl, nullptr);
+  H.d.assign(nl, nullptr);
+  mg_status st;
+  for (int l = 0; l < nl; ++l) {
+    if ((st = upload_level<T>(h, h->host[l], H.L[l])) != MG_OK) return st;
+    const size_t b = level_bytes(h->host[l], sizeof(T));
+    if (l > 0 || !caller_level0) {
+      if ((st = device_alloc(h, (void**)&H.u[l], b)) != MG_OK) return st;
+      if ((st = device_alloc(h, (void**)&H.f[l], b)) != MG_OK) return st;
+    }
+    if ((st = device_alloc(h, (void**)&H.t[l], b)) != MG_OK) return st;
+    if ((st = device_alloc(h, (void**)&H.d[l], b)) != MG_OK) return st;
+  }
+  return MG_OK;
+}
+
+// Power of two near 1 / rms of a residual with squared norm r2 over m unknowns, so
+// that the FP32 copy of the residual stays far from underflow and overflow.
+double ir_scale_for(double r2, int64_t m) {
+  const double rms = std::sqrt(r2 / (double)std::max<int64_t>(m, 1));
+  if (!(rms > 0.0) || !std::isfinite(rms)) return 1.0;
+  return std::ldexp(1.0, -std::ilogb(rms));
+}
+
+// One refinement step of the mixed-precision solve: FP64 residual r = f - L u
+// (also returns ||r||^2), then -- unless `norm_only` -- `inner_cycles` FP32 cycles
+// on L e = r * scale from e = 0, and the FP64 update u += e / scale.
+mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
+  mg_handle* h = c.h;
+  {
+    Bracket b(h, 0, MG_KERNEL_NORM, c.s);
+    LAUNCH(h, 2, launch_ir_residual(h->h64.L[0], c.exact, u, f, h->h32.f[0], h->ir_scale, h->partial,
+                                    h->scalar, c.s));
+  }
+  return read_scalar(h, c.s, r2);
+}
+
+mg_status ir_correct(const Ctx& c, double* u) {
+  mg_handle* h = c.h;
+  mg_status st;
+  for (int k = 0; k < h->opt.inner_cycles; ++k)
+    if ((st = cycle_level<float>(c, 0, h->h32.u[0], h->h32.f[0], k == 0)) != MG_OK) return st;
+  LAUNCH(h, 1, launch_ir_update(h->h64.L[0], u, h->h32.u[0], 1.0 / h->ir_scale, c.s));
   return MG_OK;
 }
 
@@ -524,7 +656,6 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   if (opt) o = *opt; else mg_default_options(&o);
   mg_status st = validate(grid, order, coarsening, coarse_op, o);
   if (st != MG_OK) return st;
-  if (o.precision != MG_PREC_FP64) return MG_ERR_UNSUPPORTED;
   mg_handle* h = new (std::nothrow) mg_handle();
   if (!h) return MG_ERR_OOM;
   h->N = grid->n;
@@ -538,33 +669,24 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   for (int l = 0; l + 1 < nl; ++l) h->transfer.push_back(transfer_of(coarsening, shapes[l].kind));
   for (const auto& L : h->host)
     if (L.c.size() > (size_t)kMaxTerms) { delete h; return MG_ERR_UNSUPPORTED; }
-  h->L64.resize(nl);
-  h->u.assign(nl, nullptr);
-  h->t.assign(nl, nullptr);
-  h->f.assign(nl, nullptr);
-  h->d.assign(nl, nullptr);
   auto fail = [&](mg_status s) { free_all(h); delete h; return s; };
-  for (int l = 0; l < nl; ++l) {
-    if ((st = upload_level<double>(h, h->host[l], h->L64[l])) != MG_OK) return fail(st);
-    const size_t b = level_bytes(h->host[l], sizeof(double));
-    if (l > 0) {
-      if ((st = device_alloc(h, (void**)&h->u[l], b)) != MG_OK) return fail(st);
-      if ((st = device_alloc(h, (void**)&h->f[l], b)) != MG_OK) return fail(st);
-    }
-    if ((st = device_alloc(h, (void**)&h->t[l], b)) != MG_OK) return fail(st);
-    if ((st = device_alloc(h, (void**)&h->d[l], b)) != MG_OK) return fail(st);
+  const HostLevel& C = h->host.back();
+  if (C.unknowns != 1) return fail(MG_ERR_UNSUPPORTED);
+  const int64_t cidx = (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
+  const double ca = fold_row(C.W, C.shape.n, 1, 1).at(Key(0, 0)) * C.s;
+  if ((st = alloc_hier<double>(h, /*caller_level0=*/true)) != MG_OK) return fail(st);
+  h->h64.coarsest_idx = cidx;
+  h->h64.coarsest_a = ca;
+  if (o.precision == MG_PREC_MIXED_FP32) {
+    if ((st = alloc_hier<float>(h, false)) != MG_OK) return fail(st);
+    h->h32.coarsest_idx = cidx;
+    h->h32.coarsest_a = (float)ca;
   }
-  h->nblocks0 = resnorm_blocks<double>(h->L64[0]);
+  h->nblocks0 = resnorm_blocks<double>(h->h64.L[0]);
   if ((st = device_alloc(h, (void**)&h->partial, h->nblocks0 * sizeof(double))) != MG_OK) return fail(st);
   if ((st = device_alloc(h, (void**)&h->scalar, 64)) != MG_OK) return fail(st);
   if (cudaMallocHost((void**)&h->hscalar, 64) != cudaSuccess) return fail(MG_ERR_CUDA);
   h->host_allocs.push_back(h->hscalar);
-  // coarsest level: one unknown at lattice node (1, 1)
-  const HostLevel& C = h->host.back();
-  if (C.unknowns != 1) return fail(MG_ERR_UNSUPPORTED);
-  h->coarsest_idx = (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
-  const Stencil row = fold_row(C.W, C.shape.n, 1, 1);
-  h->coarsest_a = row.at(Key(0, 0)) * C.s;
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(MG_ERR_CUDA);
   *out = h;
   return MG_OK;
@@ -595,12 +717,24 @@ mg_status mg_get_level_info(const mg_handle* h, int level, mg_level_info* out) {
 mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out, void* stream) {
   if (!h || !u || !f) return MG_ERR_INVALID;
   Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
-  CK(launch_zero_boundary<double>(h->L64[0], u, c.s));
-  mg_status st = cycle_level(c, 0, u, f, false);
-  if (st != MG_OK) return st;
-  if (rel_res_out) {
-    double fn2;
+  LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
+  mg_status st;
+  double fn2;
+  if (h->opt.precision == MG_PREC_MIXED_FP32) {
     if ((st = f_norm2(h, c.s, f, &fn2)) != MG_OK) return st;
+    if (h->ir_scale == 0.0) h->ir_scale = ir_scale_for(fn2, h->host[0].unknowns);
+    double r2;
+    if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;
+    if (!std::isfinite(r2)) return MG_ERR_NONFINITE;
+    h->ir_scale = ir_scale_for(r2, h->host[0].unknowns);
+    if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;  // residual at the chosen scale
+    if ((st = ir_correct(c, u)) != MG_OK) return st;
+  } else {
+    if ((st = cycle_level<double>(c, 0, u, f, false)) != MG_OK) return st;
+  }
+  ++h->cycles;
+  if (rel_res_out) {
+    if (h->opt.precision != MG_PREC_MIXED_FP32 && (st = f_norm2(h, c.s, f, &fn2)) != MG_OK) return st;
     return rel_residual(h, c, u, f, fn2, rel_res_out);
   }
   return MG_OK;
@@ -610,18 +744,40 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
                    int* cycles_out, double* history_out, void* stream) {
   if (!h || !u || !f || max_cycles < 0 || !(rtol >= 0.0)) return MG_ERR_INVALID;
   Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
-  CK(launch_zero_boundary<double>(h->L64[0], u, c.s));
+  LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   double fn2, rr;
   mg_status st = f_norm2(h, c.s, f, &fn2);
   if (st != MG_OK) return st;
-  if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
-  if (history_out) history_out[0] = rr;
   int k = 0;
-  while (k < max_cycles && rr >= rtol) {
-    if ((st = cycle_level(c, 0, u, f, false)) != MG_OK) return st;
-    ++k;
+  if (h->opt.precision == MG_PREC_MIXED_FP32) {
+    // Iterative refinement: each FP64 residual also feeds the next FP32 correction.
+    h->ir_scale = ir_scale_for(fn2, h->host[0].unknowns);
+    double r2;
+    for (;;) {
+      if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;
+      rr = std::sqrt(r2) / std::sqrt(fn2);
+      if (!std::isfinite(rr)) return MG_ERR_NONFINITE;
+      const double want = ir_scale_for(r2, h->host[0].unknowns);
+      if (want > 1024.0 * h->ir_scale || want < h->ir_scale / 1024.0) {
+        h->ir_scale = want;  // FP32 copy badly scaled: redo it at the right scale
+        if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;
+      }
+      if (history_out) history_out[k] = rr;
+      if (k >= max_cycles || rr < rtol) break;
+      if ((st = ir_correct(c, u)) != MG_OK) return st;
+      ++k;
+      ++h->cycles;
+    }
+  } else {
     if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
-    if (history_out) history_out[k] = rr;
+    if (history_out) history_out[0] = rr;
+    while (k < max_cycles && rr >= rtol) {
+      if ((st = cycle_level<double>(c, 0, u, f, false)) != MG_OK) return st;
+      ++k;
+      ++h->cycles;
+      if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
+      if (history_out) history_out[k] = rr;
+    }
   }
   if (cycles_out) *cycles_out = k;
   return rr < rtol ? MG_OK : MG_ERR_NOT_CONVERGED;
@@ -629,14 +785,14 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
 
 mg_status mg_level_apply(mg_handle* h, int level, const double* u, double* out, void* stream) {
   if (!h || !u || !out || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
-  CK(launch_apply<double>(h->L64[level], h->opt.fma_contract == 0, u, out, (cudaStream_t)stream));
+  CK(launch_apply<double>(h->h64.L[level], h->opt.fma_contract == 0, u, out, (cudaStream_t)stream));
   return MG_OK;
 }
 
 mg_status mg_level_residual(mg_handle* h, int level, const double* u, const double* f, double* d,
                             void* stream) {
   if (!h || !u || !f || !d || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
-  CK(launch_residual<double>(h->L64[level], h->opt.fma_contract == 0, u, f, d, (cudaStream_t)stream));
+  CK(launch_residual<double>(h->h64.L[level], h->opt.fma_contract == 0, u, f, d, (cudaStream_t)stream));
   return MG_OK;
 }
 
@@ -644,7 +800,7 @@ mg_status mg_level_smooth(mg_handle* h, int level, double* u, const double* f, i
   if (!h || !u || !f || sweeps < 0 || level < 0 || level >= (int)h->host.size()) return MG_ERR_INVALID;
   Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
   for (int k = 0; k < sweeps; ++k) {
-    mg_status st = smooth(c, level, u, f);
+    mg_status st = smooth<double>(c, level, u, f);
     if (st != MG_OK) return st;
   }
   return MG_OK;
@@ -652,15 +808,53 @@ mg_status mg_level_smooth(mg_handle* h, int level, double* u, const double* f, i
 
 mg_status mg_level_restrict(mg_handle* h, int level, const double* d_fine, double* f_coarse, void* stream) {
   if (!h || !d_fine || !f_coarse || level < 0 || level + 1 >= (int)h->host.size()) return MG_ERR_INVALID;
-  CK(launch_restrict<double>(h->L64[level], h->L64[level + 1], h->transfer[level], h->opt.fma_contract == 0,
+  CK(launch_restrict<double>(h->h64.L[level], h->h64.L[level + 1], h->transfer[level], h->opt.fma_contract == 0,
                              d_fine, f_coarse, (cudaStream_t)stream));
   return MG_OK;
 }
 
 mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const double* v_coarse, void* stream) {
   if (!h || !u_fine || !v_coarse || level < 0 || level + 1 >= (int)h->host.size()) return MG_ERR_INVALID;
-  CK(launch_prolong_add<double>(h->L64[level], h->L64[level + 1], h->transfer[level], h->opt.fma_contract == 0,
+  CK(launch_prolong_add<double>(h->h64.L[level], h->h64.L[level + 1], h->transfer[level], h->opt.fma_contract == 0,
                                 u_fine, v_coarse, (cudaStream_t)stream));
+  return MG_OK;
+}
+
+mg_status mg_get_counters(const mg_handle* h, mg_counters* out) {
+  if (!h || !out) return MG_ERR_INVALID;
+  out->launches = h->launches;
+  out->cycles = h->cycles;
+  return MG_OK;
+}
+
+mg_status mg_reset_counters(mg_handle* h) {
+  if (!h) return MG_ERR_INVALID;
+  h->launches = 0;
+  h->cycles = 0;
+  return MG_OK;
+}
+
+mg_status mg_set_timing(mg_handle* h, int enable) {
+  if (!h) return MG_ERR_INVALID;
+  h->timing = enable != 0;
+  for (auto& u : h->ev_used) u = 0;
+  return MG_OK;
+}
+
+mg_status mg_get_timing(mg_handle* h, int kernel_class, double* total_ms, int64_t* launches) {
+  if (!h || kernel_class < 0 || kernel_class >= MG_KERNEL_CLASSES) return MG_ERR_INVALID;
+  double tot = 0.0;
+  const size_t n = h->ev_used[kernel_class];
+  for (size_t k = 0; k < n; ++k) {
+    auto& e = h->ev[kernel_class][k];
+    CK(cudaEventSynchronize(e.second));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e.first, e.second));
+    tot += ms;
+  }
+  h->ev_used[kernel_class] = 0;
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = (int64_t)n;
   return MG_OK;
 }
 

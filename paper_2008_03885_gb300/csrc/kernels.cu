@@ -302,6 +302,35 @@ __global__ void k_zero_boundary(int n, int pitch, T* __restrict__ u) {
   u[(int64_t)k * pitch + n] = T(0);        // i = n
 }
 
+// Iterative-refinement residual: r = f - L u in FP64 (evaluation order of EXACT),
+// r32 = fl32(r * scale) for the FP32 inner cycles, and per-block sums of r^2.
+template <bool EXACT>
+__global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
+                              const double* __restrict__ f, float* __restrict__ r32, double scale,
+                              double* __restrict__ partial) {
+  const LevelDev<double>& L = *Lp;
+  int i, j;
+  double v = 0.0;
+  if (thread_node(L, i, j) && interior(L, i, j)) {
+    const int64_t at = sidx(L, i, j);
+    const double r = Arith<double>::sub(f[at], apply_at<double, EXACT>(L, u, i, j, at, nullptr));
+    r32[at] = (float)(r * scale);
+    v = r * r;
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+// u += e * inv_scale (FP64 update of the refinement step).
+__global__ void k_ir_update(const LevelDev<double>* __restrict__ Lp, double* __restrict__ u,
+                            const float* __restrict__ e, double inv_scale) {
+  const LevelDev<double>& L = *Lp;
+  int i, j;
+  if (!thread_node(L, i, j) || !interior(L, i, j)) return;
+  const int64_t at = sidx(L, i, j);
+  u[at] = u[at] + (double)e[at] * inv_scale;
+}
+
 template <typename T>
 dim3 grid_of(const LevelDev<T>& L) {
   return dim3((L.cols + kBX - 1) / kBX, (L.rows + kBY - 1) / kBY);
@@ -391,6 +420,21 @@ template <typename T>
 cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s) {
   const int n = L.h.n;
   k_zero_boundary<T><<<(n + 1 + 255) / 256, 256, 0, s>>>(n, L.h.pitch, u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
+                               float* r32, double scale, double* partial, double* out, cudaStream_t s) {
+  const dim3 g = grid_of(L.h);
+  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial);
+  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial);
+  k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
+                             cudaStream_t s) {
+  k_ir_update<<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, u, e, inv_scale);
   return cudaGetLastError();
 }
 
