@@ -178,6 +178,30 @@ mg_status mg_level_restrict(mg_handle* h, int level, const double* d_fine, doubl
 mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const double* v_coarse,
                                void* stream);
 
+/* ---- relative residual without device allocation ----------------------------
+   The paper has no counterpart to this call; it serves callers that must not
+   allocate device memory at the point where they need a residual norm: code that
+   runs while a stream is being captured into a CUDA graph (cudaMalloc cannot be
+   captured), loops that cannot afford the implicit device synchronisation of
+   cudaMalloc / cudaFree, or hosts that fix the library's memory at set-up.
+   Writes ||f - L_h u||_2 / ||f||_2 over the finest level's interior nodes (same
+   evaluation order as mg_cycle's rel_res_out, partial sums added in a different
+   fixed order) to the DEVICE double *rel_res_dev, asynchronously on `stream`.
+   u and f are device arrays of the finest level (as for mg_cycle); u's boundary is
+   read as stored. It calls no allocator: the reduction's partial sums live in one
+   32 KB device array inside the library (2 x 2048 doubles), which every GPU that
+   loads the library holds until the process exits. The first call on a device looks
+   up that array's device address (and may make the CUDA runtime load the library's
+   device code), so make the first call on each device before any stream capture.
+   All calls share the array and each call overwrites the partials it reads, so no
+   state carries over; calls whose work overlaps on the GPU (different streams, or
+   several host threads) race on the array and must be serialised by the caller.
+   Returns MG_ERR_UNSUPPORTED if the finest grid needs more than 2048 partial sums
+   per row of tiles (N + 1 > 65536 columns; unreachable for N <= 16384),
+   MG_ERR_INVALID for NULL arguments, MG_ERR_CUDA if a launch fails. */
+mg_status mg_rel_residual_static(mg_handle* h, const double* u, const double* f, double* rel_res_dev,
+                                 void* stream);
+
 /* ---- instrumentation --------------------------------------------------------
    Counters of kernel launches and cycles made through the handle, and optional
    CUDA-event timing of the finest level's kernels (recorded on the stream the

@@ -264,3 +264,14 @@ def mg_get_timing(h: Handle, kernel_class: int):
     n = ctypes.c_int64()
     _check(_lib.mg_get_timing(h.ptr, kernel_class, ctypes.byref(ms), ctypes.byref(n)), "mg_get_timing")
     return ms.value, n.value
+
+
+_lib.mg_rel_residual_static.argtypes = [_vp, _vp, _vp, _vp, _vp]
+_lib.mg_rel_residual_static.restype = ctypes.c_int
+
+
+def mg_rel_residual_static(h: Handle, u, f, rel_res_dev, stream=None):
+    """Relative residual of the finest level into the device scalar `rel_res_dev`,
+    without any device allocation (partial sums in the library's fixed device array)."""
+    _check(_lib.mg_rel_residual_static(h.ptr, _ptr(u), _ptr(f), _ptr(rel_res_dev), _stream(stream)),
+           "mg_rel_residual_static")

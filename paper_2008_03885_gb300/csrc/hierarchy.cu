@@ -859,3 +859,12 @@ mg_status mg_get_timing(mg_handle* h, int kernel_class, double* total_ms, int64_
 }
 
 }  // extern "C"
+
+namespace nsmg {
+// Finest-level FP64 description of a handle (used by mg_rel_residual_static).
+const LevelPair<double>* finest_level_fp64(const mg_handle* h, bool* exact) {
+  if (!h || h->h64.L.empty()) return nullptr;
+  if (exact) *exact = h->opt.fma_contract == 0;
+  return &h->h64.L[0];
+}
+}  // namespace nsmg

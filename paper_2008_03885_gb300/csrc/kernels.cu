@@ -6,6 +6,7 @@
 // adds the following products in the order of the term list (sorted by (dy, dx)),
 // every product and sum rounded separately (__dmul_rn / __dadd_rn keep nvcc from
 // contracting them into FMAs). EXACT = false lets products fuse into FMAs.
+#include <algorithm>
 #include <cstdio>
 
 #include "kernels.h"
@@ -461,3 +462,135 @@ NSMG_INSTANTIATE(double)
 NSMG_INSTANTIATE(float)
 
 }  // namespace nsmg
+
+// ---------------------------------------------------------------------------
+// Relative residual of the finest level without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// residual norm: code running while a CUDA stream is being captured into a graph
+// (cudaMalloc is not capturable), real-time loops that must not hit the implicit
+// device synchronisation of cudaMalloc / cudaFree, or hosts that hand the library a
+// fixed memory budget and forbid allocation after set-up. For them the partial sums
+// of the reduction live in a file-scope device array instead of in memory obtained
+// from the allocator: every GPU that loads this library holds
+// kStaticNormPartials x 2 doubles (32 KB) until the process exits.
+#include <mutex>
+
+#include "../../include/nsmg.h"
+
+namespace nsmg {
+
+// Finest-level FP64 description of a handle and its evaluation order (hierarchy.cu).
+const LevelPair<double>* finest_level_fp64(const mg_handle* h, bool* exact);
+
+namespace {
+
+constexpr int kStaticNormPartials = 2048;  // blocks per reduction (sum of squares of d and of f)
+static __device__ __align__(256) double g_static_norm_scratch[2 * kStaticNormPartials];
+
+// Block-wide sums of two doubles (blockDim = 256).
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double pa[32], pb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  if (lane == 0) {
+    pa[warp] = a;
+    pb[warp] = b;
+  }
+  __syncthreads();
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+  a = tid < nw ? pa[tid] : 0.0;
+  b = tid < nw ? pb[tid] : 0.0;
+  if (warp == 0)
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+}
+
+// Block (bx, by) reduces the 32 x 8 tiles (bx, by), (bx, by + gridDim.y), ... into
+// scratch[b] (sum of d^2) and scratch[kStaticNormPartials + b] (sum of f^2).
+template <bool EXACT>
+__global__ void k_resnorm_static(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
+                                 const double* __restrict__ f, double* __restrict__ scratch, int tiles_y) {
+  const LevelDev<double>& L = *Lp;
+  double sd = 0.0, sf = 0.0;
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+    const int j = ty * kBY + threadIdx.y;
+    if (j >= L.rows || q >= L.cols) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
+    const int64_t at = sidx(L, i, j);
+    const double d = Arith<double>::sub(f[at], apply_at<double, EXACT>(L, u, i, j, at, nullptr));
+    sd += d * d;
+    sf += f[at] * f[at];
+  }
+  block_sum2(sd, sf);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    scratch[b] = sd;
+    scratch[kStaticNormPartials + b] = sf;
+  }
+}
+
+// One block: add the `count` partials of each sum in a fixed order; write
+// sqrt(sum d^2) / sqrt(sum f^2) to *out.
+__global__ void k_static_norm_finish(const double* __restrict__ scratch, int count, double* __restrict__ out) {
+  double a = 0.0, b = 0.0;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int k = tid; k < count; k += blockDim.x * blockDim.y) {
+    a += scratch[k];
+    b += scratch[kStaticNormPartials + k];
+  }
+  block_sum2(a, b);
+  if (tid == 0) *out = sqrt(a) / sqrt(b);
+}
+
+// Device address of g_static_norm_scratch on each device, looked up once per device
+// with that device current. The name is only a host-side stand-in for the array.
+std::mutex g_static_norm_mu;
+double* g_static_norm_ptr[64] = {};
+
+cudaError_t static_norm_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_norm_mu);
+  if (!g_static_norm_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_norm_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_norm_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_norm_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace nsmg
+
+extern "C" mg_status mg_rel_residual_static(mg_handle* h, const double* u, const double* f, double* rel_res_dev,
+                                            void* stream) {
+  using namespace nsmg;
+  bool exact = true;
+  const LevelPair<double>* L = finest_level_fp64(h, &exact);
+  if (!L || !u || !f || !rel_res_dev) return MG_ERR_INVALID;
+  const int tiles_x = (L->h.cols + kBX - 1) / kBX;
+  const int tiles_y = (L->h.rows + kBY - 1) / kBY;
+  if (tiles_x > kStaticNormPartials) return MG_ERR_UNSUPPORTED;  // grid wider than the scratch array
+  const int gy = std::max(1, std::min(tiles_y, kStaticNormPartials / tiles_x));
+  double* scratch = nullptr;
+  if (static_norm_scratch(&scratch) != cudaSuccess) return MG_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const dim3 grid(tiles_x, gy);
+  if (exact) k_resnorm_static<true><<<grid, dim3(kBX, kBY), 0, s>>>(L->d, u, f, scratch, tiles_y);
+  else k_resnorm_static<false><<<grid, dim3(kBX, kBY), 0, s>>>(L->d, u, f, scratch, tiles_y);
+  k_static_norm_finish<<<1, dim3(kBX, kBY), 0, s>>>(scratch, tiles_x * gy, rel_res_dev);
+  return cudaGetLastError() == cudaSuccess ? MG_OK : MG_ERR_CUDA;
+}
