@@ -205,7 +205,6 @@ def run_ours(args, ws, rank, local):
 
     # ---- timed region: K solves, device time via events on the launching stream
     mg.mg_reset_counters(h)
-    mg.mg_set_timing(h, True)
     barrier(ws)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -219,9 +218,17 @@ def run_ours(args, ws, rank, local):
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = max_over_ranks(ws, ms)
     launches, ncyc = mg.mg_get_counters(h)
+    clocks = clk.summary()
+
+    # ---- per-kernel CUDA events: the same K solves again with event brackets around
+    # every finest-level launch (events need eager launches, so this pass does not use
+    # the cycle's CUDA graph; kernel durations are the same)
+    mg.mg_set_timing(h, True)
+    for _ in range(args.steps):
+        solve(h, u, f)
+    torch.cuda.synchronize()
     kt = {k: mg.mg_get_timing(h, k) for k in range(5)}
     mg.mg_set_timing(h, False)
-    clocks = clk.summary()
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     barrier(ws)
@@ -242,9 +249,13 @@ def run_ours(args, ws, rank, local):
     # ---- variants of the same workload (one timed solve each after one warm-up)
     variants = {}
     if not args.quick:
-        for name, co, op, omega in (("redblack_nongalerkin", "redblack", "nongalerkin", 1.0),
-                                    ("standard_galerkin_omega1.1", "standard", "galerkin", 1.1)):
-            hv = mg.mg_setup(N, ORDER, co, op, nu1=NU1, nu2=NU2, omega=omega)
+        for name, co, op, omega, extra in (
+                ("redblack_nongalerkin", "redblack", "nongalerkin", 1.0, {}),
+                ("standard_galerkin_omega1.1", "standard", "galerkin", 1.1, {}),
+                ("fp64_fma_contract", "redblack", "galerkin", 1.0, {"fma_contract": 1}),
+                ("mixed_fp32_inner", "redblack", "galerkin", 1.0,
+                 {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 2, "fma_contract": 1})):
+            hv = mg.mg_setup(N, ORDER, co, op, nu1=NU1, nu2=NU2, omega=omega, **extra)
             solve(hv, u, f)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -252,11 +263,20 @@ def run_ours(args, ws, rank, local):
             kv, hv_hist = solve(hv, u, f)
             b.record(stream)
             torch.cuda.synchronize()
+            mg.mg_set_timing(hv, True)  # kernel breakdown from a second, eagerly launched solve
+            solve(hv, u, f)
+            torch.cuda.synchronize()
+            vt = {nm: mg.mg_get_timing(hv, k) for k, nm in
+                  enumerate(("smooth", "residual", "restrict", "prolong", "norm"))}
             variants[name] = {"ms": a.elapsed_time(b), "cycles": kv, "final_rel_res": hv_hist[-1],
-                              "cr_last": hv_hist[-1] / hv_hist[-2] if kv > 1 else None}
+                              "cr_last": hv_hist[-1] / hv_hist[-2] if kv > 1 else None,
+                              "finest_kernel_ms": {k: v[0] for k, v in vt.items()},
+                              "finest_kernel_launches": {k: v[1] for k, v in vt.items()}}
+            if extra.get("precision") == mg.MG_PREC_MIXED_FP32:
+                # FP32 half-sweep on level 0: 12 bytes per node (read u, f; write u)
+                sm_ms, sm_n = vt["smooth"]
+                variants[name]["fp32_half_sweep_gbs"] = 3 * (N + 1) ** 2 * 4 / (sm_ms / max(sm_n, 1) * 1e-3) / 1e9
             hv.close()
-    h.close()
-
     # ---- roofline of the dominant kernel (finest-level red-black half-sweep)
     sm_ms, sm_n = kt[mg.MG_KERNEL_SMOOTH]
     per_launch_ms = sm_ms / max(sm_n, 1)
@@ -278,7 +298,7 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_SEPARATE_OP_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tflops / FP64_SEPARATE_OP_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "k_half_sweep<double, exact> on level 0",
+                     "kernel": "k_half_sweep_nt<double, exact, 9> on level 0",
                      "per_launch_ms": per_launch_ms, "launches": sm_n,
                      "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak,
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
@@ -324,6 +344,24 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": n, "ok": True}))
 
 
+def run_profile_mixed(args):
+    """Two mixed-precision solves of the bench workload (warm-up + one), for ncu."""
+    import torch
+    import paper_2008_03885_gb300 as mg
+    import synth
+    n = args.profile_n
+    f = torch.tensor(synth.rhs_sine_modes(n, SEED), dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    h = mg.mg_setup(n, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2,
+                    precision=mg.MG_PREC_MIXED_FP32, inner_cycles=2, fma_contract=1)
+    for _ in range(2):
+        u.zero_()
+        k, hist = mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)
+    torch.cuda.synchronize()
+    h.close()
+    print(json.dumps({"profile_mixed": n, "steps": k, "final": hist[-1]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,9 +373,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="run a few finest-level kernels (ncu)")
     ap.add_argument("--profile-n", type=int, default=4096)
+    ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_mixed:
+        run_profile_mixed(args)
         return
     ws, rank, local = dist_env()
     if ws > 1:

@@ -98,6 +98,12 @@ typedef struct {
   int32_t precision;   /* mg_precision (default MG_PREC_FP64) */
   int32_t fma_contract;/* 0 = separate rounding of every product (default), 1 = FMA allowed */
   int32_t inner_cycles;/* mixed precision: FP32 cycles per refinement step (default 2) */
+  int32_t tail_unknowns;/* levels (below the finest) with at most this many unknowns run inside
+                           one thread-block-cluster kernel; 0 = built-in default, -1 = never */
+  int32_t tail_ctas;   /* CTAs of that cluster (1..16); 0 = largest the device schedules */
+  int32_t sweep_kernel;/* red-black sweeps: 0 = auto (two half-sweep kernels), 1 = half-sweep
+                          kernels, 2 = one shared-memory tile kernel per sweep; every choice
+                          gives the same bits */
 } mg_options;
 
 typedef struct mg_handle mg_handle;

@@ -43,7 +43,9 @@ class mg_options(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("nu1", ctypes.c_int32), ("nu2", ctypes.c_int32),
                 ("gamma", ctypes.c_int32), ("smoother", ctypes.c_int32), ("n_min", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32)]
+                ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32),
+                ("tail_unknowns", ctypes.c_int32), ("tail_ctas", ctypes.c_int32),
+                ("sweep_kernel", ctypes.c_int32)]
 
 
 class mg_level_info(ctypes.Structure):

@@ -234,11 +234,14 @@ LevelDev<T> to_dev(const HostLevel& L) {
     const int dx = L.dxs[k], dy = L.dys[k];
     if (L.shape.kind == kRot) {
       // column of (i + dx) >> 1 relative to i >> 1 for i even / odd
-      d.delta[0][k] = dy * L.pitch + (dx >= 0 ? dx / 2 : -((-dx + 1) / 2));
-      d.delta[1][k] = dy * L.pitch + ((dx + 1) >= 0 ? (dx + 1) / 2 : -((-(dx + 1) + 1) / 2));
+      d.sdx[0][k] = dx >= 0 ? dx / 2 : -((-dx + 1) / 2);
+      d.sdx[1][k] = (dx + 1) >= 0 ? (dx + 1) / 2 : -((-(dx + 1) + 1) / 2);
     } else {
-      d.delta[0][k] = d.delta[1][k] = dy * L.pitch + dx;
+      d.sdx[0][k] = d.sdx[1][k] = dx;
     }
+    d.sdy[k] = dy;
+    d.delta[0][k] = dy * L.pitch + d.sdx[0][k];
+    d.delta[1][k] = dy * L.pitch + d.sdx[1][k];
   }
   return d;
 }
@@ -253,6 +256,12 @@ struct Hier {
   std::vector<T*> u, t, f, d;  // FP64 level 0: u and f are the caller's
   int64_t coarsest_idx = 0;
   T coarsest_a = T(1);
+  // small-level tail (one thread block runs the sub-cycle from tail_level down)
+  int tail_level = -1;
+  TailDesc<T>* d_tail = nullptr;
+  int4* d_prog = nullptr;  // program for a sub-cycle with zero initial guess
+  int nops = 0;
+  int tail_ctas = 1;       // CTAs in the tail's thread-block cluster
 };
 
 struct mg_handle {
@@ -269,6 +278,17 @@ struct mg_handle {
   std::vector<void*> host_allocs;
   int nblocks0 = 0;
   double ir_scale = 0.0;  // mixed precision: scale of the next refinement residual (0 = unset)
+  // CUDA graphs of the cycle: the FP64 cycle on the caller's (u, f), and the FP32
+  // inner cycles of the mixed-precision path (internal buffers only)
+  struct GraphEntry {
+    const void* u = nullptr;
+    const void* f = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+  };
+  GraphEntry g_cycle64, g_inner32;
+  cudaStream_t priv = nullptr;  // used when the caller passes the legacy default stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // instrumentation
   int64_t launches = 0, cycles = 0;
   bool timing = false;
@@ -333,6 +353,8 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
     return MG_ERR_INVALID;
   if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED_FP32) return MG_ERR_INVALID;
   if (o.precision == MG_PREC_MIXED_FP32 && (o.inner_cycles < 1 || o.inner_cycles > 64)) return MG_ERR_INVALID;
+  if (o.tail_ctas < 0 || o.tail_ctas > 16) return MG_ERR_INVALID;
+  if (o.sweep_kernel < 0 || o.sweep_kernel > 2) return MG_ERR_INVALID;
   if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
   if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
   return MG_OK;
@@ -439,6 +461,11 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P) {
 }
 
 void free_all(mg_handle* h) {
+  for (auto* g : {&h->g_cycle64, &h->g_inner32})
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (h->priv) cudaStreamDestroy(h->priv);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   for (auto& v : h->ev)
     for (auto& e : v) {
       cudaEventDestroy(e.first);
@@ -457,13 +484,86 @@ struct Ctx {
   bool exact;
 };
 
+// Work of an API call runs on the caller's stream, or -- for the legacy default
+// stream, which cannot be captured into a graph -- on the handle's own stream,
+// ordered after the caller's earlier work and before its later work by events.
+struct StreamScope {
+  mg_handle* h;
+  cudaStream_t user, s;
+  StreamScope(mg_handle* h_, void* stream) : h(h_), user((cudaStream_t)stream), s((cudaStream_t)stream) {
+    if (user || !h->priv) return;
+    cudaEventRecord(h->ev_in, user);
+    cudaStreamWaitEvent(h->priv, h->ev_in, 0);
+    s = h->priv;
+  }
+  ~StreamScope() {
+    if (s == user) return;
+    cudaEventRecord(h->ev_out, s);
+    cudaStreamWaitEvent(user, h->ev_out, 0);
+  }
+};
+
+// Run `body` (a sequence of launches on c.s) through a cached CUDA graph keyed by
+// (u, f). Launched eagerly when timing is on (events need eager launches) or when
+// the caller is already capturing the stream (the launches join the caller's graph).
+template <typename Body>
+mg_status run_graph(const Ctx& c, mg_handle::GraphEntry& g, const void* u, const void* f, Body body) {
+  mg_handle* h = c.h;
+  if (h->timing || c.s == nullptr) return body();
+  if (g.exec && g.u == u && g.f == f) {
+    CK(cudaGraphLaunch(g.exec, c.s));
+    h->launches += g.kernels;
+    return MG_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(c.s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return body();
+  const int64_t before = h->launches;
+  CK(cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal));
+  const mg_status st = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c.s, &graph);
+  if (st != MG_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return st != MG_OK ? st : MG_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return MG_ERR_CUDA;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.u = u;
+  g.f = f;
+  g.exec = exec;
+  g.kernels = h->launches - before;
+  h->launches = before + g.kernels;
+  CK(cudaGraphLaunch(exec, c.s));
+  return MG_OK;
+}
+
+// Red-black sweeps through the shared-memory tile kernel (one launch per sweep)?
+// Auto uses the two half-sweep kernels: on GB300 they are faster in both precisions
+// (measured: FP32 level-0 sweep 2 x 87 us vs 180 us; FP64 2 x 336 us vs 1080 us).
+template <typename T>
+bool fused_sweeps(const mg_handle* h) {
+  if (h->opt.smoother != MG_SMOOTH_REDBLACK) return false;
+  return h->opt.sweep_kernel == 2;
+}
+
+// One smoothing sweep in place on U (the handle's t[l] is the scratch buffer).
 template <typename T>
 mg_status smooth(const Ctx& c, int l, T* U, const T* F) {
   mg_handle* h = c.h;
   Hier<T>& H = hier<T>(h);
   T* Tb = H.t[l];
   const auto& L = H.L[l];
-  if (h->opt.smoother == MG_SMOOTH_REDBLACK) {
+  if (fused_sweeps<T>(h)) {
+    {
+      Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+      LAUNCH(h, 1, launch_sweep_fused<T>(L, c.exact, U, F, Tb, c.s));
+    }
+    CK(cudaMemcpyAsync(U, Tb, level_bytes(h->host[l], sizeof(T)), cudaMemcpyDeviceToDevice, c.s));
+  } else if (h->opt.smoother == MG_SMOOTH_REDBLACK) {
     {
       Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
       LAUNCH(h, 1, launch_half_sweep<T>(L, c.exact, U, F, Tb, 1, c.s));
@@ -478,18 +578,43 @@ mg_status smooth(const Ctx& c, int l, T* U, const T* F) {
   return MG_OK;
 }
 
+// Smoothing sweep inside a cycle: tile-kernel sweeps alternate between *cur and the
+// level's t buffer (out of place, no copy back); other sweeps stay in *cur.
+template <typename T>
+mg_status cycle_sweep(const Ctx& c, int l, T*& cur, T*& oth, const T* F) {
+  mg_handle* h = c.h;
+  if (!fused_sweeps<T>(h)) return smooth<T>(c, l, cur, F);
+  {
+    Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+    LAUNCH(h, 1, launch_sweep_fused<T>(hier<T>(h).L[l], c.exact, cur, F, oth, c.s));
+  }
+  std::swap(cur, oth);
+  return MG_OK;
+}
+
 template <typename T>
 mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
   mg_handle* h = c.h;
   Hier<T>& H = hier<T>(h);
   const int lmax = (int)h->host.size() - 1;
   mg_status st;
+  if (l == H.tail_level) {
+    // the program starts with the zeroing op; skip it to continue from U
+    LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, zero_init ? H.d_prog : H.d_prog + 1,
+                                zero_init ? H.nops : H.nops - 1, c.exact, c.s));
+    return MG_OK;
+  }
   if (zero_init) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
+  // Tile-kernel sweeps flip between U and t[l]; an odd number of them is evened out by
+  // an out-of-place interpolation so that the level ends in U.
+  T* cur = U;
+  T* oth = H.t[l];
+  const bool flips = fused_sweeps<T>(h);
   for (int k = 0; k < h->opt.nu1; ++k)
-    if ((st = smooth<T>(c, l, U, F)) != MG_OK) return st;
+    if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) return st;
   {
     Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
-    LAUNCH(h, 1, launch_residual<T>(H.L[l], c.exact, U, F, H.d[l], c.s));
+    LAUNCH(h, 1, launch_residual<T>(H.L[l], c.exact, cur, F, H.d[l], c.s));
   }
   {
     Bracket b(h, l, MG_KERNEL_RESTRICT, c.s);
@@ -503,11 +628,16 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
   }
   {
     Bracket b(h, l, MG_KERNEL_PROLONG, c.s);
-    LAUNCH(h, 1, launch_prolong_add<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, U, H.u[l + 1], c.s));
+    if (flips && ((h->opt.nu1 + h->opt.nu2) & 1)) {
+      LAUNCH(h, 1, launch_prolong_add<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, oth, H.u[l + 1], c.s, cur));
+      std::swap(cur, oth);
+    } else {
+      LAUNCH(h, 1, launch_prolong_add<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, cur, H.u[l + 1], c.s));
+    }
   }
   for (int k = 0; k < h->opt.nu2; ++k)
-    if ((st = smooth<T>(c, l, U, F)) != MG_OK) return st;
-  return MG_OK;
+    if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) return st;
+  return cur == U ? MG_OK : MG_ERR_INVALID;
 }
 
 mg_status read_scalar(mg_handle* h, cudaStream_t s, double* out) {
@@ -566,6 +696,65 @@ mg_status alloc_hier(mg_handle* h, bool caller_level0) {
   return MG_OK;
 }
 
+// Tail program for cycle_level(l, zero_init = true): the same op sequence the
+// per-level launches would make.
+void emit_tail(const mg_handle* h, int l, bool zero, std::vector<int4>& prog) {
+  const int lmax = (int)h->host.size() - 1;
+  if (zero) prog.push_back(make_int4(kOpZero, l, 0, 0));
+  for (int k = 0; k < h->opt.nu1; ++k) prog.push_back(make_int4(kOpSmooth, l, 0, 0));
+  prog.push_back(make_int4(kOpResRestrict, l, 0, 0));
+  if (l + 1 == lmax) {
+    prog.push_back(make_int4(kOpCoarsest, lmax, 0, 0));
+  } else {
+    for (int g = 0; g < h->opt.gamma; ++g) emit_tail(h, l + 1, g == 0, prog);
+  }
+  prog.push_back(make_int4(kOpProlong, l, 0, 0));
+  for (int k = 0; k < h->opt.nu2; ++k) prog.push_back(make_int4(kOpSmooth, l, 0, 0));
+}
+
+// Hand every level from the first one (below the finest) with at most
+// `max_unknowns` unknowns down to the coarsest to the tail kernel.
+template <typename T>
+mg_status build_tail(mg_handle* h, int64_t max_unknowns) {
+  Hier<T>& H = hier<T>(h);
+  const int nl = (int)h->host.size();
+  int lt = -1;
+  for (int l = 1; l + 1 < nl; ++l)
+    if (h->host[l].unknowns <= max_unknowns) { lt = l; break; }
+  if (lt < 0 || nl > kTailMaxLevels) return MG_OK;
+  TailDesc<T> td;
+  std::memset(&td, 0, sizeof(td));
+  for (int l = 0; l < nl; ++l) {
+    td.L[l] = H.L[l].d;
+    td.u[l] = H.u[l];
+    td.t[l] = H.t[l];
+    td.f[l] = H.f[l];
+    td.d[l] = H.d[l];
+    td.transfer[l] = l + 1 < nl ? h->transfer[l] : 0;
+  }
+  td.smoother = h->opt.smoother;
+  td.coarsest_idx = H.coarsest_idx;
+  td.coarsest_a = H.coarsest_a;
+  std::vector<int4> prog;
+  emit_tail(h, lt, true, prog);
+  mg_status st;
+  if ((st = device_alloc(h, (void**)&H.d_tail, sizeof(td))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&H.d_prog, prog.size() * sizeof(int4))) != MG_OK) return st;
+  CK(cudaMemcpy(H.d_tail, &td, sizeof(td), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(H.d_prog, prog.data(), prog.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  H.nops = (int)prog.size();
+  H.tail_level = lt;
+  H.tail_ctas = tail_ctas<T>(h->opt.fma_contract == 0);
+  if (h->opt.tail_ctas > 0) H.tail_ctas = std::min(H.tail_ctas, (int)h->opt.tail_ctas);
+  return MG_OK;
+}
+
+// Largest level (unknowns) run by the tail cluster (16 SMs). With the cycle in a
+// CUDA graph a small level's full-grid launch costs little, and the tail's per-phase
+// latency on 16 SMs only wins for the last few levels (measured on GB300).
+constexpr int64_t kTailUnknownsFp64 = 256;
+constexpr int64_t kTailUnknownsFp32 = 256;
+
 // Power of two near 1 / rms of a residual with squared norm r2 over m unknowns, so
 // that the FP32 copy of the residual stays far from underflow and overflow.
 double ir_scale_for(double r2, int64_t m) {
@@ -590,8 +779,13 @@ mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
 mg_status ir_correct(const Ctx& c, double* u) {
   mg_handle* h = c.h;
   mg_status st;
-  for (int k = 0; k < h->opt.inner_cycles; ++k)
-    if ((st = cycle_level<float>(c, 0, h->h32.u[0], h->h32.f[0], k == 0)) != MG_OK) return st;
+  st = run_graph(c, h->g_inner32, nullptr, nullptr, [&]() -> mg_status {
+    mg_status s2;
+    for (int k = 0; k < h->opt.inner_cycles; ++k)
+      if ((s2 = cycle_level<float>(c, 0, h->h32.u[0], h->h32.f[0], k == 0)) != MG_OK) return s2;
+    return MG_OK;
+  });
+  if (st != MG_OK) return st;
   LAUNCH(h, 1, launch_ir_update(h->h64.L[0], u, h->h32.u[0], 1.0 / h->ir_scale, c.s));
   return MG_OK;
 }
@@ -613,6 +807,9 @@ void mg_default_options(mg_options* o) {
   o->precision = MG_PREC_FP64;
   o->fma_contract = 0;
   o->inner_cycles = 2;
+  o->tail_unknowns = 0;
+  o->tail_ctas = 0;
+  o->sweep_kernel = 0;
 }
 
 const char* mg_status_string(mg_status s) {
@@ -677,11 +874,20 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   if ((st = alloc_hier<double>(h, /*caller_level0=*/true)) != MG_OK) return fail(st);
   h->h64.coarsest_idx = cidx;
   h->h64.coarsest_a = ca;
+  auto tail_limit = [&](int64_t dflt) -> int64_t {
+    return o.tail_unknowns < 0 ? 0 : (o.tail_unknowns > 0 ? (int64_t)o.tail_unknowns : dflt);
+  };
+  if ((st = build_tail<double>(h, tail_limit(kTailUnknownsFp64))) != MG_OK) return fail(st);
   if (o.precision == MG_PREC_MIXED_FP32) {
     if ((st = alloc_hier<float>(h, false)) != MG_OK) return fail(st);
     h->h32.coarsest_idx = cidx;
     h->h32.coarsest_a = (float)ca;
+    if ((st = build_tail<float>(h, tail_limit(kTailUnknownsFp32))) != MG_OK) return fail(st);
   }
+  if (cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return fail(MG_ERR_CUDA);
   h->nblocks0 = resnorm_blocks<double>(h->h64.L[0]);
   if ((st = device_alloc(h, (void**)&h->partial, h->nblocks0 * sizeof(double))) != MG_OK) return fail(st);
   if ((st = device_alloc(h, (void**)&h->scalar, 64)) != MG_OK) return fail(st);
@@ -716,7 +922,8 @@ mg_status mg_get_level_info(const mg_handle* h, int level, mg_level_info* out) {
 
 mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out, void* stream) {
   if (!h || !u || !f) return MG_ERR_INVALID;
-  Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
+  StreamScope scope(h, stream);
+  Ctx c{h, scope.s, h->opt.fma_contract == 0};
   LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   mg_status st;
   double fn2;
@@ -730,7 +937,8 @@ mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out
     if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;  // residual at the chosen scale
     if ((st = ir_correct(c, u)) != MG_OK) return st;
   } else {
-    if ((st = cycle_level<double>(c, 0, u, f, false)) != MG_OK) return st;
+    st = run_graph(c, h->g_cycle64, u, f, [&]() { return cycle_level<double>(c, 0, u, f, false); });
+    if (st != MG_OK) return st;
   }
   ++h->cycles;
   if (rel_res_out) {
@@ -743,7 +951,8 @@ mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out
 mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int max_cycles,
                    int* cycles_out, double* history_out, void* stream) {
   if (!h || !u || !f || max_cycles < 0 || !(rtol >= 0.0)) return MG_ERR_INVALID;
-  Ctx c{h, (cudaStream_t)stream, h->opt.fma_contract == 0};
+  StreamScope scope(h, stream);
+  Ctx c{h, scope.s, h->opt.fma_contract == 0};
   LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   double fn2, rr;
   mg_status st = f_norm2(h, c.s, f, &fn2);
@@ -772,7 +981,8 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
     if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
     if (history_out) history_out[0] = rr;
     while (k < max_cycles && rr >= rtol) {
-      if ((st = cycle_level<double>(c, 0, u, f, false)) != MG_OK) return st;
+      st = run_graph(c, h->g_cycle64, u, f, [&]() { return cycle_level<double>(c, 0, u, f, false); });
+      if (st != MG_OK) return st;
       ++k;
       ++h->cycles;
       if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;

@@ -7,6 +7,7 @@
 // every product and sum rounded separately (__dmul_rn / __dadd_rn keep nvcc from
 // contracting them into FMAs). EXACT = false lets products fuse into FMAs.
 #include <algorithm>
+#include <cooperative_groups.h>
 #include <cstdio>
 
 #include "kernels.h"
@@ -104,21 +105,362 @@ __device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict_
   return s;
 }
 
+// New value of node (i, j) after one relaxation: u + (f - L u) * omega / a_pp.
+template <typename T, bool EXACT>
+__device__ __forceinline__ T relax_value(const LevelDev<T>& L, const T* __restrict__ uin,
+                                         const T* __restrict__ f, int i, int j, int64_t at) {
+  T wd;
+  const T s = apply_at<T, EXACT>(L, uin, i, j, at, &wd);
+  const T r = Arith<T>::sub(f[at], s);
+  return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
+}
+
+// One colour of a red-black sweep, out of place (uin -> uout; the other colour is
+// copied). Rotated levels: one thread per node (a storage row holds one colour, so
+// warps never split). Axis levels: one thread per adjacent pair of nodes (2p, 2p+1)
+// in a row, which holds exactly one node of each colour, so every lane relaxes one
+// node and copies the other.
 template <typename T, bool EXACT>
 __global__ void k_half_sweep(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
                              const T* __restrict__ f, T* __restrict__ uout, int red) {
   const LevelDev<T>& L = *Lp;
   int i, j;
+  if (L.kind == kAxis) {
+    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
+    j = blockIdx.y * kBY + threadIdx.y;
+    if (j <= 0 || j >= L.n || i0 > L.n) return;
+    i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;  // node of colour `red`
+    const int ic = 2 * i0 + 1 - i;               // node of the other colour
+    if (ic > 0 && ic < L.n) {
+      const int64_t ac = sidx(L, ic, j);
+      uout[ac] = uin[ac];
+    }
+    if (i <= 0 || i >= L.n) return;
+  } else {
+    if (!thread_node(L, i, j) || !interior(L, i, j)) return;
+    if (is_red(L, i, j) != red) {
+      const int64_t at = sidx(L, i, j);
+      uout[at] = uin[at];
+      return;
+    }
+  }
+  const int64_t at = sidx(L, i, j);
+  uout[at] = relax_value<T, EXACT>(L, uin, f, i, j, at);
+}
+
+// ---- specialised fast path: NT-point stencils with coefficients in registers and
+// kRows rows per thread (same arithmetic as apply_at / relax_value) --------------
+constexpr int kRows = 4;
+
+template <typename T, bool EXACT, int NT>
+__device__ __forceinline__ T apply_fast(const T (&c)[NT], const int (&dl)[NT], const T* __restrict__ u,
+                                        int64_t at) {
+  T s = Arith<T>::mul(c[0], u[at + dl[0]]);
+#pragma unroll
+  for (int k = 1; k < NT; ++k) s = madd<T, EXACT>(s, c[k], u[at + dl[k]]);
+  return s;
+}
+
+template <typename T, bool EXACT, int NT>
+__device__ __forceinline__ T relax_fast(const T (&c)[NT], const int (&dl)[NT], T wd, const T* __restrict__ uin,
+                                        const T* __restrict__ f, int64_t at) {
+  const T r = Arith<T>::sub(f[at], apply_fast<T, EXACT, NT>(c, dl, uin, at));
+  return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
+}
+
+template <typename T, bool EXACT, int NT>
+__global__ void k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
+                                const T* __restrict__ f, T* __restrict__ uout, int red) {
+  const LevelDev<T>& L = *Lp;
+  T c[NT];
+  int d0[NT], d1[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) {
+    c[k] = L.c[k];
+    d0[k] = L.delta[0][k];
+    d1[k] = L.delta[1][k];
+  }
+  const T wd = L.wd;
+  const int n = L.n;
+  const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
+  if (L.kind == kAxis) {
+    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
+    if (i0 > n) return;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = jb + r * kBY;
+      if (j <= 0 || j >= n) continue;
+      const int i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;
+      const int ic = 2 * i0 + 1 - i;
+      const int64_t row = (int64_t)j * L.pitch;
+      if (ic > 0 && ic < n) uout[row + ic] = uin[row + ic];
+      if (i <= 0 || i >= n) continue;
+      const int64_t at = row + i;
+      uout[at] = fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
+                                    : relax_value<T, EXACT>(L, uin, f, i, j, at);
+    }
+  } else {
+    const int q = blockIdx.x * kBX + threadIdx.x;
+    if (q >= L.cols) return;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = jb + r * kBY;
+      if (j <= 0 || j >= n) continue;
+      const int i = 2 * q + (j & 1);
+      if (i <= 0 || i >= n) continue;
+      const int64_t at = (int64_t)j * L.pitch + q;
+      if ((i & 1) != red) {
+        uout[at] = uin[at];
+        continue;
+      }
+      uout[at] = fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
+                                    : relax_value<T, EXACT>(L, uin, f, i, j, at);
+    }
+  }
+}
+
+template <typename T, bool EXACT, int NT>
+__global__ void k_residual_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
+                              const T* __restrict__ f, T* __restrict__ d) {
+  const LevelDev<T>& L = *Lp;
+  T c[NT];
+  int d0[NT], d1[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) {
+    c[k] = L.c[k];
+    d0[k] = L.delta[0][k];
+    d1[k] = L.delta[1][k];
+  }
+  const int n = L.n;
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  if (q >= L.cols) return;
+  const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    const int j = jb + r * kBY;
+    if (j <= 0 || j >= n) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (i <= 0 || i >= n) continue;
+    const int64_t at = (int64_t)j * L.pitch + q;
+    const T s = fast_node(L, i, j) ? apply_fast<T, EXACT, NT>(c, (L.kind == kRot && (i & 1)) ? d1 : d0, u, at)
+                                   : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
+    d[at] = Arith<T>::sub(f[at], s);
+  }
+}
+
+// Wide stencils (any size): one node per thread; the interior stencil's
+// coefficients and storage offsets are staged in shared memory once per block.
+template <typename T>
+struct StencilSmem {
+  T c[kMaxTerms];
+  int d[2][kMaxTerms];
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_stencil(const LevelDev<T>& L, StencilSmem<T>& sm) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid < L.nt) {
+    sm.c[tid] = L.c[tid];
+    sm.d[0][tid] = L.delta[0][tid];
+    sm.d[1][tid] = L.delta[1][tid];
+  }
+  __syncthreads();
+}
+
+template <typename T, bool EXACT>
+__device__ __forceinline__ T apply_smem(const StencilSmem<T>& sm, int nt, int par, const T* __restrict__ u, int64_t at) {
+  const int* dl = sm.d[par];
+  T s = Arith<T>::mul(sm.c[0], u[at + dl[0]]);
+#pragma unroll 4
+  for (int k = 1; k < nt; ++k) s = madd<T, EXACT>(s, sm.c[k], u[at + dl[k]]);
+  return s;
+}
+
+template <typename T, bool EXACT>
+__global__ void k_half_sweep_gen(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
+                                 const T* __restrict__ f, T* __restrict__ uout, int red) {
+  const LevelDev<T>& L = *Lp;
+  __shared__ StencilSmem<T> sm;
+  stage_stencil(L, sm);
+  int i, j;
+  if (L.kind == kAxis) {
+    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
+    j = blockIdx.y * kBY + threadIdx.y;
+    if (j <= 0 || j >= L.n || i0 > L.n) return;
+    i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;
+    const int ic = 2 * i0 + 1 - i;
+    if (ic > 0 && ic < L.n) {
+      const int64_t ac = sidx(L, ic, j);
+      uout[ac] = uin[ac];
+    }
+    if (i <= 0 || i >= L.n) return;
+  } else {
+    if (!thread_node(L, i, j) || !interior(L, i, j)) return;
+    if (is_red(L, i, j) != red) {
+      const int64_t at = sidx(L, i, j);
+      uout[at] = uin[at];
+      return;
+    }
+  }
+  const int64_t at = sidx(L, i, j);
+  if (fast_node(L, i, j)) {
+    const T r = Arith<T>::sub(f[at], apply_smem<T, EXACT>(sm, L.nt, L.kind == kRot ? (i & 1) : 0, uin, at));
+    const T wd = L.wd;
+    uout[at] = EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
+  } else {
+    uout[at] = relax_value<T, EXACT>(L, uin, f, i, j, at);
+  }
+}
+
+template <typename T, bool EXACT>
+__global__ void k_residual_gen(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
+                               const T* __restrict__ f, T* __restrict__ d) {
+  const LevelDev<T>& L = *Lp;
+  __shared__ StencilSmem<T> sm;
+  stage_stencil(L, sm);
+  int i, j;
   if (!thread_node(L, i, j) || !interior(L, i, j)) return;
   const int64_t at = sidx(L, i, j);
-  if (is_red(L, i, j) != red) {
-    uout[at] = uin[at];
-    return;
+  const T s = fast_node(L, i, j) ? apply_smem<T, EXACT>(sm, L.nt, L.kind == kRot ? (i & 1) : 0, u, at)
+                                 : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
+  d[at] = Arith<T>::sub(f[at], s);
+}
+
+// ---- fused red-black sweep on a shared-memory tile ---------------------------
+// One kernel does the red then the black half-sweep of a kFTW x kFTH tile of storage
+// elements: the tile plus a halo of two relaxation reaches (2 rq columns, 2 ry rows)
+// of u and f is staged in shared memory, red nodes are relaxed on the tile plus one
+// reach (so every black node of the tile sees updated red neighbours), then black
+// nodes of the tile. Arithmetic per node is exactly relax_value's. Threads are a
+// 32 x 8 grid walking the shared arrays row by row (coalesced global loads).
+constexpr int kFTW = 64, kFTH = 32;
+
+// Level scalars the tile kernel needs, held in registers.
+struct TileGeom {
+  int kind, n, rows, cols, pitch, rx, ry, nt;
+};
+
+template <typename T, bool EXACT, int NT>
+__device__ __forceinline__ T relax_tile(const LevelDev<T>& L, const TileGeom& G, T wdf, const T* __restrict__ su,
+                                        const T* __restrict__ sf, const T* sc, const int* soff, int e, int i, int j,
+                                        int q0, int j0, int SW) {
+  T s, wd;
+  if (i >= G.rx && i <= G.n - G.rx && j >= G.ry && j <= G.n - G.ry) {
+    s = Arith<T>::mul(sc[0], su[e + soff[0]]);
+    if (NT > 0) {
+#pragma unroll
+      for (int k = 1; k < NT; ++k) s = madd<T, EXACT>(s, sc[k], su[e + soff[k]]);
+    } else {
+#pragma unroll 4
+      for (int k = 1; k < G.nt; ++k) s = madd<T, EXACT>(s, sc[k], su[e + soff[k]]);
+    }
+    wd = wdf;
+  } else {
+    const int cl = class_of(L, i, j);
+    const int2 ce = L.cls[cl];
+    s = T(0);
+    for (int k = 0; k < ce.y; ++k) {
+      const int t = ce.x + k;
+      const int ti = i + L.tdx[t], tj = j + L.tdy[t];
+      const int tq = G.kind == kRot ? (ti >> 1) : ti;
+      const T x = su[(tj - j0) * SW + (tq - q0)];
+      s = k == 0 ? Arith<T>::mul(L.tc[t], x) : madd<T, EXACT>(s, L.tc[t], x);
+    }
+    wd = L.cls_wd[cl];
   }
-  T wd;
-  const T s = apply_at<T, EXACT>(L, uin, i, j, at, &wd);
-  const T r = Arith<T>::sub(f[at], s);
-  uout[at] = EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
+  const T r = Arith<T>::sub(sf[e], s);
+  return EXACT ? Arith<T>::add(su[e], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, su[e]);
+}
+
+template <typename T, bool EXACT, int NT>
+__global__ void __launch_bounds__(kBX * kBY)
+    k_sweep_fused(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin, const T* __restrict__ f,
+                  T* __restrict__ uout, int rq, int ry) {
+  extern __shared__ __align__(16) unsigned char fused_smem[];
+  __shared__ T sc[kMaxTerms];
+  __shared__ int soff[2][kMaxTerms];
+  const LevelDev<T>& L = *Lp;
+  const TileGeom G{L.kind, L.n, L.rows, L.cols, L.pitch, L.rx, L.ry, L.nt};
+  const T wdf = L.wd;
+  const int hx = 2 * rq, hy = 2 * ry;
+  const int SW = kFTW + 2 * hx, SH = kFTH + 2 * hy, SN = SW * SH;
+  T* su = reinterpret_cast<T*>(fused_smem);
+  T* sf = su + SN;
+  T* st = sf + SN;
+  const int q0 = blockIdx.x * kFTW - hx;  // storage coordinates of shared element 0
+  const int j0 = blockIdx.y * kFTH - hy;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kBX + tx;
+  if (tid < G.nt) {
+    sc[tid] = L.c[tid];
+    soff[0][tid] = L.sdy[tid] * SW + L.sdx[0][tid];
+    soff[1][tid] = L.sdy[tid] * SW + L.sdx[1][tid];
+  }
+  for (int lj = ty; lj < SH; lj += kBY) {
+    const int gj = j0 + lj;
+    const bool rowok = gj >= 0 && gj < G.rows;
+    for (int lq = tx; lq < SW; lq += kBX) {
+      const int gq = q0 + lq;
+      T vu = T(0), vf = T(0);
+      if (rowok && gq >= 0 && gq < G.pitch) {
+        const int64_t at = (int64_t)gj * G.pitch + gq;
+        vu = uin[at];
+        vf = f[at];
+      }
+      su[lj * SW + lq] = vu;
+      sf[lj * SW + lq] = vf;
+    }
+  }
+  __syncthreads();
+  const bool rot = G.kind == kRot;
+  // Colour-mapped walks over a shared-memory window [lq_lo, lq_hi) x [lj_lo, lj_hi):
+  // axis grids hold one colour on every other column of a row (lanes take stride 2),
+  // rotated grids one colour per row (threads take every other row).
+  auto walk = [&](int lq_lo, int lq_hi, int lj_lo, int lj_hi, bool want_red, auto&& body) {
+    if (rot) {
+      // red rows: j odd
+      int lj = lj_lo + ((((j0 + lj_lo) & 1) != (want_red ? 1 : 0)) ? 1 : 0);
+      for (lj += 2 * ty; lj < lj_hi; lj += 2 * kBY) {
+        const int j = j0 + lj;
+        if (j <= 0 || j >= G.n) continue;
+        for (int lq = lq_lo + tx; lq < lq_hi; lq += kBX) {
+          const int gq = q0 + lq;
+          if (gq < 0 || gq >= G.cols) continue;
+          const int i = 2 * gq + (j & 1);
+          if (i <= 0 || i >= G.n) continue;
+          body(lj * SW + lq, i, j, gq);
+        }
+      }
+    } else {
+      for (int lj = lj_lo + ty; lj < lj_hi; lj += kBY) {
+        const int j = j0 + lj;
+        if (j <= 0 || j >= G.n) continue;
+        // red: (gq + j) odd
+        const int want = want_red ? 1 : 0;
+        int lq = lq_lo + ((((q0 + lq_lo + j) & 1) != want) ? 1 : 0);
+        for (lq += 2 * tx; lq < lq_hi; lq += 2 * kBX) {
+          const int gq = q0 + lq;
+          if (gq <= 0 || gq >= G.n) continue;
+          body(lj * SW + lq, gq, j, gq);
+        }
+      }
+    }
+  };
+  const int* soff_r = soff[rot ? 1 : 0];  // red nodes of a rotated grid have i odd
+  const int* soff_b = soff[0];            // black nodes of a rotated grid have i even
+  // red half-sweep on the tile plus one reach (new values into st)
+  walk(hx - rq, hx + kFTW + rq, hy - ry, hy + kFTH + ry, true, [&](int e, int i, int j, int) {
+    st[e] = relax_tile<T, EXACT, NT>(L, G, wdf, su, sf, sc, soff_r, e, i, j, q0, j0, SW);
+  });
+  __syncthreads();
+  walk(hx - rq, hx + kFTW + rq, hy - ry, hy + kFTH + ry, true, [&](int e, int, int, int) { su[e] = st[e]; });
+  __syncthreads();
+  // tile outputs: red nodes copied from shared memory, black nodes relaxed
+  walk(hx, hx + kFTW, hy, hy + kFTH, true, [&](int e, int, int j, int gq) {
+    uout[(int64_t)j * G.pitch + gq] = su[e];
+  });
+  walk(hx, hx + kFTW, hy, hy + kFTH, false, [&](int e, int i, int j, int gq) {
+    uout[(int64_t)j * G.pitch + gq] = relax_tile<T, EXACT, NT>(L, G, wdf, su, sf, sc, soff_b, e, i, j, q0, j0, SW);
+  });
 }
 
 template <typename T, bool EXACT>
@@ -144,16 +486,6 @@ __global__ void k_apply(const LevelDev<T>* __restrict__ Lp, const T* __restrict_
   out[at] = apply_at<T, EXACT>(L, u, i, j, at, nullptr);
 }
 
-template <typename T, bool EXACT>
-__global__ void k_residual(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
-                           const T* __restrict__ f, T* __restrict__ d) {
-  const LevelDev<T>& L = *Lp;
-  int i, j;
-  if (!thread_node(L, i, j) || !interior(L, i, j)) return;
-  const int64_t at = sidx(L, i, j);
-  d[at] = Arith<T>::sub(f[at], apply_at<T, EXACT>(L, u, i, j, at, nullptr));
-}
-
 // Restriction terms (dx, dy) in fine-lattice units, sorted by (dy, dx), with weights.
 struct RTerm {
   int dx, dy;
@@ -165,13 +497,10 @@ __constant__ RTerm c_rterms_std[9] = {{-1, -1, 0.0625}, {0, -1, 0.125}, {1, -1, 
                                       {-1, 0, 0.125},   {0, 0, 0.25},   {1, 0, 0.125},
                                       {-1, 1, 0.0625},  {0, 1, 0.125},  {1, 1, 0.0625}};
 
+// Restricted residual at coarse node (i, j) (coarse-level lattice).
 template <typename T, bool EXACT>
-__global__ void k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
-                           int transfer, const T* __restrict__ d, T* __restrict__ fc) {
-  const LevelDev<T>& Lf = *Lfp;
-  const LevelDev<T>& Lc = *Lcp;
-  int i, j;
-  if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
+__device__ __forceinline__ T restrict_value(const LevelDev<T>& Lf, int transfer, const T* __restrict__ d,
+                                            int i, int j) {
   // fine-lattice position of the coarse node
   const int fi = transfer == kRbAxisToRot ? i : 2 * i;
   const int fj = transfer == kRbAxisToRot ? j : 2 * j;
@@ -181,17 +510,13 @@ __global__ void k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T
   const int nt = transfer == kStandard ? 9 : 5;
   T s = Arith<T>::mul(T(rt[0].w), d[sidx(Lf, fi + rt[0].dx, fj + rt[0].dy)]);
   for (int k = 1; k < nt; ++k) s = madd<T, EXACT>(s, T(rt[k].w), d[sidx(Lf, fi + rt[k].dx, fj + rt[k].dy)]);
-  fc[sidx(Lc, i, j)] = s;
+  return s;
 }
 
+// Interpolated correction (P v)(i, j) at fine node (i, j).
 template <typename T, bool EXACT>
-__global__ void k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
-                              int transfer, T* __restrict__ uf, const T* __restrict__ vc) {
-  const LevelDev<T>& Lf = *Lfp;
-  const LevelDev<T>& Lc = *Lcp;
-  int i, j;
-  if (!thread_node(Lf, i, j) || !interior(Lf, i, j)) return;
-  const int64_t at = sidx(Lf, i, j);
+__device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, const T* __restrict__ vc,
+                                           int i, int j) {
   T e;
   if (transfer == kRbAxisToRot) {
     if (((i + j) & 1) == 0) {
@@ -219,9 +544,9 @@ __global__ void k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDe
     T wx, wy;
     int nx, ny;
     if (i & 1) { xs[0] = (i - 1) >> 1; xs[1] = (i + 1) >> 1; nx = 2; wx = T(0.5); }
-    else { xs[0] = i >> 1; nx = 1; wx = T(1); }
+    else { xs[0] = i >> 1; xs[1] = xs[0]; nx = 1; wx = T(1); }
     if (j & 1) { ys[0] = (j - 1) >> 1; ys[1] = (j + 1) >> 1; ny = 2; wy = T(0.5); }
-    else { ys[0] = j >> 1; ny = 1; wy = T(1); }
+    else { ys[0] = j >> 1; ys[1] = ys[0]; ny = 1; wy = T(1); }
     const T w = Arith<T>::mul(wx, wy);  // exact
     bool first = true;
     e = T(0);
@@ -232,7 +557,26 @@ __global__ void k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDe
         first = false;
       }
   }
-  uf[at] = Arith<T>::add(uf[at], e);
+  return e;
+}
+
+template <typename T, bool EXACT>
+__global__ void k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
+                           int transfer, const T* __restrict__ d, T* __restrict__ fc) {
+  const LevelDev<T>& Lc = *Lcp;
+  int i, j;
+  if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
+  fc[sidx(Lc, i, j)] = restrict_value<T, EXACT>(*Lfp, transfer, d, i, j);
+}
+
+template <typename T, bool EXACT>
+__global__ void k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
+                              int transfer, const T* uin, T* uf, const T* __restrict__ vc) {
+  const LevelDev<T>& Lf = *Lfp;
+  int i, j;
+  if (!thread_node(Lf, i, j) || !interior(Lf, i, j)) return;
+  const int64_t at = sidx(Lf, i, j);
+  uf[at] = Arith<T>::add(uin[at], prolong_value<T, EXACT>(*Lcp, transfer, vc, i, j));
 }
 
 template <typename T>
@@ -255,16 +599,25 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// Norm reductions use a bounded grid: block (bx, by) covers the 32 x 8 tiles
+// (bx, by), (bx, by + gridDim.y), ... so that at most kMaxPartials partial sums
+// are left for the single-block final sum.
+constexpr int kMaxPartials = 2048;
+
 template <typename T, bool EXACT>
 __global__ void k_resnorm_partial(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
-                                  const T* __restrict__ f, double* __restrict__ partial) {
+                                  const T* __restrict__ f, double* __restrict__ partial, int tiles_y) {
   const LevelDev<T>& L = *Lp;
-  int i, j;
   double v = 0.0;
-  if (thread_node(L, i, j) && interior(L, i, j)) {
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+    const int j = ty * kBY + threadIdx.y;
+    if (j >= L.rows || q >= L.cols) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
     const int64_t at = sidx(L, i, j);
     const double d = (double)Arith<T>::sub(f[at], apply_at<T, EXACT>(L, u, i, j, at, nullptr));
-    v = d * d;
+    v += d * d;
   }
   v = block_sum(v);
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
@@ -272,13 +625,17 @@ __global__ void k_resnorm_partial(const LevelDev<T>* __restrict__ Lp, const T* _
 
 template <typename T>
 __global__ void k_sumsq_partial(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ f,
-                                double* __restrict__ partial) {
+                                double* __restrict__ partial, int tiles_y) {
   const LevelDev<T>& L = *Lp;
-  int i, j;
   double v = 0.0;
-  if (thread_node(L, i, j) && interior(L, i, j)) {
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+    const int j = ty * kBY + threadIdx.y;
+    if (j >= L.rows || q >= L.cols) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
     const double x = (double)f[sidx(L, i, j)];
-    v = x * x;
+    v += x * x;
   }
   v = block_sum(v);
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
@@ -308,15 +665,19 @@ __global__ void k_zero_boundary(int n, int pitch, T* __restrict__ u) {
 template <bool EXACT>
 __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
                               const double* __restrict__ f, float* __restrict__ r32, double scale,
-                              double* __restrict__ partial) {
+                              double* __restrict__ partial, int tiles_y) {
   const LevelDev<double>& L = *Lp;
-  int i, j;
   double v = 0.0;
-  if (thread_node(L, i, j) && interior(L, i, j)) {
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+    const int j = ty * kBY + threadIdx.y;
+    if (j >= L.rows || q >= L.cols) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
     const int64_t at = sidx(L, i, j);
     const double r = Arith<double>::sub(f[at], apply_at<double, EXACT>(L, u, i, j, at, nullptr));
     r32[at] = (float)(r * scale);
-    v = r * r;
+    v += r * r;
   }
   v = block_sum(v);
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
@@ -332,19 +693,163 @@ __global__ void k_ir_update(const LevelDev<double>* __restrict__ Lp, double* __r
   u[at] = u[at] + (double)e[at] * inv_scale;
 }
 
+// ---- small-level tail ---------------------------------------------------------
+// One thread-block cluster (kTailCtas CTAs of kTailThreads threads, one per SM)
+// runs the whole sub-cycle; the hardware cluster barrier separates dependent
+// phases (release / acquire at cluster scope, covering the global-memory arrays).
+constexpr int kTailThreads = 1024;
+
+// Storage element k of a level (row-major over rows x cols) -> lattice node.
+template <typename T>
+__device__ __forceinline__ bool tail_node(const LevelDev<T>& L, int k, int& i, int& j) {
+  j = k / L.cols;
+  const int q = k - j * L.cols;
+  i = L.kind == kRot ? 2 * q + (j & 1) : q;
+  return interior(L, i, j);
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(kTailThreads)
+    k_tail(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog, int nops) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = (int)cluster.block_rank() * kTailThreads + threadIdx.x;
+  const int nth = (int)cluster.num_blocks() * kTailThreads;
+  for (int p = 0; p < nops; ++p) {
+    const int4 op = prog[p];
+    const int l = op.y;
+    const LevelDev<T>& L = *D->L[l];
+    const int total = L.rows * L.cols;
+    int i, j;
+    if (op.x == kOpZero) {
+      T* u = D->u[l];
+      const int tot = L.rows * L.pitch;
+      for (int k = tid; k < tot; k += nth) u[k] = T(0);
+    } else if (op.x == kOpSmooth) {
+      T* U = D->u[l];
+      T* Tb = D->t[l];
+      const T* F = D->f[l];
+      if (D->smoother == 0) {
+        for (int half = 1; half >= 0; --half) {  // red (1) from U into Tb, then black (0) back
+          const T* src = half ? U : Tb;
+          T* dst = half ? Tb : U;
+          for (int k = tid; k < total; k += nth) {
+            if (!tail_node(L, k, i, j)) continue;
+            const int64_t at = sidx(L, i, j);
+            dst[at] = is_red(L, i, j) == half ? relax_value<T, EXACT>(L, src, F, i, j, at) : src[at];
+          }
+          cluster.sync();
+        }
+      } else {
+        for (int k = tid; k < total; k += nth) {
+          if (!tail_node(L, k, i, j)) continue;
+          const int64_t at = sidx(L, i, j);
+          Tb[at] = relax_value<T, EXACT>(L, U, F, i, j, at);
+        }
+        cluster.sync();
+        for (int k = tid; k < total; k += nth) {
+          if (!tail_node(L, k, i, j)) continue;
+          const int64_t at = sidx(L, i, j);
+          U[at] = Tb[at];
+        }
+      }
+    } else if (op.x == kOpResRestrict) {
+      const T* U = D->u[l];
+      const T* F = D->f[l];
+      T* Dd = D->d[l];
+      for (int k = tid; k < total; k += nth) {
+        if (!tail_node(L, k, i, j)) continue;
+        const int64_t at = sidx(L, i, j);
+        Dd[at] = Arith<T>::sub(F[at], apply_at<T, EXACT>(L, U, i, j, at, nullptr));
+      }
+      cluster.sync();
+      const LevelDev<T>& Lc = *D->L[l + 1];
+      T* Fc = D->f[l + 1];
+      const int ctot = Lc.rows * Lc.cols;
+      for (int k = tid; k < ctot; k += nth) {
+        if (!tail_node(Lc, k, i, j)) continue;
+        Fc[sidx(Lc, i, j)] = restrict_value<T, EXACT>(L, D->transfer[l], Dd, i, j);
+      }
+    } else if (op.x == kOpCoarsest) {
+      if (tid == 0) D->u[l][D->coarsest_idx] = Arith<T>::div(D->f[l][D->coarsest_idx], D->coarsest_a);
+    } else {  // kOpProlong
+      const LevelDev<T>& Lc = *D->L[l + 1];
+      T* U = D->u[l];
+      const T* V = D->u[l + 1];
+      for (int k = tid; k < total; k += nth) {
+        if (!tail_node(L, k, i, j)) continue;
+        const int64_t at = sidx(L, i, j);
+        U[at] = Arith<T>::add(U[at], prolong_value<T, EXACT>(Lc, D->transfer[l], V, i, j));
+      }
+    }
+    cluster.sync();
+  }
+}
+
 template <typename T>
 dim3 grid_of(const LevelDev<T>& L) {
   return dim3((L.cols + kBX - 1) / kBX, (L.rows + kBY - 1) / kBY);
 }
 
+// Bounded grid of the norm reductions (see kMaxPartials).
+template <typename T>
+dim3 norm_grid(const LevelDev<T>& L) {
+  const dim3 g = grid_of(L);
+  return dim3(g.x, std::max(1u, std::min(g.y, (unsigned)(kMaxPartials / (int)g.x))));
+}
+
 }  // namespace
+
+template <typename T, int NT>
+cudaError_t launch_half_sweep_nt(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout, int red,
+                                 cudaStream_t s) {
+  dim3 g = grid_of(L.h);
+  if (L.h.kind == kAxis) g.x = ((L.h.n + 2) / 2 + kBX - 1) / kBX;  // pairs (2p, 2p+1), 2p <= n
+  g.y = (L.h.rows + kBY * kRows - 1) / (kBY * kRows);
+  if (exact) k_half_sweep_nt<T, true, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
+  else k_half_sweep_nt<T, false, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_half_sweep(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout,
                               int red, cudaStream_t s) {
-  if (exact) k_half_sweep<T, true><<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
-  else k_half_sweep<T, false><<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
+  if (L.h.nt == 5) return launch_half_sweep_nt<T, 5>(L, exact, uin, f, uout, red, s);
+  if (L.h.nt == 9) return launch_half_sweep_nt<T, 9>(L, exact, uin, f, uout, red, s);
+  dim3 g = grid_of(L.h);
+  if (L.h.kind == kAxis) g.x = ((L.h.n + 2) / 2 + kBX - 1) / kBX;  // pairs (2p, 2p+1), 2p <= n
+  if (exact) k_half_sweep_gen<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
+  else k_half_sweep_gen<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
   return cudaGetLastError();
+}
+
+template <typename T, bool EXACT, int NT>
+cudaError_t launch_sweep_fused_nt(const LevelPair<T>& L, const T* uin, const T* f, T* uout, int rq, int ry,
+                                  size_t smem, cudaStream_t s) {
+  const dim3 g((L.h.cols + kFTW - 1) / kFTW, (L.h.rows + kFTH - 1) / kFTH);
+  cudaFuncSetAttribute(k_sweep_fused<T, EXACT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  k_sweep_fused<T, EXACT, NT><<<g, dim3(kBX, kBY), smem, s>>>(L.d, uin, f, uout, rq, ry);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep_fused(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout, cudaStream_t s) {
+  int rq = 0, ry = 0;
+  for (int k = 0; k < L.h.nt; ++k) {
+    rq = std::max(rq, std::max(std::abs(L.h.sdx[0][k]), std::abs(L.h.sdx[1][k])));
+    ry = std::max(ry, std::abs(L.h.sdy[k]));
+  }
+  const size_t smem = 3 * (size_t)(kFTW + 4 * rq) * (kFTH + 4 * ry) * sizeof(T);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  const int nt = L.h.nt;
+  if (exact) {
+    if (nt == 5) return launch_sweep_fused_nt<T, true, 5>(L, uin, f, uout, rq, ry, smem, s);
+    if (nt == 9) return launch_sweep_fused_nt<T, true, 9>(L, uin, f, uout, rq, ry, smem, s);
+    return launch_sweep_fused_nt<T, true, 0>(L, uin, f, uout, rq, ry, smem, s);
+  }
+  if (nt == 5) return launch_sweep_fused_nt<T, false, 5>(L, uin, f, uout, rq, ry, smem, s);
+  if (nt == 9) return launch_sweep_fused_nt<T, false, 9>(L, uin, f, uout, rq, ry, smem, s);
+  return launch_sweep_fused_nt<T, false, 0>(L, uin, f, uout, rq, ry, smem, s);
 }
 
 template <typename T>
@@ -362,11 +867,23 @@ cudaError_t launch_apply(const LevelPair<T>& L, bool exact, const T* u, T* out, 
   return cudaGetLastError();
 }
 
+template <typename T, int NT>
+cudaError_t launch_residual_nt(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d, cudaStream_t s) {
+  dim3 g = grid_of(L.h);
+  g.y = (L.h.rows + kBY * kRows - 1) / (kBY * kRows);
+  if (exact) k_residual_nt<T, true, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
+  else k_residual_nt<T, false, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d,
                             cudaStream_t s) {
-  if (exact) k_residual<T, true><<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
-  else k_residual<T, false><<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
+  if (L.h.nt == 5) return launch_residual_nt<T, 5>(L, exact, u, f, d, s);
+  if (L.h.nt == 9) return launch_residual_nt<T, 9>(L, exact, u, f, d, s);
+  const dim3 g = grid_of(L.h);
+  if (exact) k_residual_gen<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
+  else k_residual_gen<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
   return cudaGetLastError();
 }
 
@@ -380,9 +897,9 @@ cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int 
 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer,
-                               bool exact, T* uf, const T* vc, cudaStream_t s) {
-  if (exact) k_prolong_add<T, true><<<grid_of(Lf.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, uf, vc);
-  else k_prolong_add<T, false><<<grid_of(Lf.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, uf, vc);
+                               bool exact, T* uf, const T* vc, cudaStream_t s, const T* uin) {
+  if (exact) k_prolong_add<T, true><<<grid_of(Lf.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, uin ? uin : uf, uf, vc);
+  else k_prolong_add<T, false><<<grid_of(Lf.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, uin ? uin : uf, uf, vc);
   return cudaGetLastError();
 }
 
@@ -394,16 +911,17 @@ cudaError_t launch_coarsest(int64_t idx, T a, const T* f, T* u, cudaStream_t s) 
 
 template <typename T>
 int resnorm_blocks(const LevelPair<T>& L) {
-  const dim3 g = grid_of(L.h);
+  const dim3 g = norm_grid(L.h);
   return (int)(g.x * g.y);
 }
 
 template <typename T>
 cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const T* f,
                            double* partial, double* out, cudaStream_t s) {
-  const dim3 g = grid_of(L.h);
-  if (exact) k_resnorm_partial<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, partial);
-  else k_resnorm_partial<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, partial);
+  const dim3 g = norm_grid(L.h);
+  const int ty = (int)grid_of(L.h).y;
+  if (exact) k_resnorm_partial<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, partial, ty);
+  else k_resnorm_partial<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, partial, ty);
   k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
   return cudaGetLastError();
 }
@@ -411,8 +929,8 @@ cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const 
 template <typename T>
 cudaError_t launch_sumsq(const LevelPair<T>& L, const T* f, double* partial, double* out,
                          cudaStream_t s) {
-  const dim3 g = grid_of(L.h);
-  k_sumsq_partial<T><<<g, dim3(kBX, kBY), 0, s>>>(L.d, f, partial);
+  const dim3 g = norm_grid(L.h);
+  k_sumsq_partial<T><<<g, dim3(kBX, kBY), 0, s>>>(L.d, f, partial, (int)grid_of(L.h).y);
   k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
   return cudaGetLastError();
 }
@@ -426,9 +944,10 @@ cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s) {
 
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
                                float* r32, double scale, double* partial, double* out, cudaStream_t s) {
-  const dim3 g = grid_of(L.h);
-  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial);
-  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial);
+  const dim3 g = norm_grid(L.h);
+  const int ty = (int)grid_of(L.h).y;
+  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty);
+  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty);
   k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
   return cudaGetLastError();
 }
@@ -437,6 +956,56 @@ cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float*
                              cudaStream_t s) {
   k_ir_update<<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, u, e, inv_scale);
   return cudaGetLastError();
+}
+
+template <typename T, bool EXACT>
+cudaError_t launch_tail_impl(int ctas, const TailDesc<T>* desc, const int4* prog, int nops, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tail<T, EXACT>, desc, prog, nops);
+}
+
+// Largest cluster the device can co-schedule for the tail kernel: 16 CTAs
+// (non-portable size) when available, else 8, else 1.
+template <typename T, bool EXACT>
+int tail_ctas_impl() {
+  cudaFuncSetAttribute(k_tail<T, EXACT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  for (int c : {16, 8, 4, 2}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kTailThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_tail<T, EXACT>, &cfg) == cudaSuccess && clusters > 0) return c;
+    cudaGetLastError();
+  }
+  return 1;
+}
+
+template <typename T>
+int tail_ctas(bool exact) {
+  return exact ? tail_ctas_impl<T, true>() : tail_ctas_impl<T, false>();
+}
+
+template <typename T>
+cudaError_t launch_tail(int ctas, const TailDesc<T>* desc, const int4* prog, int nops, bool exact, cudaStream_t s) {
+  return exact ? launch_tail_impl<T, true>(ctas, desc, prog, nops, s)
+               : launch_tail_impl<T, false>(ctas, desc, prog, nops, s);
 }
 
 #define NSMG_INSTANTIATE(T)                                                                           \
@@ -450,13 +1019,16 @@ cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float*
   template cudaError_t launch_restrict<T>(const LevelPair<T>&, const LevelPair<T>&, int, bool,        \
                                           const T*, T*, cudaStream_t);                                \
   template cudaError_t launch_prolong_add<T>(const LevelPair<T>&, const LevelPair<T>&, int, bool, T*, \
-                                             const T*, cudaStream_t);                                 \
+                                             const T*, cudaStream_t, const T*);                       \
+  template cudaError_t launch_sweep_fused<T>(const LevelPair<T>&, bool, const T*, const T*, T*, cudaStream_t); \
   template cudaError_t launch_coarsest<T>(int64_t, T, const T*, T*, cudaStream_t);                    \
   template int resnorm_blocks<T>(const LevelPair<T>&);                                                \
   template cudaError_t launch_resnorm<T>(const LevelPair<T>&, bool, const T*, const T*, double*,     \
                                          double*, cudaStream_t);                                      \
   template cudaError_t launch_sumsq<T>(const LevelPair<T>&, const T*, double*, double*, cudaStream_t); \
-  template cudaError_t launch_zero_boundary<T>(const LevelPair<T>&, T*, cudaStream_t);
+  template cudaError_t launch_zero_boundary<T>(const LevelPair<T>&, T*, cudaStream_t);                \
+  template int tail_ctas<T>(bool);                                                                    \
+  template cudaError_t launch_tail<T>(int, const TailDesc<T>*, const int4*, int, bool, cudaStream_t);
 
 NSMG_INSTANTIATE(double)
 NSMG_INSTANTIATE(float)

@@ -27,9 +27,14 @@ cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const
 template <typename T>
 cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
                             const T* d, T* fc, cudaStream_t s);
+// uf = uin + P vc (uin = nullptr: in place, uf += P vc).
 template <typename T>
 cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer,
-                               bool exact, T* uf, const T* vc, cudaStream_t s);
+                               bool exact, T* uf, const T* vc, cudaStream_t s, const T* uin = nullptr);
+// One full red-black sweep uin -> uout in a single kernel (shared-memory tiles).
+template <typename T>
+cudaError_t launch_sweep_fused(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_coarsest(int64_t idx, T a, const T* f, T* u, cudaStream_t s);
 
@@ -57,5 +62,32 @@ cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const dou
 // u += e * inv_scale on interior nodes.
 cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
                              cudaStream_t s);
+
+// ---- small-level tail: one thread block runs a whole sub-cycle ---------------
+constexpr int kTailMaxLevels = 40;
+enum TailOp : int32_t { kOpZero = 0, kOpSmooth = 1, kOpResRestrict = 2, kOpCoarsest = 3, kOpProlong = 4 };
+
+// Levels and buffers the tail program refers to (device-resident).
+template <typename T>
+struct TailDesc {
+  const LevelDev<T>* L[kTailMaxLevels];
+  T* u[kTailMaxLevels];
+  T* t[kTailMaxLevels];
+  T* f[kTailMaxLevels];
+  T* d[kTailMaxLevels];
+  int32_t transfer[kTailMaxLevels];
+  int32_t smoother;  // mg_smoother
+  int64_t coarsest_idx;
+  T coarsest_a;
+};
+
+// Run `nops` ops (x = TailOp, y = level) in order inside one thread-block cluster of
+// `ctas` CTAs, with a cluster barrier after each phase. Op semantics match the
+// per-level kernels bit for bit.
+template <typename T>
+cudaError_t launch_tail(int ctas, const TailDesc<T>* desc, const int4* prog, int nops, bool exact, cudaStream_t s);
+// Largest tail cluster the current device can schedule (16, 8, 4, 2 or 1 CTAs).
+template <typename T>
+int tail_ctas(bool exact);
 
 }  // namespace nsmg

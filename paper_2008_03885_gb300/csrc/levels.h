@@ -38,6 +38,8 @@ struct LevelDev {
   T wd;                       // omega / a_pp at fast nodes
   T c[kMaxTerms];             // fast-node coefficients
   int32_t delta[2][kMaxTerms];  // storage offsets of the fast terms for i even / odd
+  int32_t sdx[2][kMaxTerms];    // storage-column shift of the fast terms for i even / odd
+  int32_t sdy[kMaxTerms];       // row shift of the fast terms
   const int2* cls;            // per class: (first term, term count)
   const T* cls_wd;            // per class: omega / a_pp
   const int32_t* tdx;         // merged terms

@@ -194,3 +194,69 @@ def test_zero_rhs_and_nonfinite_rhs_are_reported():
         assert e.value.status == mg.MG_ERR_NONFINITE
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("order,co,op", [(2, REDBLACK, GALERKIN), (4, REDBLACK, GALERKIN), (4, STANDARD, NONGALERKIN)])
+def test_fma_contract_mode_converges_to_the_oracle_solution(order, co, op):
+    """fma_contract = 1 changes rounding only: the per-cycle histories agree with the
+    oracle to 1e-12 relative while the residual is far above roundoff (first two
+    cycles), and the converged solution matches the oracle's within cond(L) * rtol."""
+    n = 128
+    F = synth.rhs_normal(n, seed=21)
+    nu1 = 2 if order == 4 else 1
+    o = Oracle(n, order, co, op, Options(nu1=nu1))
+    f = o.to_vec(F)
+    uo, ho = o.solve(f, rtol=1e-13, max_cycles=60)
+    ft = torch.tensor(F, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(ft)
+    h = mg.mg_setup(n, order, co, op, nu1=nu1, fma_contract=1)
+    try:
+        k, hg = mg.mg_solve(h, u, ft, rtol=1e-10, max_cycles=40)
+    finally:
+        h.close()
+    assert hg[-1] < 1e-10
+    rel = [abs(a - b) / b for a, b in zip(hg[:3], ho[:3])]
+    kappa = 8.0 * n * n / (2 * np.pi ** 2)
+    # FMA rounding differs by O(eps * cond) relative to ||f|| in each residual
+    assert max(rel[1:]) <= kappa * 1e-14 / min(ho[1:3])
+    ug = o.to_vec(u.cpu().numpy())
+    assert np.linalg.norm(ug - uo) / np.linalg.norm(uo) <= kappa * 1e-10
+
+
+@pytest.mark.parametrize("order,co,op", [(2, REDBLACK, GALERKIN), (4, REDBLACK, GALERKIN), (4, REDBLACK, TRUE_HIGH),
+                                         (4, STANDARD, NONGALERKIN), (2, STANDARD, G1)])
+@pytest.mark.parametrize("nu1,nu2", [(2, 1), (1, 1)])
+def test_tile_sweep_kernel_is_bitwise_identical(order, co, op, nu1, nu2):
+    """The shared-memory tile kernel (one launch per red-black sweep, out of place)
+    reproduces the oracle bit for bit, including odd sweep counts (parity flip)."""
+    n = 256
+    F = synth.rhs_normal(n, seed=31)
+    hg, ho, ug, uo = run_pair(n, order, co, op, F, 6, nu1=nu1, nu2=nu2, sweep_kernel=2)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)
+
+
+@pytest.mark.parametrize("order,co,op", [(4, REDBLACK, GALERKIN), (4, REDBLACK, TRUE_HIGH), (2, STANDARD, GN)])
+def test_tile_sweep_single_steps_bitwise(order, co, op):
+    n = 128
+    o = Oracle(n, order, co, op)
+    h = mg.mg_setup(n, order, co, op, sweep_kernel=2)
+    try:
+        for l, lev in enumerate(o.levels):
+            u = rng_vec(5000 + l, lev.size)
+            f = rng_vec(6000 + l, lev.size) * 100.0
+            du, df = to_dev(h, l, u), to_dev(h, l, f)
+            mg.mg_level_smooth(h, l, du, df, 3)
+            ref = o.smooth(l, o.smooth(l, o.smooth(l, u, f), f), f)
+            assert np.array_equal(from_dev(h, l, du), ref), l
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("tail", [-1, 64, 100000])
+def test_tail_cluster_threshold_does_not_change_bits(tail):
+    n = 128
+    F = synth.rhs_normal(n, seed=41)
+    hg, ho, ug, uo = run_pair(n, 4, REDBLACK, GALERKIN, F, 5, nu1=2, tail_unknowns=tail)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)
