@@ -184,6 +184,34 @@ mg_status mg_level_restrict(mg_handle* h, int level, const double* d_fine, doubl
 mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const double* v_coarse,
                                void* stream);
 
+/* ---- batched solves (many independent problems) -------------------------------
+   A batch advances many handles together by a level-synchronous schedule: each step
+   of the V-cycle (a half-sweep, residual, restriction, interpolation, ... of level l)
+   is ONE kernel launch covering level l of every problem that has it, with blocks
+   mapped to (problem, tile) pairs; problems that have converged are masked by device
+   flags, so the inner cycle is one CUDA graph for the whole batch. Per-problem
+   results are bitwise those of mg_solve on each handle alone (same operations per
+   node, same order). All handles must share precision, nu1, nu2, fma_contract and
+   (mixed precision) inner_cycles; gamma must be 1 and the smoother red-black
+   (MG_ERR_UNSUPPORTED otherwise). mg_batch_create also autotunes, per level, the rows
+   per thread of the step kernels by timing them (CUDA events), so create the batch
+   once and reuse it. The batch keeps pointers to the handles: destroy the batch
+   before them. */
+typedef struct mg_batch mg_batch;
+mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out);
+/* Solve problem p: u[p], f[p] device arrays of handle p's finest level. Per problem:
+   cycles (refinement steps for mixed precision) in cycles_out[p] and the final
+   relative residual in rel_res_out[p] (either may be NULL). Returns
+   MG_ERR_NOT_CONVERGED if any problem missed rtol within max_cycles. */
+mg_status mg_batch_solve(mg_batch* b, double* const* u, const double* const* f, double rtol, int max_cycles,
+                         int* cycles_out, double* rel_res_out, void* stream);
+mg_status mg_batch_destroy(mg_batch* b);
+/* Kernels launched through the batch so far (graph launches count their kernels). */
+mg_status mg_batch_get_launches(const mg_batch* b, int64_t* launches);
+/* Convenience: create a batch, solve once, destroy it. */
+mg_status mg_solve_batched(mg_handle* const* handles, double* const* u, const double* const* f, int count,
+                           double rtol, int max_cycles, int* cycles_out, double* rel_res_out, void* stream);
+
 /* ---- relative residual without device allocation ----------------------------
    The paper has no counterpart to this call; it serves callers that must not
    allocate device memory at the point where they need a residual norm: code that

@@ -277,3 +277,76 @@ def mg_rel_residual_static(h: Handle, u, f, rel_res_dev, stream=None):
     without any device allocation (partial sums in the library's fixed device array)."""
     _check(_lib.mg_rel_residual_static(h.ptr, _ptr(u), _ptr(f), _ptr(rel_res_dev), _stream(stream)),
            "mg_rel_residual_static")
+
+
+# ---- batched solves ---------------------------------------------------------
+_lib.mg_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.mg_batch_solve.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int,
+                                _ip, _dp, _vp]
+_lib.mg_batch_destroy.argtypes = [_vp]
+_lib.mg_batch_get_launches.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+_lib.mg_solve_batched.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_int, _ip, _dp, _vp]
+for _name in ("mg_batch_create", "mg_batch_solve", "mg_batch_destroy", "mg_batch_get_launches", "mg_solve_batched"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+class Batch:
+    """Owns an mg_batch over a list of Handles (which must outlive it)."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        arr = (_vp * len(self.handles))(*[h.ptr for h in self.handles])
+        out = _vp()
+        _check(_lib.mg_batch_create(arr, len(self.handles), ctypes.byref(out)), "mg_batch_create")
+        self.ptr = out.value
+
+    def close(self):
+        if self.ptr:
+            _lib.mg_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mg_batch_create(handles) -> Batch:
+    return Batch(handles)
+
+
+def mg_batch_solve(b: Batch, us, fs, rtol: float = 1e-8, max_cycles: int = 50, stream=None,
+                   raise_not_converged: bool = True):
+    """Returns (cycles list, final relative residual list)."""
+    n = len(b.handles)
+    ua = (_vp * n)(*[_ptr(x) for x in us])
+    fa = (_vp * n)(*[_ptr(x) for x in fs])
+    cyc = (ctypes.c_int * n)()
+    rr = (ctypes.c_double * n)()
+    st = _lib.mg_batch_solve(b.ptr, ua, fa, rtol, max_cycles, cyc, rr, _stream(stream))
+    if st != MG_OK and not (st == MG_ERR_NOT_CONVERGED and not raise_not_converged):
+        raise MGError(st, "mg_batch_solve")
+    return list(cyc), list(rr)
+
+
+def mg_batch_destroy(b: Batch):
+    b.close()
+
+
+def mg_batch_get_launches(b: Batch) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.mg_batch_get_launches(b.ptr, ctypes.byref(v)), "mg_batch_get_launches")
+    return v.value
+
+
+def mg_solve_batched(handles, us, fs, rtol: float = 1e-8, max_cycles: int = 50, stream=None):
+    n = len(handles)
+    ha = (_vp * n)(*[h.ptr for h in handles])
+    ua = (_vp * n)(*[_ptr(x) for x in us])
+    fa = (_vp * n)(*[_ptr(x) for x in fs])
+    cyc = (ctypes.c_int * n)()
+    rr = (ctypes.c_double * n)()
+    _check(_lib.mg_solve_batched(ha, ua, fa, n, rtol, max_cycles, cyc, rr, _stream(stream)), "mg_solve_batched")
+    return list(cyc), list(rr)

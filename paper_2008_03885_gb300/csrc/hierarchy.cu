@@ -963,17 +963,20 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
     h->ir_scale = ir_scale_for(fn2, h->host[0].unknowns);
     double r2;
     for (;;) {
+      // FP64 residual at the scale predicted from the previous norm (the FP32 copy
+      // stays in range as long as the residual moves by far less than 2^60 per step)
       if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;
       rr = std::sqrt(r2) / std::sqrt(fn2);
       if (!std::isfinite(rr)) return MG_ERR_NONFINITE;
-      const double want = ir_scale_for(r2, h->host[0].unknowns);
-      if (want > 1024.0 * h->ir_scale || want < h->ir_scale / 1024.0) {
-        h->ir_scale = want;  // FP32 copy badly scaled: redo it at the right scale
-        if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;
-      }
       if (history_out) history_out[k] = rr;
       if (k >= max_cycles || rr < rtol) break;
+      const double want = ir_scale_for(r2, h->host[0].unknowns);
+      if (want > 0x1p60 * h->ir_scale || want < 0x1p-60 * h->ir_scale) {
+        h->ir_scale = want;  // redo the FP32 copy at a safe scale
+        if ((st = ir_residual(c, u, f, &r2)) != MG_OK) return st;
+      }
       if ((st = ir_correct(c, u)) != MG_OK) return st;
+      h->ir_scale = want;
       ++k;
       ++h->cycles;
     }
@@ -1078,3 +1081,477 @@ const LevelPair<double>* finest_level_fp64(const mg_handle* h, bool* exact) {
   return &h->h64.L[0];
 }
 }  // namespace nsmg
+
+// ===================================================================================
+// Batched solves: many independent problems (each an mg_handle) advanced by a
+// level-synchronous schedule. Every step of the V-cycle is one kernel launch covering
+// that level of all problems that have it; problems converge independently (device
+// active flags), so the whole inner cycle is captured once as a CUDA graph.
+// ===================================================================================
+namespace {
+
+template <typename T>
+struct BatchList {
+  BatchLevel<T>* d_entries = nullptr;   // problems with level l + 1 (level l not the coarsest)
+  int* d_prefix = nullptr;              // tiles over level l
+  int* d_cprefix = nullptr;             // tiles over level l + 1 (restriction)
+  int ne = 0, tiles = 0, ctiles = 0, rpt = 1;
+  BatchLevel<T>* d_coarsest = nullptr;  // problems whose level l + 1 is the coarsest
+  int nc = 0;
+  std::vector<BatchLevel<T>> host;
+};
+
+}  // namespace
+
+struct mg_batch {
+  std::vector<mg_handle*> hs;
+  int count = 0, nl = 0;  // problems, most levels of any problem
+  bool mixed = false, exact = true;
+  int nu1 = 1, nu2 = 1, inner = 2;
+  std::vector<BatchList<double>> lv64;
+  std::vector<BatchList<float>> lv32;
+  std::vector<BatchLevel<double>> fin;  // finest FP64 levels (norms, refinement)
+  BatchLevel<double>* d_fin = nullptr;
+  int* d_fin_prefix = nullptr;
+  int fin_tiles = 0;
+  std::vector<BatchLevel<double>> lv64_0;  // level-0 FP64 entries (u, f set per solve)
+  int* d_active = nullptr;
+  int* h_active = nullptr;
+  double* d_scale = nullptr;
+  double* h_scale = nullptr;
+  double* d_partial = nullptr;
+  double* d_norm2 = nullptr;
+  double* h_norm2 = nullptr;
+  cudaStream_t priv = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph = nullptr;  // mixed: inner cycles; FP64: one cycle
+  int64_t graph_kernels = 0;
+  int64_t launches = 0;
+  std::vector<void*> allocs, host_allocs;
+  std::vector<int> rpt_choice;  // autotuned rows per thread per level
+};
+
+namespace {
+
+void batch_free(mg_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->priv) cudaStreamDestroy(b->priv);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (void* p : b->allocs) cudaFree(p);
+  for (void* p : b->host_allocs) cudaFreeHost(p);
+  b->allocs.clear();
+  b->host_allocs.clear();
+}
+
+mg_status batch_alloc(mg_batch* b, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+  }
+  b->allocs.push_back(*p);
+  return MG_OK;
+}
+
+template <typename T>
+mg_status upload_vec(mg_batch* b, const std::vector<T>& v, T** d) {
+  mg_status st = batch_alloc(b, (void**)d, std::max<size_t>(v.size(), 1) * sizeof(T));
+  if (st != MG_OK) return st;
+  if (!v.empty()) CK(cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+// Prefix sums of tiles for the entries of a list (level l or level l + 1 storage).
+template <typename T>
+std::vector<int> tile_prefix(const mg_batch* b, const std::vector<BatchLevel<T>>& es, int l, bool coarse, int rpt) {
+  std::vector<int> p(1, 0);
+  for (const auto& e : es) {
+    const HostLevel& L = b->hs[e.problem]->host[coarse ? l + 1 : l];
+    p.push_back(p.back() + batch_tiles(L.cols, L.rows, rpt));
+  }
+  return p;
+}
+
+// Level lists of one precision: entries for every level l that is not the coarsest
+// of some problem, and the per-level coarsest lists.
+template <typename T>
+mg_status build_lists(mg_batch* b, std::vector<BatchList<T>>& lv) {
+  lv.assign(b->nl, BatchList<T>());
+  for (int l = 0; l + 1 < b->nl; ++l) {
+    BatchList<T>& B = lv[l];
+    std::vector<BatchLevel<T>> coarsest;
+    for (int p = 0; p < b->count; ++p) {
+      mg_handle* h = b->hs[p];
+      Hier<T>& H = hier<T>(h);
+      const int nlp = (int)h->host.size();
+      if (l + 1 >= nlp) continue;
+      BatchLevel<T> e;
+      std::memset(&e, 0, sizeof(e));
+      const HostLevel& L = h->host[l];
+      e.L = H.L[l].d;
+      e.Lc = H.L[l + 1].d;
+      e.u = H.u[l];
+      e.t = H.t[l];
+      e.f = H.f[l];
+      e.d = H.d[l];
+      e.uc = H.u[l + 1];
+      e.fc = H.f[l + 1];
+      e.transfer = h->transfer[l];
+      e.problem = p;
+      e.cols = L.cols;
+      e.rows = L.rows;
+      e.n = L.shape.n;
+      e.kind = L.shape.kind;
+      e.tiles_x = (L.cols + kBatchCols - 1) / kBatchCols;
+      e.ctiles_x = (h->host[l + 1].cols + kBatchCols - 1) / kBatchCols;
+      e.coarsest_idx = H.coarsest_idx;
+      e.coarsest_a = H.coarsest_a;
+      B.host.push_back(e);
+      if (l + 2 == nlp) coarsest.push_back(e);
+    }
+    B.ne = (int)B.host.size();
+    B.nc = (int)coarsest.size();
+    mg_status st;
+    if ((st = upload_vec(b, B.host, &B.d_entries)) != MG_OK) return st;
+    if ((st = upload_vec(b, coarsest, &B.d_coarsest)) != MG_OK) return st;
+  }
+  return MG_OK;
+}
+
+template <typename T>
+mg_status set_rpt(mg_batch* b, BatchList<T>& B, int l, int rpt) {
+  const auto pf = tile_prefix(b, B.host, l, false, rpt);
+  const auto pc = tile_prefix(b, B.host, l, true, rpt);
+  mg_status st;
+  if ((st = upload_vec(b, pf, &B.d_prefix)) != MG_OK) return st;
+  if ((st = upload_vec(b, pc, &B.d_cprefix)) != MG_OK) return st;
+  B.tiles = pf.back();
+  B.ctiles = pc.back();
+  B.rpt = rpt;
+  return MG_OK;
+}
+
+// Autotuner: per level, rows per thread (1, 2 or 4) of the step kernels, chosen by
+// timing the red half-sweep of the whole list with CUDA events.
+template <typename T>
+mg_status autotune(mg_batch* b, std::vector<BatchList<T>>& lv) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  b->rpt_choice.assign(b->nl, 1);
+  for (int l = 0; l + 1 < b->nl; ++l) {
+    BatchList<T>& B = lv[l];
+    if (B.ne == 0) continue;
+    int best = 1;
+    float best_ms = 1e30f;
+    for (int rpt : {1, 2, 4}) {
+      mg_status st = set_rpt(b, B, l, rpt);
+      if (st != MG_OK) return st;
+      for (int rep = 0; rep < 4; ++rep) {
+        if (rep == 1) CK(cudaEventRecord(e0, b->priv));
+        CK(launch_batch_step<T>(kBHalfRed, B.d_entries, B.d_prefix, B.ne, B.tiles, rpt, b->d_active, b->exact,
+                                b->priv));
+      }
+      CK(cudaEventRecord(e1, b->priv));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = rpt;
+      }
+    }
+    mg_status st = set_rpt(b, B, l, best);
+    if (st != MG_OK) return st;
+    b->rpt_choice[l] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return MG_OK;
+}
+
+#define BLAUNCH(b, expr)                            \
+  do {                                              \
+    ++(b)->launches;                                \
+    if ((expr) != cudaSuccess) return MG_ERR_CUDA; \
+  } while (0)
+
+// One V-cycle of every active problem (level-synchronous), zero initial guess on the
+// finest level when `zero0`.
+template <typename T>
+mg_status batch_cycle(mg_batch* b, std::vector<BatchList<T>>& lv, bool zero0, cudaStream_t s) {
+  const int* act = b->d_active;
+  for (int l = 0; l + 1 < b->nl; ++l) {
+    BatchList<T>& B = lv[l];
+    if (B.ne == 0) continue;
+    if (l > 0 || zero0) BLAUNCH(b, launch_batch_step<T>(kBZero, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+    for (int k = 0; k < b->nu1; ++k) {
+      BLAUNCH(b, launch_batch_step<T>(kBHalfRed, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+      BLAUNCH(b, launch_batch_step<T>(kBHalfBlack, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+    }
+    BLAUNCH(b, launch_batch_step<T>(kBResidual, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+    BLAUNCH(b, launch_batch_step<T>(kBRestrict, B.d_entries, B.d_cprefix, B.ne, B.ctiles, B.rpt, act, b->exact, s));
+    if (B.nc > 0) BLAUNCH(b, launch_batch_step<T>(kBCoarsest, B.d_coarsest, nullptr, B.nc, 0, 1, act, b->exact, s));
+  }
+  for (int l = b->nl - 2; l >= 0; --l) {
+    BatchList<T>& B = lv[l];
+    if (B.ne == 0) continue;
+    BLAUNCH(b, launch_batch_step<T>(kBProlong, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+    for (int k = 0; k < b->nu2; ++k) {
+      BLAUNCH(b, launch_batch_step<T>(kBHalfRed, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+      BLAUNCH(b, launch_batch_step<T>(kBHalfBlack, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+    }
+  }
+  return MG_OK;
+}
+
+// The inner cycles (mixed) or one cycle (FP64) as a CUDA graph on b->priv.
+mg_status batch_graph(mg_batch* b) {
+  if (b->graph) return MG_OK;
+  const int64_t before = b->launches;
+  CK(cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal));
+  mg_status st = MG_OK;
+  if (b->mixed) {
+    for (int k = 0; k < b->inner && st == MG_OK; ++k) st = batch_cycle<float>(b, b->lv32, k == 0, b->priv);
+  } else {
+    st = batch_cycle<double>(b, b->lv64, false, b->priv);
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->priv, &g);
+  if (st != MG_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return st != MG_OK ? st : MG_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return MG_ERR_CUDA;
+  b->graph_kernels = b->launches - before;
+  b->launches = before;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) {
+  if (!handles || count <= 0 || !out) return MG_ERR_INVALID;
+  *out = nullptr;
+  const mg_options& o0 = handles[0] ? handles[0]->opt : mg_options{};
+  for (int p = 0; p < count; ++p) {
+    const mg_handle* h = handles[p];
+    if (!h) return MG_ERR_INVALID;
+    const mg_options& o = h->opt;
+    if (o.precision != o0.precision || o.nu1 != o0.nu1 || o.nu2 != o0.nu2 || o.fma_contract != o0.fma_contract ||
+        (o.precision == MG_PREC_MIXED_FP32 && o.inner_cycles != o0.inner_cycles))
+      return MG_ERR_INVALID;  // one schedule for the whole batch
+    if (o.gamma != 1 || o.smoother != MG_SMOOTH_REDBLACK) return MG_ERR_UNSUPPORTED;
+    if ((int)h->host.size() > kTailMaxLevels) return MG_ERR_UNSUPPORTED;
+  }
+  mg_batch* b = new (std::nothrow) mg_batch();
+  if (!b) return MG_ERR_OOM;
+  auto fail = [&](mg_status s) { batch_free(b); delete b; return s; };
+  b->hs.assign(handles, handles + count);
+  b->count = count;
+  b->mixed = o0.precision == MG_PREC_MIXED_FP32;
+  b->exact = o0.fma_contract == 0;
+  b->nu1 = o0.nu1;
+  b->nu2 = o0.nu2;
+  b->inner = o0.inner_cycles;
+  for (auto* h : b->hs) b->nl = std::max(b->nl, (int)h->host.size());
+  if (cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return fail(MG_ERR_CUDA);
+  mg_status st;
+  if ((st = batch_alloc(b, (void**)&b->d_active, count * sizeof(int))) != MG_OK) return fail(st);
+  if ((st = batch_alloc(b, (void**)&b->d_scale, count * sizeof(double))) != MG_OK) return fail(st);
+  if ((st = batch_alloc(b, (void**)&b->d_norm2, count * sizeof(double))) != MG_OK) return fail(st);
+  if (cudaMallocHost((void**)&b->h_active, count * sizeof(int)) != cudaSuccess) return fail(MG_ERR_CUDA);
+  b->host_allocs.push_back(b->h_active);
+  if (cudaMallocHost((void**)&b->h_scale, count * sizeof(double)) != cudaSuccess) return fail(MG_ERR_CUDA);
+  b->host_allocs.push_back(b->h_scale);
+  if (cudaMallocHost((void**)&b->h_norm2, count * sizeof(double)) != cudaSuccess) return fail(MG_ERR_CUDA);
+  b->host_allocs.push_back(b->h_norm2);
+  for (int p = 0; p < count; ++p) b->h_active[p] = 1;
+  if (cudaMemcpy(b->d_active, b->h_active, count * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MG_ERR_CUDA);
+  // finest FP64 levels (norms, refinement); u / f filled in per solve
+  for (int p = 0; p < count; ++p) {
+    mg_handle* h = b->hs[p];
+    BatchLevel<double> e;
+    std::memset(&e, 0, sizeof(e));
+    const HostLevel& L = h->host[0];
+    e.L = h->h64.L[0].d;
+    e.problem = p;
+    e.cols = L.cols;
+    e.rows = L.rows;
+    e.n = L.shape.n;
+    e.kind = L.shape.kind;
+    e.tiles_x = (L.cols + kBatchCols - 1) / kBatchCols;
+    if (b->mixed) {
+      e.r32 = h->h32.f[0];
+      e.e32 = h->h32.u[0];
+    }
+    b->fin.push_back(e);
+  }
+  {
+    std::vector<int> pf(1, 0);
+    for (int p = 0; p < count; ++p) pf.push_back(pf.back() + batch_tiles(b->hs[p]->host[0].cols, b->hs[p]->host[0].rows, 1));
+    b->fin_tiles = pf.back();
+    if ((st = upload_vec(b, b->fin, &b->d_fin)) != MG_OK) return fail(st);
+    if ((st = upload_vec(b, pf, &b->d_fin_prefix)) != MG_OK) return fail(st);
+    if ((st = batch_alloc(b, (void**)&b->d_partial, std::max(b->fin_tiles, 1) * sizeof(double))) != MG_OK)
+      return fail(st);
+  }
+  if (b->mixed) {
+    if ((st = build_lists<float>(b, b->lv32)) != MG_OK) return fail(st);
+    if ((st = autotune<float>(b, b->lv32)) != MG_OK) return fail(st);
+  } else {
+    if ((st = build_lists<double>(b, b->lv64)) != MG_OK) return fail(st);
+    // level 0 runs on the caller's arrays; tune it on the handle's scratch arrays
+    auto& B0 = b->lv64[0];
+    b->lv64_0 = B0.host;
+    for (auto& e : B0.host) {
+      e.u = b->hs[e.problem]->h64.t[0];
+      e.f = b->hs[e.problem]->h64.d[0];
+    }
+    if (cudaMemcpy(B0.d_entries, B0.host.data(), B0.host.size() * sizeof(BatchLevel<double>), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return fail(MG_ERR_CUDA);
+    if ((st = autotune<double>(b, b->lv64)) != MG_OK) return fail(st);
+    B0.host = b->lv64_0;
+  }
+  if (cudaStreamSynchronize(b->priv) != cudaSuccess) return fail(MG_ERR_CUDA);
+  *out = b;
+  return MG_OK;
+}
+
+mg_status mg_batch_destroy(mg_batch* b) {
+  if (!b) return MG_OK;
+  cudaStreamSynchronize(b->priv);
+  batch_free(b);
+  delete b;
+  return MG_OK;
+}
+
+mg_status mg_batch_solve(mg_batch* b, double* const* u, const double* const* f, double rtol, int max_cycles,
+                         int* cycles_out, double* rel_res_out, void* stream) {
+  if (!b || !u || !f || max_cycles < 0 || !(rtol >= 0.0)) return MG_ERR_INVALID;
+  for (int p = 0; p < b->count; ++p)
+    if (!u[p] || !f[p]) return MG_ERR_INVALID;
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t s = b->priv;
+  CK(cudaEventRecord(b->ev_in, user));
+  CK(cudaStreamWaitEvent(s, b->ev_in, 0));
+  struct Leave {
+    mg_batch* b;
+    cudaStream_t user;
+    ~Leave() {
+      cudaEventRecord(b->ev_out, b->priv);
+      cudaStreamWaitEvent(user, b->ev_out, 0);
+    }
+  } leave{b, user};
+  const int n = b->count;
+  // caller arrays into the finest-level tables
+  for (int p = 0; p < n; ++p) {
+    b->fin[p].u = u[p];
+    b->fin[p].f = const_cast<double*>(f[p]);
+    ++b->launches;
+    CK(launch_zero_boundary<double>(b->hs[p]->h64.L[0], u[p], s));
+  }
+  CK(cudaMemcpyAsync(b->d_fin, b->fin.data(), n * sizeof(BatchLevel<double>), cudaMemcpyHostToDevice, s));
+  if (!b->mixed) {
+    auto& B0 = b->lv64[0];
+    for (auto& e : B0.host) {
+      e.u = u[e.problem];
+      e.f = const_cast<double*>(f[e.problem]);
+    }
+    CK(cudaMemcpyAsync(B0.d_entries, B0.host.data(), B0.host.size() * sizeof(BatchLevel<double>),
+                       cudaMemcpyHostToDevice, s));
+  }
+  for (int p = 0; p < n; ++p) {
+    b->h_active[p] = 1;
+    b->h_scale[p] = 1.0;
+  }
+  CK(cudaMemcpyAsync(b->d_active, b->h_active, n * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(b->d_scale, b->h_scale, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  // ||f||^2 per problem
+  b->launches += 2;
+  CK(launch_batch_norms(1, b->d_fin, b->d_fin_prefix, n, b->fin_tiles, b->d_active, b->d_scale, b->exact,
+                        b->d_partial, b->d_norm2, s));
+  CK(cudaMemcpyAsync(b->h_norm2, b->d_norm2, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> fn2(b->h_norm2, b->h_norm2 + n), rr(n, 0.0);
+  std::vector<int> cyc(n, 0);
+  for (int p = 0; p < n; ++p) {
+    if (!std::isfinite(fn2[p])) return MG_ERR_NONFINITE;
+    if (fn2[p] == 0.0) return MG_ERR_INVALID;
+    b->h_scale[p] = b->mixed ? ir_scale_for(fn2[p], b->hs[p]->host[0].unknowns) : 1.0;
+  }
+  mg_status st = batch_graph(b);
+  if (st != MG_OK) return st;
+  CK(cudaMemcpyAsync(b->d_scale, b->h_scale, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  int active = n;
+  bool nonfinite = false;
+  for (;;) {
+    // residual norms (and, mixed, the scaled FP32 residual) of the active problems
+    b->launches += 2;
+    CK(launch_batch_norms(b->mixed ? 0 : 2, b->d_fin, b->d_fin_prefix, n, b->fin_tiles, b->d_active, b->d_scale,
+                          b->exact, b->d_partial, b->d_norm2, s));
+    CK(cudaMemcpyAsync(b->h_norm2, b->d_norm2, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<double> next_scale(b->h_scale, b->h_scale + n);
+    for (int p = 0; p < n; ++p) {
+      if (!b->h_active[p]) continue;
+      rr[p] = std::sqrt(b->h_norm2[p]) / std::sqrt(fn2[p]);
+      if (!std::isfinite(rr[p])) nonfinite = true;
+      if (!std::isfinite(rr[p]) || rr[p] < rtol || cyc[p] >= max_cycles) {
+        b->h_active[p] = 0;
+        --active;
+      } else if (b->mixed) {
+        next_scale[p] = ir_scale_for(b->h_norm2[p], b->hs[p]->host[0].unknowns);
+      }
+    }
+    if (active == 0) break;
+    CK(cudaMemcpyAsync(b->d_active, b->h_active, n * sizeof(int), cudaMemcpyHostToDevice, s));
+    b->launches += b->graph_kernels;
+    CK(cudaGraphLaunch(b->graph, s));
+    if (b->mixed) {
+      ++b->launches;
+      CK(launch_batch_ir_update(b->d_fin, b->d_fin_prefix, n, b->fin_tiles, b->d_active, b->d_scale, s));
+      std::copy(next_scale.begin(), next_scale.end(), b->h_scale);
+      CK(cudaMemcpyAsync(b->d_scale, b->h_scale, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    for (int p = 0; p < n; ++p)
+      if (b->h_active[p]) ++cyc[p];
+  }
+  bool all = true;
+  for (int p = 0; p < n; ++p) {
+    if (cycles_out) cycles_out[p] = cyc[p];
+    if (rel_res_out) rel_res_out[p] = rr[p];
+    all = all && rr[p] < rtol;
+  }
+  if (nonfinite) return MG_ERR_NONFINITE;
+  return all ? MG_OK : MG_ERR_NOT_CONVERGED;
+}
+
+mg_status mg_batch_get_launches(const mg_batch* b, int64_t* launches) {
+  if (!b || !launches) return MG_ERR_INVALID;
+  *launches = b->launches;
+  return MG_OK;
+}
+
+mg_status mg_solve_batched(mg_handle* const* handles, double* const* u, const double* const* f, int count,
+                           double rtol, int max_cycles, int* cycles_out, double* rel_res_out, void* stream) {
+  mg_batch* b = nullptr;
+  mg_status st = mg_batch_create(handles, count, &b);
+  if (st != MG_OK) return st;
+  st = mg_batch_solve(b, u, f, rtol, max_cycles, cycles_out, rel_res_out, stream);
+  mg_batch_destroy(b);
+  return st;
+}
+
+}  // extern "C"

@@ -786,6 +786,147 @@ __global__ void __launch_bounds__(kTailThreads)
   }
 }
 
+// ---- batched level-synchronous step kernels ------------------------------------
+__device__ __forceinline__ int batch_entry(const int* __restrict__ prefix, int ne, int b) {
+  int lo = 0, hi = ne - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, bool EXACT, int RPT>
+__global__ void __launch_bounds__(kBX * kBY)
+    k_batch_step(int op, const BatchLevel<T>* __restrict__ E, const int* __restrict__ prefix, int ne,
+                 const int* __restrict__ active) {
+  const int b = blockIdx.x;
+  const int e = batch_entry(prefix, ne, b);
+  const BatchLevel<T>& B = E[e];
+  if (!active[B.problem]) return;
+  const int tile = b - prefix[e];
+  const bool coarse = op == kBRestrict;
+  const LevelDev<T>& L = coarse ? *B.Lc : *B.L;  // level whose storage is tiled
+  const int tx = coarse ? B.ctiles_x : B.tiles_x;
+  const int bx = tile % tx, by = tile / tx;
+  const int qb = bx * kBatchCols + 2 * threadIdx.x;
+  const int jb = by * kBY * RPT + threadIdx.y;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int j = jb + r * kBY;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int q = qb + c;
+      if (j >= L.rows || q >= L.cols) continue;
+      const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+      if (!interior(L, i, j)) continue;
+      const int64_t at = (int64_t)j * L.pitch + q;
+      switch (op) {
+        case kBZero:
+          B.u[at] = T(0);
+          break;
+        case kBHalfRed:
+          B.t[at] = is_red(L, i, j) ? relax_value<T, EXACT>(L, B.u, B.f, i, j, at) : B.u[at];
+          break;
+        case kBHalfBlack:
+          B.u[at] = is_red(L, i, j) ? B.t[at] : relax_value<T, EXACT>(L, B.t, B.f, i, j, at);
+          break;
+        case kBResidual:
+          B.d[at] = Arith<T>::sub(B.f[at], apply_at<T, EXACT>(L, B.u, i, j, at, nullptr));
+          break;
+        case kBRestrict:
+          B.fc[at] = restrict_value<T, EXACT>(*B.L, B.transfer, B.d, i, j);
+          break;
+        default:  // kBProlong
+          B.u[at] = Arith<T>::add(B.u[at], prolong_value<T, EXACT>(*B.Lc, B.transfer, B.uc, i, j));
+          break;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_batch_coarsest(const BatchLevel<T>* __restrict__ E, int ne, const int* __restrict__ active) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const BatchLevel<T>& B = E[e];
+  if (!active[B.problem]) return;
+  B.uc[B.coarsest_idx] = Arith<T>::div(B.fc[B.coarsest_idx], B.coarsest_a);
+}
+
+template <bool EXACT>
+__global__ void __launch_bounds__(kBX * kBY)
+    k_batch_norm_partial(int mode, const BatchLevel<double>* __restrict__ E, const int* __restrict__ prefix, int ne,
+                         const int* __restrict__ active, const double* __restrict__ scale,
+                         double* __restrict__ partial) {
+  const int b = blockIdx.x;
+  const int e = batch_entry(prefix, ne, b);
+  const BatchLevel<double>& B = E[e];
+  double v = 0.0;
+  if (active[B.problem]) {
+    const LevelDev<double>& L = *B.L;
+    const int tile = b - prefix[e];
+    const int bx = tile % B.tiles_x, by = tile / B.tiles_x;
+    const int qb = bx * kBatchCols + 2 * threadIdx.x;
+    const int j = by * kBY + threadIdx.y;
+    const double sc = scale[B.problem];
+    for (int c = 0; c < 2; ++c) {
+      const int q = qb + c;
+      if (j >= L.rows || q >= L.cols) continue;
+      const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+      if (!interior(L, i, j)) continue;
+      const int64_t at = (int64_t)j * L.pitch + q;
+      if (mode != 1) {
+        const double r = Arith<double>::sub(B.f[at], apply_at<double, EXACT>(L, B.u, i, j, at, nullptr));
+        if (mode == 0) B.r32[at] = (float)(r * sc);
+        v += r * r;
+      } else {
+        v += B.f[at] * B.f[at];
+      }
+    }
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[b] = v;
+}
+
+// One block per entry: add its partials in order.
+__global__ void k_batch_norm_sum(const BatchLevel<double>* __restrict__ E, const int* __restrict__ prefix,
+                                 const int* __restrict__ active, const double* __restrict__ partial,
+                                 double* __restrict__ norm2) {
+  const int e = blockIdx.x;
+  const BatchLevel<double>& B = E[e];
+  if (!active[B.problem]) return;
+  double v = 0.0;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int k = prefix[e] + tid; k < prefix[e + 1]; k += blockDim.x * blockDim.y) v += partial[k];
+  v = block_sum(v);
+  if (tid == 0) norm2[B.problem] = v;
+}
+
+__global__ void __launch_bounds__(kBX * kBY)
+    k_batch_ir_update(const BatchLevel<double>* __restrict__ E, const int* __restrict__ prefix, int ne,
+                      const int* __restrict__ active, const double* __restrict__ scale) {
+  const int b = blockIdx.x;
+  const int e = batch_entry(prefix, ne, b);
+  const BatchLevel<double>& B = E[e];
+  if (!active[B.problem]) return;
+  const LevelDev<double>& L = *B.L;
+  const int tile = b - prefix[e];
+  const int bx = tile % B.tiles_x, by = tile / B.tiles_x;
+  const int qb = bx * kBatchCols + 2 * threadIdx.x;
+  const int j = by * kBY + threadIdx.y;
+  const double inv = 1.0 / scale[B.problem];
+  for (int c = 0; c < 2; ++c) {
+    const int q = qb + c;
+    if (j >= L.rows || q >= L.cols) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
+    const int64_t at = (int64_t)j * L.pitch + q;
+    B.u[at] = B.u[at] + (double)B.e32[at] * inv;
+  }
+}
+
 template <typename T>
 dim3 grid_of(const LevelDev<T>& L) {
   return dim3((L.cols + kBX - 1) / kBX, (L.rows + kBY - 1) / kBY);
@@ -1008,6 +1149,46 @@ cudaError_t launch_tail(int ctas, const TailDesc<T>* desc, const int4* prog, int
                : launch_tail_impl<T, false>(ctas, desc, prog, nops, s);
 }
 
+template <typename T>
+cudaError_t launch_batch_step(int op, const BatchLevel<T>* entries, const int* prefix, int ne, int total_tiles,
+                              int rpt, const int* active, bool exact, cudaStream_t s) {
+  if (ne <= 0) return cudaSuccess;
+  if (op == kBCoarsest) {
+    k_batch_coarsest<T><<<(ne + 127) / 128, 128, 0, s>>>(entries, ne, active);
+    return cudaGetLastError();
+  }
+  if (total_tiles <= 0) return cudaSuccess;
+  const dim3 blk(kBX, kBY);
+#define NSMG_BSTEP(R)                                                                                   \
+  if (rpt == R) {                                                                                       \
+    if (exact) k_batch_step<T, true, R><<<total_tiles, blk, 0, s>>>(op, entries, prefix, ne, active);  \
+    else k_batch_step<T, false, R><<<total_tiles, blk, 0, s>>>(op, entries, prefix, ne, active);       \
+    return cudaGetLastError();                                                                          \
+  }
+  NSMG_BSTEP(1)
+  NSMG_BSTEP(2)
+  NSMG_BSTEP(4)
+#undef NSMG_BSTEP
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_norms(int mode, const BatchLevel<double>* entries, const int* prefix, int ne,
+                               int total_tiles, const int* active, const double* scale, bool exact,
+                               double* partial, double* norm2, cudaStream_t s) {
+  if (ne <= 0 || total_tiles <= 0) return cudaSuccess;
+  if (exact) k_batch_norm_partial<true><<<total_tiles, dim3(kBX, kBY), 0, s>>>(mode, entries, prefix, ne, active, scale, partial);
+  else k_batch_norm_partial<false><<<total_tiles, dim3(kBX, kBY), 0, s>>>(mode, entries, prefix, ne, active, scale, partial);
+  k_batch_norm_sum<<<ne, dim3(kBX, kBY), 0, s>>>(entries, prefix, active, partial, norm2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_ir_update(const BatchLevel<double>* entries, const int* prefix, int ne, int total_tiles,
+                                   const int* active, const double* scale, cudaStream_t s) {
+  if (ne <= 0 || total_tiles <= 0) return cudaSuccess;
+  k_batch_ir_update<<<total_tiles, dim3(kBX, kBY), 0, s>>>(entries, prefix, ne, active, scale);
+  return cudaGetLastError();
+}
+
 #define NSMG_INSTANTIATE(T)                                                                           \
   template cudaError_t launch_half_sweep<T>(const LevelPair<T>&, bool, const T*, const T*, T*, int,   \
                                             cudaStream_t);                                            \
@@ -1027,6 +1208,8 @@ cudaError_t launch_tail(int ctas, const TailDesc<T>* desc, const int4* prog, int
                                          double*, cudaStream_t);                                      \
   template cudaError_t launch_sumsq<T>(const LevelPair<T>&, const T*, double*, double*, cudaStream_t); \
   template cudaError_t launch_zero_boundary<T>(const LevelPair<T>&, T*, cudaStream_t);                \
+  template cudaError_t launch_batch_step<T>(int, const BatchLevel<T>*, const int*, int, int, int, const int*, bool, \
+                                            cudaStream_t);                                             \
   template int tail_ctas<T>(bool);                                                                    \
   template cudaError_t launch_tail<T>(int, const TailDesc<T>*, const int4*, int, bool, cudaStream_t);
 

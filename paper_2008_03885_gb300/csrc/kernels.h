@@ -90,4 +90,55 @@ cudaError_t launch_tail(int ctas, const TailDesc<T>* desc, const int4* prog, int
 template <typename T>
 int tail_ctas(bool exact);
 
+// ---- batched level-synchronous schedule ----------------------------------------
+// One problem's level l as seen by a batched step kernel.
+template <typename T>
+struct BatchLevel {
+  const LevelDev<T>* L;   // level l
+  const LevelDev<T>* Lc;  // level l + 1 (null at the coarsest)
+  T* u;                   // level-l arrays (level 0: refinement correction / caller's u)
+  T* t;
+  T* f;
+  T* d;
+  T* uc;                  // level l + 1 arrays
+  T* fc;
+  int32_t transfer;
+  int32_t problem;        // index into the batch's per-problem arrays
+  int32_t cols, rows, n, kind;
+  int32_t tiles_x, ctiles_x;  // tiles per row of tiles on level l / level l + 1
+  int64_t coarsest_idx;   // of level l + 1 when it is the problem's coarsest level
+  T coarsest_a;
+  float* r32;             // finest level, mixed precision: FP32 residual (inner right-hand side)
+  float* e32;             //   and FP32 correction
+};
+
+enum BatchOp : int32_t {
+  kBZero = 0, kBHalfRed = 1, kBHalfBlack = 2, kBResidual = 3, kBRestrict = 4, kBProlong = 5, kBCoarsest = 6
+};
+
+// A tile is 64 storage columns (2 per thread, so a thread holds one red and one black
+// node of an axis row) by 8 x rpt rows; a block of 32 x 8 threads handles one tile of
+// one problem. Block b belongs to the entry e with prefix[e] <= b < prefix[e + 1].
+constexpr int kBatchCols = 64;
+inline int batch_tiles(int cols, int rows, int rpt) {
+  return ((cols + kBatchCols - 1) / kBatchCols) * ((rows + 8 * rpt - 1) / (8 * rpt));
+}
+
+// One step (BatchOp) for every problem of a level list (`entries`, count ne, device
+// memory); `prefix` (ne + 1 ints) is the exclusive prefix sum of the tiles each entry
+// needs (level l's storage, or level l + 1's for kBRestrict). Problems with
+// active[problem] == 0 skip. kBCoarsest runs one thread per entry instead.
+template <typename T>
+cudaError_t launch_batch_step(int op, const BatchLevel<T>* entries, const int* prefix, int ne, int total_tiles,
+                              int rpt, const int* active, bool exact, cudaStream_t s);
+// Finest levels of a batch (FP64 entries, rpt = 1 tiles). mode 0: r = f - L u,
+// r32 = fl32(r * scale[problem]) and partial[tile] = sum of r^2; mode 1: partial =
+// sum of f^2; mode 2: partial = sum of r^2 only. Then norm2[problem] = the entry's partials added in a fixed order.
+cudaError_t launch_batch_norms(int mode, const BatchLevel<double>* entries, const int* prefix, int ne,
+                               int total_tiles, const int* active, const double* scale, bool exact,
+                               double* partial, double* norm2, cudaStream_t s);
+// u += e32 / scale[problem] on the finest levels.
+cudaError_t launch_batch_ir_update(const BatchLevel<double>* entries, const int* prefix, int ne, int total_tiles,
+                                   const int* active, const double* scale, cudaStream_t s);
+
 }  // namespace nsmg
