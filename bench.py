@@ -277,6 +277,9 @@ def run_ours(args, ws, rank, local):
                 sm_ms, sm_n = vt["smooth"]
                 variants[name]["fp32_half_sweep_gbs"] = 3 * (N + 1) ** 2 * 4 / (sm_ms / max(sm_n, 1) * 1e-3) / 1e9
             hv.close()
+    batched = run_batched(args) if not args.quick and not args.no_extras else None
+    served = run_serving(args) if not args.quick and not args.no_extras else None
+
     # ---- roofline of the dominant kernel (finest-level red-black half-sweep)
     sm_ms, sm_n = kt[mg.MG_KERNEL_SMOOTH]
     per_launch_ms = sm_ms / max(sm_n, 1)
@@ -308,6 +311,8 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
         "variants": variants,
+        "batched": batched,
+        "serving": served,
         "kernel_ms_per_step": {name: kt[k][0] / args.steps for k, name in
                                enumerate(("smooth", "residual", "restrict", "prolong", "norm"))},
     }
@@ -319,6 +324,99 @@ def run_ours(args, ws, rank, local):
                                          f"{cycles} cycles to 1e-10"}
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_batched(args):
+    """Uneven batch: problems with sides 2^k + 1, k uniform in {7..11}, order 2 or 4
+    (50/50), N(0,1) right-hand sides, mixed precision, each to 1e-8; one
+    level-synchronous batched solve vs the same problems solved one after another."""
+    import numpy as np
+    import torch
+    import paper_2008_03885_gb300 as mg
+    import synth
+    count = args.batch_count
+    z = synth.uniform01(SEED + 7, 2 * count)
+    specs = [(2 ** (7 + int(z[2 * i] * 5)), 2 if z[2 * i + 1] < 0.5 else 4) for i in range(count)]
+    rhs = {}
+    for n, _ in specs:
+        if n not in rhs:
+            rhs[n] = torch.tensor(synth.rhs_normal(n, SEED + n), dtype=torch.float64, device="cuda")
+    opts = dict(nu1=NU1, nu2=NU2, precision=mg.MG_PREC_MIXED_FP32, fma_contract=1)
+    t0 = time.perf_counter()
+    hs = [mg.mg_setup(n, order, "redblack", "galerkin", **opts) for n, order in specs]
+    fs = [rhs[n] for n, _ in specs]
+    us = [torch.zeros_like(f) for f in fs]
+    setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    b = mg.mg_batch_create(hs)
+    create_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    mg.mg_batch_solve(b, us, fs, rtol=1e-8, max_cycles=40)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    for u in us:
+        u.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = mg.mg_batch_get_launches(b)
+    e0.record(stream)
+    cyc, rr = mg.mg_batch_solve(b, us, fs, rtol=1e-8, max_cycles=40)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    batch_launches = mg.mg_batch_get_launches(b) - l0
+    b.close()
+    # the same problems one after another through mg_solve (graphs warmed first)
+    for h, u, f in zip(hs, us, fs):
+        u.zero_()
+        mg.mg_solve(h, u, f, rtol=1e-8, max_cycles=40)
+    torch.cuda.synchronize()
+    for u in us:
+        u.zero_()
+    e0.record(stream)
+    for h, u, f in zip(hs, us, fs):
+        mg.mg_solve(h, u, f, rtol=1e-8, max_cycles=40)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    for h in hs:
+        h.close()
+    points = sum((n - 1) ** 2 for n, _ in specs)
+    return {"problems": count, "sides": "2^k+1, k uniform in {7..11}", "unknowns": points,
+            "precision": "mixed FP32 inner / FP64 refinement", "rtol": 1e-8,
+            "batch_ms": batch_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms,
+            "max_cycles": max(cyc), "max_rel_res": max(rr), "batch_kernel_launches": batch_launches,
+            "unknowns_per_s": points / (batch_ms * 1e-3), "setup_s": setup_s, "batch_create_s": create_s}
+
+
+def run_serving(args):
+    """Seeded Poisson request stream at 2000 req/s, sides 2^k + 1 with k uniform in
+    [8, 12], order 2/4 and Galerkin/non-Galerkin 50/50, tolerance 1e-8, 120 GB budget:
+    continuous batching (8 slots, mixed precision) vs the plain per-request FP64 solve
+    (one slot). A bounded sample: the first `serve_count` requests of the stream."""
+    import numpy as np
+    import torch
+    from paper_2008_03885_gb300 import serve
+    import synth
+    rhs_cache = {}
+
+    def rhs(n, seed):  # one N(0,1) right-hand side per size keeps host generation bounded
+        if n not in rhs_cache:
+            rhs_cache[n] = synth.rhs_normal(n, SEED + n)
+        return rhs_cache[n]
+
+    reqs = serve.poisson_stream(SEED, args.serve_count, 2000.0, 8, 12, rtol=1e-8, rhs=rhs)
+    keys = sorted({(r.n, r.order, r.coarse_op) for r in reqs})
+    out = {"requests": len(reqs), "rate_rps": 2000.0, "sides": "2^k+1, k uniform in [8, 12]",
+           "sample": f"first {len(reqs)} requests of the seeded 20000-request stream", "budget_gb": 120}
+    for name, slots, opts in (("continuous_mixed", 8, dict(nu1=NU1, nu2=NU2, precision=1, fma_contract=1)),
+                              ("plain_fp64", 1, dict(nu1=NU1, nu2=NU2))):
+        srv = serve.Server(slots=slots, budget_bytes=120e9, **opts)
+        srv.warm(keys, per_key=min(slots, 2))
+        results, stats = srv.run(reqs, realtime=True)
+        srv.close()
+        stats["max_rel_res"] = max(r.rel_res for r in results.values())
+        out[name] = stats
+    out["offered_load_rps"] = 2000.0
+    return out
 
 
 def run_profile_case(args):
@@ -372,6 +470,9 @@ def main():
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="run a few finest-level kernels (ncu)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-count", type=int, default=400)
     ap.add_argument("--profile-n", type=int, default=4096)
     ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")
     args = ap.parse_args()

@@ -424,7 +424,7 @@ mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
     return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
   }
   h->allocs.push_back(*p);
-  if (cudaMemset(*p, 0, bytes) != cudaSuccess) return MG_ERR_CUDA;
+  if (cudaMemsetAsync(*p, 0, bytes, h->priv) != cudaSuccess) return MG_ERR_CUDA;
   return MG_OK;
 }
 
@@ -443,12 +443,12 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P) {
   if ((st = device_alloc(h, (void**)&tdy, nt * sizeof(int32_t))) != MG_OK) return st;
   if ((st = device_alloc(h, (void**)&tc, nt * sizeof(T))) != MG_OK) return st;
   std::vector<T> wd(L.cls_wd.begin(), L.cls_wd.end()), c(L.tc.begin(), L.tc.end());
-  CK(cudaMemcpy(cls, L.cls.data(), L.cls.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(cwd, wd.data(), wd.size() * sizeof(T), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(cls, L.cls.data(), L.cls.size() * sizeof(int2), cudaMemcpyHostToDevice, h->priv));
+  CK(cudaMemcpyAsync(cwd, wd.data(), wd.size() * sizeof(T), cudaMemcpyHostToDevice, h->priv));
   if (!L.tdx.empty()) {
-    CK(cudaMemcpy(tdx, L.tdx.data(), L.tdx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(tdy, L.tdy.data(), L.tdy.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(tc, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(tdx, L.tdx.data(), L.tdx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->priv));
+    CK(cudaMemcpyAsync(tdy, L.tdy.data(), L.tdy.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->priv));
+    CK(cudaMemcpyAsync(tc, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice, h->priv));
   }
   P.h.cls = cls;
   P.h.cls_wd = cwd;
@@ -456,7 +456,7 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P) {
   P.h.tdy = tdy;
   P.h.tc = tc;
   if ((st = device_alloc(h, (void**)&P.d, sizeof(LevelDev<T>))) != MG_OK) return st;
-  CK(cudaMemcpy(P.d, &P.h, sizeof(LevelDev<T>), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(P.d, &P.h, sizeof(LevelDev<T>), cudaMemcpyHostToDevice, h->priv));
   return MG_OK;
 }
 
@@ -525,12 +525,21 @@ mg_status run_graph(const Ctx& c, mg_handle::GraphEntry& g, const void* u, const
   const cudaError_t e = cudaStreamEndCapture(c.s, &graph);
   if (st != MG_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
-    return st != MG_OK ? st : MG_ERR_CUDA;
+    if (st != MG_OK) return st;
+    // The capture was invalidated (e.g. by another thread's synchronising call):
+    // nothing of it ran, so launch the same work eagerly.
+    cudaGetLastError();
+    h->launches = before;
+    return body();
   }
   cudaGraphExec_t exec = nullptr;
   const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (ei != cudaSuccess) return MG_ERR_CUDA;
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    h->launches = before;
+    return body();
+  }
   if (g.exec) cudaGraphExecDestroy(g.exec);
   g.u = u;
   g.f = f;
@@ -740,8 +749,8 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns) {
   mg_status st;
   if ((st = device_alloc(h, (void**)&H.d_tail, sizeof(td))) != MG_OK) return st;
   if ((st = device_alloc(h, (void**)&H.d_prog, prog.size() * sizeof(int4))) != MG_OK) return st;
-  CK(cudaMemcpy(H.d_tail, &td, sizeof(td), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(H.d_prog, prog.data(), prog.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(H.d_tail, &td, sizeof(td), cudaMemcpyHostToDevice, h->priv));
+  CK(cudaMemcpyAsync(H.d_prog, prog.data(), prog.size() * sizeof(int4), cudaMemcpyHostToDevice, h->priv));
   H.nops = (int)prog.size();
   H.tail_level = lt;
   H.tail_ctas = tail_ctas<T>(h->opt.fma_contract == 0);
@@ -867,6 +876,12 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   for (const auto& L : h->host)
     if (L.c.size() > (size_t)kMaxTerms) { delete h; return MG_ERR_UNSUPPORTED; }
   auto fail = [&](mg_status s) { free_all(h); delete h; return s; };
+  // Set-up work runs on the handle's own non-blocking stream: no device-wide
+  // synchronisation, so other threads may keep capturing or running their streams.
+  if (cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return fail(MG_ERR_CUDA);
   const HostLevel& C = h->host.back();
   if (C.unknowns != 1) return fail(MG_ERR_UNSUPPORTED);
   const int64_t cidx = (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
@@ -884,16 +899,12 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
     h->h32.coarsest_a = (float)ca;
     if ((st = build_tail<float>(h, tail_limit(kTailUnknownsFp32))) != MG_OK) return fail(st);
   }
-  if (cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
-    return fail(MG_ERR_CUDA);
   h->nblocks0 = resnorm_blocks<double>(h->h64.L[0]);
   if ((st = device_alloc(h, (void**)&h->partial, h->nblocks0 * sizeof(double))) != MG_OK) return fail(st);
   if ((st = device_alloc(h, (void**)&h->scalar, 64)) != MG_OK) return fail(st);
   if (cudaMallocHost((void**)&h->hscalar, 64) != cudaSuccess) return fail(MG_ERR_CUDA);
   h->host_allocs.push_back(h->hscalar);
-  if (cudaDeviceSynchronize() != cudaSuccess) return fail(MG_ERR_CUDA);
+  if (cudaStreamSynchronize(h->priv) != cudaSuccess) return fail(MG_ERR_CUDA);
   *out = h;
   return MG_OK;
 }
@@ -1159,7 +1170,7 @@ template <typename T>
 mg_status upload_vec(mg_batch* b, const std::vector<T>& v, T** d) {
   mg_status st = batch_alloc(b, (void**)d, std::max<size_t>(v.size(), 1) * sizeof(T));
   if (st != MG_OK) return st;
-  if (!v.empty()) CK(cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!v.empty()) CK(cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->priv));
   return MG_OK;
 }
 
@@ -1376,7 +1387,7 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) 
   if (cudaMallocHost((void**)&b->h_norm2, count * sizeof(double)) != cudaSuccess) return fail(MG_ERR_CUDA);
   b->host_allocs.push_back(b->h_norm2);
   for (int p = 0; p < count; ++p) b->h_active[p] = 1;
-  if (cudaMemcpy(b->d_active, b->h_active, count * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+  if (cudaMemcpyAsync(b->d_active, b->h_active, count * sizeof(int), cudaMemcpyHostToDevice, b->priv) != cudaSuccess)
     return fail(MG_ERR_CUDA);
   // finest FP64 levels (norms, refinement); u / f filled in per solve
   for (int p = 0; p < count; ++p) {
@@ -1418,8 +1429,8 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) 
       e.u = b->hs[e.problem]->h64.t[0];
       e.f = b->hs[e.problem]->h64.d[0];
     }
-    if (cudaMemcpy(B0.d_entries, B0.host.data(), B0.host.size() * sizeof(BatchLevel<double>), cudaMemcpyHostToDevice) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(B0.d_entries, B0.host.data(), B0.host.size() * sizeof(BatchLevel<double>),
+                        cudaMemcpyHostToDevice, b->priv) != cudaSuccess)
       return fail(MG_ERR_CUDA);
     if ((st = autotune<double>(b, b->lv64)) != MG_OK) return fail(st);
     B0.host = b->lv64_0;

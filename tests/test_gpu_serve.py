@@ -1,0 +1,58 @@
+"""Serving with continuous batching: every result equals the same request solved
+alone, and the budget is respected."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2008_03885_gb300 as mg  # noqa: E402
+from paper_2008_03885_gb300 import serve  # noqa: E402
+
+
+def alone(r, **opts):
+    f = torch.tensor(r.f, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    h = mg.mg_setup(r.n, r.order, "redblack", r.coarse_op, **opts)
+    try:
+        k, hist = mg.mg_solve(h, u, f, rtol=r.rtol, max_cycles=60)
+    finally:
+        h.close()
+    return u.cpu().numpy(), k
+
+
+@pytest.mark.parametrize("opts", [dict(nu1=2, nu2=1),
+                                  dict(nu1=2, nu2=1, precision=mg.MG_PREC_MIXED_FP32, fma_contract=1)])
+def test_results_identical_alone_and_in_the_mix(opts):
+    reqs = serve.poisson_stream(seed=5, count=40, rate=2000.0, k_lo=4, k_hi=8, rtol=1e-8)
+    srv = serve.Server(slots=6, budget_bytes=8e9, **opts)
+    try:
+        results, stats = srv.run(reqs, realtime=True)
+    finally:
+        srv.close()
+    assert stats["requests"] == 40 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    for r in reqs:
+        res = results[r.rid]
+        assert res.rel_res < 1e-8
+        u, k = alone(r, **opts)
+        assert res.cycles == k
+        assert np.array_equal(res.u, u), r.rid
+
+
+def test_small_budget_evicts_and_stays_correct():
+    reqs = serve.poisson_stream(seed=9, count=24, rate=5000.0, k_lo=5, k_hi=8, rtol=1e-8)
+    big = max(mg.mg_workspace_bytes(r.n, r.order, "redblack", r.coarse_op, nu1=2, nu2=1) + 2 * (r.n + 1) ** 2 * 8
+              for r in reqs)
+    srv = serve.Server(slots=3, budget_bytes=1.6 * big, nu1=2, nu2=1)
+    try:
+        results, stats = srv.run(reqs, realtime=False)
+    finally:
+        srv.close()
+    assert stats["hierarchies_evicted"] > 0
+    assert stats["hbm_peak_gb"] * 1e9 <= 1.6 * big + 1
+    for r in reqs[:6]:
+        u, _ = alone(r, nu1=2, nu2=1)
+        assert np.array_equal(results[r.rid].u, u)
