@@ -279,6 +279,7 @@ def run_ours(args, ws, rank, local):
                 sm_ms, sm_n = vt["smooth"]
                 variants[name]["fp32_half_sweep_gbs"] = 3 * (N + 1) ** 2 * 4 / (sm_ms / max(sm_n, 1) * 1e-3) / 1e9
             hv.close()
+    large = run_mixed_large(args) if not args.quick and not args.no_extras else None
     batched = run_batched(args) if not args.quick and not args.no_extras else None
     served = run_serving(args) if not args.quick and not args.no_extras else None
 
@@ -313,6 +314,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
         "variants": variants,
+        "mixed_vs_fp64_8193": large,
         "batched": batched,
         "serving": served,
         "kernel_ms_per_step": {name: kt[k][0] / args.steps for k, name in
@@ -326,6 +328,43 @@ def run_ours(args, ws, rank, local):
                                          f"{cycles} cycles to 1e-10"}
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_mixed_large(args):
+    """8193^2 (N = 8192), orders 2 and 4, N(0,1) right-hand side: time to 1e-10 of the
+    FP64 path (exact evaluation order, bitwise equal to the oracle's iterates) and of
+    the mixed path (FP32 inner cycles, FP64 refinement), and the mixed solution's
+    relative error against the FP64 solution."""
+    import torch
+    import paper_2008_03885_gb300 as mg
+    import synth
+    n = args.large_n
+    f = torch.tensor(synth.rhs_normal(n, SEED + 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"n": n, "rhs": "N(0,1) i.i.d.", "rtol": RTOL}
+    for order in (2, 4):
+        res = {}
+        sols = {}
+        for name, extra in (("fp64", {}), ("mixed", {"precision": mg.MG_PREC_MIXED_FP32, "fma_contract": 1})):
+            h = mg.mg_setup(n, order, "redblack", "galerkin", nu1=NU1 if order == 4 else 1, nu2=1, **extra)
+            u = torch.zeros_like(f)
+            mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)  # warm-up (graph capture)
+            torch.cuda.synchronize()
+            u.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            k, hist = mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)
+            b.record(stream)
+            torch.cuda.synchronize()
+            h.close()
+            res[name] = {"ms": a.elapsed_time(b), "cycles": k, "final_rel_res": hist[-1]}
+            sols[name] = u
+        err = float(torch.linalg.norm(sols["mixed"] - sols["fp64"]) / torch.linalg.norm(sols["fp64"]))
+        res["mixed"]["rel_error_vs_fp64_solution"] = err
+        res["speedup_mixed_vs_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
+        out[f"order{order}"] = res
+        del sols
+    return out
 
 
 def run_batched(args):
@@ -474,6 +513,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true", help="run a few finest-level kernels (ncu)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--large-n", type=int, default=8192)
     ap.add_argument("--serve-count", type=int, default=400)
     ap.add_argument("--profile-n", type=int, default=4096)
     ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")

@@ -168,8 +168,6 @@ __device__ __forceinline__ T relax_fast(const T (&c)[NT], const int (&dl)[NT], T
   return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
 }
 
-// All loads of the thread's kRows nodes are issued before any arithmetic (more
-// bytes in flight per thread); the arithmetic per node is relax_value's.
 template <typename T, bool EXACT, int NT>
 __global__ void k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
                                 const T* __restrict__ f, T* __restrict__ uout, int red) {
@@ -183,76 +181,40 @@ __global__ void k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __r
     d1[k] = L.delta[1][k];
   }
   const T wd = L.wd;
-  const int n = L.n, pitch = L.pitch;
-  const bool axis = L.kind == kAxis;
+  const int n = L.n;
   const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
-  const int cq = blockIdx.x * kBX + threadIdx.x;
-  int64_t at[kRows], ac[kRows];
-  int ii[kRows];
-  bool upd[kRows], cpy[kRows], fast[kRows];
-  T nb[kRows][NT], fv[kRows], uc[kRows], cv[kRows];
+  if (L.kind == kAxis) {
+    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
+    if (i0 > n) return;
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    const int j = jb + r * kBY;
-    upd[r] = cpy[r] = fast[r] = false;
-    at[r] = ac[r] = 0;
-    ii[r] = 0;
-    if (j <= 0 || j >= n) continue;
-    const int64_t row = (int64_t)j * pitch;
-    if (axis) {
-      const int i0 = 2 * cq;
-      if (i0 > n) continue;
+    for (int r = 0; r < kRows; ++r) {
+      const int j = jb + r * kBY;
+      if (j <= 0 || j >= n) continue;
       const int i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;
       const int ic = 2 * i0 + 1 - i;
-      if (ic > 0 && ic < n) {
-        cpy[r] = true;
-        ac[r] = row + ic;
-      }
-      if (i > 0 && i < n) {
-        upd[r] = true;
-        ii[r] = i;
-        at[r] = row + i;
-      }
-    } else {
-      if (cq >= L.cols) continue;
-      const int i = 2 * cq + (j & 1);
+      const int64_t row = (int64_t)j * L.pitch;
+      if (ic > 0 && ic < n) uout[row + ic] = uin[row + ic];
       if (i <= 0 || i >= n) continue;
+      const int64_t at = row + i;
+      uout[at] = fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
+                                    : relax_value<T, EXACT>(L, uin, f, i, j, at);
+    }
+  } else {
+    const int q = blockIdx.x * kBX + threadIdx.x;
+    if (q >= L.cols) return;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = jb + r * kBY;
+      if (j <= 0 || j >= n) continue;
+      const int i = 2 * q + (j & 1);
+      if (i <= 0 || i >= n) continue;
+      const int64_t at = (int64_t)j * L.pitch + q;
       if ((i & 1) != red) {
-        cpy[r] = true;
-        ac[r] = row + cq;
-      } else {
-        upd[r] = true;
-        ii[r] = i;
-        at[r] = row + cq;
+        uout[at] = uin[at];
+        continue;
       }
-    }
-    if (upd[r]) fast[r] = fast_node(L, ii[r], j);
-  }
-  // gather
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    if (cpy[r]) cv[r] = uin[ac[r]];
-    if (fast[r]) {
-      const int* dl = (!axis && (ii[r] & 1)) ? d1 : d0;
-#pragma unroll
-      for (int k = 0; k < NT; ++k) nb[r][k] = uin[at[r] + dl[k]];
-      fv[r] = f[at[r]];
-      uc[r] = uin[at[r]];
-    }
-  }
-  // relax and store
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    if (cpy[r]) uout[ac[r]] = cv[r];
-    if (!upd[r]) continue;
-    if (fast[r]) {
-      T sum = Arith<T>::mul(c[0], nb[r][0]);
-#pragma unroll
-      for (int k = 1; k < NT; ++k) sum = madd<T, EXACT>(sum, c[k], nb[r][k]);
-      const T rr = Arith<T>::sub(fv[r], sum);
-      uout[at[r]] = EXACT ? Arith<T>::add(uc[r], Arith<T>::mul(rr, wd)) : Arith<T>::fma(rr, wd, uc[r]);
-    } else {
-      uout[at[r]] = relax_value<T, EXACT>(L, uin, f, ii[r], jb + r * kBY, at[r]);
+      uout[at] = fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
+                                    : relax_value<T, EXACT>(L, uin, f, i, j, at);
     }
   }
 }
