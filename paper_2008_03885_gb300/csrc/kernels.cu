@@ -17,6 +17,14 @@ namespace {
 
 constexpr int kBX = 32, kBY = 8;
 
+// Minimum resident 256-thread blocks per SM requested from the compiler: FP32 stencil
+// kernels are memory-latency bound and gain from full occupancy (8 blocks: 32
+// registers); FP64 kernels are bound by the FP64 pipe and keep their registers.
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
+};
+
 template <typename T>
 struct Arith;
 template <>
@@ -150,7 +158,12 @@ __global__ void k_half_sweep(const LevelDev<T>* __restrict__ Lp, const T* __rest
 
 // ---- specialised fast path: NT-point stencils with coefficients in registers and
 // kRows rows per thread (same arithmetic as apply_at / relax_value) --------------
-constexpr int kRows = 4;
+constexpr int kRowsMax = 4;
+// Rows per thread of the 5/9-point kernels (2 and 4 measured equal for FP32 on GB300).
+template <typename T>
+struct RowsPer {
+  static constexpr int value = 4;
+};
 
 template <typename T, bool EXACT, int NT>
 __device__ __forceinline__ T apply_fast(const T (&c)[NT], const int (&dl)[NT], const T* __restrict__ u,
@@ -169,8 +182,9 @@ __device__ __forceinline__ T relax_fast(const T (&c)[NT], const int (&dl)[NT], T
 }
 
 template <typename T, bool EXACT, int NT>
-__global__ void k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
                                 const T* __restrict__ f, T* __restrict__ uout, int red) {
+  constexpr int kRows = RowsPer<T>::value;
   const LevelDev<T>& L = *Lp;
   T c[NT];
   int d0[NT], d1[NT];
@@ -220,8 +234,9 @@ __global__ void k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __r
 }
 
 template <typename T, bool EXACT, int NT>
-__global__ void k_residual_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
                               const T* __restrict__ f, T* __restrict__ d) {
+  constexpr int kRows = RowsPer<T>::value;
   const LevelDev<T>& L = *Lp;
   T c[NT];
   int d0[NT], d1[NT];
@@ -277,7 +292,7 @@ __device__ __forceinline__ T apply_smem(const StencilSmem<T>& sm, int nt, int pa
 }
 
 template <typename T, bool EXACT>
-__global__ void k_half_sweep_gen(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_gen(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
                                  const T* __restrict__ f, T* __restrict__ uout, int red) {
   const LevelDev<T>& L = *Lp;
   __shared__ StencilSmem<T> sm;
@@ -313,7 +328,7 @@ __global__ void k_half_sweep_gen(const LevelDev<T>* __restrict__ Lp, const T* __
 }
 
 template <typename T, bool EXACT>
-__global__ void k_residual_gen(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_gen(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
                                const T* __restrict__ f, T* __restrict__ d) {
   const LevelDev<T>& L = *Lp;
   __shared__ StencilSmem<T> sm;
@@ -561,7 +576,7 @@ __device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, 
 }
 
 template <typename T, bool EXACT>
-__global__ void k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
                            int transfer, const T* __restrict__ d, T* __restrict__ fc) {
   const LevelDev<T>& Lc = *Lcp;
   int i, j;
@@ -570,7 +585,7 @@ __global__ void k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T
 }
 
 template <typename T, bool EXACT>
-__global__ void k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
                               int transfer, const T* uin, T* uf, const T* __restrict__ vc) {
   const LevelDev<T>& Lf = *Lfp;
   int i, j;
@@ -946,7 +961,7 @@ cudaError_t launch_half_sweep_nt(const LevelPair<T>& L, bool exact, const T* uin
                                  cudaStream_t s) {
   dim3 g = grid_of(L.h);
   if (L.h.kind == kAxis) g.x = ((L.h.n + 2) / 2 + kBX - 1) / kBX;  // pairs (2p, 2p+1), 2p <= n
-  g.y = (L.h.rows + kBY * kRows - 1) / (kBY * kRows);
+  g.y = (L.h.rows + kBY * RowsPer<T>::value - 1) / (kBY * RowsPer<T>::value);
   if (exact) k_half_sweep_nt<T, true, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
   else k_half_sweep_nt<T, false, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
   return cudaGetLastError();
@@ -1011,7 +1026,7 @@ cudaError_t launch_apply(const LevelPair<T>& L, bool exact, const T* u, T* out, 
 template <typename T, int NT>
 cudaError_t launch_residual_nt(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d, cudaStream_t s) {
   dim3 g = grid_of(L.h);
-  g.y = (L.h.rows + kBY * kRows - 1) / (kBY * kRows);
+  g.y = (L.h.rows + kBY * RowsPer<T>::value - 1) / (kBY * RowsPer<T>::value);
   if (exact) k_residual_nt<T, true, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
   else k_residual_nt<T, false, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
   return cudaGetLastError();
