@@ -35,6 +35,11 @@ WORKLOAD = ("2D Poisson -Lap u = f, 4th-order 9-point Laplacian, 4097x4097 nodes
             "f = 16 seeded sin*sin modes (freq 1-64, N(0,1) amplitudes); red-black coarsening to 3x3, "
             "Galerkin G^(2) coarse operators, V(2,1) red-black smoothing, omega=1, solve from u=0 to 1e-10")
 
+# DRAM bytes (read + write) per launch of the dominant kernel, k_half_sweep_nt<double,
+# exact, 9> on level 0, from one ncu capture of `bench.py --profile-case`
+# (profiles/k_half_sweep_nt_fp64_order4_N4096.md); None whenever that kernel changes.
+DOMINANT_KERNEL_TRAFFIC_BYTES = 373.08e6
+
 # FP64 ALU peak for non-fused FP64 operations: GB300 FP64 1.25 TFLOP/s counts an FMA as
 # two flops, i.e. 0.625 T FP64 instructions/s; a kernel that rounds every product
 # separately issues one instruction per flop.
@@ -303,7 +308,8 @@ def run_ours(args, ws, rank, local):
                    "l2": "inputs larger than L2: f alone is 134 MB and the hierarchy ~1.1 GB per solve",
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_SEPARATE_OP_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_SEPARATE_OP_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_SEPARATE_OP_PEAK_TFLOPS,
+                     "traffic": DOMINANT_KERNEL_TRAFFIC_BYTES, "algorithmic_bytes": bytes_per_launch,
                      "kernel": "k_half_sweep_nt<double, exact, 9> on level 0",
                      "per_launch_ms": per_launch_ms, "launches": sm_n,
                      "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak,

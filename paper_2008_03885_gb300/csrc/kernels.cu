@@ -123,39 +123,6 @@ __device__ __forceinline__ T relax_value(const LevelDev<T>& L, const T* __restri
   return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
 }
 
-// One colour of a red-black sweep, out of place (uin -> uout; the other colour is
-// copied). Rotated levels: one thread per node (a storage row holds one colour, so
-// warps never split). Axis levels: one thread per adjacent pair of nodes (2p, 2p+1)
-// in a row, which holds exactly one node of each colour, so every lane relaxes one
-// node and copies the other.
-template <typename T, bool EXACT>
-__global__ void k_half_sweep(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
-                             const T* __restrict__ f, T* __restrict__ uout, int red) {
-  const LevelDev<T>& L = *Lp;
-  int i, j;
-  if (L.kind == kAxis) {
-    const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
-    j = blockIdx.y * kBY + threadIdx.y;
-    if (j <= 0 || j >= L.n || i0 > L.n) return;
-    i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;  // node of colour `red`
-    const int ic = 2 * i0 + 1 - i;               // node of the other colour
-    if (ic > 0 && ic < L.n) {
-      const int64_t ac = sidx(L, ic, j);
-      uout[ac] = uin[ac];
-    }
-    if (i <= 0 || i >= L.n) return;
-  } else {
-    if (!thread_node(L, i, j) || !interior(L, i, j)) return;
-    if (is_red(L, i, j) != red) {
-      const int64_t at = sidx(L, i, j);
-      uout[at] = uin[at];
-      return;
-    }
-  }
-  const int64_t at = sidx(L, i, j);
-  uout[at] = relax_value<T, EXACT>(L, uin, f, i, j, at);
-}
-
 // ---- specialised fast path: NT-point stencils with coefficients in registers and
 // kRows rows per thread (same arithmetic as apply_at / relax_value) --------------
 constexpr int kRowsMax = 4;
