@@ -61,7 +61,8 @@ typedef enum {
 
 typedef enum {
   MG_COARSEN_STANDARD = 0, /* H = 2h, Eq. (G_H_d) */
-  MG_COARSEN_REDBLACK = 1  /* H = sqrt(2) h, black points of the finer level, Eq. (G_r2) */
+  MG_COARSEN_REDBLACK = 1, /* H = sqrt(2) h, black points of the finer level, Eq. (G_r2) */
+  MG_COARSEN_VARIABLE = 2  /* red-black for coarse levels 1 and 2, standard below (Sec. 4.4 "VC") */
 } mg_coarsening;
 
 typedef enum {
@@ -91,7 +92,8 @@ typedef struct {
 typedef struct {
   double omega;        /* relaxation parameter (default 1.0) */
   int32_t nu1, nu2;    /* pre- and post-smoothing sweeps (default 1, 1) */
-  int32_t gamma;       /* 1 = V cycle, 2 = W cycle (default 1) */
+  int32_t gamma;       /* 1 = V cycle, 2 = W cycle, 3 = "Wn" cycle: 2 coarse cycles on
+                          levels 0 and 1, 1 below (Sec. 4.4) (default 1) */
   int32_t smoother;    /* mg_smoother (default MG_SMOOTH_REDBLACK) */
   int32_t n_min;       /* coarsest axis grid cells per side (default 2: one unknown) */
   int32_t max_levels;  /* 0 = no limit */

@@ -56,6 +56,7 @@ import scipy.sparse as sp
 
 REDBLACK = "redblack"
 STANDARD = "standard"
+VARIABLE = "variable"  # red-black for coarse levels 1 and 2, standard below (Sec. 4.4 "VC")
 
 NONGALERKIN = "nongalerkin"
 GALERKIN = "galerkin"
@@ -137,7 +138,7 @@ def level_shapes(n: int, coarsening: str, n_min: int = 2, max_levels: int | None
             break
         if kind == "axis" and m <= n_min:
             break
-        if coarsening == REDBLACK:
+        if coarsening == REDBLACK or (coarsening == VARIABLE and len(shapes) < 3):
             shapes.append(("rot", m, 2.0 * r2) if kind == "axis" else ("axis", m // 2, 2.0 * r2))
         else:
             shapes.append(("axis", m // 2, 4.0 * r2))
@@ -240,7 +241,7 @@ class Options:
     omega: float = 1.0
     nu1: int = 1
     nu2: int = 1
-    gamma: int = 1
+    gamma: int = 1  # 1 = V, 2 = W, 3 = "Wn" (2 on levels 0 and 1, 1 below; Sec. 4.4)
     smoother: str = "rb"  # "rb" or "jacobi"
     n_min: int = 2
     max_levels: int | None = None
@@ -260,8 +261,9 @@ class Oracle:
                        level_shapes(n, coarsening, self.opt.n_min, self.opt.max_levels)]
         self.P, self.R = [], []
         for l in range(len(self.levels) - 1):
-            P = interpolation(self.levels[l], self.levels[l + 1], coarsening)
-            R = (P.T * (0.5 if coarsening == REDBLACK else 0.25)).tocsr()
+            step = coarsening if coarsening != VARIABLE else (REDBLACK if l < 2 else STANDARD)
+            P = interpolation(self.levels[l], self.levels[l + 1], step)
+            R = (P.T * (0.5 if step == REDBLACK else 0.25)).tocsr()
             R.sort_indices()
             self.P.append(P)
             self.R.append(R)
@@ -355,12 +357,18 @@ class Oracle:
             uc = self.coarse_solve(fc)
         else:
             uc = np.zeros_like(fc)
-            for _ in range(o.gamma):
+            for _ in range(self.gamma_at(l)):
                 uc = self.cycle_level(l + 1, uc, fc)
         u = u + self._P[l] @ uc
         for _ in range(o.nu2):
             u = self.smooth(l, u, f)
         return u
+
+    def gamma_at(self, l: int) -> int:
+        """Coarse-level cycles per visit of level l (Wn: 2 on levels 0 and 1, 1 below)."""
+        if self.opt.gamma == 3:
+            return 2 if l <= 1 else 1
+        return self.opt.gamma
 
     def cycle(self, u: np.ndarray, f: np.ndarray) -> np.ndarray:
         if self.lmax == 0:
@@ -398,5 +406,5 @@ def work_units(oracle: Oracle) -> float:
     visits = 1
     for l, lev in enumerate(oracle.levels[:-1]):
         wu += visits * (o.nu1 + o.nu2 + 2) * lev.size / n0
-        visits *= o.gamma if l + 1 < oracle.lmax else 1
+        visits *= oracle.gamma_at(l) if l + 1 < oracle.lmax else 1
     return wu

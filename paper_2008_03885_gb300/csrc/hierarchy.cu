@@ -137,7 +137,9 @@ std::vector<LevelShape> level_shapes(int N, int coarsening, int n_min, int max_l
     const LevelShape c = s.back();
     if (max_levels > 0 && (int)s.size() >= max_levels) break;
     if (c.kind == kAxis && c.n <= n_min) break;
-    if (coarsening == MG_COARSEN_REDBLACK)
+    // variable coarsening (Sec. 4.4): red-black for levels 1 and 2, standard below
+    const bool rb = coarsening == MG_COARSEN_REDBLACK || (coarsening == MG_COARSEN_VARIABLE && s.size() < 3);
+    if (rb)
       s.push_back(c.kind == kAxis ? LevelShape{kRot, c.n, 2.0 * c.hh} : LevelShape{kAxis, c.n / 2, 2.0 * c.hh});
     else
       s.push_back({kAxis, c.n / 2, 4.0 * c.hh});
@@ -145,8 +147,9 @@ std::vector<LevelShape> level_shapes(int N, int coarsening, int n_min, int max_l
   return s;
 }
 
-int transfer_of(int coarsening, int fine_kind) {
-  if (coarsening == MG_COARSEN_STANDARD) return kStandard;
+// Transfer between level l (fine) and l + 1.
+int transfer_of(int coarsening, int l, int fine_kind) {
+  if (coarsening == MG_COARSEN_STANDARD || (coarsening == MG_COARSEN_VARIABLE && l >= 2)) return kStandard;
   return fine_kind == kAxis ? kRbAxisToRot : kRbRotToAxis;
 }
 
@@ -346,10 +349,11 @@ bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op, const mg_options& o) {
   if (!grid || !pow2(grid->n) || grid->n < 4 || grid->n > 16384) return MG_ERR_INVALID;
   if (order != 2 && order != 4) return MG_ERR_INVALID;
-  if (coarsening != MG_COARSEN_STANDARD && coarsening != MG_COARSEN_REDBLACK) return MG_ERR_INVALID;
+  if (coarsening != MG_COARSEN_STANDARD && coarsening != MG_COARSEN_REDBLACK && coarsening != MG_COARSEN_VARIABLE)
+    return MG_ERR_INVALID;
   if (coarse_op < MG_OP_NONGALERKIN || coarse_op > MG_OP_GALERKIN_TRUE_HIGH) return MG_ERR_INVALID;
   if (!(o.omega > 0.0 && o.omega < 2.0) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 ||
-      o.gamma < 1 || o.gamma > 2 || (o.smoother != MG_SMOOTH_REDBLACK && o.smoother != MG_SMOOTH_JACOBI))
+      o.gamma < 1 || o.gamma > 3 || (o.smoother != MG_SMOOTH_REDBLACK && o.smoother != MG_SMOOTH_JACOBI))
     return MG_ERR_INVALID;
   if (o.precision != MG_PREC_FP64 && o.precision != MG_PREC_MIXED_FP32) return MG_ERR_INVALID;
   if (o.precision == MG_PREC_MIXED_FP32 && (o.inner_cycles < 1 || o.inner_cycles > 64)) return MG_ERR_INVALID;
@@ -390,7 +394,7 @@ void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
   Stencil gal = base;
   for (int l = 1; l < nl; ++l) {
     HostLevel& L = h->host[l];
-    gal = galerkin(gal, transfer_of(h->coarsening, shapes[l - 1].kind));
+    gal = galerkin(gal, transfer_of(h->coarsening, l - 1, shapes[l - 1].kind));
     const int op = h->coarse_op;
     if (op == MG_OP_GALERKIN || op == MG_OP_GALERKIN_TRUE_HIGH || (op == MG_OP_GALERKIN_GN && l == 1)) {
       L.W = gal;
@@ -475,6 +479,13 @@ void free_all(mg_handle* h) {
   for (void* p : h->host_allocs) cudaFreeHost(p);
   h->allocs.clear();
   h->host_allocs.clear();
+}
+
+// Coarse-level cycles per visit of level l: gamma 1 (V), 2 (W), or 3 = "Wn" (Sec. 4.4):
+// two on levels 0 and 1, one below.
+int gamma_at(const mg_handle* h, int l) {
+  if (h->opt.gamma == 3) return l <= 1 ? 2 : 1;
+  return h->opt.gamma;
 }
 
 // ---------------------------------------------------------------- cycle
@@ -632,7 +643,7 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
   if (l + 1 == lmax) {
     LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.f[lmax], H.u[lmax], c.s));
   } else {
-    for (int g = 0; g < h->opt.gamma; ++g)
+    for (int g = 0; g < gamma_at(h, l); ++g)
       if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0)) != MG_OK) return st;
   }
   {
@@ -715,7 +726,7 @@ void emit_tail(const mg_handle* h, int l, bool zero, std::vector<int4>& prog) {
   if (l + 1 == lmax) {
     prog.push_back(make_int4(kOpCoarsest, lmax, 0, 0));
   } else {
-    for (int g = 0; g < h->opt.gamma; ++g) emit_tail(h, l + 1, g == 0, prog);
+    for (int g = 0; g < gamma_at(h, l); ++g) emit_tail(h, l + 1, g == 0, prog);
   }
   prog.push_back(make_int4(kOpProlong, l, 0, 0));
   for (int k = 0; k < h->opt.nu2; ++k) prog.push_back(make_int4(kOpSmooth, l, 0, 0));
@@ -872,7 +883,7 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   const auto shapes = level_shapes(h->N, coarsening, o.n_min, o.max_levels);
   build_operators(h, shapes);
   const int nl = (int)shapes.size();
-  for (int l = 0; l + 1 < nl; ++l) h->transfer.push_back(transfer_of(coarsening, shapes[l].kind));
+  for (int l = 0; l + 1 < nl; ++l) h->transfer.push_back(transfer_of(coarsening, l, shapes[l].kind));
   for (const auto& L : h->host)
     if (L.c.size() > (size_t)kMaxTerms) { delete h; return MG_ERR_UNSUPPORTED; }
   auto fail = [&](mg_status s) { free_all(h); delete h; return s; };

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle.mg import (G1, GALERKIN, GN, NONGALERKIN, REDBLACK, STANDARD, TRUE_HIGH,
+from oracle.mg import (G1, GALERKIN, GN, NONGALERKIN, REDBLACK, STANDARD, TRUE_HIGH, VARIABLE,
                        Options, Oracle)
 
 pytestmark = pytest.mark.gpu
@@ -125,7 +125,7 @@ def test_cycle_histories_match_oracle(order, co, op):
     assert np.array_equal(ug, uo)
 
 
-@pytest.mark.parametrize("opts", [dict(gamma=2), dict(nu1=0, nu2=2), dict(omega=0.9, nu1=3, nu2=2),
+@pytest.mark.parametrize("opts", [dict(gamma=2), dict(gamma=3), dict(nu1=0, nu2=2), dict(omega=0.9, nu1=3, nu2=2),
                                   dict(smoother="jacobi", omega=0.8, nu1=2, nu2=2)])
 def test_cycle_variants_match_oracle(opts):
     n = 64
@@ -260,3 +260,24 @@ def test_tail_cluster_threshold_does_not_change_bits(tail):
     hg, ho, ug, uo = run_pair(n, 4, REDBLACK, GALERKIN, F, 5, nu1=2, tail_unknowns=tail)
     assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
     assert np.array_equal(ug, uo)
+
+
+@pytest.mark.parametrize("order,op", [(2, GALERKIN), (4, GALERKIN), (4, NONGALERKIN), (2, G1), (4, TRUE_HIGH)])
+def test_variable_coarsening_bitwise(order, op):
+    n = 128
+    F = synth.rhs_normal(n, seed=51)
+    hg, ho, ug, uo = run_pair(n, order, VARIABLE, op, F, 6, nu1=2 if order == 4 else 1)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)
+    o = Oracle(n, order, VARIABLE, op)
+    h = mg.mg_setup(n, order, VARIABLE, op)
+    try:
+        check_order_matches(h, o)
+        for l, lev in enumerate(o.levels[:-1]):
+            v = rng_vec(7000 + l, o.levels[l + 1].size)
+            d = rng_vec(8000 + l, lev.size)
+            fc = mg.level_array(h, l + 1)
+            mg.mg_level_restrict(h, l, to_dev(h, l, d), fc)
+            assert np.array_equal(from_dev(h, l + 1, fc), o.restrict(l, d)), l
+    finally:
+        h.close()

@@ -13,7 +13,7 @@ import scipy.sparse as sp
 
 import synth
 from oracle import lfa
-from oracle.mg import (G1, GALERKIN, GN, NONGALERKIN, REDBLACK, STANDARD, TRUE_HIGH,
+from oracle.mg import (G1, GALERKIN, GN, NONGALERKIN, REDBLACK, STANDARD, TRUE_HIGH, VARIABLE,
                        Options, Oracle)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -324,3 +324,30 @@ def test_red_points_have_black_neighbours_only_for_five_point():
         A = lev.A.tocoo()
         off = A.row != A.col
         assert np.all(lev.red[A.row[off]] != lev.red[A.col[off]])
+
+
+def test_wn_cycle_printed_ecr():
+    """Sec. 4.4: the Wn cycle (gamma 2 on levels 0, 1) keeps W-like rates at lower cost."""
+    ref = golden("paper_rates.json")["rbc_7level_Wn11_ecr"]
+    nu = 2
+    o = Oracle(ref["N"], 2, REDBLACK, GALERKIN, Options(gamma=3, max_levels=7))
+    assert [o.gamma_at(l) for l in range(4)] == [2, 2, 1, 1]
+    cr = _asymptotic_cr(o, cycles=6)
+    wu = (nu + 2) * (1 + 2 / 2 + 4 / 4 + 4 / 8 + 4 / 16 + 4 / 32)
+    ecr = cr ** (1.0 / wu)
+    assert ref["band"][0] * ref["value"] <= ecr <= ref["band"][1] * ref["value"], ecr
+
+
+def test_variable_coarsening_levels_and_printed_ecr():
+    """Sec. 4.4: red-black coarsening for levels 1 and 2, then standard coarsening."""
+    o = Oracle(64, 2, VARIABLE, GALERKIN)
+    assert [(lev.kind, lev.n) for lev in o.levels] == [
+        ("axis", 64), ("rot", 64), ("axis", 32), ("axis", 16), ("axis", 8), ("axis", 4), ("axis", 2)]
+    # transfers: red-black (1/2 P^T) for the first two pairs, full weighting (1/4 P^T) below
+    assert abs(o.P[1] - 2 * o.R[1].T).max() == 0 and abs(o.P[2] - 4 * o.R[2].T).max() == 0
+    ref = golden("paper_rates.json")["vc_5level_W11_ecr"]
+    nu = 2
+    best = min(_asymptotic_cr(Oracle(ref["N"], 2, VARIABLE, GALERKIN, Options(omega=w, gamma=2, max_levels=5)),
+                              cycles=6) for w in (1.0, 1.1))
+    ecr = best ** (1.0 / ((nu + 2) * (1 + 2 / 2 + 4 / 4 + 8 / 16)))
+    assert ref["band"][0] * ref["value"] <= ecr <= ref["band"][1] * ref["value"], ecr
