@@ -261,7 +261,9 @@ def run_ours(args, ws, rank, local):
                 ("standard_galerkin_omega1.1", "standard", "galerkin", 1.1, {}),
                 ("fp64_fma_contract", "redblack", "galerkin", 1.0, {"fma_contract": 1}),
                 ("mixed_fp32_inner", "redblack", "galerkin", 1.0,
-                 {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 2, "fma_contract": 1})):
+                 {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1, "fma_contract": 1}),
+                ("mixed_fp32_inner_nongalerkin_coarse", "redblack", "nongalerkin", 1.0,
+                 {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1, "fma_contract": 1})):
             hv = mg.mg_setup(N, ORDER, co, op, nu1=NU1, nu2=NU2, omega=omega, **extra)
             solve(hv, u, f)
             torch.cuda.synchronize()
@@ -498,7 +500,7 @@ def run_profile_mixed(args):
     f = torch.tensor(synth.rhs_sine_modes(n, SEED), dtype=torch.float64, device="cuda")
     u = torch.zeros_like(f)
     h = mg.mg_setup(n, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2,
-                    precision=mg.MG_PREC_MIXED_FP32, inner_cycles=2, fma_contract=1)
+                    precision=mg.MG_PREC_MIXED_FP32, inner_cycles=1, fma_contract=1)
     for _ in range(2):
         u.zero_()
         k, hist = mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)

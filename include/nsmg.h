@@ -99,7 +99,9 @@ typedef struct {
   int32_t max_levels;  /* 0 = no limit */
   int32_t precision;   /* mg_precision (default MG_PREC_FP64) */
   int32_t fma_contract;/* 0 = separate rounding of every product (default), 1 = FMA allowed */
-  int32_t inner_cycles;/* mixed precision: FP32 cycles per refinement step (default 2) */
+  int32_t inner_cycles;/* mixed precision: FP32 cycles per refinement step (default 1: FP32
+                          rounding caps a step's reduction near 5e-4, so more cycles per
+                          step cost more than extra steps) */
   int32_t tail_unknowns;/* levels (below the finest) with at most this many unknowns run inside
                            one thread-block-cluster kernel; 0 = built-in default, -1 = never */
   int32_t tail_ctas;   /* CTAs of that cluster (1..16); 0 = largest the device schedules */
@@ -258,7 +260,10 @@ typedef enum {
 
 mg_status mg_get_counters(const mg_handle* h, mg_counters* out);
 mg_status mg_reset_counters(mg_handle* h);
-/* enable != 0: record a CUDA event pair around every finest-level launch. */
+/* enable = 1: record a CUDA event pair around every finest-level launch; 2: around
+   every launch of every level (kernel class k of level l is read as k + 5 l; a tail
+   kernel counts as level l's MG_KERNEL_SMOOTH); 0: off. Timed runs launch eagerly
+   (no CUDA graph). */
 mg_status mg_set_timing(mg_handle* h, int enable);
 /* Total device milliseconds and launch count of a kernel class since timing was
    enabled or last read (waits for the recorded events; resets the class). */

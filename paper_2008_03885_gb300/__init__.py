@@ -256,8 +256,9 @@ def mg_reset_counters(h: Handle):
     _check(_lib.mg_reset_counters(h.ptr), "mg_reset_counters")
 
 
-def mg_set_timing(h: Handle, enable: bool = True):
-    _check(_lib.mg_set_timing(h.ptr, int(bool(enable))), "mg_set_timing")
+def mg_set_timing(h: Handle, enable=True):
+    """True / 1: finest-level kernels; 2: every level (class k of level l is k + 5 l)."""
+    _check(_lib.mg_set_timing(h.ptr, int(enable)), "mg_set_timing")
 
 
 def mg_get_timing(h: Handle, kernel_class: int):

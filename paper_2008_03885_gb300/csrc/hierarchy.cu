@@ -265,6 +265,7 @@ struct Hier {
   int4* d_prog = nullptr;  // program for a sub-cycle with zero initial guess
   int nops = 0;
   int tail_ctas = 1;       // CTAs in the tail's thread-block cluster
+  int tail_smem = 0;       // > 0: the tail's levels live in shared memory (elements)
 };
 
 struct mg_handle {
@@ -294,9 +295,9 @@ struct mg_handle {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // instrumentation
   int64_t launches = 0, cycles = 0;
-  bool timing = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[MG_KERNEL_CLASSES];
-  size_t ev_used[MG_KERNEL_CLASSES] = {};
+  int timing = 0;  // 1: finest-level kernels, 2: every level (class + 5 * level)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[MG_KERNEL_CLASSES * (kTailMaxLevels + 1)];
+  size_t ev_used[MG_KERNEL_CLASSES * (kTailMaxLevels + 1)] = {};
 };
 
 template <typename T>
@@ -326,7 +327,9 @@ struct Bracket {
   int cls;
   cudaStream_t s;
   bool on;
-  Bracket(mg_handle* h_, int level, int cls_, cudaStream_t s_) : h(h_), cls(cls_), s(s_), on(h_->timing && level == 0) {
+  Bracket(mg_handle* h_, int level, int cls_, cudaStream_t s_)
+      : h(h_), cls(cls_ + (h_->timing == 2 ? MG_KERNEL_CLASSES * level : 0)), s(s_),
+        on(h_->timing == 2 ? level <= kTailMaxLevels : (h_->timing != 0 && level == 0)) {
     if (!on) return;
     auto& v = h->ev[cls];
     if (h->ev_used[cls] == v.size()) {
@@ -620,8 +623,11 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
   mg_status st;
   if (l == H.tail_level) {
     // the program starts with the zeroing op; skip it to continue from U
-    LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, zero_init ? H.d_prog : H.d_prog + 1,
-                                zero_init ? H.nops : H.nops - 1, c.exact, c.s));
+    const int4* prog = zero_init ? H.d_prog : H.d_prog + 1;
+    const int nops = zero_init ? H.nops : H.nops - 1;
+    Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+    if (H.tail_smem > 0) LAUNCH(h, 1, launch_tail_smem<T>(H.d_tail, H.tail_smem, prog, nops, c.exact, c.s));
+    else LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, prog, nops, c.exact, c.s));
     return MG_OK;
   }
   if (zero_init) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
@@ -734,16 +740,42 @@ void emit_tail(const mg_handle* h, int l, bool zero, std::vector<int4>& prog) {
 
 // Hand every level from the first one (below the finest) with at most
 // `max_unknowns` unknowns down to the coarsest to the tail kernel.
+// smem_elems > 0: instead of the unknowns threshold, take the first level (below the
+// finest) from which all levels' u, t, f, d fit in that many shared-memory elements,
+// and run the tail from shared memory.
 template <typename T>
-mg_status build_tail(mg_handle* h, int64_t max_unknowns) {
+mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0) {
   Hier<T>& H = hier<T>(h);
   const int nl = (int)h->host.size();
   int lt = -1;
-  for (int l = 1; l + 1 < nl; ++l)
-    if (h->host[l].unknowns <= max_unknowns) { lt = l; break; }
+  if (smem_elems > 0) {
+    int64_t acc = 0;
+    for (int l = nl - 1; l >= 1; --l) {
+      acc += 4 * (int64_t)h->host[l].rows * h->host[l].cols;
+      if (acc > smem_elems) break;
+      if (l + 1 < nl) lt = l;
+    }
+  } else {
+    for (int l = 1; l + 1 < nl; ++l)
+      if (h->host[l].unknowns <= max_unknowns) { lt = l; break; }
+  }
   if (lt < 0 || nl > kTailMaxLevels) return MG_OK;
   TailDesc<T> td;
   std::memset(&td, 0, sizeof(td));
+  if (smem_elems > 0) {
+    int off = 0;
+    for (int l = lt; l < nl; ++l) {
+      const int e = h->host[l].rows * h->host[l].cols;
+      td.sm_u[l] = off;
+      td.sm_t[l] = off + e;
+      td.sm_f[l] = off + 2 * e;
+      td.sm_d[l] = off + 3 * e;
+      off += 4 * e;
+    }
+    td.sm_top = lt;
+    td.sm_elems = off;
+    H.tail_smem = off;
+  }
   for (int l = 0; l < nl; ++l) {
     td.L[l] = H.L[l].d;
     td.u[l] = H.u[l];
@@ -773,7 +805,9 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns) {
 // CUDA graph a small level's full-grid launch costs little, and the tail's per-phase
 // latency on 16 SMs only wins for the last few levels (measured on GB300).
 constexpr int64_t kTailUnknownsFp64 = 256;
-constexpr int64_t kTailUnknownsFp32 = 256;
+// FP32 inner hierarchies by default keep their small levels in one block's shared
+// memory (up to 48K elements = 192 KB for u, t, f and d of every tail level).
+constexpr int64_t kTailSmemElemsFp32 = 48 * 1024;
 
 // Power of two near 1 / rms of a residual with squared norm r2 over m unknowns, so
 // that the FP32 copy of the residual stays far from underflow and overflow.
@@ -826,7 +860,7 @@ void mg_default_options(mg_options* o) {
   o->max_levels = 0;
   o->precision = MG_PREC_FP64;
   o->fma_contract = 0;
-  o->inner_cycles = 2;
+  o->inner_cycles = 1;
   o->tail_unknowns = 0;
   o->tail_ctas = 0;
   o->sweep_kernel = 0;
@@ -908,7 +942,9 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
     if ((st = alloc_hier<float>(h, false)) != MG_OK) return fail(st);
     h->h32.coarsest_idx = cidx;
     h->h32.coarsest_a = (float)ca;
-    if ((st = build_tail<float>(h, tail_limit(kTailUnknownsFp32))) != MG_OK) return fail(st);
+    if (o.tail_unknowns == 0) st = build_tail<float>(h, 0, kTailSmemElemsFp32);
+    else st = build_tail<float>(h, tail_limit(0));
+    if (st != MG_OK) return fail(st);
   }
   h->nblocks0 = resnorm_blocks<double>(h->h64.L[0]);
   if ((st = device_alloc(h, (void**)&h->partial, h->nblocks0 * sizeof(double))) != MG_OK) return fail(st);
@@ -1070,14 +1106,14 @@ mg_status mg_reset_counters(mg_handle* h) {
 }
 
 mg_status mg_set_timing(mg_handle* h, int enable) {
-  if (!h) return MG_ERR_INVALID;
-  h->timing = enable != 0;
+  if (!h || enable < 0 || enable > 2) return MG_ERR_INVALID;
+  h->timing = enable;
   for (auto& u : h->ev_used) u = 0;
   return MG_OK;
 }
 
 mg_status mg_get_timing(mg_handle* h, int kernel_class, double* total_ms, int64_t* launches) {
-  if (!h || kernel_class < 0 || kernel_class >= MG_KERNEL_CLASSES) return MG_ERR_INVALID;
+  if (!h || kernel_class < 0 || kernel_class >= MG_KERNEL_CLASSES * (kTailMaxLevels + 1)) return MG_ERR_INVALID;
   double tot = 0.0;
   const size_t n = h->ev_used[kernel_class];
   for (size_t k = 0; k < n; ++k) {

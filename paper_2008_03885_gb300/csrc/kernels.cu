@@ -909,6 +909,182 @@ __global__ void __launch_bounds__(kBX * kBY)
   }
 }
 
+// ---- shared-memory-resident tail ---------------------------------------------
+// Levels from sm_top down live in one block's shared memory in a compact rows x cols
+// layout; node (i, j) of a level is at j * cols + (rot ? i >> 1 : i). Arithmetic
+// per node is the same as relax_value / apply_at / restrict_value / prolong_value.
+template <typename T>
+__device__ __forceinline__ int smem_idx(const LevelDev<T>& L, int i, int j) {
+  return j * L.cols + (L.kind == kRot ? (i >> 1) : i);
+}
+
+template <typename T, bool EXACT>
+__device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i, int j, T* wd) {
+  T s;
+  if (fast_node(L, i, j)) {
+    const int par = L.kind == kRot ? (i & 1) : 0;
+    const int e = smem_idx(L, i, j);
+    s = Arith<T>::mul(L.c[0], u[e + L.sdy[0] * L.cols + L.sdx[par][0]]);
+    for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, L.c[k], u[e + L.sdy[k] * L.cols + L.sdx[par][k]]);
+    if (wd) *wd = L.wd;
+  } else {
+    const int cl = class_of(L, i, j);
+    const int2 ce = L.cls[cl];
+    s = T(0);
+    for (int k = 0; k < ce.y; ++k) {
+      const int t = ce.x + k;
+      const T x = u[smem_idx(L, i + L.tdx[t], j + L.tdy[t])];
+      s = k == 0 ? Arith<T>::mul(L.tc[t], x) : madd<T, EXACT>(s, L.tc[t], x);
+    }
+    if (wd) *wd = L.cls_wd[cl];
+  }
+  return s;
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(kTailThreads)
+    k_tail_smem(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog, int nops) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  T* sm = reinterpret_cast<T*>(tail_smem);
+  const int tid = threadIdx.x;
+  const int top = D->sm_top;
+  for (int k = tid; k < D->sm_elems; k += kTailThreads) sm[k] = T(0);
+  __syncthreads();
+  {  // top level: u and f from global memory
+    const LevelDev<T>& L = *D->L[top];
+    for (int k = tid; k < L.rows * L.cols; k += kTailThreads) {
+      const int j = k / L.cols, q = k - j * L.cols;
+      sm[D->sm_u[top] + k] = D->u[top][(int64_t)j * L.pitch + q];
+      sm[D->sm_f[top] + k] = D->f[top][(int64_t)j * L.pitch + q];
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < nops; ++p) {
+    const int4 op = prog[p];
+    const int l = op.y;
+    const LevelDev<T>& L = *D->L[l];
+    const int total = L.rows * L.cols;
+    T* U = sm + D->sm_u[l];
+    T* Tb = sm + D->sm_t[l];
+    T* F = sm + D->sm_f[l];
+    int i, j;
+    if (op.x == kOpZero) {
+      for (int k = tid; k < total; k += kTailThreads) U[k] = T(0);
+    } else if (op.x == kOpSmooth) {
+      if (D->smoother == 0) {
+        for (int half = 1; half >= 0; --half) {
+          const T* src = half ? U : Tb;
+          T* dst = half ? Tb : U;
+          for (int k = tid; k < total; k += kTailThreads) {
+            if (!tail_node(L, k, i, j)) continue;
+            if (is_red(L, i, j) == half) {
+              T wd;
+              const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, src, i, j, &wd));
+              dst[k] = EXACT ? Arith<T>::add(src[k], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, src[k]);
+            } else {
+              dst[k] = src[k];
+            }
+          }
+          __syncthreads();
+        }
+      } else {
+        for (int k = tid; k < total; k += kTailThreads) {
+          if (!tail_node(L, k, i, j)) continue;
+          T wd;
+          const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, U, i, j, &wd));
+          Tb[k] = EXACT ? Arith<T>::add(U[k], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, U[k]);
+        }
+        __syncthreads();
+        for (int k = tid; k < total; k += kTailThreads) {
+          if (!tail_node(L, k, i, j)) continue;
+          U[k] = Tb[k];
+        }
+      }
+    } else if (op.x == kOpResRestrict) {
+      T* Dd = sm + D->sm_d[l];
+      for (int k = tid; k < total; k += kTailThreads) {
+        if (!tail_node(L, k, i, j)) continue;
+        Dd[k] = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, U, i, j, nullptr));
+      }
+      __syncthreads();
+      const LevelDev<T>& Lc = *D->L[l + 1];
+      T* Fc = sm + D->sm_f[l + 1];
+      const int tr = D->transfer[l];
+      const RTerm* rt = tr == kRbAxisToRot ? c_rterms_rb_axis : tr == kRbRotToAxis ? c_rterms_rb_rot : c_rterms_std;
+      const int nt = tr == kStandard ? 9 : 5;
+      for (int k = tid; k < Lc.rows * Lc.cols; k += kTailThreads) {
+        if (!tail_node(Lc, k, i, j)) continue;
+        const int fi = tr == kRbAxisToRot ? i : 2 * i, fj = tr == kRbAxisToRot ? j : 2 * j;
+        T s = Arith<T>::mul(T(rt[0].w), Dd[smem_idx(L, fi + rt[0].dx, fj + rt[0].dy)]);
+        for (int t = 1; t < nt; ++t) s = madd<T, EXACT>(s, T(rt[t].w), Dd[smem_idx(L, fi + rt[t].dx, fj + rt[t].dy)]);
+        Fc[k] = s;
+      }
+    } else if (op.x == kOpCoarsest) {
+      if (tid == 0) {
+        const int c = smem_idx(L, 1, 1);
+        U[c] = Arith<T>::div(F[c], D->coarsest_a);
+      }
+    } else {  // kOpProlong
+      const LevelDev<T>& Lc = *D->L[l + 1];
+      const T* V = sm + D->sm_u[l + 1];
+      const int tr = D->transfer[l];
+      for (int k = tid; k < total; k += kTailThreads) {
+        if (!tail_node(L, k, i, j)) continue;
+        T e;
+        if (tr == kRbAxisToRot) {
+          if (((i + j) & 1) == 0) {
+            e = V[smem_idx(Lc, i, j)];
+          } else {
+            const T q = T(0.25);
+            e = Arith<T>::mul(q, V[smem_idx(Lc, i, j - 1)]);
+            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i - 1, j)]);
+            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i + 1, j)]);
+            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i, j + 1)]);
+          }
+        } else if (tr == kRbRotToAxis) {
+          if ((i & 1) == 0) {
+            e = V[smem_idx(Lc, i >> 1, j >> 1)];
+          } else {
+            const T q = T(0.25);
+            const int i0 = (i - 1) >> 1, i1 = (i + 1) >> 1, j0 = (j - 1) >> 1, j1 = (j + 1) >> 1;
+            e = Arith<T>::mul(q, V[smem_idx(Lc, i0, j0)]);
+            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i1, j0)]);
+            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i0, j1)]);
+            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i1, j1)]);
+          }
+        } else {
+          int xs[2], ys[2];
+          int nx, ny;
+          T wx, wy;
+          if (i & 1) { xs[0] = (i - 1) >> 1; xs[1] = (i + 1) >> 1; nx = 2; wx = T(0.5); }
+          else { xs[0] = i >> 1; xs[1] = xs[0]; nx = 1; wx = T(1); }
+          if (j & 1) { ys[0] = (j - 1) >> 1; ys[1] = (j + 1) >> 1; ny = 2; wy = T(0.5); }
+          else { ys[0] = j >> 1; ys[1] = ys[0]; ny = 1; wy = T(1); }
+          const T w = Arith<T>::mul(wx, wy);
+          bool first = true;
+          e = T(0);
+          for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) {
+              const T x = V[smem_idx(Lc, xs[a], ys[b])];
+              e = first ? Arith<T>::mul(w, x) : madd<T, EXACT>(e, w, x);
+              first = false;
+            }
+        }
+        U[k] = Arith<T>::add(U[k], e);
+      }
+    }
+    __syncthreads();
+  }
+  {  // top level: u back to global memory (interior nodes)
+    const LevelDev<T>& L = *D->L[top];
+    for (int k = tid; k < L.rows * L.cols; k += kTailThreads) {
+      int i, j;
+      if (!tail_node(L, k, i, j)) continue;
+      D->u[top][(int64_t)j * L.pitch + (k - j * L.cols)] = sm[D->sm_u[top] + k];
+    }
+  }
+}
+
 template <typename T>
 dim3 grid_of(const LevelDev<T>& L) {
   return dim3((L.cols + kBX - 1) / kBX, (L.rows + kBY - 1) / kBY);
@@ -1171,6 +1347,18 @@ cudaError_t launch_batch_ir_update(const BatchLevel<double>* entries, const int*
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, const int4* prog, int nops, bool exact,
+                             cudaStream_t s) {
+  const size_t bytes = (size_t)sm_elems * sizeof(T);
+  if (bytes > 200 * 1024) return cudaErrorInvalidValue;
+  const void* fn = exact ? (const void*)k_tail_smem<T, true> : (const void*)k_tail_smem<T, false>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (exact) k_tail_smem<T, true><<<1, kTailThreads, bytes, s>>>(desc, prog, nops);
+  else k_tail_smem<T, false><<<1, kTailThreads, bytes, s>>>(desc, prog, nops);
+  return cudaGetLastError();
+}
+
 #define NSMG_INSTANTIATE(T)                                                                           \
   template cudaError_t launch_half_sweep<T>(const LevelPair<T>&, bool, const T*, const T*, T*, int,   \
                                             cudaStream_t);                                            \
@@ -1193,6 +1381,7 @@ cudaError_t launch_batch_ir_update(const BatchLevel<double>* entries, const int*
   template cudaError_t launch_batch_step<T>(int, const BatchLevel<T>*, const int*, int, int, int, const int*, bool, \
                                             cudaStream_t);                                             \
   template int tail_ctas<T>(bool);                                                                    \
+  template cudaError_t launch_tail_smem<T>(const TailDesc<T>*, int, const int4*, int, bool, cudaStream_t); \
   template cudaError_t launch_tail<T>(int, const TailDesc<T>*, const int4*, int, bool, cudaStream_t);
 
 NSMG_INSTANTIATE(double)

@@ -79,7 +79,18 @@ struct TailDesc {
   int32_t smoother;  // mg_smoother
   int64_t coarsest_idx;
   T coarsest_a;
+  // shared-memory-resident variant: per level, element offsets of u, t, f, d in the
+  // block's shared memory (compact rows x cols layout) and the number of levels held
+  int32_t sm_u[kTailMaxLevels], sm_t[kTailMaxLevels], sm_f[kTailMaxLevels], sm_d[kTailMaxLevels];
+  int32_t sm_top;     // first level held (the sub-cycle's top level)
+  int32_t sm_elems;   // shared-memory elements used
 };
+
+// The same op list, with every level from sm_top down held in one block's shared
+// memory (u and f of the top level are loaded at start, u written back at the end).
+template <typename T>
+cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, const int4* prog, int nops, bool exact,
+                             cudaStream_t s);
 
 // Run `nops` ops (x = TailOp, y = level) in order inside one thread-block cluster of
 // `ctas` CTAs, with a cluster barrier after each phase. Op semantics match the
