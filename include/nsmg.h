@@ -108,6 +108,9 @@ typedef struct {
   int32_t sweep_kernel;/* red-black sweeps: 0 = auto (two half-sweep kernels), 1 = half-sweep
                           kernels, 2 = one shared-memory tile kernel per sweep; every choice
                           gives the same bits */
+  int32_t bf16_levels; /* mixed precision, storage trial: values stored on the k finest FP32
+                          inner levels are rounded to bfloat16 (0 = off, at most 4; the
+                          arrays stay FP32, so this measures accuracy, not bandwidth) */
 } mg_options;
 
 typedef struct mg_handle mg_handle;

@@ -45,7 +45,7 @@ class mg_options(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32),
                 ("tail_unknowns", ctypes.c_int32), ("tail_ctas", ctypes.c_int32),
-                ("sweep_kernel", ctypes.c_int32)]
+                ("sweep_kernel", ctypes.c_int32), ("bf16_levels", ctypes.c_int32)]
 
 
 class mg_level_info(ctypes.Structure):

@@ -362,6 +362,8 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
   if (o.precision == MG_PREC_MIXED_FP32 && (o.inner_cycles < 1 || o.inner_cycles > 64)) return MG_ERR_INVALID;
   if (o.tail_ctas < 0 || o.tail_ctas > 16) return MG_ERR_INVALID;
   if (o.sweep_kernel < 0 || o.sweep_kernel > 2) return MG_ERR_INVALID;
+  if (o.bf16_levels < 0 || o.bf16_levels > 4) return MG_ERR_INVALID;
+  if (o.bf16_levels > 0 && (o.precision != MG_PREC_MIXED_FP32 || o.sweep_kernel == 2)) return MG_ERR_UNSUPPORTED;
   if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
   if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
   return MG_OK;
@@ -436,8 +438,9 @@ mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
 }
 
 template <typename T>
-mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P) {
+mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P, int bf16 = 0) {
   P.h = to_dev<T>(L);
+  P.h.bf16 = bf16;
   int2* cls;
   T* cwd;
   int32_t *tdx, *tdy;
@@ -710,7 +713,8 @@ mg_status alloc_hier(mg_handle* h, bool caller_level0) {
   H.d.assign(nl, nullptr);
   mg_status st;
   for (int l = 0; l < nl; ++l) {
-    if ((st = upload_level<T>(h, h->host[l], H.L[l])) != MG_OK) return st;
+    const int bf16 = (!caller_level0 && l < h->opt.bf16_levels) ? 1 : 0;
+    if ((st = upload_level<T>(h, h->host[l], H.L[l], bf16)) != MG_OK) return st;
     const size_t b = level_bytes(h->host[l], sizeof(T));
     if (l > 0 || !caller_level0) {
       if ((st = device_alloc(h, (void**)&H.u[l], b)) != MG_OK) return st;
@@ -825,7 +829,7 @@ mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
   {
     Bracket b(h, 0, MG_KERNEL_NORM, c.s);
     LAUNCH(h, 2, launch_ir_residual(h->h64.L[0], c.exact, u, f, h->h32.f[0], h->ir_scale, h->partial,
-                                    h->scalar, c.s));
+                                    h->scalar, c.s, h->opt.bf16_levels > 0 ? 1 : 0));
   }
   return read_scalar(h, c.s, r2);
 }
@@ -864,6 +868,7 @@ void mg_default_options(mg_options* o) {
   o->tail_unknowns = 0;
   o->tail_ctas = 0;
   o->sweep_kernel = 0;
+  o->bf16_levels = 0;
 }
 
 const char* mg_status_string(mg_status s) {
@@ -1405,7 +1410,7 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) 
     if (o.precision != o0.precision || o.nu1 != o0.nu1 || o.nu2 != o0.nu2 || o.fma_contract != o0.fma_contract ||
         (o.precision == MG_PREC_MIXED_FP32 && o.inner_cycles != o0.inner_cycles))
       return MG_ERR_INVALID;  // one schedule for the whole batch
-    if (o.gamma != 1 || o.smoother != MG_SMOOTH_REDBLACK) return MG_ERR_UNSUPPORTED;
+    if (o.gamma != 1 || o.smoother != MG_SMOOTH_REDBLACK || o.bf16_levels != 0) return MG_ERR_UNSUPPORTED;
     if ((int)h->host.size() > kTailMaxLevels) return MG_ERR_UNSUPPORTED;
   }
   mg_batch* b = new (std::nothrow) mg_batch();

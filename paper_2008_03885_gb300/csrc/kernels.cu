@@ -8,6 +8,7 @@
 // contracting them into FMAs). EXACT = false lets products fuse into FMAs.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 #include <cstdio>
 
 #include "kernels.h"
@@ -45,6 +46,16 @@ struct Arith<float> {
 };
 
 // s + c * x in the chosen rounding mode.
+// Value as stored on a level: FP32 levels of the bfloat16 storage trial round it.
+template <typename T>
+__device__ __forceinline__ T rnd(const LevelDev<T>& L, T v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float rnd<float>(const LevelDev<float>& L, float v) {
+  return L.bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+}
+
 template <typename T, bool EXACT>
 __device__ __forceinline__ T madd(T s, T c, T x) {
   return EXACT ? Arith<T>::add(s, Arith<T>::mul(c, x)) : Arith<T>::fma(c, x, s);
@@ -177,8 +188,8 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
       if (ic > 0 && ic < n) uout[row + ic] = uin[row + ic];
       if (i <= 0 || i >= n) continue;
       const int64_t at = row + i;
-      uout[at] = fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
-                                    : relax_value<T, EXACT>(L, uin, f, i, j, at);
+      uout[at] = rnd(L, fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
+                                           : relax_value<T, EXACT>(L, uin, f, i, j, at));
     }
   } else {
     const int q = blockIdx.x * kBX + threadIdx.x;
@@ -194,8 +205,8 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
         uout[at] = uin[at];
         continue;
       }
-      uout[at] = fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
-                                    : relax_value<T, EXACT>(L, uin, f, i, j, at);
+      uout[at] = rnd(L, fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
+                                           : relax_value<T, EXACT>(L, uin, f, i, j, at));
     }
   }
 }
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_nt(
     const int64_t at = (int64_t)j * L.pitch + q;
     const T s = fast_node(L, i, j) ? apply_fast<T, EXACT, NT>(c, (L.kind == kRot && (i & 1)) ? d1 : d0, u, at)
                                    : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
-    d[at] = Arith<T>::sub(f[at], s);
+    d[at] = rnd(L, Arith<T>::sub(f[at], s));
   }
 }
 
@@ -288,9 +299,9 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_g
   if (fast_node(L, i, j)) {
     const T r = Arith<T>::sub(f[at], apply_smem<T, EXACT>(sm, L.nt, L.kind == kRot ? (i & 1) : 0, uin, at));
     const T wd = L.wd;
-    uout[at] = EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
+    uout[at] = rnd(L, EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]));
   } else {
-    uout[at] = relax_value<T, EXACT>(L, uin, f, i, j, at);
+    uout[at] = rnd(L, relax_value<T, EXACT>(L, uin, f, i, j, at));
   }
 }
 
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_gen
   const int64_t at = sidx(L, i, j);
   const T s = fast_node(L, i, j) ? apply_smem<T, EXACT>(sm, L.nt, L.kind == kRot ? (i & 1) : 0, u, at)
                                  : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
-  d[at] = Arith<T>::sub(f[at], s);
+  d[at] = rnd(L, Arith<T>::sub(f[at], s));
 }
 
 // ---- fused red-black sweep on a shared-memory tile ---------------------------
@@ -455,7 +466,7 @@ __global__ void k_jacobi(const LevelDev<T>* __restrict__ Lp, const T* __restrict
   T wd;
   const T s = apply_at<T, EXACT>(L, uin, i, j, at, &wd);
   const T r = Arith<T>::sub(f[at], s);
-  uout[at] = EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
+  uout[at] = rnd(L, EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]));
 }
 
 template <typename T, bool EXACT>
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_restrict(con
   const LevelDev<T>& Lc = *Lcp;
   int i, j;
   if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
-  fc[sidx(Lc, i, j)] = restrict_value<T, EXACT>(*Lfp, transfer, d, i, j);
+  fc[sidx(Lc, i, j)] = rnd(Lc, restrict_value<T, EXACT>(*Lfp, transfer, d, i, j));
 }
 
 template <typename T, bool EXACT>
@@ -558,7 +569,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_prolong_add(
   int i, j;
   if (!thread_node(Lf, i, j) || !interior(Lf, i, j)) return;
   const int64_t at = sidx(Lf, i, j);
-  uf[at] = Arith<T>::add(uin[at], prolong_value<T, EXACT>(*Lcp, transfer, vc, i, j));
+  uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_value<T, EXACT>(*Lcp, transfer, vc, i, j)));
 }
 
 template <typename T>
@@ -647,7 +658,7 @@ __global__ void k_zero_boundary(int n, int pitch, T* __restrict__ u) {
 template <bool EXACT>
 __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
                               const double* __restrict__ f, float* __restrict__ r32, double scale,
-                              double* __restrict__ partial, int tiles_y) {
+                              double* __restrict__ partial, int tiles_y, int bf16) {
   const LevelDev<double>& L = *Lp;
   double v = 0.0;
   const int q = blockIdx.x * kBX + threadIdx.x;
@@ -658,7 +669,8 @@ __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const dou
     if (!interior(L, i, j)) continue;
     const int64_t at = sidx(L, i, j);
     const double r = Arith<double>::sub(f[at], apply_at<double, EXACT>(L, u, i, j, at, nullptr));
-    r32[at] = (float)(r * scale);
+    const float r32v = (float)(r * scale);
+    r32[at] = bf16 ? __bfloat162float(__float2bfloat16_rn(r32v)) : r32v;
     v += r * r;
   }
   v = block_sum(v);
@@ -1242,11 +1254,11 @@ cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s) {
 }
 
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
-                               float* r32, double scale, double* partial, double* out, cudaStream_t s) {
+                               float* r32, double scale, double* partial, double* out, cudaStream_t s, int bf16) {
   const dim3 g = norm_grid(L.h);
   const int ty = (int)grid_of(L.h).y;
-  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty);
-  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty);
+  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16);
+  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16);
   k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
   return cudaGetLastError();
 }

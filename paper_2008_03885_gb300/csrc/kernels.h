@@ -58,7 +58,8 @@ cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s);
 // Refinement step, finest level (FP64 grid, FP32 grid of the same storage layout):
 // r32 = fl32((f - L u) * scale), *out = sum of (f - L u)^2 (two launches).
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
-                               float* r32, double scale, double* partial, double* out, cudaStream_t s);
+                               float* r32, double scale, double* partial, double* out, cudaStream_t s,
+                               int bf16 = 0);
 // u += e * inv_scale on interior nodes.
 cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
                              cudaStream_t s);

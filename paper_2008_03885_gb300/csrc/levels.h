@@ -45,6 +45,7 @@ struct LevelDev {
   const int32_t* tdx;         // merged terms
   const int32_t* tdy;
   const T* tc;
+  int32_t bf16;  // FP32 inner levels: round every stored value to bfloat16 (storage trial)
 };
 
 }  // namespace nsmg

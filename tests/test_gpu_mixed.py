@@ -59,3 +59,23 @@ def test_mixed_history_is_monotone_and_fast():
     assert hist[-1] < 1e-10
     assert k <= 8
     assert all(hist[i + 1] < hist[i] for i in range(k))
+
+
+@pytest.mark.parametrize("bf16_levels", [1, 2])
+def test_bf16_storage_trial_still_reaches_1e10(bf16_levels):
+    """Values stored on the finest FP32 inner levels rounded to bfloat16: the FP64
+    refinement still reaches 1e-10 (more steps), checked by the oracle's residual."""
+    n = 256
+    F = synth.rhs_normal(n, seed=13)
+    u, k, hist = mixed_solve(n, 4, REDBLACK, GALERKIN, F, nu1=2, bf16_levels=bf16_levels)
+    assert hist[-1] < 1e-10
+    o = Oracle(n, 4, REDBLACK, GALERKIN, Options(nu1=2))
+    assert o.rel_residual(o.to_vec(u), o.to_vec(F)) < 1.5e-10
+    _, k0, _ = mixed_solve(n, 4, REDBLACK, GALERKIN, F, nu1=2)
+    assert k >= k0
+
+
+def test_bf16_trial_is_rejected_outside_mixed_precision():
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, 2, bf16_levels=1)
+    assert e.value.status == mg.MG_ERR_UNSUPPORTED
