@@ -132,7 +132,10 @@ typedef struct {
 void mg_default_options(mg_options* opt);
 
 /* Build a hierarchy (Sec. 2.2 components 1-4 for the chosen coarsening and
-   coarse operators). order is 2 (Eq. L_h_2) or 4 (Eq. L_h_2d_4o). opt may be
+   coarse operators). order is 2 (Eq. L_h_2), 4 (Eq. L_h_2d_4o) or 6 (Eq. LhOrder6,
+   the 13-point cross (-2, 27, -270, 980, -270, 27, -2) / (180 h^2); the printed right
+   arm's missing separator read as "27, -2"); for orders 4 and 6 the coarse operators
+   derive from L_h^(2) except MG_OP_GALERKIN_TRUE_HIGH. opt may be
    NULL (defaults). On success *out owns device memory until mg_destroy.
    Errors: MG_ERR_INVALID (n not a power of two in [4, 16384], bad enum, out NULL),
    MG_ERR_UNSUPPORTED, MG_ERR_OOM, MG_ERR_CUDA. */

@@ -8,10 +8,11 @@ nonstandard coarsening", arXiv:2008.03885):
 
 * Problem: -Laplace u = f on the unit square, homogeneous Dirichlet data, N cells
   per side (h = 1/N, N a power of two), unknowns = interior nodes (Sec. 2.1).
-* Fine operators: the 5-point second-order Laplacian, Eq. (L_h_2), and the wide
-  9-point fourth-order one, Eq. (L_h_2d_4o). Next to the boundary the fourth-order
-  stencil reaches one node outside; that ghost is closed by odd reflection
-  u(-x) = -u(x) (the paper analyses infinite or periodic grids and is silent here).
+* Fine operators: the 5-point second-order Laplacian, Eq. (L_h_2), the wide
+  9-point fourth-order one, Eq. (L_h_2d_4o), and the 13-point sixth-order one,
+  Eq. (LhOrder6). Next to the boundary the wide stencils reach nodes outside; those
+  ghosts are closed by odd reflection u(-x) = -u(x) (the paper analyses infinite or
+  periodic grids and is silent here).
 * Coarse grids: standard coarsening H = 2h (Eq. G_H_d) or red-black coarsening
   (Sec. 4.3, Eq. G_r2, Fig. "redBlackCoarseLevelGrids"): level 2m is an axis grid
   of spacing 2^m h, level 2m+1 is the set of black points (i+j even) of level 2m,
@@ -71,6 +72,12 @@ FOURTH_ORDER = {  # Eq. L_h_2d_4o, times 12 h^2
     (0, 0): 60.0,
     (-1, 0): -16.0, (1, 0): -16.0, (0, -1): -16.0, (0, 1): -16.0,
     (-2, 0): 1.0, (2, 0): 1.0, (0, -2): 1.0, (0, 2): 1.0,
+}
+SIXTH_ORDER = {  # Eq. LhOrder6, times 180 h^2 (printed "27 -2" read as "27, -2")
+    (0, 0): 980.0,
+    (-1, 0): -270.0, (1, 0): -270.0, (0, -1): -270.0, (0, 1): -270.0,
+    (-2, 0): 27.0, (2, 0): 27.0, (0, -2): 27.0, (0, 2): 27.0,
+    (-3, 0): -2.0, (3, 0): -2.0, (0, -3): -2.0, (0, 3): -2.0,
 }
 FIRST_GALERKIN = {  # Eq. L_G1 / Eq. L_2h_G, times H^2
     (0, 0): 3.0,
@@ -253,7 +260,7 @@ class Oracle:
     def __init__(self, n: int, order: int = 2, coarsening: str = REDBLACK,
                  coarse_op: str = GALERKIN, options: Options | None = None):
         assert n >= 2 and (n & (n - 1)) == 0, "N must be a power of two"
-        assert order in (2, 4)
+        assert order in (2, 4, 6)
         self.n, self.order, self.coarsening, self.coarse_op = n, order, coarsening, coarse_op
         self.opt = options or Options()
         h = 1.0 / n
@@ -275,9 +282,11 @@ class Oracle:
             L0.W, L0.s = stencil_weights(L0, FIVE_POINT, 1.0), s2
             base_W, base_s = L0.W, s2
         else:
-            L0.W, L0.s = stencil_weights(L0, FOURTH_ORDER, 1.0), s4
+            s6 = 1.0 / (180.0 * h * h)  # scale of the sixth-order operator
+            L0.W = stencil_weights(L0, FOURTH_ORDER if order == 4 else SIXTH_ORDER, 1.0)
+            L0.s = s4 if order == 4 else s6
             if coarse_op == TRUE_HIGH:
-                base_W, base_s = L0.W, s4
+                base_W, base_s = L0.W, L0.s
             else:
                 base_W, base_s = stencil_weights(L0, FIVE_POINT, 1.0), s2  # L_h^(2)
         gal_W = base_W

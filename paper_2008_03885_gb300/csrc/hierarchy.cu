@@ -47,6 +47,10 @@ const std::vector<std::pair<Key, double>> kFivePoint = {  // Eq. (L_h_2) times h
 const std::vector<std::pair<Key, double>> kFourthOrder = {  // Eq. (L_h_2d_4o) times 12 h^2
     {{0, 0}, 60.0}, {{-1, 0}, -16.0}, {{1, 0}, -16.0}, {{0, -1}, -16.0}, {{0, 1}, -16.0},
     {{-2, 0}, 1.0}, {{2, 0}, 1.0}, {{0, -2}, 1.0}, {{0, 2}, 1.0}};
+const std::vector<std::pair<Key, double>> kSixthOrder = {  // Eq. (LhOrder6) times 180 h^2
+    {{0, 0}, 980.0}, {{-1, 0}, -270.0}, {{1, 0}, -270.0}, {{0, -1}, -270.0}, {{0, 1}, -270.0},
+    {{-2, 0}, 27.0}, {{2, 0}, 27.0}, {{0, -2}, 27.0}, {{0, 2}, 27.0},
+    {{-3, 0}, -2.0}, {{3, 0}, -2.0}, {{0, -3}, -2.0}, {{0, 3}, -2.0}};
 const std::vector<std::pair<Key, double>> kFirstGalerkin = {  // Eq. (L_G1) times H^2
     {{0, 0}, 3.0}, {{-1, 0}, -0.5}, {{1, 0}, -0.5}, {{0, -1}, -0.5}, {{0, 1}, -0.5},
     {{-1, -1}, -0.25}, {{1, -1}, -0.25}, {{-1, 1}, -0.25}, {{1, 1}, -0.25}};
@@ -351,7 +355,7 @@ bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op, const mg_options& o) {
   if (!grid || !pow2(grid->n) || grid->n < 4 || grid->n > 16384) return MG_ERR_INVALID;
-  if (order != 2 && order != 4) return MG_ERR_INVALID;
+  if (order != 2 && order != 4 && order != 6) return MG_ERR_INVALID;
   if (coarsening != MG_COARSEN_STANDARD && coarsening != MG_COARSEN_REDBLACK && coarsening != MG_COARSEN_VARIABLE)
     return MG_ERR_INVALID;
   if (coarse_op < MG_OP_NONGALERKIN || coarse_op > MG_OP_GALERKIN_TRUE_HIGH) return MG_ERR_INVALID;
@@ -386,11 +390,13 @@ void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
     base = L0.W;
     base_s = s2;
   } else {
-    L0.W = from_frame(kAxis, kFourthOrder, 1.0);
-    L0.s = s4;
+    // fourth or sixth order: coarse levels from L_h^(2) unless "true high"
+    const double s6 = 1.0 / (180.0 * hf * hf);
+    L0.W = from_frame(kAxis, h->order == 4 ? kFourthOrder : kSixthOrder, 1.0);
+    L0.s = h->order == 4 ? s4 : s6;
     if (h->coarse_op == MG_OP_GALERKIN_TRUE_HIGH) {
       base = L0.W;
-      base_s = s4;
+      base_s = L0.s;
     } else {
       base = from_frame(kAxis, kFivePoint, 1.0);
       base_s = s2;

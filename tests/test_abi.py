@@ -49,7 +49,7 @@ def test_workspace_bytes_validates_without_gpu(lib):
     import paper_2008_03885_gb300 as mg
     assert mg.mg_workspace_bytes(64) > 0
     assert mg.mg_workspace_bytes(63) == 0  # not a power of two
-    assert mg.mg_workspace_bytes(64, order=3) == 0
+    assert mg.mg_workspace_bytes(64, order=3) == 0 and mg.mg_workspace_bytes(64, order=6) > 0
     assert mg.mg_workspace_bytes(2) == 0
     # FP64 red-black V: roughly 2 arrays on level 0 plus 4 per coarse level
     b = mg.mg_workspace_bytes(1024)
@@ -58,7 +58,7 @@ def test_workspace_bytes_validates_without_gpu(lib):
 
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     import paper_2008_03885_gb300 as mg
-    for kwargs in (dict(n=48), dict(n=64, order=6)):
+    for kwargs in (dict(n=48), dict(n=64, order=8), dict(n=64, order=3)):
         with pytest.raises(mg.MGError) as e:
             mg.mg_setup(kwargs.pop("n"), **kwargs)
         assert e.value.status == mg.MG_ERR_INVALID

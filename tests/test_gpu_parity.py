@@ -281,3 +281,13 @@ def test_variable_coarsening_bitwise(order, op):
             assert np.array_equal(from_dev(h, l + 1, fc), o.restrict(l, d)), l
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("co,op", [(REDBLACK, GALERKIN), (REDBLACK, NONGALERKIN), (REDBLACK, TRUE_HIGH),
+                                   (STANDARD, GALERKIN), (VARIABLE, GN)])
+def test_sixth_order_bitwise(co, op):
+    n = 128
+    F = synth.rhs_normal(n, seed=61)
+    hg, ho, ug, uo = run_pair(n, 6, co, op, F, 6, nu1=2)
+    assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
+    assert np.array_equal(ug, uo)

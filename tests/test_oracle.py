@@ -351,3 +351,43 @@ def test_variable_coarsening_levels_and_printed_ecr():
                               cycles=6) for w in (1.0, 1.1))
     ecr = best ** (1.0 / ((nu + 2) * (1 + 2 / 2 + 4 / 4 + 8 / 16)))
     assert ref["band"][0] * ref["value"] <= ecr <= ref["band"][1] * ref["value"], ecr
+
+
+def _symbol_L6(t1, t2, h):
+    """Fourier symbol of the sixth-order cross, from its weights: per axis
+    (490 - 540 cos t + 54 cos 2t - 4 cos 3t) / (180 h^2)."""
+    axis = lambda t: 490 - 540 * math.cos(t) + 54 * math.cos(2 * t) - 4 * math.cos(3 * t)
+    return (axis(t1) + axis(t2)) / (180.0 * h * h)
+
+
+def test_sixth_order_operator_matches_printed_stencil_and_symbol():
+    st = printed(golden("paper_stencils.json")["LhOrder6"])
+    n = 32
+    o = Oracle(n, 6, REDBLACK, GALERKIN)
+    lev = o.levels[0]
+    row = row_stencil(lev, lev.A, 16, 16)
+    assert row == pytest.approx({k: w * n * n / 180.0 for k, w in st.items()}, rel=1e-15)
+    for k, l in ((1, 1), (3, 7), (13, 2)):
+        v = o.to_vec(synth.rhs_single_mode(n, k, l))
+        lam = _symbol_L6(k * math.pi / n, l * math.pi / n, 1.0 / n)
+        assert np.max(np.abs(o.apply(0, v) - lam * v)) <= 1e-12 * lam * np.max(np.abs(v))
+
+
+def test_sixth_order_manufactured_solution_converges_at_order_six():
+    errs = []
+    for n in (16, 32, 64):
+        o = Oracle(n, 6, REDBLACK, GALERKIN)
+        x = np.arange(n + 1) / n
+        U = np.outer(np.sin(math.pi * x), np.sin(math.pi * x))
+        u = o.direct(o.to_vec(2 * math.pi ** 2 * U))
+        errs.append(np.max(np.abs(u - o.to_vec(U))))
+    assert errs[1] / errs[2] == pytest.approx(64.0, rel=0.05)
+
+
+def test_sixth_order_with_second_order_coarse_operators_converges():
+    """Sec. 3.3: second-order coarse operators keep multigrid rates for a sixth-order
+    fine level (Galerkin G^(2) and non-Galerkin nG^(2))."""
+    for op in (GALERKIN, NONGALERKIN):
+        o = Oracle(64, 6, REDBLACK, op, Options(nu1=2, nu2=1))
+        cr = _asymptotic_cr(o)
+        assert cr < 0.1, (op, cr)
