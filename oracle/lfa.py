@@ -76,3 +76,23 @@ def jacobi_smoothing_factor(omega: float, r: float = 2.0, d: int = 2, m: int = 2
         high |= np.abs(t) >= np.pi / r
     x = sum(np.sin(t / 2) ** 2 for t in T) / d
     return float(np.max(np.abs(1 - 2 * omega * x)[high]))
+
+
+def rbc_two_level_rho_periodic(n: int, omega=1.0, nu1=1, nu2=1, coarse="galerkin"):
+    """The same supremum over the frequencies a periodic N x N grid carries,
+    theta = 2 pi k / N (k integer), theta != 0 (the constant mode is the null space
+    of the periodic operator). On a periodic grid the red-black smoother, the
+    transfers and the coarse operator leave every E_theta invariant, so this is
+    the exact spectral radius of the two-level iteration there."""
+    ks = np.arange(-n // 2, n // 2)
+    best = 0.0
+    for k1 in ks:
+        for k2 in ks:
+            if k1 == 0 and k2 == 0:
+                continue
+            t1, t2 = 2 * np.pi * k1 / n, 2 * np.pi * k2 / n
+            if not (-np.pi <= t1 - t2 < np.pi and -np.pi <= t1 + t2 < np.pi):
+                continue
+            M = rbc_two_level_matrix(t1, t2, omega, nu1, nu2, coarse)
+            best = max(best, float(np.max(np.abs(np.linalg.eigvals(M)))))
+    return best

@@ -6,8 +6,12 @@ is measured against this module; the library never calls it.
 What is computed, and where the paper defines it (Liu & Henshaw, "Multigrid with
 nonstandard coarsening", arXiv:2008.03885):
 
-* Problem: -Laplace u = f on the unit square, homogeneous Dirichlet data, N cells
-  per side (h = 1/N, N a power of two), unknowns = interior nodes (Sec. 2.1).
+* Problem: -Laplace u = f on the unit square, N cells per side (h = 1/N, N a power
+  of two), Eq. (G_h_N). Homogeneous Dirichlet data with the interior nodes as
+  unknowns (Sec. 2.1), or periodic boundaries, the setting of the paper's computed
+  results (Sec. 2.2, computations), with the nodes 0 <= i, j < N as unknowns: every
+  stencil and transfer wraps around modulo the level's lattice size (the block-
+  circulant matrix of Sec. "Red-black reduction in two dimensions").
 * Fine operators: the 5-point second-order Laplacian, Eq. (L_h_2), the wide
   9-point fourth-order one, Eq. (L_h_2d_4o), and the 13-point sixth-order one,
   Eq. (LhOrder6). Next to the boundary the wide stencils reach nodes outside; those
@@ -37,7 +41,10 @@ nonstandard coarsening", arXiv:2008.03885):
   Weighted Jacobi, S = I - omega h^2/(2d) L_h (Sec. 5.3), is the other option.
 * Cycle: the gamma-cycle MG(f; maxIters) of Sec. 2.2 (Algorithm "MG"): pre-smooth,
   residual, restrict, recurse (zero initial guess, Eq. L_H_approx) or solve exactly
-  on the coarsest level, interpolate, correct, post-smooth.
+  on the coarsest level, interpolate, correct, post-smooth. A periodic operator is
+  singular (the constants are its null space); its exact coarsest solve is the
+  minimum-norm (zero-mean) solution. Periodic hierarchies coarsen down to a single
+  node, whose operator row is zero and whose zero-mean solution is 0.
 
 Floating-point evaluation order (so that any implementation following the same
 order reproduces every iterate bit for bit): each operator application
@@ -86,6 +93,10 @@ FIRST_GALERKIN = {  # Eq. L_G1 / Eq. L_2h_G, times H^2
 }
 
 
+DIRICHLET = "dirichlet"
+PERIODIC = "periodic"
+
+
 def fold(t: np.ndarray, n: int):
     """Odd-periodic reflection of lattice coordinate t into [0, n].
 
@@ -103,6 +114,7 @@ class Level:
     kind: str  # "axis" or "rot"
     n: int  # cells per side of the lattice the level's points live on
     h2: float  # squared grid spacing of this level (in the level's own frame)
+    periodic: bool = False
     pi: np.ndarray = field(repr=False, default=None)  # unknowns' lattice i
     pj: np.ndarray = field(repr=False, default=None)  # unknowns' lattice j
     index: np.ndarray = field(repr=False, default=None)  # (n+1, n+1) -> unknown or -1
@@ -124,8 +136,9 @@ class Level:
         return (a, b) if self.kind == "axis" else (a + b, b - a)
 
 
-def _make_level(kind: str, n: int, h2: float) -> Level:
-    jj, ii = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+def _make_level(kind: str, n: int, h2: float, periodic: bool = False) -> Level:
+    lo, hi = (0, n) if periodic else (1, n)  # unknowns lo <= i, j < hi
+    jj, ii = np.meshgrid(np.arange(lo, hi), np.arange(lo, hi), indexing="ij")
     pi, pj = ii.ravel(), jj.ravel()  # row-major: j major, i minor
     if kind == "rot":
         keep = (pi + pj) % 2 == 0
@@ -133,7 +146,7 @@ def _make_level(kind: str, n: int, h2: float) -> Level:
     index = -np.ones((n + 1, n + 1), dtype=np.int64)
     index[pj, pi] = np.arange(pi.size)
     red = ((pi + pj) % 2 == 1) if kind == "axis" else (pi % 2 == 1)
-    return Level(kind=kind, n=n, h2=h2, pi=pi, pj=pj, index=index, red=red)
+    return Level(kind=kind, n=n, h2=h2, periodic=periodic, pi=pi, pj=pj, index=index, red=red)
 
 
 def level_shapes(n: int, coarsening: str, n_min: int = 2, max_levels: int | None = None):
@@ -153,14 +166,20 @@ def level_shapes(n: int, coarsening: str, n_min: int = 2, max_levels: int | None
 
 
 def stencil_weights(level: Level, stencil: dict, factor: float) -> sp.csr_matrix:
-    """Dirichlet matrix of an own-frame stencil (times `factor`) with odd-reflection ghosts."""
+    """Matrix of an own-frame stencil (times `factor`): Dirichlet with odd-reflection
+    ghosts, or periodic (offsets wrap modulo the lattice size)."""
     n = level.n
     rows, cols, vals = [], [], []
     for (a, b), w in stencil.items():
         dx, dy = level.frame(a, b)
-        ti, si, bi = fold(level.pi + dx, n)
-        tj, sj, bj = fold(level.pj + dy, n)
-        keep = ~(bi | bj)
+        if level.periodic:
+            ti, tj = np.mod(level.pi + dx, n), np.mod(level.pj + dy, n)
+            si = sj = np.ones(level.size)
+            keep = np.ones(level.size, dtype=bool)
+        else:
+            ti, si, bi = fold(level.pi + dx, n)
+            tj, sj, bj = fold(level.pj + dy, n)
+            keep = ~(bi | bj)
         rows.append(np.nonzero(keep)[0])
         cols.append(level.index[tj[keep], ti[keep]])
         vals.append((si * sj)[keep] * (w * factor))
@@ -174,13 +193,19 @@ def stencil_weights(level: Level, stencil: dict, factor: float) -> sp.csr_matrix
 
 
 def interpolation(fine: Level, coarse: Level, coarsening: str) -> sp.csr_matrix:
-    """Explicit interpolation P: coarse unknowns -> fine unknowns (Dirichlet)."""
+    """Explicit interpolation P: coarse unknowns -> fine unknowns. Dirichlet: coarse
+    boundary nodes contribute nothing; periodic: coarse positions wrap modulo the
+    coarse lattice size."""
     rows, cols, vals = [], [], []
     fi, fj = fine.pi, fine.pj
     nf, nc = fine.n, coarse.n
 
     def add(mask, ci, cj, w):
+        if coarse.periodic:
+            ci, cj = np.mod(ci, nc), np.mod(cj, nc)
         inside = mask & (ci >= 1) & (ci <= nc - 1) & (cj >= 1) & (cj <= nc - 1)
+        if coarse.periodic:
+            inside = mask
         r = np.nonzero(inside)[0]
         rows.append(r)
         cols.append(coarse.index[cj[inside], ci[inside]])
@@ -250,7 +275,7 @@ class Options:
     nu2: int = 1
     gamma: int = 1  # 1 = V, 2 = W, 3 = "Wn" (2 on levels 0 and 1, 1 below; Sec. 4.4)
     smoother: str = "rb"  # "rb" or "jacobi"
-    n_min: int = 2
+    n_min: int | None = None  # coarsest axis lattice size: 2 (Dirichlet) / 1 (periodic) by default
     max_levels: int | None = None
 
 
@@ -258,14 +283,19 @@ class Oracle:
     """Multigrid hierarchy over explicit sparse matrices (FP64)."""
 
     def __init__(self, n: int, order: int = 2, coarsening: str = REDBLACK,
-                 coarse_op: str = GALERKIN, options: Options | None = None):
+                 coarse_op: str = GALERKIN, options: Options | None = None,
+                 boundary: str = DIRICHLET):
         assert n >= 2 and (n & (n - 1)) == 0, "N must be a power of two"
         assert order in (2, 4, 6)
+        assert boundary in (DIRICHLET, PERIODIC)
         self.n, self.order, self.coarsening, self.coarse_op = n, order, coarsening, coarse_op
+        self.boundary = boundary
+        self.periodic = boundary == PERIODIC
         self.opt = options or Options()
         h = 1.0 / n
-        self.levels = [_make_level(k, m, r2) for k, m, r2 in
-                       level_shapes(n, coarsening, self.opt.n_min, self.opt.max_levels)]
+        n_min = self.opt.n_min if self.opt.n_min is not None else (1 if self.periodic else 2)
+        self.levels = [_make_level(k, m, r2, self.periodic) for k, m, r2 in
+                       level_shapes(n, coarsening, n_min, self.opt.max_levels)]
         self.P, self.R = [], []
         for l in range(len(self.levels) - 1):
             step = coarsening if coarsening != VARIABLE else (REDBLACK if l < 2 else STANDARD)
@@ -307,7 +337,8 @@ class Oracle:
         self._A = [Ell(lev.A) for lev in self.levels]
         self._P = [Ell(P) for P in self.P]
         self._R = [Ell(R) for R in self.R]
-        self.wd = [self.opt.omega / lev.A.diagonal() for lev in self.levels]
+        with np.errstate(divide="ignore"):  # a periodic single-node level has a_pp = 0 (never smoothed)
+            self.wd = [self.opt.omega / lev.A.diagonal() for lev in self.levels]
         last = self.levels[-1]
         self._coarse_dense = last.A.toarray()
 
@@ -352,6 +383,10 @@ class Oracle:
         return self.half_sweep(l, u, f, red=False)
 
     def coarse_solve(self, d: np.ndarray) -> np.ndarray:
+        if self.periodic:
+            # singular (constants): the minimum-norm least-squares solution, which is
+            # the zero-mean solution of the compatible part of d
+            return np.linalg.lstsq(self._coarse_dense, d, rcond=None)[0]
         if d.size == 1:
             return d / self._coarse_dense[0, 0]
         return np.linalg.solve(self._coarse_dense, d)
@@ -401,7 +436,10 @@ class Oracle:
         return u, hist
 
     def direct(self, f: np.ndarray) -> np.ndarray:
-        """Sparse direct solution of A_0 u = f (a check, not part of the cycle)."""
+        """Direct solution of A_0 u = f (a check, not part of the cycle); periodic:
+        the zero-mean (minimum-norm) solution from a dense least-squares solve."""
+        if self.periodic:
+            return np.linalg.lstsq(self.levels[0].A.toarray(), f, rcond=None)[0]
         import scipy.sparse.linalg as spla
         return spla.spsolve(self.levels[0].A.tocsc(), f)
 

@@ -117,3 +117,23 @@ def rhs_single_mode(n: int, k: int, l: int) -> np.ndarray:
     x = node_coords(n)
     f = np.outer(np.sin(l * math.pi * x), np.sin(k * math.pi * x))
     return _zero_boundary(f)
+
+
+# ---- periodic problems: unknowns are the nodes 0 <= i, j < n; row and column n of
+# the (n+1) x (n+1) arrays are not unknowns and are left 0 ------------------------
+def rhs_periodic_normal(n: int, seed: int = 0) -> np.ndarray:
+    """f i.i.d. N(0,1) on the nodes 0 <= i, j < n (row-major), minus its mean, so that
+    the singular periodic problem is solvable (f orthogonal to the constants)."""
+    f = np.zeros((n + 1, n + 1))
+    g = normal(seed, n * n).reshape(n, n)
+    f[:n, :n] = g - g.mean()
+    return f
+
+
+def rhs_periodic_mode(n: int, k: int, l: int) -> np.ndarray:
+    """f = cos(2 pi k x) cos(2 pi l y) on the nodes 0 <= i, j < n (x along columns);
+    zero mean for (k, l) != (0, 0) modulo n."""
+    x = np.arange(n, dtype=np.float64) / n
+    f = np.zeros((n + 1, n + 1))
+    f[:n, :n] = np.outer(np.cos(2 * math.pi * l * x), np.cos(2 * math.pi * k * x))
+    return f
