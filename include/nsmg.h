@@ -15,11 +15,21 @@
  * Conventions shared by every call
  * --------------------------------
  * - Domain: the unit square, N cells per side (N a power of two, 4 <= N <= 16384),
- *   h = 1/N, homogeneous Dirichlet boundary values.
+ *   h = 1/N, Eq. (G_h_N), with homogeneous Dirichlet boundary values (default) or
+ *   periodic boundaries (mg_options.boundary), the setting of the paper's computed
+ *   results (Sec. 2.2).
  * - Grid arrays on the finest level are caller-owned DEVICE pointers to
  *   (N+1) x (N+1) contiguous doubles, row-major with x fastest:
- *   a[j*(N+1) + i] is the node (i h, j h). Boundary entries of f are ignored; the
- *   boundary entries of u are set to zero by mg_cycle / mg_solve.
+ *   a[j*(N+1) + i] is the node (i h, j h).
+ *   Dirichlet: the unknowns are the interior nodes 0 < i, j < N; boundary entries
+ *   of f are ignored and those of u are set to zero by mg_cycle / mg_solve.
+ *   Periodic: the unknowns are the nodes 0 <= i, j < N (node N is node 0); row N
+ *   and column N of u and f are neither read nor written. The periodic operator
+ *   annihilates constants, so f must have zero mean over the unknowns (else the
+ *   residual cannot drop below that mean's share of ||f||), and u is determined up
+ *   to a constant: the coarsest level's exact solve is the zero-mean one, but
+ *   relaxation moves the mean of the iterate, so compare solutions after removing
+ *   their means.
  * - u is the initial guess and is overwritten with the new iterate.
  * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *   Work is enqueued on it; calls with *_out arguments synchronise the stream
@@ -85,6 +95,12 @@ typedef enum {
   MG_PREC_MIXED_FP32 = 1  /* FP64 residual/update, FP32 inner cycles (iterative refinement) */
 } mg_precision;
 
+typedef enum {
+  MG_BOUNDARY_DIRICHLET = 0, /* u = 0 on the boundary; ghosts of wide stencils by odd reflection */
+  MG_BOUNDARY_PERIODIC = 1   /* [0,1]^2 periodic (Sec. 2.2): stencils and transfers wrap modulo
+                                each level's lattice; coarsening continues to a single node */
+} mg_boundary;
+
 typedef struct {
   int32_t n; /* cells per side, power of two */
 } mg_grid;
@@ -95,7 +111,8 @@ typedef struct {
   int32_t gamma;       /* 1 = V cycle, 2 = W cycle, 3 = "Wn" cycle: 2 coarse cycles on
                           levels 0 and 1, 1 below (Sec. 4.4) (default 1) */
   int32_t smoother;    /* mg_smoother (default MG_SMOOTH_REDBLACK) */
-  int32_t n_min;       /* coarsest axis grid cells per side (default 2: one unknown) */
+  int32_t n_min;       /* coarsest axis grid cells per side (default 2: one unknown; only 2 is
+                          accepted; periodic hierarchies go on to one node, N_l = 1) */
   int32_t max_levels;  /* 0 = no limit */
   int32_t precision;   /* mg_precision (default MG_PREC_FP64) */
   int32_t fma_contract;/* 0 = separate rounding of every product (default), 1 = FMA allowed */
@@ -111,6 +128,8 @@ typedef struct {
   int32_t bf16_levels; /* mixed precision, storage trial: values stored on the k finest FP32
                           inner levels are rounded to bfloat16 (0 = off, at most 4; the
                           arrays stay FP32, so this measures accuracy, not bandwidth) */
+  int32_t boundary;    /* mg_boundary (default MG_BOUNDARY_DIRICHLET). Periodic is not
+                          available with sweep_kernel = 2 or the batch API (MG_ERR_UNSUPPORTED) */
 } mg_options;
 
 typedef struct mg_handle mg_handle;
@@ -121,8 +140,9 @@ typedef struct {
   int32_t rows;     /* storage rows (n + 1) */
   int32_t cols;     /* used storage columns: n + 1 (axis) or n/2 + 1 (rotated) */
   int32_t pitch;    /* elements between rows */
-  int32_t unknowns; /* interior unknowns */
+  int32_t unknowns; /* unknowns of the level */
   int32_t nterms;   /* interior stencil size */
+  int32_t periodic; /* 1: unknowns are the nodes 0 <= i, j < n; 0: interior nodes 0 < i, j < n */
 } mg_level_info;
 /* Storage of a level: a rows x pitch array of the level's precision. Axis
    grid: element [j*pitch + i] is lattice node (i, j). Rotated grid: only nodes
@@ -202,8 +222,8 @@ mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const do
    flags, so the inner cycle is one CUDA graph for the whole batch. Per-problem
    results are bitwise those of mg_solve on each handle alone (same operations per
    node, same order). All handles must share precision, nu1, nu2, fma_contract and
-   (mixed precision) inner_cycles; gamma must be 1 and the smoother red-black
-   (MG_ERR_UNSUPPORTED otherwise). mg_batch_create also autotunes, per level, the rows
+   (mixed precision) inner_cycles; gamma must be 1, the smoother red-black and the
+   boundary Dirichlet (MG_ERR_UNSUPPORTED otherwise). mg_batch_create also autotunes, per level, the rows
    per thread of the step kernels by timing them (CUDA events), so create the batch
    once and reuse it. The batch keeps pointers to the handles: destroy the batch
    before them. */

@@ -29,6 +29,7 @@ MG_COARSEN_STANDARD, MG_COARSEN_REDBLACK, MG_COARSEN_VARIABLE = 0, 1, 2
 MG_OP_NONGALERKIN, MG_OP_GALERKIN, MG_OP_GALERKIN_G1, MG_OP_GALERKIN_GN, MG_OP_GALERKIN_TRUE_HIGH = range(5)
 MG_SMOOTH_REDBLACK, MG_SMOOTH_JACOBI = 0, 1
 MG_PREC_FP64, MG_PREC_MIXED_FP32 = 0, 1
+MG_BOUNDARY_DIRICHLET, MG_BOUNDARY_PERIODIC = 0, 1
 
 COARSENING = {"standard": MG_COARSEN_STANDARD, "redblack": MG_COARSEN_REDBLACK, "variable": MG_COARSEN_VARIABLE}
 COARSE_OP = {"nongalerkin": MG_OP_NONGALERKIN, "galerkin": MG_OP_GALERKIN, "g1": MG_OP_GALERKIN_G1,
@@ -45,13 +46,14 @@ class mg_options(ctypes.Structure):
                 ("max_levels", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32),
                 ("tail_unknowns", ctypes.c_int32), ("tail_ctas", ctypes.c_int32),
-                ("sweep_kernel", ctypes.c_int32), ("bf16_levels", ctypes.c_int32)]
+                ("sweep_kernel", ctypes.c_int32), ("bf16_levels", ctypes.c_int32),
+                ("boundary", ctypes.c_int32)]
 
 
 class mg_level_info(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("rows", ctypes.c_int32),
                 ("cols", ctypes.c_int32), ("pitch", ctypes.c_int32), ("unknowns", ctypes.c_int32),
-                ("nterms", ctypes.c_int32)]
+                ("nterms", ctypes.c_int32), ("periodic", ctypes.c_int32)]
 
 
 _vp, _dp, _ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
@@ -121,10 +123,15 @@ def _stream(stream) -> int | None:
     return stream.cuda_stream
 
 
+BOUNDARY = {"dirichlet": MG_BOUNDARY_DIRICHLET, "periodic": MG_BOUNDARY_PERIODIC}
+
+
 def mg_default_options(**overrides) -> mg_options:
     o = mg_options()
     _lib.mg_default_options(ctypes.byref(o))
     for k, v in overrides.items():
+        if k == "boundary":
+            v = BOUNDARY.get(v, v)
         setattr(o, k, v)
     return o
 
@@ -229,12 +236,14 @@ def level_array(h: Handle, level: int, device="cuda"):
 
 
 def level_nodes(h: Handle, level: int):
-    """(i, j, row, col) numpy index arrays of the level's interior nodes in row-major
-    (j, then i) order, with their storage row/column."""
+    """(i, j, row, col) numpy index arrays of the level's unknowns (interior nodes, or
+    nodes 0 <= i, j < n of a periodic level) in row-major (j, then i) order, with their
+    storage row/column."""
     import numpy as np
     info = mg_get_level_info(h, level)
     n = info.n
-    jj, ii = np.meshgrid(np.arange(1, n), np.arange(1, n), indexing="ij")
+    lo = 0 if info.periodic else 1
+    jj, ii = np.meshgrid(np.arange(lo, n), np.arange(lo, n), indexing="ij")
     i, j = ii.ravel(), jj.ravel()
     if info.kind == 1:
         keep = (i + j) % 2 == 0

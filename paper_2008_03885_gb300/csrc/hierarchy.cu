@@ -130,6 +130,20 @@ Stencil fold_row(const Stencil& st, int n, int i, int j) {
   return row;
 }
 
+// Periodic row of node (i, j): offsets wrapped modulo n into [0, n), duplicates
+// summed, sorted by (dy, dx) of the wrapped offset (the column order).
+Stencil wrap_row(const Stencil& st, int n, int i, int j) {
+  Stencil row;
+  for (const auto& t : st) {
+    int ti = (i + t.first.second) % n;
+    if (ti < 0) ti += n;
+    int tj = (j + t.first.first) % n;
+    if (tj < 0) tj += n;
+    put(row, ti - i, tj - j, t.second);
+  }
+  return row;
+}
+
 struct LevelShape {
   int kind, n;
   double hh;  // (h_l / h_0)^2
@@ -160,6 +174,7 @@ int transfer_of(int coarsening, int l, int fine_kind) {
 // Host-side build of one level's operator description (both precisions).
 struct HostLevel {
   LevelShape shape;
+  int per = 0;  // periodic level: unknowns 0 <= i, j < n, stencils wrap
   int rows, cols, pitch;
   Stencil W;  // exact weights
   double s;   // scale: coefficient = fl(w * s)
@@ -190,6 +205,8 @@ void build_classes(HostLevel& L, double omega) {
   }
   L.wd_fast = omega / (L.W.at(Key(0, 0)) * L.s);
   const int R = std::max(L.rx, L.ry);
+  const int e = n - L.per;  // last lattice index a fast stencil may reach
+  const int lo = 1 - L.per;  // first unknown index
   L.small = (n <= 4 * R + 4) ? 1 : 0;
   L.clsw = L.small ? n + 1 : 2 * L.rx + 1;
   const int clsh = L.small ? n + 1 : 2 * L.ry + 1;
@@ -198,7 +215,7 @@ void build_classes(HostLevel& L, double omega) {
   L.cls_wd.assign(L.ncls, 0.0);
   auto rep = [&](int c, int r) -> int {  // representative coordinate of class c
     if (c < r) return c;
-    if (c > r) return n - (2 * r - c);
+    if (c > r) return e - (2 * r - c);
     return n / 2;
   };
   for (int cy = 0; cy < clsh; ++cy)
@@ -206,9 +223,9 @@ void build_classes(HostLevel& L, double omega) {
       const int i = L.small ? cx : rep(cx, L.rx);
       const int j = L.small ? cy : rep(cy, L.ry);
       const int k = cy * L.clsw + cx;
-      if (i <= 0 || i >= n || j <= 0 || j >= n) continue;
+      if (i < lo || i >= n || j < lo || j >= n) continue;
       if (L.small && L.shape.kind == kRot && ((i + j) & 1)) continue;
-      const Stencil row = fold_row(L.W, n, i, j);
+      const Stencil row = L.per ? wrap_row(L.W, n, i, j) : fold_row(L.W, n, i, j);
       L.cls[k] = make_int2((int)L.tdx.size(), (int)row.size());
       double diag = 0.0;
       for (const auto& t : row) {
@@ -235,6 +252,10 @@ LevelDev<T> to_dev(const HostLevel& L) {
   d.ry = L.ry;
   d.small = L.small;
   d.clsw = L.clsw;
+  d.per = L.per;
+  d.lo = 1 - L.per;
+  d.fxe = L.shape.n - L.per - L.rx;
+  d.fye = L.shape.n - L.per - L.ry;
   d.wd = (T)L.wd_fast;
   for (int k = 0; k < d.nt; ++k) {
     d.c[k] = (T)L.c[k];
@@ -263,6 +284,7 @@ struct Hier {
   std::vector<T*> u, t, f, d;  // FP64 level 0: u and f are the caller's
   int64_t coarsest_idx = 0;
   T coarsest_a = T(1);
+  int coarsest_zero = 0;  // periodic: the coarsest single node's zero-mean solution is 0
   // small-level tail (one thread block runs the sub-cycle from tail_level down)
   int tail_level = -1;
   TailDesc<T>* d_tail = nullptr;
@@ -353,6 +375,10 @@ struct Bracket {
 
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// Lattice size of the coarsest axis level: n_min (Dirichlet: one interior unknown at
+// n = 2), or 1 for periodic hierarchies (a single node).
+int coarsest_n(const mg_options& o) { return o.boundary == MG_BOUNDARY_PERIODIC ? 1 : o.n_min; }
+
 mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op, const mg_options& o) {
   if (!grid || !pow2(grid->n) || grid->n < 4 || grid->n > 16384) return MG_ERR_INVALID;
   if (order != 2 && order != 4 && order != 6) return MG_ERR_INVALID;
@@ -368,6 +394,8 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
   if (o.sweep_kernel < 0 || o.sweep_kernel > 2) return MG_ERR_INVALID;
   if (o.bf16_levels < 0 || o.bf16_levels > 4) return MG_ERR_INVALID;
   if (o.bf16_levels > 0 && (o.precision != MG_PREC_MIXED_FP32 || o.sweep_kernel == 2)) return MG_ERR_UNSUPPORTED;
+  if (o.boundary != MG_BOUNDARY_DIRICHLET && o.boundary != MG_BOUNDARY_PERIODIC) return MG_ERR_INVALID;
+  if (o.boundary == MG_BOUNDARY_PERIODIC && o.sweep_kernel == 2) return MG_ERR_UNSUPPORTED;
   if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
   if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
   return MG_OK;
@@ -420,11 +448,17 @@ void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
   }
   for (int l = 0; l < nl; ++l) {
     HostLevel& L = h->host[l];
+    L.per = h->opt.boundary == MG_BOUNDARY_PERIODIC ? 1 : 0;
     L.rows = L.shape.n + 1;
     L.cols = storage_cols(L.shape.kind, L.shape.n);
     L.pitch = l == 0 ? L.cols : round_pitch(L.cols);
-    const int64_t m = L.shape.n - 1;
-    L.unknowns = L.shape.kind == kAxis ? m * m : (m * m + 1) / 2;
+    if (L.per) {
+      const int64_t m = L.shape.n;  // nodes 0 .. n-1; n even on rotated levels
+      L.unknowns = L.shape.kind == kAxis ? m * m : m * m / 2;
+    } else {
+      const int64_t m = L.shape.n - 1;
+      L.unknowns = L.shape.kind == kAxis ? m * m : (m * m + 1) / 2;
+    }
     build_classes(L, h->opt.omega);
   }
 }
@@ -656,7 +690,7 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
     LAUNCH(h, 1, launch_restrict<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, H.d[l], H.f[l + 1], c.s));
   }
   if (l + 1 == lmax) {
-    LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.f[lmax], H.u[lmax], c.s));
+    LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.coarsest_zero, H.f[lmax], H.u[lmax], c.s));
   } else {
     for (int g = 0; g < gamma_at(h, l); ++g)
       if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0)) != MG_OK) return st;
@@ -797,6 +831,7 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
   td.smoother = h->opt.smoother;
   td.coarsest_idx = H.coarsest_idx;
   td.coarsest_a = H.coarsest_a;
+  td.coarsest_zero = H.coarsest_zero;
   std::vector<int4> prog;
   emit_tail(h, lt, true, prog);
   mg_status st;
@@ -875,6 +910,7 @@ void mg_default_options(mg_options* o) {
   o->tail_ctas = 0;
   o->sweep_kernel = 0;
   o->bf16_levels = 0;
+  o->boundary = MG_BOUNDARY_DIRICHLET;
 }
 
 const char* mg_status_string(mg_status s) {
@@ -897,7 +933,7 @@ size_t mg_workspace_bytes(const mg_grid* grid, int order, mg_coarsening coarseni
   mg_options o;
   if (opt) o = *opt; else mg_default_options(&o);
   if (validate(grid, order, coarsening, coarse_op, o) != MG_OK) return 0;
-  const auto shapes = level_shapes(grid->n, coarsening, o.n_min, o.max_levels);
+  const auto shapes = level_shapes(grid->n, coarsening, coarsest_n(o), o.max_levels);
   size_t bytes = 0;
   for (size_t l = 0; l < shapes.size(); ++l) {
     const size_t rows = shapes[l].n + 1;
@@ -925,7 +961,7 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   h->coarsening = coarsening;
   h->coarse_op = coarse_op;
   h->opt = o;
-  const auto shapes = level_shapes(h->N, coarsening, o.n_min, o.max_levels);
+  const auto shapes = level_shapes(h->N, coarsening, coarsest_n(o), o.max_levels);
   build_operators(h, shapes);
   const int nl = (int)shapes.size();
   for (int l = 0; l + 1 < nl; ++l) h->transfer.push_back(transfer_of(coarsening, l, shapes[l].kind));
@@ -940,11 +976,14 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
     return fail(MG_ERR_CUDA);
   const HostLevel& C = h->host.back();
   if (C.unknowns != 1) return fail(MG_ERR_UNSUPPORTED);
-  const int64_t cidx = (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
-  const double ca = fold_row(C.W, C.shape.n, 1, 1).at(Key(0, 0)) * C.s;
+  // Dirichlet: node (1, 1) with a_pp from its folded row; periodic: node (0, 0), whose
+  // row is zero (the zero-mean solution is 0)
+  const int64_t cidx = C.per ? 0 : (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
+  const double ca = C.per ? 1.0 : fold_row(C.W, C.shape.n, 1, 1).at(Key(0, 0)) * C.s;
   if ((st = alloc_hier<double>(h, /*caller_level0=*/true)) != MG_OK) return fail(st);
   h->h64.coarsest_idx = cidx;
   h->h64.coarsest_a = ca;
+  h->h64.coarsest_zero = C.per;
   auto tail_limit = [&](int64_t dflt) -> int64_t {
     return o.tail_unknowns < 0 ? 0 : (o.tail_unknowns > 0 ? (int64_t)o.tail_unknowns : dflt);
   };
@@ -953,6 +992,7 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
     if ((st = alloc_hier<float>(h, false)) != MG_OK) return fail(st);
     h->h32.coarsest_idx = cidx;
     h->h32.coarsest_a = (float)ca;
+    h->h32.coarsest_zero = C.per;
     if (o.tail_unknowns == 0) st = build_tail<float>(h, 0, kTailSmemElemsFp32);
     else st = build_tail<float>(h, tail_limit(0));
     if (st != MG_OK) return fail(st);
@@ -986,6 +1026,7 @@ mg_status mg_get_level_info(const mg_handle* h, int level, mg_level_info* out) {
   out->pitch = L.pitch;
   out->unknowns = (int32_t)L.unknowns;
   out->nterms = (int32_t)L.c.size();
+  out->periodic = L.per;
   return MG_OK;
 }
 
@@ -993,7 +1034,7 @@ mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out
   if (!h || !u || !f) return MG_ERR_INVALID;
   StreamScope scope(h, stream);
   Ctx c{h, scope.s, h->opt.fma_contract == 0};
-  LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
+  if (!h->host[0].per) LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   mg_status st;
   double fn2;
   if (h->opt.precision == MG_PREC_MIXED_FP32) {
@@ -1022,7 +1063,7 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
   if (!h || !u || !f || max_cycles < 0 || !(rtol >= 0.0)) return MG_ERR_INVALID;
   StreamScope scope(h, stream);
   Ctx c{h, scope.s, h->opt.fma_contract == 0};
-  LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
+  if (!h->host[0].per) LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   double fn2, rr;
   mg_status st = f_norm2(h, c.s, f, &fn2);
   if (st != MG_OK) return st;
@@ -1416,7 +1457,9 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) 
     if (o.precision != o0.precision || o.nu1 != o0.nu1 || o.nu2 != o0.nu2 || o.fma_contract != o0.fma_contract ||
         (o.precision == MG_PREC_MIXED_FP32 && o.inner_cycles != o0.inner_cycles))
       return MG_ERR_INVALID;  // one schedule for the whole batch
-    if (o.gamma != 1 || o.smoother != MG_SMOOTH_REDBLACK || o.bf16_levels != 0) return MG_ERR_UNSUPPORTED;
+    if (o.gamma != 1 || o.smoother != MG_SMOOTH_REDBLACK || o.bf16_levels != 0 ||
+        o.boundary != MG_BOUNDARY_DIRICHLET)
+      return MG_ERR_UNSUPPORTED;
     if ((int)h->host.size() > kTailMaxLevels) return MG_ERR_UNSUPPORTED;
   }
   mg_batch* b = new (std::nothrow) mg_batch();

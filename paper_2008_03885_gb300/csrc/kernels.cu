@@ -78,7 +78,7 @@ __device__ __forceinline__ bool thread_node(const LevelDev<T>& L, int& i, int& j
 
 template <typename T>
 __device__ __forceinline__ bool interior(const LevelDev<T>& L, int i, int j) {
-  return i > 0 && i < L.n && j > 0 && j < L.n;
+  return i >= L.lo && i < L.n && j >= L.lo && j < L.n;
 }
 
 template <typename T>
@@ -90,14 +90,15 @@ __device__ __forceinline__ bool is_red(const LevelDev<T>& L, int i, int j) {
 template <typename T>
 __device__ __forceinline__ int class_of(const LevelDev<T>& L, int i, int j) {
   if (L.small) return j * L.clsw + i;
-  const int cx = i < L.rx ? i : (i > L.n - L.rx ? 2 * L.rx - (L.n - i) : L.rx);
-  const int cy = j < L.ry ? j : (j > L.n - L.ry ? 2 * L.ry - (L.n - j) : L.ry);
+  const int e = L.n - L.per;  // last lattice index a fast stencil may reach
+  const int cx = i < L.rx ? i : (i > e - L.rx ? 2 * L.rx - (e - i) : L.rx);
+  const int cy = j < L.ry ? j : (j > e - L.ry ? 2 * L.ry - (e - j) : L.ry);
   return cy * L.clsw + cx;
 }
 
 template <typename T>
 __device__ __forceinline__ bool fast_node(const LevelDev<T>& L, int i, int j) {
-  return i >= L.rx && i <= L.n - L.rx && j >= L.ry && j <= L.n - L.ry;
+  return i >= L.rx && i <= L.fxe && j >= L.ry && j <= L.fye;
 }
 
 // (L u)(i, j) and the node's omega / a_pp.
@@ -159,7 +160,15 @@ __device__ __forceinline__ T relax_fast(const T (&c)[NT], const int (&dl)[NT], T
   return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
 }
 
-template <typename T, bool EXACT, int NT>
+// fast_node with the boundary kind fixed at compile time (the NT kernels run at the
+// register limit; constant bounds keep the Dirichlet instantiation free of spills).
+template <bool PER, typename T>
+__device__ __forceinline__ bool fast_node_c(const LevelDev<T>& L, int i, int j) {
+  const int e = L.n - (PER ? 1 : 0);
+  return i >= L.rx && i <= e - L.rx && j >= L.ry && j <= e - L.ry;
+}
+
+template <typename T, bool EXACT, int NT, bool PER>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
                                 const T* __restrict__ f, T* __restrict__ uout, int red) {
   constexpr int kRows = RowsPer<T>::value;
@@ -174,6 +183,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
   }
   const T wd = L.wd;
   const int n = L.n;
+  constexpr int lo = PER ? 0 : 1;
   const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
   if (L.kind == kAxis) {
     const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
@@ -181,15 +191,15 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = jb + r * kBY;
-      if (j <= 0 || j >= n) continue;
+      if (j < lo || j >= n) continue;
       const int i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;
       const int ic = 2 * i0 + 1 - i;
       const int64_t row = (int64_t)j * L.pitch;
-      if (ic > 0 && ic < n) uout[row + ic] = uin[row + ic];
-      if (i <= 0 || i >= n) continue;
+      if (ic >= lo && ic < n) uout[row + ic] = uin[row + ic];
+      if (i < lo || i >= n) continue;
       const int64_t at = row + i;
-      uout[at] = rnd(L, fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
-                                           : relax_value<T, EXACT>(L, uin, f, i, j, at));
+      uout[at] = rnd(L, fast_node_c<PER>(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
+                                                  : relax_value<T, EXACT>(L, uin, f, i, j, at));
     }
   } else {
     const int q = blockIdx.x * kBX + threadIdx.x;
@@ -197,21 +207,21 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = jb + r * kBY;
-      if (j <= 0 || j >= n) continue;
+      if (j < lo || j >= n) continue;
       const int i = 2 * q + (j & 1);
-      if (i <= 0 || i >= n) continue;
+      if (i < lo || i >= n) continue;
       const int64_t at = (int64_t)j * L.pitch + q;
       if ((i & 1) != red) {
         uout[at] = uin[at];
         continue;
       }
-      uout[at] = rnd(L, fast_node(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
-                                           : relax_value<T, EXACT>(L, uin, f, i, j, at));
+      uout[at] = rnd(L, fast_node_c<PER>(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
+                                                  : relax_value<T, EXACT>(L, uin, f, i, j, at));
     }
   }
 }
 
-template <typename T, bool EXACT, int NT>
+template <typename T, bool EXACT, int NT, bool PER>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
                               const T* __restrict__ f, T* __restrict__ d) {
   constexpr int kRows = RowsPer<T>::value;
@@ -225,18 +235,19 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_nt(
     d1[k] = L.delta[1][k];
   }
   const int n = L.n;
+  constexpr int lo = PER ? 0 : 1;
   const int q = blockIdx.x * kBX + threadIdx.x;
   if (q >= L.cols) return;
   const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
     const int j = jb + r * kBY;
-    if (j <= 0 || j >= n) continue;
+    if (j < lo || j >= n) continue;
     const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
-    if (i <= 0 || i >= n) continue;
+    if (i < lo || i >= n) continue;
     const int64_t at = (int64_t)j * L.pitch + q;
-    const T s = fast_node(L, i, j) ? apply_fast<T, EXACT, NT>(c, (L.kind == kRot && (i & 1)) ? d1 : d0, u, at)
-                                   : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
+    const T s = fast_node_c<PER>(L, i, j) ? apply_fast<T, EXACT, NT>(c, (L.kind == kRot && (i & 1)) ? d1 : d0, u, at)
+                                          : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
     d[at] = rnd(L, Arith<T>::sub(f[at], s));
   }
 }
@@ -279,14 +290,15 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_g
   if (L.kind == kAxis) {
     const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
     j = blockIdx.y * kBY + threadIdx.y;
-    if (j <= 0 || j >= L.n || i0 > L.n) return;
+    const int lo = L.lo;
+    if (j < lo || j >= L.n || i0 > L.n) return;
     i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;
     const int ic = 2 * i0 + 1 - i;
-    if (ic > 0 && ic < L.n) {
+    if (ic >= lo && ic < L.n) {
       const int64_t ac = sidx(L, ic, j);
       uout[ac] = uin[ac];
     }
-    if (i <= 0 || i >= L.n) return;
+    if (i < lo || i >= L.n) return;
   } else {
     if (!thread_node(L, i, j) || !interior(L, i, j)) return;
     if (is_red(L, i, j) != red) {
@@ -490,47 +502,165 @@ __constant__ RTerm c_rterms_std[9] = {{-1, -1, 0.0625}, {0, -1, 0.125}, {1, -1, 
                                       {-1, 0, 0.125},   {0, 0, 0.25},   {1, 0, 0.125},
                                       {-1, 1, 0.0625},  {0, 1, 0.125},  {1, 1, 0.0625}};
 
-// Restricted residual at coarse node (i, j) (coarse-level lattice).
-template <typename T, bool EXACT>
-__device__ __forceinline__ T restrict_value(const LevelDev<T>& Lf, int transfer, const T* __restrict__ d,
-                                            int i, int j) {
-  // fine-lattice position of the coarse node
-  const int fi = transfer == kRbAxisToRot ? i : 2 * i;
-  const int fj = transfer == kRbAxisToRot ? j : 2 * j;
+// Storage position of lattice node (i, j): in the level's global storage, or in the
+// compact rows x cols layout of the shared-memory tail.
+template <typename T>
+__device__ __forceinline__ int smem_idx(const LevelDev<T>& L, int i, int j) {
+  return j * L.cols + (L.kind == kRot ? (i >> 1) : i);
+}
+struct GlobalIdx {
+  template <typename T>
+  __device__ __forceinline__ int64_t operator()(const LevelDev<T>& L, int i, int j) const { return sidx(L, i, j); }
+};
+struct SmemIdx {
+  template <typename T>
+  __device__ __forceinline__ int64_t operator()(const LevelDev<T>& L, int i, int j) const { return smem_idx(L, i, j); }
+};
+
+// Periodic transfers: terms (lattice i, j, weight) on level L wrap modulo L.n, are
+// ordered by storage position (which is the row-major column order) and terms that
+// land on the same node merge by adding their weights (powers of two and their
+// small sums, so the merged weight is exact); then the usual ordered sum.
+constexpr int kMaxTransferTerms = 9;
+template <typename T, bool EXACT, class Idx>
+__device__ __forceinline__ T wrapped_sum(const LevelDev<T>& L, int nt, const int* ti, const int* tj, const T* w,
+                         const T* __restrict__ x, Idx idx) {
+  int64_t pos[kMaxTransferTerms];
+  T wt[kMaxTransferTerms];
+  int m = 0;
+  for (int k = 0; k < nt; ++k) {
+    int a = ti[k] % L.n;
+    if (a < 0) a += L.n;
+    int b = tj[k] % L.n;
+    if (b < 0) b += L.n;
+    const int64_t p = idx(L, a, b);
+    int q = 0;
+    while (q < m && pos[q] < p) ++q;
+    if (q < m && pos[q] == p) {
+      wt[q] = Arith<T>::add(wt[q], w[k]);
+      continue;
+    }
+    for (int r = m; r > q; --r) {
+      pos[r] = pos[r - 1];
+      wt[r] = wt[r - 1];
+    }
+    pos[q] = p;
+    wt[q] = w[k];
+    ++m;
+  }
+  T s = Arith<T>::mul(wt[0], x[pos[0]]);
+  for (int k = 1; k < m; ++k) s = madd<T, EXACT>(s, wt[k], x[pos[k]]);
+  return s;
+}
+
+// Restriction from a periodic level.
+template <typename T, bool EXACT, class Idx>
+__device__ __forceinline__ T restrict_wrapped(const LevelDev<T>& Lf, int transfer, const T* __restrict__ d,
+                                           int fi, int fj, Idx idx) {
   const RTerm* rt = transfer == kRbAxisToRot ? c_rterms_rb_axis
                     : transfer == kRbRotToAxis ? c_rterms_rb_rot
                                                : c_rterms_std;
   const int nt = transfer == kStandard ? 9 : 5;
-  T s = Arith<T>::mul(T(rt[0].w), d[sidx(Lf, fi + rt[0].dx, fj + rt[0].dy)]);
-  for (int k = 1; k < nt; ++k) s = madd<T, EXACT>(s, T(rt[k].w), d[sidx(Lf, fi + rt[k].dx, fj + rt[k].dy)]);
+  int ti[kMaxTransferTerms], tj[kMaxTransferTerms];
+  T w[kMaxTransferTerms];
+  for (int k = 0; k < nt; ++k) {
+    ti[k] = fi + rt[k].dx;
+    tj[k] = fj + rt[k].dy;
+    w[k] = T(rt[k].w);
+  }
+  return wrapped_sum<T, EXACT>(Lf, nt, ti, tj, w, d, idx);
+}
+
+// Restricted residual at coarse node (i, j) (coarse-level lattice). PER: the levels
+// are periodic (a compile-time choice, so that the Dirichlet kernels carry none of
+// the wrap-around code).
+template <typename T, bool EXACT, bool PER, class Idx = GlobalIdx>
+__device__ __forceinline__ T restrict_value(const LevelDev<T>& Lf, int transfer, const T* __restrict__ d,
+                                            int i, int j, Idx idx = Idx()) {
+  // fine-lattice position of the coarse node
+  const int fi = transfer == kRbAxisToRot ? i : 2 * i;
+  const int fj = transfer == kRbAxisToRot ? j : 2 * j;
+  if (PER) return restrict_wrapped<T, EXACT>(Lf, transfer, d, fi, fj, idx);
+  const RTerm* rt = transfer == kRbAxisToRot ? c_rterms_rb_axis
+                    : transfer == kRbRotToAxis ? c_rterms_rb_rot
+                                               : c_rterms_std;
+  const int nt = transfer == kStandard ? 9 : 5;
+  T s = Arith<T>::mul(T(rt[0].w), d[idx(Lf, fi + rt[0].dx, fj + rt[0].dy)]);
+  for (int k = 1; k < nt; ++k) s = madd<T, EXACT>(s, T(rt[k].w), d[idx(Lf, fi + rt[k].dx, fj + rt[k].dy)]);
   return s;
 }
 
-// Interpolated correction (P v)(i, j) at fine node (i, j).
-template <typename T, bool EXACT>
+// Coarse terms (lattice i, j, weight) of the interpolated value at fine node (i, j),
+// in row-major order of the coarse nodes before any wrap-around.
+template <typename T>
+__device__ __forceinline__ int prolong_terms(int transfer, int i, int j, int* ti, int* tj, T* w) {
+  if (transfer == kRbAxisToRot) {
+    if (((i + j) & 1) == 0) {
+      ti[0] = i; tj[0] = j; w[0] = T(1);
+      return 1;
+    }
+    const int di[4] = {0, -1, 1, 0}, dj[4] = {-1, 0, 0, 1};
+    for (int k = 0; k < 4; ++k) { ti[k] = i + di[k]; tj[k] = j + dj[k]; w[k] = T(0.25); }
+    return 4;
+  }
+  if (transfer == kRbRotToAxis) {
+    if ((i & 1) == 0) {
+      ti[0] = i >> 1; tj[0] = j >> 1; w[0] = T(1);
+      return 1;
+    }
+    const int i0 = (i - 1) >> 1, i1 = (i + 1) >> 1, j0 = (j - 1) >> 1, j1 = (j + 1) >> 1;
+    ti[0] = i0; tj[0] = j0; ti[1] = i1; tj[1] = j0; ti[2] = i0; tj[2] = j1; ti[3] = i1; tj[3] = j1;
+    for (int k = 0; k < 4; ++k) w[k] = T(0.25);
+    return 4;
+  }
+  const int nx = (i & 1) ? 2 : 1, ny = (j & 1) ? 2 : 1;
+  const T wv = Arith<T>::mul((i & 1) ? T(0.5) : T(1), (j & 1) ? T(0.5) : T(1));  // exact
+  int m = 0;
+  for (int b = 0; b < ny; ++b)
+    for (int a = 0; a < nx; ++a) {
+      ti[m] = (i & 1) ? ((i - 1) >> 1) + a : i >> 1;
+      tj[m] = (j & 1) ? ((j - 1) >> 1) + b : j >> 1;
+      w[m++] = wv;
+    }
+  return m;
+}
+
+// Interpolation from a periodic coarse level.
+template <typename T, bool EXACT, class Idx>
+__device__ __forceinline__ T prolong_wrapped(const LevelDev<T>& Lc, int transfer, const T* __restrict__ vc,
+                                          int i, int j, Idx idx) {
+  int ti[4], tj[4];
+  T w[4];
+  const int nt = prolong_terms<T>(transfer, i, j, ti, tj, w);
+  return wrapped_sum<T, EXACT>(Lc, nt, ti, tj, w, vc, idx);
+}
+
+// Interpolated correction (P v)(i, j) at fine node (i, j) (PER as in restrict_value).
+template <typename T, bool EXACT, bool PER, class Idx = GlobalIdx>
 __device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, const T* __restrict__ vc,
-                                           int i, int j) {
+                                           int i, int j, Idx idx = Idx()) {
+  if (PER) return prolong_wrapped<T, EXACT>(Lc, transfer, vc, i, j, idx);
   T e;
   if (transfer == kRbAxisToRot) {
     if (((i + j) & 1) == 0) {
-      e = vc[sidx(Lc, i, j)];
+      e = vc[idx(Lc, i, j)];
     } else {
       const T q = T(0.25);
-      e = Arith<T>::mul(q, vc[sidx(Lc, i, j - 1)]);
-      e = madd<T, EXACT>(e, q, vc[sidx(Lc, i - 1, j)]);
-      e = madd<T, EXACT>(e, q, vc[sidx(Lc, i + 1, j)]);
-      e = madd<T, EXACT>(e, q, vc[sidx(Lc, i, j + 1)]);
+      e = Arith<T>::mul(q, vc[idx(Lc, i, j - 1)]);
+      e = madd<T, EXACT>(e, q, vc[idx(Lc, i - 1, j)]);
+      e = madd<T, EXACT>(e, q, vc[idx(Lc, i + 1, j)]);
+      e = madd<T, EXACT>(e, q, vc[idx(Lc, i, j + 1)]);
     }
   } else if (transfer == kRbRotToAxis) {
     if ((i & 1) == 0) {
-      e = vc[sidx(Lc, i >> 1, j >> 1)];
+      e = vc[idx(Lc, i >> 1, j >> 1)];
     } else {
       const T q = T(0.25);
       const int i0 = (i - 1) >> 1, i1 = (i + 1) >> 1, j0 = (j - 1) >> 1, j1 = (j + 1) >> 1;
-      e = Arith<T>::mul(q, vc[sidx(Lc, i0, j0)]);
-      e = madd<T, EXACT>(e, q, vc[sidx(Lc, i1, j0)]);
-      e = madd<T, EXACT>(e, q, vc[sidx(Lc, i0, j1)]);
-      e = madd<T, EXACT>(e, q, vc[sidx(Lc, i1, j1)]);
+      e = Arith<T>::mul(q, vc[idx(Lc, i0, j0)]);
+      e = madd<T, EXACT>(e, q, vc[idx(Lc, i1, j0)]);
+      e = madd<T, EXACT>(e, q, vc[idx(Lc, i0, j1)]);
+      e = madd<T, EXACT>(e, q, vc[idx(Lc, i1, j1)]);
     }
   } else {
     int xs[2], ys[2];
@@ -545,7 +675,7 @@ __device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, 
     e = T(0);
     for (int b = 0; b < ny; ++b)
       for (int a = 0; a < nx; ++a) {
-        const T x = vc[sidx(Lc, xs[a], ys[b])];
+        const T x = vc[idx(Lc, xs[a], ys[b])];
         e = first ? Arith<T>::mul(w, x) : madd<T, EXACT>(e, w, x);
         first = false;
       }
@@ -553,28 +683,30 @@ __device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, 
   return e;
 }
 
-template <typename T, bool EXACT>
+template <typename T, bool EXACT, bool PER>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
                            int transfer, const T* __restrict__ d, T* __restrict__ fc) {
   const LevelDev<T>& Lc = *Lcp;
   int i, j;
   if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
-  fc[sidx(Lc, i, j)] = rnd(Lc, restrict_value<T, EXACT>(*Lfp, transfer, d, i, j));
+  fc[sidx(Lc, i, j)] = rnd(Lc, restrict_value<T, EXACT, PER>(*Lfp, transfer, d, i, j));
 }
 
-template <typename T, bool EXACT>
+template <typename T, bool EXACT, bool PER>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
                               int transfer, const T* uin, T* uf, const T* __restrict__ vc) {
   const LevelDev<T>& Lf = *Lfp;
   int i, j;
   if (!thread_node(Lf, i, j) || !interior(Lf, i, j)) return;
   const int64_t at = sidx(Lf, i, j);
-  uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_value<T, EXACT>(*Lcp, transfer, vc, i, j)));
+  uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_value<T, EXACT, PER>(*Lcp, transfer, vc, i, j)));
 }
 
+// Exact solve on the one-unknown coarsest level: u = f / a_pp (Dirichlet), or the
+// zero-mean solution u = 0 of a periodic single node, whose operator row is zero.
 template <typename T>
-__global__ void k_coarsest(int64_t idx, T a, const T* __restrict__ f, T* __restrict__ u) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) u[idx] = Arith<T>::div(f[idx], a);
+__global__ void k_coarsest(int64_t idx, T a, int zero_mean, const T* __restrict__ f, T* __restrict__ u) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) u[idx] = zero_mean ? T(0) : Arith<T>::div(f[idx], a);
 }
 
 // Block-wide sum of a double (blockDim = kBX * kBY = 256 threads).
@@ -762,10 +894,13 @@ __global__ void __launch_bounds__(kTailThreads)
       const int ctot = Lc.rows * Lc.cols;
       for (int k = tid; k < ctot; k += nth) {
         if (!tail_node(Lc, k, i, j)) continue;
-        Fc[sidx(Lc, i, j)] = restrict_value<T, EXACT>(L, D->transfer[l], Dd, i, j);
+        Fc[sidx(Lc, i, j)] = L.per ? restrict_value<T, EXACT, true>(L, D->transfer[l], Dd, i, j)
+                                   : restrict_value<T, EXACT, false>(L, D->transfer[l], Dd, i, j);
       }
     } else if (op.x == kOpCoarsest) {
-      if (tid == 0) D->u[l][D->coarsest_idx] = Arith<T>::div(D->f[l][D->coarsest_idx], D->coarsest_a);
+      if (tid == 0)
+        D->u[l][D->coarsest_idx] =
+            D->coarsest_zero ? T(0) : Arith<T>::div(D->f[l][D->coarsest_idx], D->coarsest_a);
     } else {  // kOpProlong
       const LevelDev<T>& Lc = *D->L[l + 1];
       T* U = D->u[l];
@@ -773,7 +908,8 @@ __global__ void __launch_bounds__(kTailThreads)
       for (int k = tid; k < total; k += nth) {
         if (!tail_node(L, k, i, j)) continue;
         const int64_t at = sidx(L, i, j);
-        U[at] = Arith<T>::add(U[at], prolong_value<T, EXACT>(Lc, D->transfer[l], V, i, j));
+        U[at] = Arith<T>::add(U[at], Lc.per ? prolong_value<T, EXACT, true>(Lc, D->transfer[l], V, i, j)
+                                            : prolong_value<T, EXACT, false>(Lc, D->transfer[l], V, i, j));
       }
     }
     cluster.sync();
@@ -830,10 +966,10 @@ __global__ void __launch_bounds__(kBX * kBY)
           B.d[at] = Arith<T>::sub(B.f[at], apply_at<T, EXACT>(L, B.u, i, j, at, nullptr));
           break;
         case kBRestrict:
-          B.fc[at] = restrict_value<T, EXACT>(*B.L, B.transfer, B.d, i, j);
+          B.fc[at] = restrict_value<T, EXACT, false>(*B.L, B.transfer, B.d, i, j);
           break;
         default:  // kBProlong
-          B.u[at] = Arith<T>::add(B.u[at], prolong_value<T, EXACT>(*B.Lc, B.transfer, B.uc, i, j));
+          B.u[at] = Arith<T>::add(B.u[at], prolong_value<T, EXACT, false>(*B.Lc, B.transfer, B.uc, i, j));
           break;
       }
     }
@@ -925,11 +1061,6 @@ __global__ void __launch_bounds__(kBX * kBY)
 // Levels from sm_top down live in one block's shared memory in a compact rows x cols
 // layout; node (i, j) of a level is at j * cols + (rot ? i >> 1 : i). Arithmetic
 // per node is the same as relax_value / apply_at / restrict_value / prolong_value.
-template <typename T>
-__device__ __forceinline__ int smem_idx(const LevelDev<T>& L, int i, int j) {
-  return j * L.cols + (L.kind == kRot ? (i >> 1) : i);
-}
-
 template <typename T, bool EXACT>
 __device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i, int j, T* wd) {
   T s;
@@ -1022,19 +1153,15 @@ __global__ void __launch_bounds__(kTailThreads)
       const LevelDev<T>& Lc = *D->L[l + 1];
       T* Fc = sm + D->sm_f[l + 1];
       const int tr = D->transfer[l];
-      const RTerm* rt = tr == kRbAxisToRot ? c_rterms_rb_axis : tr == kRbRotToAxis ? c_rterms_rb_rot : c_rterms_std;
-      const int nt = tr == kStandard ? 9 : 5;
       for (int k = tid; k < Lc.rows * Lc.cols; k += kTailThreads) {
         if (!tail_node(Lc, k, i, j)) continue;
-        const int fi = tr == kRbAxisToRot ? i : 2 * i, fj = tr == kRbAxisToRot ? j : 2 * j;
-        T s = Arith<T>::mul(T(rt[0].w), Dd[smem_idx(L, fi + rt[0].dx, fj + rt[0].dy)]);
-        for (int t = 1; t < nt; ++t) s = madd<T, EXACT>(s, T(rt[t].w), Dd[smem_idx(L, fi + rt[t].dx, fj + rt[t].dy)]);
-        Fc[k] = s;
+        Fc[k] = L.per ? restrict_value<T, EXACT, true>(L, tr, Dd, i, j, SmemIdx())
+                      : restrict_value<T, EXACT, false>(L, tr, Dd, i, j, SmemIdx());
       }
     } else if (op.x == kOpCoarsest) {
       if (tid == 0) {
-        const int c = smem_idx(L, 1, 1);
-        U[c] = Arith<T>::div(F[c], D->coarsest_a);
+        const int c = D->coarsest_zero ? smem_idx(L, 0, 0) : smem_idx(L, 1, 1);
+        U[c] = D->coarsest_zero ? T(0) : Arith<T>::div(F[c], D->coarsest_a);
       }
     } else {  // kOpProlong
       const LevelDev<T>& Lc = *D->L[l + 1];
@@ -1042,46 +1169,8 @@ __global__ void __launch_bounds__(kTailThreads)
       const int tr = D->transfer[l];
       for (int k = tid; k < total; k += kTailThreads) {
         if (!tail_node(L, k, i, j)) continue;
-        T e;
-        if (tr == kRbAxisToRot) {
-          if (((i + j) & 1) == 0) {
-            e = V[smem_idx(Lc, i, j)];
-          } else {
-            const T q = T(0.25);
-            e = Arith<T>::mul(q, V[smem_idx(Lc, i, j - 1)]);
-            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i - 1, j)]);
-            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i + 1, j)]);
-            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i, j + 1)]);
-          }
-        } else if (tr == kRbRotToAxis) {
-          if ((i & 1) == 0) {
-            e = V[smem_idx(Lc, i >> 1, j >> 1)];
-          } else {
-            const T q = T(0.25);
-            const int i0 = (i - 1) >> 1, i1 = (i + 1) >> 1, j0 = (j - 1) >> 1, j1 = (j + 1) >> 1;
-            e = Arith<T>::mul(q, V[smem_idx(Lc, i0, j0)]);
-            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i1, j0)]);
-            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i0, j1)]);
-            e = madd<T, EXACT>(e, q, V[smem_idx(Lc, i1, j1)]);
-          }
-        } else {
-          int xs[2], ys[2];
-          int nx, ny;
-          T wx, wy;
-          if (i & 1) { xs[0] = (i - 1) >> 1; xs[1] = (i + 1) >> 1; nx = 2; wx = T(0.5); }
-          else { xs[0] = i >> 1; xs[1] = xs[0]; nx = 1; wx = T(1); }
-          if (j & 1) { ys[0] = (j - 1) >> 1; ys[1] = (j + 1) >> 1; ny = 2; wy = T(0.5); }
-          else { ys[0] = j >> 1; ys[1] = ys[0]; ny = 1; wy = T(1); }
-          const T w = Arith<T>::mul(wx, wy);
-          bool first = true;
-          e = T(0);
-          for (int b = 0; b < ny; ++b)
-            for (int a = 0; a < nx; ++a) {
-              const T x = V[smem_idx(Lc, xs[a], ys[b])];
-              e = first ? Arith<T>::mul(w, x) : madd<T, EXACT>(e, w, x);
-              first = false;
-            }
-        }
+        const T e = Lc.per ? prolong_value<T, EXACT, true>(Lc, tr, V, i, j, SmemIdx())
+                           : prolong_value<T, EXACT, false>(Lc, tr, V, i, j, SmemIdx());
         U[k] = Arith<T>::add(U[k], e);
       }
     }
@@ -1117,8 +1206,14 @@ cudaError_t launch_half_sweep_nt(const LevelPair<T>& L, bool exact, const T* uin
   dim3 g = grid_of(L.h);
   if (L.h.kind == kAxis) g.x = ((L.h.n + 2) / 2 + kBX - 1) / kBX;  // pairs (2p, 2p+1), 2p <= n
   g.y = (L.h.rows + kBY * RowsPer<T>::value - 1) / (kBY * RowsPer<T>::value);
-  if (exact) k_half_sweep_nt<T, true, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
-  else k_half_sweep_nt<T, false, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
+  const dim3 b(kBX, kBY);
+  if (L.h.per) {
+    if (exact) k_half_sweep_nt<T, true, NT, true><<<g, b, 0, s>>>(L.d, uin, f, uout, red);
+    else k_half_sweep_nt<T, false, NT, true><<<g, b, 0, s>>>(L.d, uin, f, uout, red);
+  } else {
+    if (exact) k_half_sweep_nt<T, true, NT, false><<<g, b, 0, s>>>(L.d, uin, f, uout, red);
+    else k_half_sweep_nt<T, false, NT, false><<<g, b, 0, s>>>(L.d, uin, f, uout, red);
+  }
   return cudaGetLastError();
 }
 
@@ -1182,8 +1277,14 @@ template <typename T, int NT>
 cudaError_t launch_residual_nt(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d, cudaStream_t s) {
   dim3 g = grid_of(L.h);
   g.y = (L.h.rows + kBY * RowsPer<T>::value - 1) / (kBY * RowsPer<T>::value);
-  if (exact) k_residual_nt<T, true, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
-  else k_residual_nt<T, false, NT><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
+  const dim3 b(kBX, kBY);
+  if (L.h.per) {
+    if (exact) k_residual_nt<T, true, NT, true><<<g, b, 0, s>>>(L.d, u, f, d);
+    else k_residual_nt<T, false, NT, true><<<g, b, 0, s>>>(L.d, u, f, d);
+  } else {
+    if (exact) k_residual_nt<T, true, NT, false><<<g, b, 0, s>>>(L.d, u, f, d);
+    else k_residual_nt<T, false, NT, false><<<g, b, 0, s>>>(L.d, u, f, d);
+  }
   return cudaGetLastError();
 }
 
@@ -1201,22 +1302,35 @@ cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const
 template <typename T>
 cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
                             const T* d, T* fc, cudaStream_t s) {
-  if (exact) k_restrict<T, true><<<grid_of(Lc.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
-  else k_restrict<T, false><<<grid_of(Lc.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+  const dim3 g = grid_of(Lc.h), b(kBX, kBY);
+  if (Lf.h.per) {
+    if (exact) k_restrict<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    else k_restrict<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+  } else {
+    if (exact) k_restrict<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    else k_restrict<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer,
                                bool exact, T* uf, const T* vc, cudaStream_t s, const T* uin) {
-  if (exact) k_prolong_add<T, true><<<grid_of(Lf.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, uin ? uin : uf, uf, vc);
-  else k_prolong_add<T, false><<<grid_of(Lf.h), dim3(kBX, kBY), 0, s>>>(Lf.d, Lc.d, transfer, uin ? uin : uf, uf, vc);
+  const dim3 g = grid_of(Lf.h), b(kBX, kBY);
+  const T* ui = uin ? uin : uf;
+  if (Lc.h.per) {
+    if (exact) k_prolong_add<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+    else k_prolong_add<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+  } else {
+    if (exact) k_prolong_add<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+    else k_prolong_add<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_coarsest(int64_t idx, T a, const T* f, T* u, cudaStream_t s) {
-  k_coarsest<T><<<1, 32, 0, s>>>(idx, a, f, u);
+cudaError_t launch_coarsest(int64_t idx, T a, int zero_mean, const T* f, T* u, cudaStream_t s) {
+  k_coarsest<T><<<1, 32, 0, s>>>(idx, a, zero_mean, f, u);
   return cudaGetLastError();
 }
 
@@ -1384,7 +1498,7 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, const int4* 
   template cudaError_t launch_prolong_add<T>(const LevelPair<T>&, const LevelPair<T>&, int, bool, T*, \
                                              const T*, cudaStream_t, const T*);                       \
   template cudaError_t launch_sweep_fused<T>(const LevelPair<T>&, bool, const T*, const T*, T*, cudaStream_t); \
-  template cudaError_t launch_coarsest<T>(int64_t, T, const T*, T*, cudaStream_t);                    \
+  template cudaError_t launch_coarsest<T>(int64_t, T, int, const T*, T*, cudaStream_t);                    \
   template int resnorm_blocks<T>(const LevelPair<T>&);                                                \
   template cudaError_t launch_resnorm<T>(const LevelPair<T>&, bool, const T*, const T*, double*,     \
                                          double*, cudaStream_t);                                      \

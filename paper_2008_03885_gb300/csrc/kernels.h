@@ -36,7 +36,7 @@ template <typename T>
 cudaError_t launch_sweep_fused(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout,
                                cudaStream_t s);
 template <typename T>
-cudaError_t launch_coarsest(int64_t idx, T a, const T* f, T* u, cudaStream_t s);
+cudaError_t launch_coarsest(int64_t idx, T a, int zero_mean, const T* f, T* u, cudaStream_t s);
 
 // Sum of squares of d = f - L u over interior nodes of an axis level, in FP64:
 // per-block partial sums into `partial` (size >= resnorm_blocks(L)), then one
@@ -80,6 +80,7 @@ struct TailDesc {
   int32_t smoother;  // mg_smoother
   int64_t coarsest_idx;
   T coarsest_a;
+  int32_t coarsest_zero;  // periodic single node: the zero-mean solution 0
   // shared-memory-resident variant: per level, element offsets of u, t, f, d in the
   // block's shared memory (compact rows x cols layout) and the number of levels held
   int32_t sm_u[kTailMaxLevels], sm_t[kTailMaxLevels], sm_f[kTailMaxLevels], sm_d[kTailMaxLevels];

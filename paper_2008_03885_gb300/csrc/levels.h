@@ -21,15 +21,20 @@ enum Transfer : int32_t {
 //
 // Points live on an integer lattice (i, j), 0 <= i, j <= n. Axis levels hold every
 // node; rotated levels hold nodes with i + j even and store node (i, j) at column
-// i >> 1. Interior nodes are the unknowns; boundary entries of every array are 0.
+// i >> 1. Dirichlet (per = 0): interior nodes 0 < i, j < n are the unknowns and
+// boundary entries of every array are 0. Periodic (per = 1): nodes 0 <= i, j < n are
+// the unknowns (node n is node 0); row and column n are never read.
 //
-// The operator is a constant stencil (dx, dy, c) sorted by (dy, dx) for nodes whose
-// stencil stays inside [0, n]^2 ("fast" nodes: rx <= i <= n - rx, ry <= j <= n - ry).
-// Other nodes use a per-class merged term list: the stencil folded by odd
-// reflection at the boundary lines, duplicate columns summed, boundary columns
-// dropped, sorted by (dy, dx). A class is (cx, cy):
+// The operator is a constant stencil (dx, dy, c) sorted by (dy, dx) for "fast"
+// nodes, rx <= i <= n - per - rx (the same for j with ry): their stencil reaches no
+// ghost (Dirichlet) and does not wrap (periodic). Other nodes use a per-class merged
+// term list: the stencil folded by odd reflection at the boundary lines with
+// boundary columns dropped (Dirichlet) or wrapped modulo n (periodic; the stored
+// offsets are the wrapped ones), duplicate columns summed, sorted by (dy, dx), which
+// is the storage (column) order. A class is (cx, cy):
 //   small levels: cx = i, cy = j (table (n+1) x (n+1));
-//   otherwise: cx = i for i < rx, 2 rx - (n - i) for i > n - rx, rx in between.
+//   otherwise: cx = i for i < rx, 2 rx - (n - per - i) for i > n - per - rx, rx in
+//   between (single coordinates at both edges, so every class has one term list).
 template <typename T>
 struct LevelDev {
   int32_t kind, n, rows, cols, pitch;
@@ -46,6 +51,9 @@ struct LevelDev {
   const int32_t* tdy;
   const T* tc;
   int32_t bf16;  // FP32 inner levels: round every stored value to bfloat16 (storage trial)
+  int32_t per;   // 1: periodic level (see above)
+  int32_t lo;    // first unknown index: 1 - per
+  int32_t fxe, fye;  // last fast-node i and j: n - per - rx, n - per - ry
 };
 
 }  // namespace nsmg

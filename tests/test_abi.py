@@ -43,6 +43,7 @@ def test_status_strings_and_defaults(lib):
         assert mg._lib.mg_status_string(s)
     o = mg.mg_default_options()
     assert o.omega == 1.0 and o.nu1 == 1 and o.nu2 == 1 and o.gamma == 1 and o.n_min == 2
+    assert o.boundary == mg.MG_BOUNDARY_DIRICHLET
 
 
 def test_workspace_bytes_validates_without_gpu(lib):
@@ -51,6 +52,9 @@ def test_workspace_bytes_validates_without_gpu(lib):
     assert mg.mg_workspace_bytes(63) == 0  # not a power of two
     assert mg.mg_workspace_bytes(64, order=3) == 0 and mg.mg_workspace_bytes(64, order=6) > 0
     assert mg.mg_workspace_bytes(2) == 0
+    # periodic hierarchies coarsen to one node: more (tiny) levels, about the same bytes
+    bp, bd = mg.mg_workspace_bytes(64, boundary="periodic"), mg.mg_workspace_bytes(64)
+    assert bd < bp < 1.2 * bd
     # FP64 red-black V: roughly 2 arrays on level 0 plus 4 per coarse level
     b = mg.mg_workspace_bytes(1024)
     assert 2 * 1025 * 1025 * 8 <= b <= 12 * 1025 * 1025 * 8
@@ -67,4 +71,10 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert e.value.status == mg.MG_ERR_INVALID
     with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, n_min=8)
+    assert e.value.status == mg.MG_ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, boundary=2)
+    assert e.value.status == mg.MG_ERR_INVALID
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, boundary="periodic", sweep_kernel=2)
     assert e.value.status == mg.MG_ERR_UNSUPPORTED
