@@ -25,10 +25,15 @@ nonstandard coarsening", arXiv:2008.03885):
 * Transfers: red-black coarsening uses Eq. (transfer_r2) in each fine level's own
   frame: interpolation 1/4 ]. 1 .; 1 4 1; . 1 .[ and restriction R = 1/2 P^T;
   standard coarsening uses bilinear interpolation and full weighting R = 1/4 P^T,
-  Eq. (transfer_2d). Both are assembled here as explicit sparse matrices.
+  Eq. (transfer_2d), or (transfer_order = 4, Sec. "High-order accurate transfer
+  operators") cubic interpolation Eq. (interp_2d4o) with its adjoint restriction
+  Eq. (restr_2d4o), R = 1/4 P^T. The cubic stencil reaches coarse nodes beyond the
+  boundary; those ghosts are odd reflections (Dirichlet) or wrap (periodic), as for
+  the wide fine stencils. All are assembled here as explicit sparse matrices.
 * Coarse operators (Sec. 2.3 notation, Sec. 4.4): non-Galerkin = the 5-point
   stencil on the coarse grid with spacing H (Eq. L_H_2d; for fourth order this is
-  nG^(2)); Galerkin = the recursion L_{l+1} = R L_l P, Eq. (L_G_l), formed here by
+  nG^(2)); "non-Galerkin high" = the fine operator's own stencil with spacing H
+  (for fourth order nG^(4), Eq. L_H_4n_2d); Galerkin = the recursion L_{l+1} = R L_l P, Eq. (L_G_l), formed here by
   an explicit sparse product; for a fourth-order fine level the recursion starts
   from the second-order L_h^(2), Eq. (L_H_2G_2d), i.e. G^(2); "true high" starts it
   from the fourth-order L_h itself; G1 = the first-generation Galerkin stencil
@@ -43,8 +48,9 @@ nonstandard coarsening", arXiv:2008.03885):
   residual, restrict, recurse (zero initial guess, Eq. L_H_approx) or solve exactly
   on the coarsest level, interpolate, correct, post-smooth. A periodic operator is
   singular (the constants are its null space); its exact coarsest solve is the
-  minimum-norm (zero-mean) solution. Periodic hierarchies coarsen down to a single
-  node, whose operator row is zero and whose zero-mean solution is 0.
+  zero-mean solution, computed with the constant mode removed explicitly. Periodic
+  hierarchies coarsen down to a single node, whose operator row is zero (up to the
+  rounding of deep Galerkin products) and whose zero-mean solution is 0.
 
 Floating-point evaluation order (so that any implementation following the same
 order reproduces every iterate bit for bit): each operator application
@@ -71,6 +77,7 @@ GALERKIN = "galerkin"
 G1 = "g1"
 GN = "gn"
 TRUE_HIGH = "galerkin_true_high"
+NONGALERKIN_HIGH = "nongalerkin_high"
 
 # Stencils in a level's own frame, as {(a, b): weight}; a along the frame's first
 # axis, b along its second. Scales are applied separately.
@@ -192,10 +199,49 @@ def stencil_weights(level: Level, stencil: dict, factor: float) -> sp.csr_matrix
     return m
 
 
-def interpolation(fine: Level, coarse: Level, coarsening: str) -> sp.csr_matrix:
+def _cubic_interpolation(fine: Level, coarse: Level) -> sp.csr_matrix:
+    """Eq. (interp_2d4o): per axis, a fine node at an even position takes its coarse
+    node (weight 1); at an odd position the coarse nodes at fine offsets -3, -1, 1, 3
+    with weights -1/16, 9/16, 9/16, -1/16; the 2D weights are products. Ghost coarse
+    nodes: odd reflection with sign (Dirichlet; coarse boundary nodes carry nothing)
+    or wrap-around (periodic)."""
+    nc = coarse.n
+    taps = {0: ((0, 1.0),), 1: ((-3, -1.0 / 16), (-1, 9.0 / 16), (1, 9.0 / 16), (3, -1.0 / 16))}
+    rows, cols, vals = [], [], []
+    for px in (0, 1):
+        for py in (0, 1):
+            sel = np.nonzero((fine.pi % 2 == px) & (fine.pj % 2 == py))[0]
+            fi, fj = fine.pi[sel], fine.pj[sel]
+            for ox, wx in taps[px]:
+                for oy, wy in taps[py]:
+                    ci, cj = (fi + ox) // 2, (fj + oy) // 2
+                    if coarse.periodic:
+                        ci, cj = np.mod(ci, nc), np.mod(cj, nc)
+                        sign = np.ones(sel.size)
+                        keep = np.ones(sel.size, dtype=bool)
+                    else:
+                        ci, si, bi = fold(ci, nc)
+                        cj, sj, bj = fold(cj, nc)
+                        sign, keep = si * sj, ~(bi | bj)
+                    rows.append(sel[keep])
+                    cols.append(coarse.index[cj[keep], ci[keep]])
+                    vals.append(sign[keep] * (wx * wy))
+    m = sp.coo_matrix(
+        (np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+        shape=(fine.size, coarse.size),
+    ).tocsr()
+    m.sum_duplicates()
+    m.sort_indices()
+    return m
+
+
+def interpolation(fine: Level, coarse: Level, coarsening: str, order: int = 2) -> sp.csr_matrix:
     """Explicit interpolation P: coarse unknowns -> fine unknowns. Dirichlet: coarse
     boundary nodes contribute nothing; periodic: coarse positions wrap modulo the
     coarse lattice size."""
+    if order == 4:
+        assert coarsening == STANDARD
+        return _cubic_interpolation(fine, coarse)
     rows, cols, vals = [], [], []
     fi, fj = fine.pi, fine.pj
     nf, nc = fine.n, coarse.n
@@ -240,6 +286,53 @@ def interpolation(fine: Level, coarse: Level, coarsening: str) -> sp.csr_matrix:
     return m
 
 
+# ---- exact dyadic sparse products (Galerkin operators with cubic transfers) -------
+# A matrix is (rows, cols, numerators, e): entry = numerator / 2^e, numerators Python
+# integers (numpy object arrays), so products and sums are exact at any depth.
+def _exact_from(m: sp.csr_matrix, e: int):
+    c = m.tocoo()
+    num = np.array([int(v * 2 ** e) for v in c.data], dtype=object)
+    assert all(float(n) == v * 2 ** e for n, v in zip(num, c.data)), "not a multiple of 2^-e"
+    return c.row.astype(np.int64), c.col.astype(np.int64), num, e
+
+
+def _exact_mul(A, B, shape):
+    """Exact sparse product A B."""
+    ra, ca, na, ea = A
+    rb, cb, nb, eb = B
+    order = np.argsort(rb, kind="stable")
+    rb, cb, nb = rb[order], cb[order], nb[order]
+    ptr = np.searchsorted(rb, np.arange(shape[1] + 1))
+    cnt = ptr[ca + 1] - ptr[ca]
+    total = int(cnt.sum())
+    first = np.repeat(ptr[ca], cnt)
+    pos = first + np.arange(total) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    if total == 0:  # e.g. a periodic operator times the constant interpolation
+        return np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0, dtype=object), ea + eb
+    rows = np.repeat(ra, cnt)
+    cols = cb[pos]
+    vals = np.repeat(na, cnt) * nb[pos]
+    key = rows * shape[2] + cols
+    order = np.argsort(key, kind="stable")
+    key, vals = key[order], vals[order]
+    starts = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+    sums = np.add.reduceat(vals, starts)
+    keep = np.array([v != 0 for v in sums], dtype=bool)
+    k = key[starts][keep]
+    return k // shape[2], k % shape[2], sums[keep], ea + eb
+
+
+def _exact_round(E, shape) -> sp.csr_matrix:
+    """Each exact entry rounded once to the nearest double (int / int division is
+    correctly rounded)."""
+    r, c, num, e = E
+    vals = np.array([n / (1 << e) for n in num], dtype=np.float64)
+    m = sp.coo_matrix((vals, (r, c)), shape=shape).tocsr()
+    m.sum_duplicates()
+    m.sort_indices()
+    return m
+
+
 class Ell:
     """A CSR matrix as padded rows with sorted columns, applied in column order."""
 
@@ -276,6 +369,7 @@ class Options:
     gamma: int = 1  # 1 = V, 2 = W, 3 = "Wn" (2 on levels 0 and 1, 1 below; Sec. 4.4)
     smoother: str = "rb"  # "rb" or "jacobi"
     n_min: int | None = None  # coarsest axis lattice size: 2 (Dirichlet) / 1 (periodic) by default
+    transfer_order: int = 2  # 4: cubic transfers (standard coarsening only)
     max_levels: int | None = None
 
 
@@ -297,9 +391,11 @@ class Oracle:
         self.levels = [_make_level(k, m, r2, self.periodic) for k, m, r2 in
                        level_shapes(n, coarsening, n_min, self.opt.max_levels)]
         self.P, self.R = [], []
+        assert self.opt.transfer_order in (2, 4)
+        assert self.opt.transfer_order == 2 or coarsening == STANDARD
         for l in range(len(self.levels) - 1):
             step = coarsening if coarsening != VARIABLE else (REDBLACK if l < 2 else STANDARD)
-            P = interpolation(self.levels[l], self.levels[l + 1], step)
+            P = interpolation(self.levels[l], self.levels[l + 1], step, self.opt.transfer_order)
             R = (P.T * (0.5 if step == REDBLACK else 0.25)).tocsr()
             R.sort_indices()
             self.P.append(P)
@@ -320,15 +416,30 @@ class Oracle:
             else:
                 base_W, base_s = stencil_weights(L0, FIVE_POINT, 1.0), s2  # L_h^(2)
         gal_W = base_W
+        # Cubic transfers: the Galerkin recursion is formed exactly (its dyadic
+        # coefficients outgrow 53 bits after three levels) and each level rounded once;
+        # with the other transfers the floating-point product below is already exact.
+        exact = self.opt.transfer_order == 4 and coarse_op in (GALERKIN, TRUE_HIGH, GN)
+        if exact:
+            gal_E = _exact_from(base_W, 0)
         for l in range(1, len(self.levels)):
             lev = self.levels[l]
-            gal_W = (self.R[l - 1] @ gal_W @ self.P[l - 1]).tocsr()
-            gal_W.sort_indices()
+            if exact:
+                nf, nc = self.levels[l - 1].size, lev.size
+                WP = _exact_mul(gal_E, _exact_from(self.P[l - 1], 8), (nf, nf, nc))
+                gal_E = _exact_mul(_exact_from(self.R[l - 1], 10), WP, (nc, nf, nc))
+                gal_W = _exact_round(gal_E, (nc, nc))
+            else:
+                gal_W = (self.R[l - 1] @ gal_W @ self.P[l - 1]).tocsr()
+                gal_W.sort_indices()
             hh = lev.h2  # (h_l / h_0)^2
             if coarse_op in (GALERKIN, TRUE_HIGH) or (coarse_op == GN and l == 1):
                 lev.W, lev.s = gal_W, base_s
             elif coarse_op == G1:
                 lev.W, lev.s = stencil_weights(lev, FIRST_GALERKIN, 1.0 / hh), s2
+            elif coarse_op == NONGALERKIN_HIGH:  # the fine stencil with spacing H (nG^(4) at order 4)
+                fine_st = {2: FIVE_POINT, 4: FOURTH_ORDER, 6: SIXTH_ORDER}[order]
+                lev.W, lev.s = stencil_weights(lev, fine_st, 1.0 / hh), L0.s
             else:  # non-Galerkin 5-point with spacing H = h_l
                 lev.W, lev.s = stencil_weights(lev, FIVE_POINT, 1.0 / hh), s2
         for lev in self.levels:
@@ -384,9 +495,13 @@ class Oracle:
 
     def coarse_solve(self, d: np.ndarray) -> np.ndarray:
         if self.periodic:
-            # singular (constants): the minimum-norm least-squares solution, which is
-            # the zero-mean solution of the compatible part of d
-            return np.linalg.lstsq(self._coarse_dense, d, rcond=None)[0]
+            # singular (constants): the zero-mean solution of A v = Q d, Q the projector
+            # onto zero-mean vectors, from the nonsingular (A + 1 1^T / m) v = Q d: its
+            # solution has 1^T v = 0 because 1^T A = 0. The constant mode is removed
+            # explicitly, so rounding left in a deep Galerkin operator's row sums
+            # cannot put a near-zero pivot on it (one node: v = 0).
+            m = d.size
+            return np.linalg.solve(self._coarse_dense + np.full((m, m), 1.0 / m), d - d.mean())
         if d.size == 1:
             return d / self._coarse_dense[0, 0]
         return np.linalg.solve(self._coarse_dense, d)
