@@ -82,7 +82,10 @@ typedef enum {
                                    recursion starts from L_h^(2) (G^(2), Eq. L_H_2G_2d) */
   MG_OP_GALERKIN_G1 = 2,        /* Eq. (L_G1) stencil on every coarse level (Sec. 4.4 "G1") */
   MG_OP_GALERKIN_GN = 3,        /* Galerkin on level 1, non-Galerkin below (Sec. 4.4 "Gn") */
-  MG_OP_GALERKIN_TRUE_HIGH = 4  /* Galerkin recursion from the order-4 operator itself */
+  MG_OP_GALERKIN_TRUE_HIGH = 4, /* Galerkin recursion from the order-4 (or 6) operator itself */
+  MG_OP_NONGALERKIN_HIGH = 5    /* the fine operator's own stencil with spacing H on every coarse
+                                   level: nG^(4) (Eq. L_H_4n_2d) for order 4, nG^(6) for order 6;
+                                   the same as MG_OP_NONGALERKIN for order 2 */
 } mg_coarse_op;
 
 typedef enum {
@@ -130,6 +133,14 @@ typedef struct {
                           arrays stay FP32, so this measures accuracy, not bandwidth) */
   int32_t boundary;    /* mg_boundary (default MG_BOUNDARY_DIRICHLET). Periodic is not
                           available with sweep_kernel = 2 or the batch API (MG_ERR_UNSUPPORTED) */
+  int32_t transfer_order; /* 2 (default): Eq. (transfer_2d) / (transfer_r2); 4: cubic
+                          interpolation and its adjoint restriction, the pair Eq. (interp_2d4o) /
+                          (restr_2d4o) (App. A), standard coarsening only (MG_ERR_UNSUPPORTED
+                          otherwise, and with the batch API). Ghost coarse nodes beyond the
+                          boundary are odd reflections (Dirichlet) or wrap (periodic). Galerkin
+                          coefficients over cubic transfers need more than 53 bits from the
+                          fourth coarse level on: the recursion is done exactly and each level
+                          rounded once to FP64 */
 } mg_options;
 
 typedef struct mg_handle mg_handle;

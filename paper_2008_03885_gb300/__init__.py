@@ -26,14 +26,16 @@ _lib = ctypes.CDLL(LIB_PATH)
 MG_OK, MG_ERR_INVALID, MG_ERR_UNSUPPORTED, MG_ERR_OOM, MG_ERR_BUDGET, MG_ERR_CUDA, \
     MG_ERR_NONFINITE, MG_ERR_NOT_CONVERGED, MG_ERR_TIMEOUT = range(9)
 MG_COARSEN_STANDARD, MG_COARSEN_REDBLACK, MG_COARSEN_VARIABLE = 0, 1, 2
-MG_OP_NONGALERKIN, MG_OP_GALERKIN, MG_OP_GALERKIN_G1, MG_OP_GALERKIN_GN, MG_OP_GALERKIN_TRUE_HIGH = range(5)
+(MG_OP_NONGALERKIN, MG_OP_GALERKIN, MG_OP_GALERKIN_G1, MG_OP_GALERKIN_GN, MG_OP_GALERKIN_TRUE_HIGH,
+ MG_OP_NONGALERKIN_HIGH) = range(6)
 MG_SMOOTH_REDBLACK, MG_SMOOTH_JACOBI = 0, 1
 MG_PREC_FP64, MG_PREC_MIXED_FP32 = 0, 1
 MG_BOUNDARY_DIRICHLET, MG_BOUNDARY_PERIODIC = 0, 1
 
 COARSENING = {"standard": MG_COARSEN_STANDARD, "redblack": MG_COARSEN_REDBLACK, "variable": MG_COARSEN_VARIABLE}
 COARSE_OP = {"nongalerkin": MG_OP_NONGALERKIN, "galerkin": MG_OP_GALERKIN, "g1": MG_OP_GALERKIN_G1,
-             "gn": MG_OP_GALERKIN_GN, "galerkin_true_high": MG_OP_GALERKIN_TRUE_HIGH}
+             "gn": MG_OP_GALERKIN_GN, "galerkin_true_high": MG_OP_GALERKIN_TRUE_HIGH,
+             "nongalerkin_high": MG_OP_NONGALERKIN_HIGH}
 
 
 class mg_grid(ctypes.Structure):
@@ -47,7 +49,7 @@ class mg_options(ctypes.Structure):
                 ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32),
                 ("tail_unknowns", ctypes.c_int32), ("tail_ctas", ctypes.c_int32),
                 ("sweep_kernel", ctypes.c_int32), ("bf16_levels", ctypes.c_int32),
-                ("boundary", ctypes.c_int32)]
+                ("boundary", ctypes.c_int32), ("transfer_order", ctypes.c_int32)]
 
 
 class mg_level_info(ctypes.Structure):

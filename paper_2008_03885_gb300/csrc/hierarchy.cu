@@ -58,6 +58,14 @@ const std::vector<std::pair<Key, double>> kFirstGalerkin = {  // Eq. (L_G1) time
 // Interpolation weights from a coarse node at fine-lattice position (0, 0) to fine
 // offsets (dx, dy) (Eq. transfer_r2 in the fine level's own frame; Eq. transfer_2d).
 std::vector<std::pair<Key, double>> interp_stencil(int transfer) {
+  if (transfer == kStandardCubic) {  // Eq. (interp_2d4o): products of the 1D taps
+    const double t[7] = {-1.0 / 16, 0.0, 9.0 / 16, 1.0, 9.0 / 16, 0.0, -1.0 / 16};
+    std::vector<std::pair<Key, double>> p;
+    for (int dy = -3; dy <= 3; ++dy)
+      for (int dx = -3; dx <= 3; ++dx)
+        if (t[dx + 3] != 0.0 && t[dy + 3] != 0.0) p.push_back({{dx, dy}, t[dx + 3] * t[dy + 3]});
+    return p;
+  }
   if (transfer == kRbAxisToRot)
     return {{{0, 0}, 1.0}, {{1, 0}, 0.25}, {{-1, 0}, 0.25}, {{0, 1}, 0.25}, {{0, -1}, 0.25}};
   if (transfer == kRbRotToAxis)
@@ -79,7 +87,7 @@ int radius(const Stencil& s, bool x) {
 // coarse node at the origin. R = 1/2 P^T (red-black) or 1/4 P^T (standard).
 Stencil galerkin(const Stencil& W, int transfer) {
   const auto P = interp_stencil(transfer);
-  const double rscale = transfer == kStandard ? 0.25 : 0.5;
+  const double rscale = (transfer == kStandard || transfer == kStandardCubic) ? 0.25 : 0.5;
   const int step = transfer == kRbAxisToRot ? 1 : 2;  // fine-lattice units per coarse unit
   const int M = (std::max(radius(W, true), radius(W, false)) + 4) / step + 2;
   Stencil out;
@@ -102,6 +110,165 @@ Stencil galerkin(const Stencil& W, int transfer) {
       }
       if (g != 0.0) put(out, a, b, g);
     }
+  return out;
+}
+
+// ---- exact dyadic stencils (Galerkin recursion over cubic transfers) ------------
+// The cubic weights make the Galerkin coefficients dyadic fractions whose numerators
+// grow by about 14 bits per level, past FP64's 53 from the fourth coarse level on.
+// The recursion is therefore carried exactly (value = numerator / 2^exp with a
+// 256-bit signed numerator) and every level's weights are rounded once to FP64, as in
+// the oracle's exact sparse products.
+struct Big {
+  uint64_t w[4] = {0, 0, 0, 0};  // two's complement, little-endian limbs
+  static Big of(int64_t v) {
+    Big b;
+    const uint64_t ext = v < 0 ? ~0ull : 0ull;
+    b.w[0] = (uint64_t)v;
+    b.w[1] = b.w[2] = b.w[3] = ext;
+    return b;
+  }
+  bool neg() const { return (int64_t)w[3] < 0; }
+  bool zero() const { return !(w[0] | w[1] | w[2] | w[3]); }
+  Big operator+(const Big& o) const {
+    Big r;
+    unsigned __int128 c = 0;
+    for (int k = 0; k < 4; ++k) {
+      c += (unsigned __int128)w[k] + o.w[k];
+      r.w[k] = (uint64_t)c;
+      c >>= 64;
+    }
+    return r;
+  }
+  Big negated() const {
+    Big r;
+    for (int k = 0; k < 4; ++k) r.w[k] = ~w[k];
+    return r + of(1);
+  }
+  Big abs() const { return neg() ? negated() : *this; }
+  // times a small integer (|m| < 2^62)
+  Big times(int64_t m) const {
+    const bool sn = neg() != (m < 0);
+    const Big a = abs();
+    const uint64_t um = (uint64_t)(m < 0 ? -m : m);
+    Big r;
+    unsigned __int128 c = 0;
+    for (int k = 0; k < 4; ++k) {
+      c += (unsigned __int128)a.w[k] * um;
+      r.w[k] = (uint64_t)c;
+      c >>= 64;
+    }
+    return sn ? r.negated() : r;
+  }
+  int bits() const {  // bit length of |value|
+    const Big a = abs();
+    for (int k = 3; k >= 0; --k)
+      if (a.w[k]) return 64 * k + 64 - __builtin_clzll(a.w[k]);
+    return 0;
+  }
+  bool even() const { return !(w[0] & 1); }
+  Big half() const {  // exact division by 2 of an even value
+    Big r;
+    for (int k = 0; k < 4; ++k) r.w[k] = (w[k] >> 1) | (k < 3 ? (w[k + 1] << 63) : (w[3] & (1ull << 63)));
+    return r;
+  }
+  bool bit(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+  // value * 2^-exp rounded to nearest (ties to even)
+  double to_double(int exp) const {
+    const Big a = abs();
+    const int nb = a.bits();
+    if (nb == 0) return 0.0;
+    uint64_t mant;
+    int shift = 0;
+    if (nb <= 53) {
+      mant = a.w[0];
+    } else {
+      shift = nb - 53;
+      mant = 0;
+      for (int i = 0; i < 53; ++i) mant |= (uint64_t)a.bit(shift + i) << i;
+      const bool round = a.bit(shift - 1);
+      bool sticky = false;
+      for (int i = 0; i < shift - 1 && !sticky; ++i) sticky = a.bit(i);
+      if (round && (sticky || (mant & 1))) ++mant;  // 2^53 stays exact
+    }
+    const double v = std::ldexp((double)mant, shift - exp);
+    return neg() ? -v : v;
+  }
+};
+
+struct XStencil {  // (dy, dx) -> numerator; value = numerator / 2^exp
+  std::map<Key, Big> t;
+  int exp = 0;
+};
+
+constexpr int kMaxExactBits = 240;
+
+void xput(std::map<Key, Big>& s, const Key& k, const Big& v) {
+  if (v.zero()) return;
+  auto it = s.find(k);
+  if (it == s.end()) {
+    s.emplace(k, v);
+    return;
+  }
+  it->second = it->second + v;
+  if (it->second.zero()) s.erase(it);
+}
+
+// Exact copy of an integer-weighted stencil.
+XStencil exact_of(const Stencil& W) {
+  XStencil x;
+  for (const auto& t : W) {
+    const double w = t.second;
+    if (w != std::floor(w) || std::fabs(w) > 1e15) return XStencil{{}, -1};  // not an integer stencil
+    xput(x.t, t.first, Big::of((int64_t)w));
+  }
+  return x;
+}
+
+Stencil rounded(const XStencil& x) {
+  Stencil s;
+  for (const auto& t : x.t) s[t.first] = t.second.to_double(x.exp);
+  return s;
+}
+
+// Exact Galerkin product R W P on the infinite lattice for the cubic transfers
+// (same loop structure as galerkin()); P = taps / 2^8, R = P^T / 4.
+// Returns exp = -1 if a numerator would exceed kMaxExactBits.
+XStencil galerkin_exact(const XStencil& W) {
+  const int64_t t1[7] = {-1, 0, 9, 16, 9, 0, -1};  // 1D taps times 16
+  std::vector<std::pair<Key, int64_t>> P;  // (dx, dy) -> 2D tap times 256
+  for (int dy = -3; dy <= 3; ++dy)
+    for (int dx = -3; dx <= 3; ++dx)
+      if (t1[dx + 3] && t1[dy + 3]) P.push_back({{dx, dy}, t1[dx + 3] * t1[dy + 3]});
+  int rW = 0;
+  for (const auto& t : W.t) rW = std::max({rW, std::abs(t.first.first), std::abs(t.first.second)});
+  const int M = (rW + 4) / 2 + 2;
+  XStencil out;
+  out.exp = W.exp + 8 + 8 + 2;
+  for (int b = -M; b <= M; ++b)
+    for (int a = -M; a <= M; ++a) {
+      std::map<Key, int64_t> v;  // P e_(a,b) on the fine lattice, keyed (dy, dx)
+      for (const auto& t : P) v[Key(2 * b + t.first.second, 2 * a + t.first.first)] += t.second;
+      Big g;
+      for (const auto& r : P) {
+        Big wv;
+        for (const auto& w : W.t) {
+          auto it = v.find(Key(r.first.second + w.first.first, r.first.first + w.first.second));
+          if (it != v.end()) wv = wv + w.second.times(it->second);
+        }
+        g = g + wv.times(r.second);
+      }
+      if (g.bits() > kMaxExactBits) return XStencil{{}, -1};
+      if (!g.zero()) out.t[Key(b, a)] = g;
+    }
+  // drop common factors of two
+  while (out.exp > 0) {
+    bool all_even = true;
+    for (const auto& t : out.t) all_even = all_even && t.second.even();
+    if (!all_even) break;
+    for (auto& t : out.t) t.second = t.second.half();
+    --out.exp;
+  }
   return out;
 }
 
@@ -128,6 +295,33 @@ Stencil fold_row(const Stencil& st, int n, int i, int j) {
     put(row, ti - i, tj - j, si * sj * t.second);
   }
   return row;
+}
+
+// The same rows from an exact stencil: the merged weights are summed exactly and
+// rounded once.
+Stencil fold_row_x(const XStencil& st, int n, int i, int j) {
+  std::map<Key, Big> row;
+  for (const auto& t : st.t) {
+    double si, sj;
+    bool bi, bj;
+    const int ti = fold(i + t.first.second, n, si, bi);
+    const int tj = fold(j + t.first.first, n, sj, bj);
+    if (bi || bj) continue;
+    xput(row, Key(tj - j, ti - i), si * sj < 0 ? t.second.negated() : t.second);
+  }
+  return rounded(XStencil{row, st.exp});
+}
+
+Stencil wrap_row_x(const XStencil& st, int n, int i, int j) {
+  std::map<Key, Big> row;
+  for (const auto& t : st.t) {
+    int ti = (i + t.first.second) % n;
+    if (ti < 0) ti += n;
+    int tj = (j + t.first.first) % n;
+    if (tj < 0) tj += n;
+    xput(row, Key(tj - j, ti - i), t.second);
+  }
+  return rounded(XStencil{row, st.exp});
 }
 
 // Periodic row of node (i, j): offsets wrapped modulo n into [0, n), duplicates
@@ -165,9 +359,11 @@ std::vector<LevelShape> level_shapes(int N, int coarsening, int n_min, int max_l
   return s;
 }
 
-// Transfer between level l (fine) and l + 1.
-int transfer_of(int coarsening, int l, int fine_kind) {
-  if (coarsening == MG_COARSEN_STANDARD || (coarsening == MG_COARSEN_VARIABLE && l >= 2)) return kStandard;
+// Transfer between level l (fine) and l + 1 (transfer_order 4: cubic, standard
+// coarsening only).
+int transfer_of(int coarsening, int l, int fine_kind, int transfer_order) {
+  if (coarsening == MG_COARSEN_STANDARD) return transfer_order == 4 ? kStandardCubic : kStandard;
+  if (coarsening == MG_COARSEN_VARIABLE && l >= 2) return kStandard;
   return fine_kind == kAxis ? kRbAxisToRot : kRbRotToAxis;
 }
 
@@ -175,6 +371,8 @@ int transfer_of(int coarsening, int l, int fine_kind) {
 struct HostLevel {
   LevelShape shape;
   int per = 0;  // periodic level: unknowns 0 <= i, j < n, stencils wrap
+  int exact = 0;  // W is the rounding of the exact stencil Wx (boundary rows from Wx)
+  XStencil Wx;
   int rows, cols, pitch;
   Stencil W;  // exact weights
   double s;   // scale: coefficient = fl(w * s)
@@ -225,7 +423,8 @@ void build_classes(HostLevel& L, double omega) {
       const int k = cy * L.clsw + cx;
       if (i < lo || i >= n || j < lo || j >= n) continue;
       if (L.small && L.shape.kind == kRot && ((i + j) & 1)) continue;
-      const Stencil row = L.per ? wrap_row(L.W, n, i, j) : fold_row(L.W, n, i, j);
+      const Stencil row = L.exact ? (L.per ? wrap_row_x(L.Wx, n, i, j) : fold_row_x(L.Wx, n, i, j))
+                                  : (L.per ? wrap_row(L.W, n, i, j) : fold_row(L.W, n, i, j));
       L.cls[k] = make_int2((int)L.tdx.size(), (int)row.size());
       double diag = 0.0;
       for (const auto& t : row) {
@@ -384,7 +583,7 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
   if (order != 2 && order != 4 && order != 6) return MG_ERR_INVALID;
   if (coarsening != MG_COARSEN_STANDARD && coarsening != MG_COARSEN_REDBLACK && coarsening != MG_COARSEN_VARIABLE)
     return MG_ERR_INVALID;
-  if (coarse_op < MG_OP_NONGALERKIN || coarse_op > MG_OP_GALERKIN_TRUE_HIGH) return MG_ERR_INVALID;
+  if (coarse_op < MG_OP_NONGALERKIN || coarse_op > MG_OP_NONGALERKIN_HIGH) return MG_ERR_INVALID;
   if (!(o.omega > 0.0 && o.omega < 2.0) || o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1 ||
       o.gamma < 1 || o.gamma > 3 || (o.smoother != MG_SMOOTH_REDBLACK && o.smoother != MG_SMOOTH_JACOBI))
     return MG_ERR_INVALID;
@@ -395,6 +594,8 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
   if (o.bf16_levels < 0 || o.bf16_levels > 4) return MG_ERR_INVALID;
   if (o.bf16_levels > 0 && (o.precision != MG_PREC_MIXED_FP32 || o.sweep_kernel == 2)) return MG_ERR_UNSUPPORTED;
   if (o.boundary != MG_BOUNDARY_DIRICHLET && o.boundary != MG_BOUNDARY_PERIODIC) return MG_ERR_INVALID;
+  if (o.transfer_order != 2 && o.transfer_order != 4) return MG_ERR_INVALID;
+  if (o.transfer_order == 4 && coarsening != MG_COARSEN_STANDARD) return MG_ERR_UNSUPPORTED;
   if (o.boundary == MG_BOUNDARY_PERIODIC && o.sweep_kernel == 2) return MG_ERR_UNSUPPORTED;
   if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
   if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
@@ -402,7 +603,8 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
 }
 
 // Level operators for the chosen coarse-operator family (Sec. 2.3 notation).
-void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
+// Returns false if an exact Galerkin recursion outgrows its integer width.
+bool build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
   const double hf = 1.0 / h->N;
   const double s2 = 1.0 / (hf * hf);         // operators derived from L_h^(2)
   const double s4 = 1.0 / (12.0 * hf * hf);  // operators derived from L_h^(4)
@@ -431,16 +633,39 @@ void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
     }
   }
   Stencil gal = base;
+  const int op = h->coarse_op;
+  // cubic transfers: the Galerkin recursion in exact arithmetic (see XStencil)
+  const bool exact = h->opt.transfer_order == 4;
+  XStencil galx;
+  if (exact) galx = exact_of(base);
   for (int l = 1; l < nl; ++l) {
     HostLevel& L = h->host[l];
-    gal = galerkin(gal, transfer_of(h->coarsening, l - 1, shapes[l - 1].kind));
-    const int op = h->coarse_op;
-    if (op == MG_OP_GALERKIN || op == MG_OP_GALERKIN_TRUE_HIGH || (op == MG_OP_GALERKIN_GN && l == 1)) {
-      L.W = gal;
+    const bool galerkin_level =
+        op == MG_OP_GALERKIN || op == MG_OP_GALERKIN_TRUE_HIGH || (op == MG_OP_GALERKIN_GN && l == 1);
+    if (exact) {
+      if (galerkin_level) {
+        galx = galerkin_exact(galx);
+        if (galx.exp < 0) return false;
+      }
+    } else {
+      gal = galerkin(gal, transfer_of(h->coarsening, l - 1, shapes[l - 1].kind, h->opt.transfer_order));
+    }
+    if (galerkin_level) {
+      if (exact) {
+        L.W = rounded(galx);
+        L.Wx = galx;
+        L.exact = 1;
+      } else {
+        L.W = gal;
+      }
       L.s = base_s;
     } else if (op == MG_OP_GALERKIN_G1) {
       L.W = from_frame(L.shape.kind, kFirstGalerkin, 1.0 / L.shape.hh);
       L.s = s2;
+    } else if (op == MG_OP_NONGALERKIN_HIGH && h->order > 2) {
+      // the fine operator's stencil with spacing H (nG^(4), Eq. L_H_4n_2d; nG^(6))
+      L.W = from_frame(L.shape.kind, h->order == 4 ? kFourthOrder : kSixthOrder, 1.0 / L.shape.hh);
+      L.s = L0.s;
     } else {
       L.W = from_frame(L.shape.kind, kFivePoint, 1.0 / L.shape.hh);
       L.s = s2;
@@ -461,6 +686,7 @@ void build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
     }
     build_classes(L, h->opt.omega);
   }
+  return true;
 }
 
 size_t level_bytes(const HostLevel& L, size_t elem) { return (size_t)L.rows * L.pitch * elem; }
@@ -911,6 +1137,7 @@ void mg_default_options(mg_options* o) {
   o->sweep_kernel = 0;
   o->bf16_levels = 0;
   o->boundary = MG_BOUNDARY_DIRICHLET;
+  o->transfer_order = 2;
 }
 
 const char* mg_status_string(mg_status s) {
@@ -962,9 +1189,13 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   h->coarse_op = coarse_op;
   h->opt = o;
   const auto shapes = level_shapes(h->N, coarsening, coarsest_n(o), o.max_levels);
-  build_operators(h, shapes);
+  if (!build_operators(h, shapes)) {
+    delete h;
+    return MG_ERR_UNSUPPORTED;
+  }
   const int nl = (int)shapes.size();
-  for (int l = 0; l + 1 < nl; ++l) h->transfer.push_back(transfer_of(coarsening, l, shapes[l].kind));
+  for (int l = 0; l + 1 < nl; ++l)
+    h->transfer.push_back(transfer_of(coarsening, l, shapes[l].kind, o.transfer_order));
   for (const auto& L : h->host)
     if (L.c.size() > (size_t)kMaxTerms) { delete h; return MG_ERR_UNSUPPORTED; }
   auto fail = [&](mg_status s) { free_all(h); delete h; return s; };
@@ -979,7 +1210,8 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   // Dirichlet: node (1, 1) with a_pp from its folded row; periodic: node (0, 0), whose
   // row is zero (the zero-mean solution is 0)
   const int64_t cidx = C.per ? 0 : (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
-  const double ca = C.per ? 1.0 : fold_row(C.W, C.shape.n, 1, 1).at(Key(0, 0)) * C.s;
+  const double ca = C.per ? 1.0
+                          : (C.exact ? fold_row_x(C.Wx, C.shape.n, 1, 1) : fold_row(C.W, C.shape.n, 1, 1)).at(Key(0, 0)) * C.s;
   if ((st = alloc_hier<double>(h, /*caller_level0=*/true)) != MG_OK) return fail(st);
   h->h64.coarsest_idx = cidx;
   h->h64.coarsest_a = ca;
@@ -1458,7 +1690,7 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) 
         (o.precision == MG_PREC_MIXED_FP32 && o.inner_cycles != o0.inner_cycles))
       return MG_ERR_INVALID;  // one schedule for the whole batch
     if (o.gamma != 1 || o.smoother != MG_SMOOTH_REDBLACK || o.bf16_levels != 0 ||
-        o.boundary != MG_BOUNDARY_DIRICHLET)
+        o.boundary != MG_BOUNDARY_DIRICHLET || o.transfer_order != 2)
       return MG_ERR_UNSUPPORTED;
     if ((int)h->host.size() > kTailMaxLevels) return MG_ERR_UNSUPPORTED;
   }

@@ -521,7 +521,7 @@ struct SmemIdx {
 // ordered by storage position (which is the row-major column order) and terms that
 // land on the same node merge by adding their weights (powers of two and their
 // small sums, so the merged weight is exact); then the usual ordered sum.
-constexpr int kMaxTransferTerms = 9;
+constexpr int kMaxTransferTerms = 25;
 template <typename T, bool EXACT, class Idx>
 __device__ __forceinline__ T wrapped_sum(const LevelDev<T>& L, int nt, const int* ti, const int* tj, const T* w,
                          const T* __restrict__ x, Idx idx) {
@@ -681,6 +681,179 @@ __device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, 
       }
   }
   return e;
+}
+
+// ---- cubic transfers (standard coarsening, App. A, Eq. interp_2d4o / restr_2d4o) ----
+// Per axis, the interpolated value at an odd fine position takes the coarse nodes at
+// fine offsets -3, -1, 1, 3 with weights -1/16, 9/16, 9/16, -1/16 (even positions
+// copy their coarse node); 2D weights are products. R = 1/4 P^T: per axis taps
+// (-1, 9, 16, 9, -1) / 32 at fine offsets (-3, -1, 0, 1, 3). All weights and their
+// products are exact in FP32 and FP64.
+__constant__ int c_cubic_off[5] = {-3, -1, 0, 1, 3};
+__constant__ float c_cubic_r1[5] = {-1.0f / 32, 9.0f / 32, 16.0f / 32, 9.0f / 32, -1.0f / 32};
+
+// Dirichlet edge terms: coordinates folded into [0, n] by odd reflection (sign -1 per
+// reflection), boundary positions dropped; then as wrapped_sum (ordered by storage
+// position, equal positions merged by exact weight sums).
+template <typename T, bool EXACT, class Idx>
+__device__ __forceinline__ T folded_sum(const LevelDev<T>& L, int nt, const int* ti, const int* tj, const T* w,
+                                        const T* __restrict__ x, Idx idx) {
+  int64_t pos[kMaxTransferTerms];
+  T wt[kMaxTransferTerms];
+  int m = 0;
+  const int n2 = 2 * L.n;
+  for (int k = 0; k < nt; ++k) {
+    int a = ti[k] % n2, b = tj[k] % n2;
+    if (a < 0) a += n2;
+    if (b < 0) b += n2;
+    T wk = w[k];
+    if (a > L.n) { a = n2 - a; wk = -wk; }
+    if (b > L.n) { b = n2 - b; wk = -wk; }
+    if (a == 0 || a == L.n || b == 0 || b == L.n) continue;
+    const int64_t p = idx(L, a, b);
+    int q = 0;
+    while (q < m && pos[q] < p) ++q;
+    if (q < m && pos[q] == p) {
+      wt[q] = Arith<T>::add(wt[q], wk);
+      continue;
+    }
+    for (int r = m; r > q; --r) {
+      pos[r] = pos[r - 1];
+      wt[r] = wt[r - 1];
+    }
+    pos[q] = p;
+    wt[q] = wk;
+    ++m;
+  }
+  // weights that cancel (exact zeros) are kept as terms: the oracle's sparse products
+  // keep such entries too, and w * x = +-0 leaves a nonzero sum unchanged
+  if (m == 0) return T(0);
+  T s = Arith<T>::mul(wt[0], x[pos[0]]);
+  for (int k = 1; k < m; ++k) s = madd<T, EXACT>(s, wt[k], x[pos[k]]);
+  return s;
+}
+
+template <typename T, bool EXACT, bool PER, class Idx>
+__device__ __forceinline__ T edge_sum(const LevelDev<T>& L, int nt, const int* ti, const int* tj, const T* w,
+                                      const T* __restrict__ x, Idx idx) {
+  if (PER) return wrapped_sum<T, EXACT>(L, nt, ti, tj, w, x, idx);
+  return folded_sum<T, EXACT>(L, nt, ti, tj, w, x, idx);
+}
+
+// Restricted residual at coarse node (i, j) with the cubic adjoint.
+template <typename T, bool EXACT, bool PER, class Idx = GlobalIdx>
+__device__ __forceinline__ T restrict_cubic_value(const LevelDev<T>& Lf, const T* __restrict__ d, int i, int j,
+                                                  Idx idx = Idx()) {
+  const int fi = 2 * i, fj = 2 * j;
+  const int lo = PER ? 3 : 4, hi = Lf.n - (PER ? 4 : 4);  // all taps on unknowns, no wrap
+  if (fi >= lo && fi <= hi && fj >= lo && fj <= hi) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        const T w = Arith<T>::mul(T(c_cubic_r1[a]), T(c_cubic_r1[b]));  // exact
+        const T x = d[idx(Lf, fi + c_cubic_off[a], fj + c_cubic_off[b])];
+        s = (a == 0 && b == 0) ? Arith<T>::mul(w, x) : madd<T, EXACT>(s, w, x);
+      }
+    return s;
+  }
+  int ti[25], tj[25];
+  T w[25];
+  int m = 0;
+  for (int b = 0; b < 5; ++b)
+    for (int a = 0; a < 5; ++a) {
+      ti[m] = fi + c_cubic_off[a];
+      tj[m] = fj + c_cubic_off[b];
+      w[m++] = Arith<T>::mul(T(c_cubic_r1[a]), T(c_cubic_r1[b]));
+    }
+  return edge_sum<T, EXACT, PER>(Lf, 25, ti, tj, w, d, idx);
+}
+
+// 1D cubic interpolation taps of fine position i: coarse positions and weights.
+template <typename T>
+__device__ __forceinline__ int cubic_taps(int i, int* c, T* w) {
+  if ((i & 1) == 0) {
+    c[0] = i >> 1;
+    w[0] = T(1);
+    return 1;
+  }
+  const int c0 = (i - 3) >> 1;
+  c[0] = c0; c[1] = c0 + 1; c[2] = c0 + 2; c[3] = c0 + 3;
+  w[0] = T(-0.0625); w[1] = T(0.5625); w[2] = T(0.5625); w[3] = T(-0.0625);
+  return 4;
+}
+
+// Interpolated correction (P v)(i, j) at fine node (i, j) with cubic interpolation.
+template <typename T, bool EXACT, bool PER, class Idx = GlobalIdx>
+__device__ __forceinline__ T prolong_cubic_value(const LevelDev<T>& Lc, const T* __restrict__ vc, int i, int j,
+                                                 Idx idx = Idx()) {
+  int cx[4], cy[4];
+  T wx[4], wy[4];
+  const int nx = cubic_taps<T>(i, cx, wx), ny = cubic_taps<T>(j, cy, wy);
+  const int lo = PER ? 0 : 1;
+  if (cx[0] >= lo && cx[nx - 1] <= Lc.n - 1 && cy[0] >= lo && cy[ny - 1] <= Lc.n - 1) {
+    T e = T(0);
+    for (int b = 0; b < ny; ++b)
+      for (int a = 0; a < nx; ++a) {
+        const T w = Arith<T>::mul(wx[a], wy[b]);  // exact
+        const T x = vc[idx(Lc, cx[a], cy[b])];
+        e = (a == 0 && b == 0) ? Arith<T>::mul(w, x) : madd<T, EXACT>(e, w, x);
+      }
+    return e;
+  }
+  int ti[16], tj[16];
+  T w[16];
+  int m = 0;
+  for (int b = 0; b < ny; ++b)
+    for (int a = 0; a < nx; ++a) {
+      ti[m] = cx[a];
+      tj[m] = cy[b];
+      w[m++] = Arith<T>::mul(wx[a], wy[b]);
+    }
+  return edge_sum<T, EXACT, PER>(Lc, m, ti, tj, w, vc, idx);
+}
+
+// Any transfer, boundary kind chosen at run time (tail kernels).
+template <typename T, bool EXACT, class Idx = GlobalIdx>
+__device__ __forceinline__ T restrict_any(const LevelDev<T>& Lf, int transfer, const T* __restrict__ d, int i, int j,
+                                          Idx idx = Idx()) {
+  if (transfer == kStandardCubic)
+    return Lf.per ? restrict_cubic_value<T, EXACT, true>(Lf, d, i, j, idx)
+                  : restrict_cubic_value<T, EXACT, false>(Lf, d, i, j, idx);
+  return Lf.per ? restrict_value<T, EXACT, true>(Lf, transfer, d, i, j, idx)
+                : restrict_value<T, EXACT, false>(Lf, transfer, d, i, j, idx);
+}
+
+template <typename T, bool EXACT, class Idx = GlobalIdx>
+__device__ __forceinline__ T prolong_any(const LevelDev<T>& Lc, int transfer, const T* __restrict__ vc, int i, int j,
+                                         Idx idx = Idx()) {
+  if (transfer == kStandardCubic)
+    return Lc.per ? prolong_cubic_value<T, EXACT, true>(Lc, vc, i, j, idx)
+                  : prolong_cubic_value<T, EXACT, false>(Lc, vc, i, j, idx);
+  return Lc.per ? prolong_value<T, EXACT, true>(Lc, transfer, vc, i, j, idx)
+                : prolong_value<T, EXACT, false>(Lc, transfer, vc, i, j, idx);
+}
+
+template <typename T, bool EXACT, bool PER>
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value)
+    k_restrict_cubic(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp, const T* __restrict__ d,
+                     T* __restrict__ fc) {
+  const LevelDev<T>& Lc = *Lcp;
+  int i, j;
+  if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
+  fc[sidx(Lc, i, j)] = rnd(Lc, restrict_cubic_value<T, EXACT, PER>(*Lfp, d, i, j));
+}
+
+template <typename T, bool EXACT, bool PER>
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value)
+    k_prolong_cubic(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp, const T* uin, T* uf,
+                    const T* __restrict__ vc) {
+  const LevelDev<T>& Lf = *Lfp;
+  int i, j;
+  if (!thread_node(Lf, i, j) || !interior(Lf, i, j)) return;
+  const int64_t at = sidx(Lf, i, j);
+  uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_cubic_value<T, EXACT, PER>(*Lcp, vc, i, j)));
 }
 
 template <typename T, bool EXACT, bool PER>
@@ -894,8 +1067,7 @@ __global__ void __launch_bounds__(kTailThreads)
       const int ctot = Lc.rows * Lc.cols;
       for (int k = tid; k < ctot; k += nth) {
         if (!tail_node(Lc, k, i, j)) continue;
-        Fc[sidx(Lc, i, j)] = L.per ? restrict_value<T, EXACT, true>(L, D->transfer[l], Dd, i, j)
-                                   : restrict_value<T, EXACT, false>(L, D->transfer[l], Dd, i, j);
+        Fc[sidx(Lc, i, j)] = restrict_any<T, EXACT>(L, D->transfer[l], Dd, i, j);
       }
     } else if (op.x == kOpCoarsest) {
       if (tid == 0)
@@ -908,8 +1080,7 @@ __global__ void __launch_bounds__(kTailThreads)
       for (int k = tid; k < total; k += nth) {
         if (!tail_node(L, k, i, j)) continue;
         const int64_t at = sidx(L, i, j);
-        U[at] = Arith<T>::add(U[at], Lc.per ? prolong_value<T, EXACT, true>(Lc, D->transfer[l], V, i, j)
-                                            : prolong_value<T, EXACT, false>(Lc, D->transfer[l], V, i, j));
+        U[at] = Arith<T>::add(U[at], prolong_any<T, EXACT>(Lc, D->transfer[l], V, i, j));
       }
     }
     cluster.sync();
@@ -1155,8 +1326,7 @@ __global__ void __launch_bounds__(kTailThreads)
       const int tr = D->transfer[l];
       for (int k = tid; k < Lc.rows * Lc.cols; k += kTailThreads) {
         if (!tail_node(Lc, k, i, j)) continue;
-        Fc[k] = L.per ? restrict_value<T, EXACT, true>(L, tr, Dd, i, j, SmemIdx())
-                      : restrict_value<T, EXACT, false>(L, tr, Dd, i, j, SmemIdx());
+        Fc[k] = restrict_any<T, EXACT>(L, tr, Dd, i, j, SmemIdx());
       }
     } else if (op.x == kOpCoarsest) {
       if (tid == 0) {
@@ -1169,8 +1339,7 @@ __global__ void __launch_bounds__(kTailThreads)
       const int tr = D->transfer[l];
       for (int k = tid; k < total; k += kTailThreads) {
         if (!tail_node(L, k, i, j)) continue;
-        const T e = Lc.per ? prolong_value<T, EXACT, true>(Lc, tr, V, i, j, SmemIdx())
-                           : prolong_value<T, EXACT, false>(Lc, tr, V, i, j, SmemIdx());
+        const T e = prolong_any<T, EXACT>(Lc, tr, V, i, j, SmemIdx());
         U[k] = Arith<T>::add(U[k], e);
       }
     }
@@ -1303,7 +1472,15 @@ template <typename T>
 cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
                             const T* d, T* fc, cudaStream_t s) {
   const dim3 g = grid_of(Lc.h), b(kBX, kBY);
-  if (Lf.h.per) {
+  if (transfer == kStandardCubic) {
+    if (Lf.h.per) {
+      if (exact) k_restrict_cubic<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
+      else k_restrict_cubic<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
+    } else {
+      if (exact) k_restrict_cubic<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
+      else k_restrict_cubic<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
+    }
+  } else if (Lf.h.per) {
     if (exact) k_restrict<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
     else k_restrict<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
   } else {
@@ -1318,7 +1495,15 @@ cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, i
                                bool exact, T* uf, const T* vc, cudaStream_t s, const T* uin) {
   const dim3 g = grid_of(Lf.h), b(kBX, kBY);
   const T* ui = uin ? uin : uf;
-  if (Lc.h.per) {
+  if (transfer == kStandardCubic) {
+    if (Lc.h.per) {
+      if (exact) k_prolong_cubic<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, ui, uf, vc);
+      else k_prolong_cubic<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, ui, uf, vc);
+    } else {
+      if (exact) k_prolong_cubic<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, ui, uf, vc);
+      else k_prolong_cubic<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, ui, uf, vc);
+    }
+  } else if (Lc.h.per) {
     if (exact) k_prolong_add<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
     else k_prolong_add<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
   } else {

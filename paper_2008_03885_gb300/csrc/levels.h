@@ -6,7 +6,8 @@
 
 namespace nsmg {
 
-constexpr int kMaxTerms = 64;  // largest interior stencil a level may carry
+constexpr int kMaxTerms = 128;  // largest interior stencil a level may carry (cubic-transfer
+                                // Galerkin stencils reach 11 x 11 = 121 terms)
 
 enum Kind : int32_t { kAxis = 0, kRot = 1 };
 
@@ -14,7 +15,8 @@ enum Kind : int32_t { kAxis = 0, kRot = 1 };
 enum Transfer : int32_t {
   kRbAxisToRot = 0,  // axis fine grid -> its black points (same lattice)
   kRbRotToAxis = 1,  // rotated fine grid -> points with i, j even (lattice n/2)
-  kStandard = 2      // axis n -> axis n/2, bilinear / full weighting
+  kStandard = 2,     // axis n -> axis n/2, bilinear / full weighting
+  kStandardCubic = 3 // axis n -> axis n/2, cubic interpolation and its adjoint (R = 1/4 P^T)
 };
 
 // Device-resident description of one level in precision T.

@@ -43,7 +43,7 @@ def test_status_strings_and_defaults(lib):
         assert mg._lib.mg_status_string(s)
     o = mg.mg_default_options()
     assert o.omega == 1.0 and o.nu1 == 1 and o.nu2 == 1 and o.gamma == 1 and o.n_min == 2
-    assert o.boundary == mg.MG_BOUNDARY_DIRICHLET
+    assert o.boundary == mg.MG_BOUNDARY_DIRICHLET and o.transfer_order == 2
 
 
 def test_workspace_bytes_validates_without_gpu(lib):
@@ -78,3 +78,12 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, boundary="periodic", sweep_kernel=2)
     assert e.value.status == mg.MG_ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, 4, "standard", transfer_order=3)
+    assert e.value.status == mg.MG_ERR_INVALID
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, 4, "redblack", transfer_order=4)
+    assert e.value.status == mg.MG_ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, 4, "standard", 6)
+    assert e.value.status == mg.MG_ERR_INVALID
