@@ -265,6 +265,7 @@ def run_ours(args, ws, rank, local):
                  {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1, "fma_contract": 1}),
                 ("mixed_fp32_inner_nongalerkin_coarse", "redblack", "nongalerkin", 1.0,
                  {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1, "fma_contract": 1}),
+                ("standard_cubic_nongalerkin4_omega1.1", "standard", "nongalerkin_high", 1.1, {"transfer_order": 4}),
                 ("periodic_redblack_galerkin", "redblack", "galerkin", 1.0, {"boundary": "periodic"}),
                 ("periodic_mixed_fp32_inner", "redblack", "galerkin", 1.0,
                  {"boundary": "periodic", "precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1,
@@ -292,6 +293,7 @@ def run_ours(args, ws, rank, local):
             variants[name] = {"ms": a.elapsed_time(b), "cycles": kv, "final_rel_res": hv_hist[-1],
                               "cr_last": hv_hist[-1] / hv_hist[-2] if kv > 1 else None,
                               "boundary": extra.get("boundary", "dirichlet"),
+                              "transfer_order": extra.get("transfer_order", 2),
                               "finest_kernel_ms": {k: v[0] for k, v in vt.items()},
                               "finest_kernel_launches": {k: v[1] for k, v in vt.items()}}
             if extra.get("precision") == mg.MG_PREC_MIXED_FP32:
