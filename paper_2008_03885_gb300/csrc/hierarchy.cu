@@ -709,28 +709,27 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P, int bf
   P.h.bf16 = bf16;
   int2* cls;
   T* cwd;
-  int32_t *tdx, *tdy;
-  T* tc;
+  ClassTerm<T>* terms;
   mg_status st;
   const size_t nt = std::max<size_t>(L.tdx.size(), 1);
   if ((st = device_alloc(h, (void**)&cls, L.cls.size() * sizeof(int2))) != MG_OK) return st;
   if ((st = device_alloc(h, (void**)&cwd, L.cls_wd.size() * sizeof(T))) != MG_OK) return st;
-  if ((st = device_alloc(h, (void**)&tdx, nt * sizeof(int32_t))) != MG_OK) return st;
-  if ((st = device_alloc(h, (void**)&tdy, nt * sizeof(int32_t))) != MG_OK) return st;
-  if ((st = device_alloc(h, (void**)&tc, nt * sizeof(T))) != MG_OK) return st;
-  std::vector<T> wd(L.cls_wd.begin(), L.cls_wd.end()), c(L.tc.begin(), L.tc.end());
+  if ((st = device_alloc(h, (void**)&terms, nt * sizeof(ClassTerm<T>))) != MG_OK) return st;
+  std::vector<T> wd(L.cls_wd.begin(), L.cls_wd.end());
+  std::vector<ClassTerm<T>> tt(L.tdx.size());
+  for (size_t k = 0; k < tt.size(); ++k) {
+    std::memset(&tt[k], 0, sizeof(tt[k]));
+    tt[k].c = (T)L.tc[k];
+    tt[k].dx = L.tdx[k];
+    tt[k].dy = L.tdy[k];
+  }
   CK(cudaMemcpyAsync(cls, L.cls.data(), L.cls.size() * sizeof(int2), cudaMemcpyHostToDevice, h->priv));
   CK(cudaMemcpyAsync(cwd, wd.data(), wd.size() * sizeof(T), cudaMemcpyHostToDevice, h->priv));
-  if (!L.tdx.empty()) {
-    CK(cudaMemcpyAsync(tdx, L.tdx.data(), L.tdx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->priv));
-    CK(cudaMemcpyAsync(tdy, L.tdy.data(), L.tdy.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->priv));
-    CK(cudaMemcpyAsync(tc, c.data(), c.size() * sizeof(T), cudaMemcpyHostToDevice, h->priv));
-  }
+  if (!tt.empty())
+    CK(cudaMemcpyAsync(terms, tt.data(), tt.size() * sizeof(ClassTerm<T>), cudaMemcpyHostToDevice, h->priv));
   P.h.cls = cls;
   P.h.cls_wd = cwd;
-  P.h.tdx = tdx;
-  P.h.tdy = tdy;
-  P.h.tc = tc;
+  P.h.terms = terms;
   if ((st = device_alloc(h, (void**)&P.d, sizeof(LevelDev<T>))) != MG_OK) return st;
   CK(cudaMemcpyAsync(P.d, &P.h, sizeof(LevelDev<T>), cudaMemcpyHostToDevice, h->priv));
   return MG_OK;

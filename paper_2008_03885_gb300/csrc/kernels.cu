@@ -45,6 +45,23 @@ struct Arith<float> {
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
 };
 
+// One class term by a single 16-byte load.
+template <typename T>
+__device__ __forceinline__ ClassTerm<T> load_term(const ClassTerm<T>* p) {
+  const int4 w = __ldg(reinterpret_cast<const int4*>(p));
+  ClassTerm<T> t;
+  if (sizeof(T) == 8) {
+    t.c = (T)__hiloint2double(w.y, w.x);
+    t.dx = w.z;
+    t.dy = w.w;
+  } else {
+    t.c = (T)__int_as_float(w.x);
+    t.dx = w.y;
+    t.dy = w.z;
+  }
+  return t;
+}
+
 // s + c * x in the chosen rounding mode.
 // Value as stored on a level: FP32 levels of the bfloat16 storage trial round it.
 template <typename T>
@@ -102,7 +119,9 @@ __device__ __forceinline__ bool fast_node(const LevelDev<T>& L, int i, int j) {
 }
 
 // (L u)(i, j) and the node's omega / a_pp.
-template <typename T, bool EXACT>
+// CU: unroll factor of the boundary-class term loop (its loads then run ahead of the
+// ordered sum); 1 in the register-tight NT kernels.
+template <typename T, bool EXACT, int CU = 4>
 __device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict__ u, int i, int j,
                                       int64_t at, T* wd) {
   T s;
@@ -114,11 +133,13 @@ __device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict_
   } else {
     const int cl = class_of(L, i, j);
     const int2 e = L.cls[cl];
+    const ClassTerm<T>* tt = L.terms + e.x;
     s = T(0);
+#pragma unroll CU
     for (int k = 0; k < e.y; ++k) {
-      const int t = e.x + k;
-      const T x = u[sidx(L, i + L.tdx[t], j + L.tdy[t])];
-      s = k == 0 ? Arith<T>::mul(L.tc[t], x) : madd<T, EXACT>(s, L.tc[t], x);
+      const ClassTerm<T> t = load_term(tt + k);
+      const T x = u[sidx(L, i + t.dx, j + t.dy)];
+      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
     }
     if (wd) *wd = L.cls_wd[cl];
   }
@@ -126,11 +147,11 @@ __device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict_
 }
 
 // New value of node (i, j) after one relaxation: u + (f - L u) * omega / a_pp.
-template <typename T, bool EXACT>
+template <typename T, bool EXACT, int CU = 4>
 __device__ __forceinline__ T relax_value(const LevelDev<T>& L, const T* __restrict__ uin,
                                          const T* __restrict__ f, int i, int j, int64_t at) {
   T wd;
-  const T s = apply_at<T, EXACT>(L, uin, i, j, at, &wd);
+  const T s = apply_at<T, EXACT, CU>(L, uin, i, j, at, &wd);
   const T r = Arith<T>::sub(f[at], s);
   return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
 }
@@ -199,7 +220,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
       if (i < lo || i >= n) continue;
       const int64_t at = row + i;
       uout[at] = rnd(L, fast_node_c<PER>(L, i, j) ? relax_fast<T, EXACT, NT>(c, d0, wd, uin, f, at)
-                                                  : relax_value<T, EXACT>(L, uin, f, i, j, at));
+                                                  : relax_value<T, EXACT, 1>(L, uin, f, i, j, at));
     }
   } else {
     const int q = blockIdx.x * kBX + threadIdx.x;
@@ -216,7 +237,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
         continue;
       }
       uout[at] = rnd(L, fast_node_c<PER>(L, i, j) ? relax_fast<T, EXACT, NT>(c, (i & 1) ? d1 : d0, wd, uin, f, at)
-                                                  : relax_value<T, EXACT>(L, uin, f, i, j, at));
+                                                  : relax_value<T, EXACT, 1>(L, uin, f, i, j, at));
     }
   }
 }
@@ -247,7 +268,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_nt(
     if (i < lo || i >= n) continue;
     const int64_t at = (int64_t)j * L.pitch + q;
     const T s = fast_node_c<PER>(L, i, j) ? apply_fast<T, EXACT, NT>(c, (L.kind == kRot && (i & 1)) ? d1 : d0, u, at)
-                                          : apply_at<T, EXACT>(L, u, i, j, at, nullptr);
+                                          : apply_at<T, EXACT, 1>(L, u, i, j, at, nullptr);
     d[at] = rnd(L, Arith<T>::sub(f[at], s));
   }
 }
@@ -363,13 +384,15 @@ __device__ __forceinline__ T relax_tile(const LevelDev<T>& L, const TileGeom& G,
   } else {
     const int cl = class_of(L, i, j);
     const int2 ce = L.cls[cl];
+    const ClassTerm<T>* tt = L.terms + ce.x;
     s = T(0);
+#pragma unroll 4
     for (int k = 0; k < ce.y; ++k) {
-      const int t = ce.x + k;
-      const int ti = i + L.tdx[t], tj = j + L.tdy[t];
+      const ClassTerm<T> t = load_term(tt + k);
+      const int ti = i + t.dx, tj = j + t.dy;
       const int tq = G.kind == kRot ? (ti >> 1) : ti;
       const T x = su[(tj - j0) * SW + (tq - q0)];
-      s = k == 0 ? Arith<T>::mul(L.tc[t], x) : madd<T, EXACT>(s, L.tc[t], x);
+      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
     }
     wd = L.cls_wd[cl];
   }
@@ -1008,7 +1031,7 @@ __device__ __forceinline__ bool tail_node(const LevelDev<T>& L, int k, int& i, i
 }
 
 template <typename T, bool EXACT>
-__global__ void __launch_bounds__(kTailThreads)
+__global__ void __launch_bounds__(kTailThreads, 1)
     k_tail(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog, int nops) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -1244,11 +1267,13 @@ __device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i,
   } else {
     const int cl = class_of(L, i, j);
     const int2 ce = L.cls[cl];
+    const ClassTerm<T>* tt = L.terms + ce.x;
     s = T(0);
+#pragma unroll 4
     for (int k = 0; k < ce.y; ++k) {
-      const int t = ce.x + k;
-      const T x = u[smem_idx(L, i + L.tdx[t], j + L.tdy[t])];
-      s = k == 0 ? Arith<T>::mul(L.tc[t], x) : madd<T, EXACT>(s, L.tc[t], x);
+      const ClassTerm<T> t = load_term(tt + k);
+      const T x = u[smem_idx(L, i + t.dx, j + t.dy)];
+      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
     }
     if (wd) *wd = L.cls_wd[cl];
   }
@@ -1256,7 +1281,7 @@ __device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i,
 }
 
 template <typename T, bool EXACT>
-__global__ void __launch_bounds__(kTailThreads)
+__global__ void __launch_bounds__(kTailThreads, 1)
     k_tail_smem(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog, int nops) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
   T* sm = reinterpret_cast<T*>(tail_smem);

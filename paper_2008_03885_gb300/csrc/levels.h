@@ -19,6 +19,14 @@ enum Transfer : int32_t {
   kStandardCubic = 3 // axis n -> axis n/2, cubic interpolation and its adjoint (R = 1/4 P^T)
 };
 
+// A merged boundary-class term: coefficient and lattice offset in one aligned 16-byte
+// record, so that one vector load fetches it.
+template <typename T>
+struct __align__(16) ClassTerm {
+  T c;
+  int32_t dx, dy;
+};
+
 // Device-resident description of one level in precision T.
 //
 // Points live on an integer lattice (i, j), 0 <= i, j <= n. Axis levels hold every
@@ -49,9 +57,7 @@ struct LevelDev {
   int32_t sdy[kMaxTerms];       // row shift of the fast terms
   const int2* cls;            // per class: (first term, term count)
   const T* cls_wd;            // per class: omega / a_pp
-  const int32_t* tdx;         // merged terms
-  const int32_t* tdy;
-  const T* tc;
+  const ClassTerm<T>* terms;  // merged terms of every class
   int32_t bf16;  // FP32 inner levels: round every stored value to bfloat16 (storage trial)
   int32_t per;   // 1: periodic level (see above)
   int32_t lo;    // first unknown index: 1 - per
