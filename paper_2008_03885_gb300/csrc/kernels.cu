@@ -1151,13 +1151,13 @@ __global__ void __launch_bounds__(kBX * kBY)
           B.u[at] = T(0);
           break;
         case kBHalfRed:
-          B.t[at] = is_red(L, i, j) ? relax_value<T, EXACT>(L, B.u, B.f, i, j, at) : B.u[at];
+          B.t[at] = is_red(L, i, j) ? relax_value<T, EXACT, 1>(L, B.u, B.f, i, j, at) : B.u[at];
           break;
         case kBHalfBlack:
-          B.u[at] = is_red(L, i, j) ? B.t[at] : relax_value<T, EXACT>(L, B.t, B.f, i, j, at);
+          B.u[at] = is_red(L, i, j) ? B.t[at] : relax_value<T, EXACT, 1>(L, B.t, B.f, i, j, at);
           break;
         case kBResidual:
-          B.d[at] = Arith<T>::sub(B.f[at], apply_at<T, EXACT>(L, B.u, i, j, at, nullptr));
+          B.d[at] = Arith<T>::sub(B.f[at], apply_at<T, EXACT, 1>(L, B.u, i, j, at, nullptr));
           break;
         case kBRestrict:
           B.fc[at] = restrict_value<T, EXACT, false>(*B.L, B.transfer, B.d, i, j);
