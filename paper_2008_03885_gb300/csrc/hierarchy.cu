@@ -894,7 +894,9 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
     const int4* prog = zero_init ? H.d_prog : H.d_prog + 1;
     const int nops = zero_init ? H.nops : H.nops - 1;
     Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
-    if (H.tail_smem > 0) LAUNCH(h, 1, launch_tail_smem<T>(H.d_tail, H.tail_smem, prog, nops, c.exact, c.s));
+    if (H.tail_smem > 0)
+      LAUNCH(h, 1, launch_tail_smem<T>(H.d_tail, H.tail_smem, (int)h->host.size() - H.tail_level, prog, nops,
+                                       c.exact, c.s));
     else LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, prog, nops, c.exact, c.s));
     return MG_OK;
   }
@@ -1041,6 +1043,7 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
       td.sm_d[l] = off + 3 * e;
       off += 4 * e;
     }
+    if (tail_smem_bytes<T>(off, nl - lt) > kTailSmemMaxBytes) return MG_OK;  // no tail
     td.sm_top = lt;
     td.sm_elems = off;
     H.tail_smem = off;
@@ -1054,6 +1057,7 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
     td.transfer[l] = l + 1 < nl ? h->transfer[l] : 0;
   }
   td.smoother = h->opt.smoother;
+  td.nlev = nl;
   td.coarsest_idx = H.coarsest_idx;
   td.coarsest_a = H.coarsest_a;
   td.coarsest_zero = H.coarsest_zero;

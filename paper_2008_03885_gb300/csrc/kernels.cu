@@ -128,6 +128,7 @@ __device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict_
   if (fast_node(L, i, j)) {
     const int32_t* dl = L.delta[L.kind == kRot ? (i & 1) : 0];
     s = Arith<T>::mul(L.c[0], u[at + dl[0]]);
+#pragma unroll CU
     for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, L.c[k], u[at + dl[k]]);
     if (wd) *wd = L.wd;
   } else {
@@ -1255,14 +1256,26 @@ __global__ void __launch_bounds__(kBX * kBY)
 // Levels from sm_top down live in one block's shared memory in a compact rows x cols
 // layout; node (i, j) of a level is at j * cols + (rot ? i >> 1 : i). Arithmetic
 // per node is the same as relax_value / apply_at / restrict_value / prolong_value.
+// The interior stencils of the levels held are staged in shared memory too (per level:
+// coefficients, and shared-memory offsets for even and odd i), so that a fast node's
+// terms need no global-memory reads.
+struct TailStencil {
+  template <typename T>
+  static __host__ __device__ __forceinline__ size_t base(int sm_elems) {  // byte offset of the stencil area
+    return ((size_t)sm_elems * sizeof(T) + 15) & ~(size_t)15;
+  }
+};
+
 template <typename T, bool EXACT>
-__device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i, int j, T* wd) {
+__device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i, int j, T* wd, const T* __restrict__ cs,
+                                        const int* __restrict__ os2) {
   T s;
   if (fast_node(L, i, j)) {
-    const int par = L.kind == kRot ? (i & 1) : 0;
+    const int* os = os2 + (L.kind == kRot ? (i & 1) : 0) * kMaxTerms;
     const int e = smem_idx(L, i, j);
-    s = Arith<T>::mul(L.c[0], u[e + L.sdy[0] * L.cols + L.sdx[par][0]]);
-    for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, L.c[k], u[e + L.sdy[k] * L.cols + L.sdx[par][k]]);
+    s = Arith<T>::mul(cs[0], u[e + os[0]]);
+#pragma unroll 8
+    for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, cs[k], u[e + os[k]]);
     if (wd) *wd = L.wd;
   } else {
     const int cl = class_of(L, i, j);
@@ -1288,6 +1301,20 @@ __global__ void __launch_bounds__(kTailThreads, 1)
   const int tid = threadIdx.x;
   const int top = D->sm_top;
   for (int k = tid; k < D->sm_elems; k += kTailThreads) sm[k] = T(0);
+  // interior stencils of the levels held: coefficients [level][kMaxTerms], offsets
+  // [level][parity][kMaxTerms]
+  const int nst = D->nlev - top;
+  T* stc = reinterpret_cast<T*>(tail_smem + TailStencil::base<T>(D->sm_elems));
+  int* sto = reinterpret_cast<int*>(stc + nst * kMaxTerms);
+  for (int x = tid; x < nst * kMaxTerms; x += kTailThreads) {
+    const int l = top + x / kMaxTerms, k = x - (x / kMaxTerms) * kMaxTerms;
+    const LevelDev<T>& L = *D->L[l];
+    if (k < L.nt) {
+      stc[x] = L.c[k];
+      sto[2 * (l - top) * kMaxTerms + k] = L.sdy[k] * L.cols + L.sdx[0][k];
+      sto[(2 * (l - top) + 1) * kMaxTerms + k] = L.sdy[k] * L.cols + L.sdx[1][k];
+    }
+  }
   __syncthreads();
   {  // top level: u and f from global memory
     const LevelDev<T>& L = *D->L[top];
@@ -1306,6 +1333,8 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     T* U = sm + D->sm_u[l];
     T* Tb = sm + D->sm_t[l];
     T* F = sm + D->sm_f[l];
+    const T* cs = stc + (l - top) * kMaxTerms;
+    const int* os2 = sto + 2 * (l - top) * kMaxTerms;
     int i, j;
     if (op.x == kOpZero) {
       for (int k = tid; k < total; k += kTailThreads) U[k] = T(0);
@@ -1318,7 +1347,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
             if (!tail_node(L, k, i, j)) continue;
             if (is_red(L, i, j) == half) {
               T wd;
-              const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, src, i, j, &wd));
+              const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, src, i, j, &wd, cs, os2));
               dst[k] = EXACT ? Arith<T>::add(src[k], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, src[k]);
             } else {
               dst[k] = src[k];
@@ -1330,7 +1359,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         for (int k = tid; k < total; k += kTailThreads) {
           if (!tail_node(L, k, i, j)) continue;
           T wd;
-          const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, U, i, j, &wd));
+          const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, U, i, j, &wd, cs, os2));
           Tb[k] = EXACT ? Arith<T>::add(U[k], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, U[k]);
         }
         __syncthreads();
@@ -1343,7 +1372,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
       T* Dd = sm + D->sm_d[l];
       for (int k = tid; k < total; k += kTailThreads) {
         if (!tail_node(L, k, i, j)) continue;
-        Dd[k] = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, U, i, j, nullptr));
+        Dd[k] = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, U, i, j, nullptr, cs, os2));
       }
       __syncthreads();
       const LevelDev<T>& Lc = *D->L[l + 1];
@@ -1684,12 +1713,17 @@ cudaError_t launch_batch_ir_update(const BatchLevel<double>* entries, const int*
 }
 
 template <typename T>
-cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, const int4* prog, int nops, bool exact,
+size_t tail_smem_bytes(int sm_elems, int nst) {
+  return TailStencil::base<T>(sm_elems) + (size_t)nst * kMaxTerms * (sizeof(T) + 2 * sizeof(int));
+}
+
+template <typename T>
+cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, const int4* prog, int nops, bool exact,
                              cudaStream_t s) {
-  const size_t bytes = (size_t)sm_elems * sizeof(T);
-  if (bytes > 200 * 1024) return cudaErrorInvalidValue;
+  const size_t bytes = tail_smem_bytes<T>(sm_elems, nst);
+  if (bytes > kTailSmemMaxBytes) return cudaErrorInvalidValue;
   const void* fn = exact ? (const void*)k_tail_smem<T, true> : (const void*)k_tail_smem<T, false>;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (exact) k_tail_smem<T, true><<<1, kTailThreads, bytes, s>>>(desc, prog, nops);
   else k_tail_smem<T, false><<<1, kTailThreads, bytes, s>>>(desc, prog, nops);
   return cudaGetLastError();
@@ -1717,7 +1751,8 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, const int4* 
   template cudaError_t launch_batch_step<T>(int, const BatchLevel<T>*, const int*, int, int, int, const int*, bool, \
                                             cudaStream_t);                                             \
   template int tail_ctas<T>(bool);                                                                    \
-  template cudaError_t launch_tail_smem<T>(const TailDesc<T>*, int, const int4*, int, bool, cudaStream_t); \
+  template cudaError_t launch_tail_smem<T>(const TailDesc<T>*, int, int, const int4*, int, bool, cudaStream_t); \
+  template size_t tail_smem_bytes<T>(int, int);                                                       \
   template cudaError_t launch_tail<T>(int, const TailDesc<T>*, const int4*, int, bool, cudaStream_t);
 
 NSMG_INSTANTIATE(double)

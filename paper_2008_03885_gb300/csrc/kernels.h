@@ -85,14 +85,20 @@ struct TailDesc {
   // block's shared memory (compact rows x cols layout) and the number of levels held
   int32_t sm_u[kTailMaxLevels], sm_t[kTailMaxLevels], sm_f[kTailMaxLevels], sm_d[kTailMaxLevels];
   int32_t sm_top;     // first level held (the sub-cycle's top level)
-  int32_t sm_elems;   // shared-memory elements used
+  int32_t sm_elems;   // shared-memory elements of the level arrays
+  int32_t nlev;       // levels of the hierarchy (those from sm_top on are held)
 };
 
 // The same op list, with every level from sm_top down held in one block's shared
 // memory (u and f of the top level are loaded at start, u written back at the end).
 template <typename T>
-cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, const int4* prog, int nops, bool exact,
+cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, const int4* prog, int nops, bool exact,
                              cudaStream_t s);
+// Dynamic shared memory of the shared-memory tail: the level arrays (sm_elems values)
+// and the interior stencils of its nst levels; at most kTailSmemMaxBytes.
+template <typename T>
+size_t tail_smem_bytes(int sm_elems, int nst);
+constexpr size_t kTailSmemMaxBytes = 227 * 1024;
 
 // Run `nops` ops (x = TailOp, y = level) in order inside one thread-block cluster of
 // `ctas` CTAs, with a cluster barrier after each phase. Op semantics match the
