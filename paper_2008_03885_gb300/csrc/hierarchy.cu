@@ -1080,8 +1080,11 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
 // latency on 16 SMs only wins for the last few levels (measured on GB300).
 constexpr int64_t kTailUnknownsFp64 = 256;
 // FP32 inner hierarchies by default keep their small levels in one block's shared
-// memory (up to 48K elements = 192 KB for u, t, f and d of every tail level).
-constexpr int64_t kTailSmemElemsFp32 = 48 * 1024;
+// memory (up to 12K elements = 48 KB for u, t, f and d of every tail level). A larger
+// tail leaves too little L1 for the boundary-class term records the small levels read
+// (measured on GB300, 4097^2 mixed solve: 48K elements 19.4 ms, 24K 19.0, 12K 19.0,
+// 6K 19.2; 129^2: 2.79, 2.60, 2.54, 2.70 ms).
+constexpr int64_t kTailSmemElemsFp32 = 12 * 1024;
 
 // Power of two near 1 / rms of a residual with squared norm r2 over m unknowns, so
 // that the FP32 copy of the residual stays far from underflow and overflow.
