@@ -122,8 +122,10 @@ typedef struct {
   int32_t inner_cycles;/* mixed precision: FP32 cycles per refinement step (default 1: FP32
                           rounding caps a step's reduction near 5e-4, so more cycles per
                           step cost more than extra steps) */
-  int32_t tail_unknowns;/* levels (below the finest) with at most this many unknowns run inside
-                           one thread-block-cluster kernel; 0 = built-in default, -1 = never */
+  int32_t tail_unknowns;/* the smallest levels run inside one kernel: 0 = built-in default (the
+                           levels whose arrays fit a small budget live in one block's shared
+                           memory), > 0 = levels (below the finest) with at most this many
+                           unknowns run in one thread-block-cluster kernel, -1 = never */
   int32_t tail_ctas;   /* CTAs of that cluster (1..16); 0 = largest the device schedules */
   int32_t sweep_kernel;/* red-black sweeps: 0 = auto (two half-sweep kernels), 1 = half-sweep
                           kernels, 2 = one shared-memory tile kernel per sweep; every choice

@@ -1085,6 +1085,11 @@ constexpr int64_t kTailUnknownsFp64 = 256;
 // (measured on GB300, 4097^2 mixed solve: 48K elements 19.4 ms, 24K 19.0, 12K 19.0,
 // 6K 19.2; 129^2: 2.79, 2.60, 2.54, 2.70 ms).
 constexpr int64_t kTailSmemElemsFp32 = 12 * 1024;
+// FP64 hierarchies by default use a shared-memory tail too, of 3K elements (24 KB);
+// measured on GB300 (FP64 solve, 4097^2 / 513^2 / 129^2): cluster tail 65.8 / 8.45 /
+// 5.55 ms, 3K 65.0 / 7.64 / 4.77, 6K 65.4 / 8.10 / 5.25, 12K 66.6 / 9.42 / 6.33.
+// tail_unknowns > 0 selects the cluster tail with that threshold.
+constexpr int64_t kTailSmemElemsFp64 = 3 * 1024;
 
 // Power of two near 1 / rms of a residual with squared norm r2 over m unknowns, so
 // that the FP32 copy of the residual stays far from underflow and overflow.
@@ -1225,7 +1230,9 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   auto tail_limit = [&](int64_t dflt) -> int64_t {
     return o.tail_unknowns < 0 ? 0 : (o.tail_unknowns > 0 ? (int64_t)o.tail_unknowns : dflt);
   };
-  if ((st = build_tail<double>(h, tail_limit(kTailUnknownsFp64))) != MG_OK) return fail(st);
+  if (o.tail_unknowns == 0 && kTailSmemElemsFp64 > 0) st = build_tail<double>(h, 0, kTailSmemElemsFp64);
+  else st = build_tail<double>(h, tail_limit(kTailUnknownsFp64));
+  if (st != MG_OK) return fail(st);
   if (o.precision == MG_PREC_MIXED_FP32) {
     if ((st = alloc_hier<float>(h, false)) != MG_OK) return fail(st);
     h->h32.coarsest_idx = cidx;
