@@ -193,3 +193,27 @@ def test_printed_multilevel_ecr():
     ref = g["vc_5level_W11_ecr"]
     cr = _cr(per(ref["N"], co=VARIABLE, op=ref["coarse_op"], omega=ref["omega"], gamma=2, max_levels=5), cycles=6)
     assert _in_band(ref, cr ** (1.0 / ((nu + 2) * (1 + 2 / 2 + 4 / 4 + 8 / 16)))), cr
+
+
+def test_printed_three_level_ecr_and_operator_ranking():
+    """App. A: three-level V[1,1] / W[1,1] ECR with Galerkin coarse operators (WU from
+    the appendix formula, which counts the coarsest solve), and the ranking stated
+    there: the true Galerkin operator is best for V and W, G1 and Gn close behind for W."""
+    g = golden("paper_rates_periodic.json")
+    for key, gamma, wu in (("rbc_3level_V11_galerkin_ecr", 1, 10.0), ("rbc_3level_W11_galerkin_ecr", 2, 16.0)):
+        ref = g[key]
+        cr = min(_cr(per(ref["N"], op=GALERKIN, omega=w, gamma=gamma, max_levels=3)) for w in ref["omegas"])
+        assert _in_band(ref, cr ** (1.0 / wu)), (key, cr)
+    for gamma in (1, 2):
+        crs = {op: _cr(per(32, op=op, gamma=gamma, max_levels=3)) for op in (GALERKIN, G1, GN, NONGALERKIN)}
+        assert crs[GALERKIN] == min(crs.values()), crs
+        if gamma == 2:
+            assert max(crs[G1], crs[GN]) < 0.1 * crs[NONGALERKIN], crs
+
+
+def test_printed_fourth_order_two_level_ecr():
+    """Sec. 4.4: fourth-order fine operator, red-black coarsening, second-order
+    non-Galerkin coarse operator: two-level V[1,1] ECR 0.6 (WU = 2 (nu + 2))."""
+    ref = golden("paper_rates_periodic.json")["rbc_2level_V11_order4_ng2_ecr"]
+    cr = min(_cr(per(ref["N"], 4, op=NONGALERKIN, omega=w, max_levels=2)) for w in ref["omegas"])
+    assert _in_band(ref, cr ** (1.0 / 8.0)), cr
