@@ -245,3 +245,26 @@ def test_mixed_precision_8193_reaches_tolerance(order):
     del f, u
     torch.cuda.empty_cache()
     assert math.isfinite(rr)
+
+
+def test_batched_workload_512_problems_reach_tolerance():
+    """512 problems, sides 2^k + 1 with k uniform in {7..11}, order 2 or 4 (50/50),
+    N(0,1) right-hand sides, mixed precision, one level-synchronous batched solve to 1e-8;
+    every problem's reported residual and, for a sample, an independent FP64 residual."""
+    count = 512
+    z = synth.uniform01(91, 2 * count)
+    specs = [(2 ** (7 + int(z[2 * i] * 5)), 2 if z[2 * i + 1] < 0.5 else 4) for i in range(count)]
+    hs, us, fs = [], [], []
+    try:
+        for p, (n, order) in enumerate(specs):
+            hs.append(mg.mg_setup(n, order, "redblack", "galerkin", nu1=2, nu2=1,  # one schedule per batch
+                                  precision=mg.MG_PREC_MIXED_FP32, fma_contract=1))
+            fs.append(torch.tensor(synth.rhs_normal(n, 1000 + p), dtype=torch.float64, device="cuda"))
+            us.append(torch.zeros_like(fs[-1]))
+        cycles, rr = mg.mg_solve_batched(hs, us, fs, rtol=1e-8, max_cycles=40)
+        assert max(rr) < 1e-8 and max(cycles) <= 12
+        for p in range(0, count, 64):
+            assert torch_residual(us[p], fs[p], specs[p][1]) < 1.5e-8, p
+    finally:
+        for h in hs:
+            h.close()
