@@ -192,6 +192,17 @@ mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out
 mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int max_cycles,
                    int* cycles_out, double* history_out, void* stream);
 
+/* mg_solve with u and f in HOST memory ((N+1) x (N+1) doubles, the layout of the
+   device arrays above): copies f and u to device arrays the handle owns (allocated
+   with cudaMalloc on the first call, 2 (N+1)^2 doubles, freed by mg_destroy), runs
+   mg_solve on them, copies the new u back and synchronises the stream before
+   returning. The copies are asynchronous only from pinned (page-locked) host memory;
+   from pageable memory they are staged by the CUDA runtime. Same results, statuses and
+   history as mg_solve; on statuses other than MG_OK and MG_ERR_NOT_CONVERGED u_host is
+   left unchanged. */
+mg_status mg_solve_host(mg_handle* h, double* u_host, const double* f_host, double rtol, int max_cycles,
+                        int* cycles_out, double* history_out, void* stream);
+
 /* Release every buffer of the handle (NULL is accepted). */
 mg_status mg_destroy(mg_handle* h);
 

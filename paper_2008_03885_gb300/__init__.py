@@ -66,6 +66,7 @@ _lib.mg_setup.argtypes = [ctypes.POINTER(mg_grid), ctypes.c_int, ctypes.c_int, c
                           ctypes.POINTER(mg_options), ctypes.POINTER(_vp)]
 _lib.mg_cycle.argtypes = [_vp, _vp, _vp, _dp, _vp]
 _lib.mg_solve.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip, _dp, _vp]
+_lib.mg_solve_host.argtypes = [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip, _dp, _vp]
 _lib.mg_destroy.argtypes = [_vp]
 _lib.mg_status_string.argtypes = [ctypes.c_int]
 _lib.mg_status_string.restype = ctypes.c_char_p
@@ -196,6 +197,33 @@ def mg_solve(h: Handle, u, f, rtol: float = 1e-10, max_cycles: int = 50, stream=
     st = _lib.mg_solve(h.ptr, _ptr(u), _ptr(f), rtol, max_cycles, ctypes.byref(cyc), hist, _stream(stream))
     if st != MG_OK and not (st == MG_ERR_NOT_CONVERGED and not raise_not_converged):
         raise MGError(st, "mg_solve")
+    return cyc.value, [hist[k] for k in range(cyc.value + 1)]
+
+
+def _host_ptr(a, writable: bool) -> int:
+    """Address of a C-contiguous float64 host array: numpy, or a CPU torch tensor."""
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("expected a contiguous float64 CPU tensor")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous float64 numpy array")
+    if writable and not a.flags["WRITEABLE"]:
+        raise ValueError("u must be writable")
+    return a.ctypes.data
+
+
+def mg_solve_host(h: Handle, u, f, rtol: float = 1e-10, max_cycles: int = 50, stream=None,
+                  raise_not_converged: bool = True):
+    """mg_solve on host arrays ((N+1) x (N+1) float64; pinned memory copies fastest):
+    u is overwritten with the new iterate. Returns (cycles, history)."""
+    hist = (ctypes.c_double * (max_cycles + 1))()
+    cyc = ctypes.c_int()
+    st = _lib.mg_solve_host(h.ptr, _host_ptr(u, True), _host_ptr(f, False), rtol, max_cycles,
+                            ctypes.byref(cyc), hist, _stream(stream))
+    if st != MG_OK and not (st == MG_ERR_NOT_CONVERGED and not raise_not_converged):
+        raise MGError(st, "mg_solve_host")
     return cyc.value, [hist[k] for k in range(cyc.value + 1)]
 
 

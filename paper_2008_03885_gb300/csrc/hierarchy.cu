@@ -517,6 +517,8 @@ struct mg_handle {
   };
   GraphEntry g_cycle64, g_inner32;
   cudaStream_t priv = nullptr;  // used when the caller passes the legacy default stream
+  double* host_u = nullptr;     // mg_solve_host: device copies of the caller's u and f
+  double* host_f = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // instrumentation
   int64_t launches = 0, cycles = 0;
@@ -1349,6 +1351,26 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
   }
   if (cycles_out) *cycles_out = k;
   return rr < rtol ? MG_OK : MG_ERR_NOT_CONVERGED;
+}
+
+mg_status mg_solve_host(mg_handle* h, double* u_host, const double* f_host, double rtol, int max_cycles,
+                        int* cycles_out, double* history_out, void* stream) {
+  if (!h || !u_host || !f_host) return MG_ERR_INVALID;
+  const size_t bytes = (size_t)(h->N + 1) * (h->N + 1) * sizeof(double);
+  if (!h->host_u) {  // first call: the handle's device copies of u and f
+    mg_status st;
+    if ((st = device_alloc(h, (void**)&h->host_u, bytes)) != MG_OK) return st;
+    if ((st = device_alloc(h, (void**)&h->host_f, bytes)) != MG_OK) return st;
+    if (cudaStreamSynchronize(h->priv) != cudaSuccess) return MG_ERR_CUDA;  // the zero fills
+  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->host_f, f_host, bytes, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->host_u, u_host, bytes, cudaMemcpyHostToDevice, s));
+  const mg_status st = mg_solve(h, h->host_u, h->host_f, rtol, max_cycles, cycles_out, history_out, stream);
+  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+  CK(cudaMemcpyAsync(u_host, h->host_u, bytes, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
 }
 
 mg_status mg_level_apply(mg_handle* h, int level, const double* u, double* out, void* stream) {

@@ -291,3 +291,26 @@ def test_sixth_order_bitwise(co, op):
     hg, ho, ug, uo = run_pair(n, 6, co, op, F, 6, nu1=2)
     assert np.max(np.abs(hg - ho) / ho) <= HIST_RTOL
     assert np.array_equal(ug, uo)
+
+
+@pytest.mark.parametrize("precision", [mg.MG_PREC_FP64, mg.MG_PREC_MIXED_FP32])
+def test_host_buffer_solve_equals_device_solve(precision):
+    """mg_solve_host (u, f in host memory, pageable numpy or pinned torch) gives the
+    device solve's iterate bit for bit and the same history, on repeated calls."""
+    n = 128
+    F = synth.rhs_sine_modes(n, seed=4, n_modes=8, kmax=32)
+    h = mg.mg_setup(n, 4, REDBLACK, GALERKIN, nu1=2, precision=precision)
+    try:
+        f = torch.tensor(F, dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(f)
+        k, hist = mg.mg_solve(h, u, f, rtol=1e-10, max_cycles=30)
+        for rep in range(2):
+            uh = np.zeros((n + 1, n + 1))
+            kh, hh = mg.mg_solve_host(h, uh, np.ascontiguousarray(F), rtol=1e-10, max_cycles=30)
+            assert kh == k and hh == hist
+            assert np.array_equal(uh, u.cpu().numpy())
+        up = torch.zeros((n + 1, n + 1), dtype=torch.float64).pin_memory()
+        mg.mg_solve_host(h, up, torch.tensor(F).pin_memory(), rtol=1e-10, max_cycles=30)
+        assert torch.equal(up, u.cpu())
+    finally:
+        h.close()
