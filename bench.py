@@ -339,6 +339,7 @@ def run_ours(args, ws, rank, local):
                      "peak_kind": "FP64 1.25 TFLOP/s nominal counted per separately rounded op",
                      "share_of_finest_level_kernel_time": sm_ms / total_kernel_ms if total_kernel_ms else None},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * bytes_grid, "d2h_bytes_per_step": bytes_grid},
+        "throughput": solve_throughput(ms_max, cycles, variants.get("mixed_fp32_inner")),
         "gpu_launches": launches,
         "clocks": clocks,
         "variants": variants,
@@ -527,6 +528,30 @@ def run_profile_mixed(args):
     torch.cuda.synchronize()
     h.close()
     print(json.dumps({"profile_mixed": n, "steps": k, "final": hist[-1]}))
+
+
+# Algorithmic HBM bytes per fine grid point per cycle (every kernel reading its inputs
+# and writing its outputs once; coarse levels of red-black coarsening add a factor
+# sum 2^-l = 2): FP64 V(2,1) 224 B, FP32 V(2,1) 112 B; a refinement step adds the FP64
+# residual (read u, f: 16 B; write the FP32 copy: 4 B) and the update (read u, e; write
+# u: 20 B) to the FP32 cycle.
+BYTES_PER_POINT_FP64_V21 = 224
+BYTES_PER_POINT_MIXED_STEP = 20 + 112 + 20
+
+
+def solve_throughput(fp64_ms, fp64_cycles, mixed):
+    """Grid-point-cycles/s and effective HBM GB/s of whole solves, FP64 vs mixed."""
+    pts = (N + 1) ** 2
+    out = {"fp64": {"grid_point_cycles_per_s": pts * fp64_cycles / (fp64_ms * 1e-3),
+                    "effective_hbm_gbs": BYTES_PER_POINT_FP64_V21 * pts * fp64_cycles / (fp64_ms * 1e-3) / 1e9}}
+    if mixed:
+        out["mixed"] = {"grid_point_cycles_per_s": pts * mixed["cycles"] / (mixed["ms"] * 1e-3),
+                        "effective_hbm_gbs": BYTES_PER_POINT_MIXED_STEP * pts * mixed["cycles"]
+                        / (mixed["ms"] * 1e-3) / 1e9}
+    out["model"] = ("algorithmic bytes per fine point per cycle: FP64 V(2,1) 224 (both FP64-pipe and "
+                    "latency bound, so far below HBM); mixed refinement step 152 (FP64 residual 20 + "
+                    "FP32 V(2,1) 112 + FP64 update 20)")
+    return out
 
 
 def main():
