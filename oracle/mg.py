@@ -6,7 +6,7 @@ is measured against this module; the library never calls it.
 What is computed, and where the paper defines it (Liu & Henshaw, "Multigrid with
 nonstandard coarsening", arXiv:2008.03885):
 
-* Problem: -Laplace u = f on the unit square, N cells per side (h = 1/N, N a power
+* Problem: -Laplace u = f on the square [0, L]^2 (L = 1 by default), N cells per side (h = 1/N, N a power
   of two), Eq. (G_h_N). Homogeneous Dirichlet data with the interior nodes as
   unknowns (Sec. 2.1), or periodic boundaries, the setting of the paper's computed
   results (Sec. 2.2, computations), with the nodes 0 <= i, j < N as unknowns: every
@@ -378,7 +378,7 @@ class Oracle:
 
     def __init__(self, n: int, order: int = 2, coarsening: str = REDBLACK,
                  coarse_op: str = GALERKIN, options: Options | None = None,
-                 boundary: str = DIRICHLET):
+                 boundary: str = DIRICHLET, length: float = 1.0):
         assert n >= 2 and (n & (n - 1)) == 0, "N must be a power of two"
         assert order in (2, 4, 6)
         assert boundary in (DIRICHLET, PERIODIC)
@@ -386,7 +386,7 @@ class Oracle:
         self.boundary = boundary
         self.periodic = boundary == PERIODIC
         self.opt = options or Options()
-        h = 1.0 / n
+        h = length / n  # the square [0, length]^2 (the paper's unit square: length 1)
         n_min = self.opt.n_min if self.opt.n_min is not None else (1 if self.periodic else 2)
         self.levels = [_make_level(k, m, r2, self.periodic) for k, m, r2 in
                        level_shapes(n, coarsening, n_min, self.opt.max_levels)]
@@ -452,6 +452,36 @@ class Oracle:
             self.wd = [self.opt.omega / lev.A.diagonal() for lev in self.levels]
         last = self.levels[-1]
         self._coarse_dense = last.A.toarray()
+        self._g = None  # nonzero Dirichlet data (set_boundary), level 0 only
+
+    # ---- nonzero Dirichlet data (second order) ------------------------------
+    def set_boundary(self, grid: np.ndarray) -> None:
+        """Use the boundary entries of an (n+1) x (n+1) grid as Dirichlet data g (the
+        paper's B u = g, Sec. 2.1), order 2 only. Level 0 then applies the 5-point stencil
+        to the full grid [interior u; boundary g], summing in increasing full-grid
+        (row-major) column order; the coarse levels keep solving homogeneous correction
+        equations."""
+        assert self.order == 2 and not self.periodic
+        lev = self.levels[0]
+        n = lev.n
+        rows, cols, vals = [], [], []
+        for (a, b), w in FIVE_POINT.items():
+            rows.append(np.arange(lev.size))
+            cols.append((lev.pj + b) * (n + 1) + (lev.pi + a))
+            vals.append(np.full(lev.size, w))
+        W = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(lev.size, (n + 1) ** 2)).tocsr()
+        W.sort_indices()
+        self._A0_full = Ell((W * lev.s).tocsr())
+        self._interior = lev.pj * (n + 1) + lev.pi
+        self._g = np.ascontiguousarray(grid, dtype=np.float64).ravel().copy()
+
+    def _Au(self, l: int, u: np.ndarray) -> np.ndarray:
+        if l == 0 and self._g is not None:
+            full = self._g.copy()
+            full[self._interior] = u
+            return self._A0_full @ full
+        return self._A[l] @ u
 
     # ---- grid <-> vector -------------------------------------------------
     def to_vec(self, grid: np.ndarray, level: int = 0) -> np.ndarray:
@@ -470,10 +500,10 @@ class Oracle:
 
     # ---- level operations ------------------------------------------------
     def apply(self, l: int, u: np.ndarray) -> np.ndarray:
-        return self._A[l] @ u
+        return self._Au(l, u)
 
     def residual(self, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
-        return f - self._A[l] @ u
+        return f - self._Au(l, u)
 
     def restrict(self, l: int, d: np.ndarray) -> np.ndarray:
         return self._R[l] @ d
@@ -483,12 +513,12 @@ class Oracle:
 
     def half_sweep(self, l: int, u: np.ndarray, f: np.ndarray, red: bool) -> np.ndarray:
         mask = self.levels[l].red if red else ~self.levels[l].red
-        r = f - self._A[l] @ u
+        r = f - self._Au(l, u)
         return np.where(mask, u + r * self.wd[l], u)
 
     def smooth(self, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
         if self.opt.smoother == "jacobi":
-            r = f - self._A[l] @ u
+            r = f - self._Au(l, u)
             return u + r * self.wd[l]
         u = self.half_sweep(l, u, f, red=True)
         return self.half_sweep(l, u, f, red=False)
@@ -510,7 +540,7 @@ class Oracle:
         o = self.opt
         for _ in range(o.nu1):
             u = self.smooth(l, u, f)
-        d = f - self._A[l] @ u
+        d = f - self._Au(l, u)
         fc = self._R[l] @ d
         if l + 1 == self.lmax:
             uc = self.coarse_solve(fc)
@@ -535,7 +565,7 @@ class Oracle:
         return self.cycle_level(0, u, f)
 
     def rel_residual(self, u: np.ndarray, f: np.ndarray) -> float:
-        d = f - self._A[0] @ u
+        d = f - self._Au(0, u)
         return math.sqrt(float(np.dot(d, d))) / math.sqrt(float(np.dot(f, f)))
 
     def solve(self, f: np.ndarray, u: np.ndarray | None = None, rtol: float = 1e-10,

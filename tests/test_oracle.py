@@ -391,3 +391,46 @@ def test_sixth_order_with_second_order_coarse_operators_converges():
         o = Oracle(64, 6, REDBLACK, op, Options(nu1=2, nu2=1))
         cr = _asymptotic_cr(o)
         assert cr < 0.1, (op, cr)
+
+
+def test_domain_length_scales_every_level_operator():
+    """On [0, L]^2 the grid spacing is L/N (Eq. G_h_N with h = L/N): for L = 2 every
+    level operator is exactly 1/4 of the unit square's; for L = 3 a single sine mode
+    is still solved by f / symbol with the symbol evaluated at h = L/N."""
+    for order, co, op in ((2, REDBLACK, GALERKIN), (4, STANDARD, NONGALERKIN), (4, REDBLACK, TRUE_HIGH)):
+        o1 = Oracle(32, order, co, op)
+        o2 = Oracle(32, order, co, op, length=2.0)
+        for a, b in zip(o1.levels, o2.levels):
+            assert abs(a.A * 0.25 - b.A).max() == 0
+    n, k, l, L = 64, 3, 7, 3.0
+    o = Oracle(n, 4, REDBLACK, GALERKIN, Options(nu1=2), length=L)
+    f = o.to_vec(synth.rhs_single_mode(n, k, l))  # sin(k pi x/L) sin(l pi y/L) at the nodes
+    lam = lfa.symbol_L4(k * math.pi / n, l * math.pi / n, L / n)
+    u, _ = o.solve(f, rtol=1e-14, max_cycles=30)
+    assert np.max(np.abs(u - f / lam)) <= 1e-12 * np.max(np.abs(f / lam))
+
+
+def test_nonzero_dirichlet_data_reproduces_a_quadratic_exactly():
+    """B u = g (Sec. 2.1) with second order: the 5-point operator is exact on quadratics,
+    so for u = x^2 - 2 y^2 + 3 x y (-Laplace u = 2) and g = u on the boundary the
+    discrete solution is u itself at every node."""
+    for n, co, op in ((32, REDBLACK, GALERKIN), (64, STANDARD, NONGALERKIN), (64, REDBLACK, G1)):
+        x = np.arange(n + 1) / n
+        X, Y = np.meshgrid(x, x)  # rows = y
+        U = X ** 2 - 2 * Y ** 2 + 3 * X * Y
+        o = Oracle(n, 2, co, op)
+        o.set_boundary(U)
+        f = o.to_vec(np.full((n + 1, n + 1), 2.0))
+        u, h = o.solve(f, rtol=1e-12, max_cycles=60)  # rounding floor ~3e-13 here
+        assert h[-1] < 1e-12
+        assert np.max(np.abs(u - o.to_vec(U))) <= 1e-12 * np.max(np.abs(U))
+
+
+def test_zero_dirichlet_data_gives_the_homogeneous_iterates():
+    n = 32
+    o1, o2 = Oracle(n, 2, REDBLACK, GALERKIN), Oracle(n, 2, REDBLACK, GALERKIN)
+    o2.set_boundary(np.zeros((n + 1, n + 1)))
+    f = o1.to_vec(synth.rhs_normal(n, 2))
+    u1, h1 = o1.solve(f, max_cycles=6, fixed_cycles=True)
+    u2, h2 = o2.solve(f, max_cycles=6, fixed_cycles=True)
+    assert np.array_equal(u1, u2) and h1 == h2
