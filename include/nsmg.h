@@ -14,15 +14,17 @@
  *
  * Conventions shared by every call
  * --------------------------------
- * - Domain: the unit square, N cells per side (N a power of two, 4 <= N <= 16384),
- *   h = 1/N, Eq. (G_h_N), with homogeneous Dirichlet boundary values (default) or
+ * - Domain: the square [0, length]^2 (default the unit square), N cells per side (N a
+ *   power of two, 4 <= N <= 16384), h = length/N, Eq. (G_h_N), with homogeneous Dirichlet boundary values (default) or
  *   periodic boundaries (mg_options.boundary), the setting of the paper's computed
  *   results (Sec. 2.2).
  * - Grid arrays on the finest level are caller-owned DEVICE pointers to
  *   (N+1) x (N+1) contiguous doubles, row-major with x fastest:
  *   a[j*(N+1) + i] is the node (i h, j h).
  *   Dirichlet: the unknowns are the interior nodes 0 < i, j < N; boundary entries
- *   of f are ignored and those of u are set to zero by mg_cycle / mg_solve.
+ *   of f are ignored and those of u are set to zero by mg_cycle / mg_solve, unless
+ *   mg_options.dirichlet_data = 1 (second order), where they hold the data g and are
+ *   kept.
  *   Periodic: the unknowns are the nodes 0 <= i, j < N (node N is node 0); row N
  *   and column N of u and f are neither read nor written. The periodic operator
  *   annihilates constants, so f must have zero mean over the unknowns (else the
@@ -105,7 +107,9 @@ typedef enum {
 } mg_boundary;
 
 typedef struct {
-  int32_t n; /* cells per side, power of two */
+  int32_t n;     /* cells per side, power of two */
+  double length; /* side of the square domain [0, length]^2, h = length / n; 0 means 1 (the
+                    paper's unit square); negative or non-finite: MG_ERR_INVALID */
 } mg_grid;
 
 typedef struct {
@@ -143,6 +147,18 @@ typedef struct {
                           coefficients over cubic transfers need more than 53 bits from the
                           fourth coarse level on: the recursion is done exactly and each level
                           rounded once to FP64 */
+  int32_t dirichlet_data; /* 0 (default): homogeneous Dirichlet data, the boundary entries of u
+                          are set to zero; 1: the boundary entries of u hold the data g of
+                          B u = g (Sec. 2.1) and are kept (second order, Dirichlet boundary
+                          only; MG_ERR_UNSUPPORTED otherwise) */
+  /* Device memory of the handle's buffers (default NULL, NULL: cudaMalloc / cudaFree),
+     e.g. a framework's caching allocator. Both or neither must be set. dev_alloc returns
+     NULL on failure (MG_ERR_OOM); memory must be usable from any stream of the current
+     device. mg_destroy synchronises the device before handing buffers to dev_free. The
+     callbacks run inside mg_setup, mg_solve_host (its first call) and mg_destroy. */
+  void* (*dev_alloc)(size_t bytes, void* ctx);
+  void (*dev_free)(void* ptr, void* ctx);
+  void* alloc_ctx;
 } mg_options;
 
 typedef struct mg_handle mg_handle;

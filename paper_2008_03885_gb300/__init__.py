@@ -39,7 +39,7 @@ COARSE_OP = {"nongalerkin": MG_OP_NONGALERKIN, "galerkin": MG_OP_GALERKIN, "g1":
 
 
 class mg_grid(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32)]
+    _fields_ = [("n", ctypes.c_int32), ("length", ctypes.c_double)]
 
 
 class mg_options(ctypes.Structure):
@@ -49,7 +49,11 @@ class mg_options(ctypes.Structure):
                 ("fma_contract", ctypes.c_int32), ("inner_cycles", ctypes.c_int32),
                 ("tail_unknowns", ctypes.c_int32), ("tail_ctas", ctypes.c_int32),
                 ("sweep_kernel", ctypes.c_int32), ("bf16_levels", ctypes.c_int32),
-                ("boundary", ctypes.c_int32), ("transfer_order", ctypes.c_int32)]
+                ("boundary", ctypes.c_int32), ("transfer_order", ctypes.c_int32),
+                ("dirichlet_data", ctypes.c_int32),
+                ("dev_alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)),
+                ("dev_free", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)),
+                ("alloc_ctx", ctypes.c_void_p)]
 
 
 class mg_level_info(ctypes.Structure):
@@ -139,8 +143,9 @@ def mg_default_options(**overrides) -> mg_options:
     return o
 
 
-def mg_workspace_bytes(n: int, order: int = 2, coarsening="redblack", coarse_op="galerkin", **opts) -> int:
-    g = mg_grid(n)
+def mg_workspace_bytes(n: int, order: int = 2, coarsening="redblack", coarse_op="galerkin", length: float = 1.0,
+                       **opts) -> int:
+    g = mg_grid(n, length)
     o = mg_default_options(**opts)
     return int(_lib.mg_workspace_bytes(ctypes.byref(g), order, COARSENING.get(coarsening, coarsening),
                                        COARSE_OP.get(coarse_op, coarse_op), ctypes.byref(o)))
@@ -170,13 +175,44 @@ class Handle:
         self.close()
 
 
-def mg_setup(n: int, order: int = 2, coarsening="redblack", coarse_op="galerkin", **opts) -> Handle:
-    g = mg_grid(n)
+def _torch_allocator():
+    """(dev_alloc, dev_free) callbacks drawing the handle's buffers from torch's CUDA
+    caching allocator on the current device."""
+    import torch
+    dev = torch.cuda.current_device()
+    alloc_t = mg_options._fields_[-3][1]
+    free_t = mg_options._fields_[-2][1]
+
+    def alloc(size, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), dev)
+        except Exception:  # out of memory: the library reports MG_ERR_OOM
+            return None
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return alloc_t(alloc), free_t(free)
+
+
+def mg_setup(n: int, order: int = 2, coarsening="redblack", coarse_op="galerkin", length: float = 1.0,
+             allocator=None, **opts) -> Handle:
+    """Build a hierarchy for the square [0, length]^2 with n cells per side.
+    allocator=None: cudaMalloc; "torch": torch's CUDA caching allocator."""
+    g = mg_grid(n, length)
     o = mg_default_options(**opts)
+    keep = None
+    if allocator == "torch":
+        keep = _torch_allocator()
+        o.dev_alloc, o.dev_free = keep
+    elif allocator is not None:
+        raise ValueError("allocator must be None or 'torch'")
     out = _vp()
     _check(_lib.mg_setup(ctypes.byref(g), order, COARSENING.get(coarsening, coarsening),
                          COARSE_OP.get(coarse_op, coarse_op), ctypes.byref(o), ctypes.byref(out)), "mg_setup")
-    return Handle(out.value)
+    h = Handle(out.value)
+    h._callbacks = keep  # the callbacks must outlive the handle
+    return h
 
 
 def mg_destroy(h: Handle):

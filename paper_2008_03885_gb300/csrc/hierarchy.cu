@@ -495,6 +495,7 @@ struct Hier {
 
 struct mg_handle {
   int N = 0, order = 2, coarsening = 1, coarse_op = 1;
+  double length = 1.0;  // side of the square domain
   mg_options opt;
   std::vector<HostLevel> host;
   std::vector<int> transfer;
@@ -582,6 +583,7 @@ int coarsest_n(const mg_options& o) { return o.boundary == MG_BOUNDARY_PERIODIC 
 
 mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op, const mg_options& o) {
   if (!grid || !pow2(grid->n) || grid->n < 4 || grid->n > 16384) return MG_ERR_INVALID;
+  if (!(grid->length >= 0.0) || !std::isfinite(grid->length)) return MG_ERR_INVALID;
   if (order != 2 && order != 4 && order != 6) return MG_ERR_INVALID;
   if (coarsening != MG_COARSEN_STANDARD && coarsening != MG_COARSEN_REDBLACK && coarsening != MG_COARSEN_VARIABLE)
     return MG_ERR_INVALID;
@@ -597,6 +599,9 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
   if (o.bf16_levels > 0 && (o.precision != MG_PREC_MIXED_FP32 || o.sweep_kernel == 2)) return MG_ERR_UNSUPPORTED;
   if (o.boundary != MG_BOUNDARY_DIRICHLET && o.boundary != MG_BOUNDARY_PERIODIC) return MG_ERR_INVALID;
   if (o.transfer_order != 2 && o.transfer_order != 4) return MG_ERR_INVALID;
+  if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr)) return MG_ERR_INVALID;
+  if (o.dirichlet_data != 0 && o.dirichlet_data != 1) return MG_ERR_INVALID;
+  if (o.dirichlet_data == 1 && (order != 2 || o.boundary != MG_BOUNDARY_DIRICHLET)) return MG_ERR_UNSUPPORTED;
   if (o.transfer_order == 4 && coarsening != MG_COARSEN_STANDARD) return MG_ERR_UNSUPPORTED;
   if (o.boundary == MG_BOUNDARY_PERIODIC && o.sweep_kernel == 2) return MG_ERR_UNSUPPORTED;
   if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
@@ -607,7 +612,7 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
 // Level operators for the chosen coarse-operator family (Sec. 2.3 notation).
 // Returns false if an exact Galerkin recursion outgrows its integer width.
 bool build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
-  const double hf = 1.0 / h->N;
+  const double hf = h->length / h->N;
   const double s2 = 1.0 / (hf * hf);         // operators derived from L_h^(2)
   const double s4 = 1.0 / (12.0 * hf * hf);  // operators derived from L_h^(4)
   const int nl = (int)shapes.size();
@@ -695,10 +700,15 @@ size_t level_bytes(const HostLevel& L, size_t elem) { return (size_t)L.rows * L.
 
 mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
   if (bytes == 0) bytes = 256;
-  cudaError_t e = cudaMalloc(p, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+  if (h->opt.dev_alloc) {  // caller's allocator
+    *p = h->opt.dev_alloc(bytes, h->opt.alloc_ctx);
+    if (!*p) return MG_ERR_OOM;
+  } else {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+    }
   }
   h->allocs.push_back(*p);
   if (cudaMemsetAsync(*p, 0, bytes, h->priv) != cudaSuccess) return MG_ERR_CUDA;
@@ -748,7 +758,13 @@ void free_all(mg_handle* h) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
-  for (void* p : h->allocs) cudaFree(p);
+  if (h->opt.dev_free) {
+    // the caller's allocator may hand the memory out again at once: wait for every stream
+    if (!h->allocs.empty()) cudaDeviceSynchronize();
+    for (void* p : h->allocs) h->opt.dev_free(p, h->opt.alloc_ctx);
+  } else {
+    for (void* p : h->allocs) cudaFree(p);
+  }
   for (void* p : h->host_allocs) cudaFreeHost(p);
   h->allocs.clear();
   h->host_allocs.clear();
@@ -1197,6 +1213,7 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   mg_handle* h = new (std::nothrow) mg_handle();
   if (!h) return MG_ERR_OOM;
   h->N = grid->n;
+  h->length = grid->length > 0.0 ? grid->length : 1.0;
   h->order = order;
   h->coarsening = coarsening;
   h->coarse_op = coarse_op;
@@ -1281,7 +1298,10 @@ mg_status mg_cycle(mg_handle* h, double* u, const double* f, double* rel_res_out
   if (!h || !u || !f) return MG_ERR_INVALID;
   StreamScope scope(h, stream);
   Ctx c{h, scope.s, h->opt.fma_contract == 0};
-  if (!h->host[0].per) LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
+  if (h->opt.dirichlet_data)  // the ping-pong array's boundary holds the data g too
+    LAUNCH(h, 1, launch_copy_boundary<double>(h->h64.L[0], u, h->h64.t[0], c.s));
+  else if (!h->host[0].per)
+    LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   mg_status st;
   double fn2;
   if (h->opt.precision == MG_PREC_MIXED_FP32) {
@@ -1310,7 +1330,10 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
   if (!h || !u || !f || max_cycles < 0 || !(rtol >= 0.0)) return MG_ERR_INVALID;
   StreamScope scope(h, stream);
   Ctx c{h, scope.s, h->opt.fma_contract == 0};
-  if (!h->host[0].per) LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
+  if (h->opt.dirichlet_data)  // the ping-pong array's boundary holds the data g too
+    LAUNCH(h, 1, launch_copy_boundary<double>(h->h64.L[0], u, h->h64.t[0], c.s));
+  else if (!h->host[0].per)
+    LAUNCH(h, 1, launch_zero_boundary<double>(h->h64.L[0], u, c.s));
   double fn2, rr;
   mg_status st = f_norm2(h, c.s, f, &fn2);
   if (st != MG_OK) return st;
@@ -1839,7 +1862,10 @@ mg_status mg_batch_solve(mg_batch* b, double* const* u, const double* const* f, 
     b->fin[p].u = u[p];
     b->fin[p].f = const_cast<double*>(f[p]);
     ++b->launches;
-    CK(launch_zero_boundary<double>(b->hs[p]->h64.L[0], u[p], s));
+    if (b->hs[p]->opt.dirichlet_data)  // the boundary of u holds the data g: into the ping-pong array
+      CK(launch_copy_boundary<double>(b->hs[p]->h64.L[0], u[p], b->hs[p]->h64.t[0], s));
+    else
+      CK(launch_zero_boundary<double>(b->hs[p]->h64.L[0], u[p], s));
   }
   CK(cudaMemcpyAsync(b->d_fin, b->fin.data(), n * sizeof(BatchLevel<double>), cudaMemcpyHostToDevice, s));
   if (!b->mixed) {

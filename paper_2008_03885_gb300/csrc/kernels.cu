@@ -972,6 +972,15 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int count, do
   if (tid == 0) *out = v;
 }
 
+// Boundary ring of src into dst (Dirichlet data g into the level-0 ping-pong array).
+template <typename T>
+__global__ void k_copy_boundary(int n, int pitch, const T* __restrict__ src, T* __restrict__ dst) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > n) return;
+  const int64_t at[4] = {k, (int64_t)n * pitch + k, (int64_t)k * pitch, (int64_t)k * pitch + n};
+  for (int m = 0; m < 4; ++m) dst[at[m]] = src[at[m]];
+}
+
 template <typename T>
 __global__ void k_zero_boundary(int n, int pitch, T* __restrict__ u) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1600,6 +1609,13 @@ cudaError_t launch_sumsq(const LevelPair<T>& L, const T* f, double* partial, dou
 }
 
 template <typename T>
+cudaError_t launch_copy_boundary(const LevelPair<T>& L, const T* src, T* dst, cudaStream_t s) {
+  const int n = L.h.n;
+  k_copy_boundary<T><<<(n + 1 + 255) / 256, 256, 0, s>>>(n, L.h.pitch, src, dst);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s) {
   const int n = L.h.n;
   k_zero_boundary<T><<<(n + 1 + 255) / 256, 256, 0, s>>>(n, L.h.pitch, u);
@@ -1748,6 +1764,7 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, con
                                          double*, cudaStream_t);                                      \
   template cudaError_t launch_sumsq<T>(const LevelPair<T>&, const T*, double*, double*, cudaStream_t); \
   template cudaError_t launch_zero_boundary<T>(const LevelPair<T>&, T*, cudaStream_t);                \
+  template cudaError_t launch_copy_boundary<T>(const LevelPair<T>&, const T*, T*, cudaStream_t);      \
   template cudaError_t launch_batch_step<T>(int, const BatchLevel<T>*, const int*, int, int, int, const int*, bool, \
                                             cudaStream_t);                                             \
   template int tail_ctas<T>(bool);                                                                    \

@@ -54,6 +54,9 @@ cudaError_t launch_sumsq(const LevelPair<T>& L, const T* f, double* partial, dou
 // Zero the boundary entries of an axis-level array.
 template <typename T>
 cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s);
+// Copy the boundary ring of src (a level's storage) into dst.
+template <typename T>
+cudaError_t launch_copy_boundary(const LevelPair<T>& L, const T* src, T* dst, cudaStream_t s);
 
 // Refinement step, finest level (FP64 grid, FP32 grid of the same storage layout):
 // r32 = fl32((f - L u) * scale), *out = sum of (f - L u)^2 (two launches).

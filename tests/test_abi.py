@@ -73,6 +73,12 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
         mg.mg_setup(64, n_min=8)
     assert e.value.status == mg.MG_ERR_UNSUPPORTED
     with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, length=-1.0)
+    assert e.value.status == mg.MG_ERR_INVALID
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, length=float("inf"))
+    assert e.value.status == mg.MG_ERR_INVALID
+    with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, boundary=2)
     assert e.value.status == mg.MG_ERR_INVALID
     with pytest.raises(mg.MGError) as e:

@@ -314,3 +314,98 @@ def test_host_buffer_solve_equals_device_solve(precision):
         assert torch.equal(up, u.cpu())
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("length", [2.5, 0.25])
+def test_domain_length_matches_oracle(length):
+    n = 64
+    F = synth.rhs_normal(n, seed=31)
+    o = Oracle(n, 4, REDBLACK, GALERKIN, Options(nu1=2), length=length)
+    uo, ho = o.solve(o.to_vec(F), max_cycles=8, fixed_cycles=True)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
+    u = torch.zeros_like(f)
+    h = mg.mg_setup(n, 4, REDBLACK, GALERKIN, nu1=2, length=length)
+    try:
+        k, hg = mg.mg_solve(h, u, f, rtol=0.0, max_cycles=8, raise_not_converged=False)
+    finally:
+        h.close()
+    assert np.max(np.abs(np.array(hg) - np.array(ho)) / np.array(ho)) <= HIST_RTOL
+    assert np.array_equal(o.to_vec(u.cpu().numpy()), uo)
+
+
+def test_torch_caching_allocator_holds_the_hierarchy():
+    """allocator="torch": every handle buffer comes from torch's caching allocator
+    (visible in torch.cuda.memory_allocated, returned on close) and the iterates are
+    those of the cudaMalloc path bit for bit."""
+    n = 256
+    F = synth.rhs_normal(n, seed=5)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
+    outs = []
+    for allocator in (None, "torch"):
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        h = mg.mg_setup(n, 4, REDBLACK, GALERKIN, nu1=2, allocator=allocator,
+                        precision=mg.MG_PREC_MIXED_FP32)
+        held = torch.cuda.memory_allocated() - before
+        u = torch.zeros_like(f)
+        k, hist = mg.mg_solve(h, u, f, rtol=1e-10, max_cycles=30)
+        h.close()
+        torch.cuda.synchronize()
+        outs.append((u.cpu().numpy(), hist))
+        if allocator == "torch":
+            assert held >= mg.mg_workspace_bytes(n, 4, REDBLACK, GALERKIN, precision=mg.MG_PREC_MIXED_FP32)
+            assert torch.cuda.memory_allocated() == before
+        else:
+            assert held == 0
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("co,op", [(REDBLACK, GALERKIN), (STANDARD, NONGALERKIN)])
+def test_nonzero_dirichlet_data_matches_oracle(co, op):
+    """dirichlet_data = 1 (second order): the boundary entries of u hold g and stay;
+    iterates and histories bitwise those of the oracle with the same data."""
+    n = 128
+    x = np.arange(n + 1) / n
+    X, Y = np.meshgrid(x, x)
+    G = np.sin(3 * X) * np.cosh(2 * Y) + X * Y  # boundary data
+    F = synth.rhs_normal(n, seed=12)
+    o = Oracle(n, 2, co, op)
+    o.set_boundary(G)
+    uo, ho = o.solve(o.to_vec(F), max_cycles=8, fixed_cycles=True)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
+    u = torch.tensor(G, dtype=torch.float64, device="cuda")
+    u[1:-1, 1:-1] = 0.0
+    h = mg.mg_setup(n, 2, co, op, dirichlet_data=1)
+    try:
+        k, hg = mg.mg_solve(h, u, f, rtol=0.0, max_cycles=8, raise_not_converged=False)
+    finally:
+        h.close()
+    ug = u.cpu().numpy()
+    assert np.max(np.abs(np.array(hg) - np.array(ho)) / np.array(ho)) <= HIST_RTOL
+    assert np.array_equal(o.to_vec(ug), uo)
+    edge = np.ones((n + 1, n + 1), dtype=bool)
+    edge[1:-1, 1:-1] = False
+    assert np.array_equal(ug[edge], G[edge])
+
+
+def test_dirichlet_data_quadratic_is_exact_in_mixed_precision():
+    n = 512
+    x = np.arange(n + 1) / n
+    X, Y = np.meshgrid(x, x)
+    U = X ** 2 - 2 * Y ** 2 + 3 * X * Y
+    f = torch.full((n + 1, n + 1), 2.0, dtype=torch.float64, device="cuda")
+    u = torch.tensor(U, dtype=torch.float64, device="cuda")
+    u[1:-1, 1:-1] = 0.0
+    h = mg.mg_setup(n, 2, REDBLACK, GALERKIN, dirichlet_data=1, precision=mg.MG_PREC_MIXED_FP32)
+    try:
+        # the rounding floor of the residual is ~1e-10 here (terms ~1e6 against f = 2)
+        k, hist = mg.mg_solve(h, u, f, rtol=1e-9, max_cycles=30)
+    finally:
+        h.close()
+    assert np.max(np.abs(u.cpu().numpy() - U)) <= 1e-8
+
+
+def test_dirichlet_data_rejected_for_wide_stencils():
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_setup(64, 4, REDBLACK, GALERKIN, dirichlet_data=1)
+    assert e.value.status == mg.MG_ERR_UNSUPPORTED
