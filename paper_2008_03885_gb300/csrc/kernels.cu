@@ -62,6 +62,10 @@ __device__ __forceinline__ ClassTerm<T> load_term(const ClassTerm<T>* p) {
   return t;
 }
 
+// Hint: bring the line holding *p into L2, so that the loads issued later wait on L2
+// rather than DRAM (more bytes in flight than the registers of a thread allow).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // s + c * x in the chosen rounding mode.
 // Value as stored on a level: FP32 levels of the bfloat16 storage trial round it.
 template <typename T>
@@ -207,6 +211,20 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_n
   const int n = L.n;
   constexpr int lo = PER ? 0 : 1;
   const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
+  // Prefetch the thread's u and f lines of all its rows into L2 before the first row's
+  // loads. Measured on GB300 at 4097^2: FP32 axis half-sweep 59.5 -> 55.3 us (order 4),
+  // 52.3 -> 45.8 us (order 2); FP64 rotated 178 -> 173 us; no gain (or a loss) for the
+  // other two combinations, which skip it.
+  if ((sizeof(T) == 4) == (L.kind == kAxis)) {
+    const int col = L.kind == kAxis ? min(2 * (int)(blockIdx.x * kBX + threadIdx.x), n)
+                                    : min((int)(blockIdx.x * kBX + threadIdx.x), L.cols - 1);
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int64_t at = (int64_t)min(jb + r * kBY, L.rows - 1) * L.pitch + col;
+      prefetch_l2(uin + at);
+      prefetch_l2(f + at);
+    }
+  }
   if (L.kind == kAxis) {
     const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
     if (i0 > n) return;
@@ -261,6 +279,16 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_residual_nt(
   const int q = blockIdx.x * kBX + threadIdx.x;
   if (q >= L.cols) return;
   const int jb = blockIdx.y * (kBY * kRows) + threadIdx.y;
+  // Same L2 prefetch as the half-sweeps: FP32 level-0 residual 120 -> 103 us at 4097^2
+  // (order 4); FP64 (bound by the FP64 pipe) unchanged, so it skips it.
+  if (sizeof(T) == 4) {
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int64_t at = (int64_t)min(jb + r * kBY, L.rows - 1) * L.pitch + q;
+      prefetch_l2(u + at);
+      prefetch_l2(f + at);
+    }
+  }
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
     const int j = jb + r * kBY;
