@@ -38,7 +38,7 @@ WORKLOAD = ("2D Poisson -Lap u = f, 4th-order 9-point Laplacian, 4097x4097 nodes
 # DRAM bytes (read + write) per launch of the dominant kernel, k_half_sweep_nt<double,
 # exact, 9> on level 0, from one ncu capture of `bench.py --profile-case`
 # (profiles/k_half_sweep_nt_fp64_order4_N4096.md); None whenever that kernel changes.
-DOMINANT_KERNEL_TRAFFIC_BYTES = 373.28e6
+DOMINANT_KERNEL_TRAFFIC_BYTES = 373.26e6
 
 # FP64 ALU peak for non-fused FP64 operations: GB300 FP64 1.25 TFLOP/s counts an FMA as
 # two flops, i.e. 0.625 T FP64 instructions/s; a kernel that rounds every product
