@@ -908,23 +908,77 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value)
   uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_cubic_value<T, EXACT, PER>(*Lcp, vc, i, j)));
 }
 
-template <typename T, bool EXACT, bool PER>
+// On large levels the restriction and interpolation kernels give each thread
+// kTransferRows rows (kBY apart) and prefetch the lines those rows read into L2 first;
+// interpolation onto an axis level also takes a node pair (2p, 2p + 1) per thread, so
+// that every lane evaluates one node of each kind (a copied coarse value and an
+// average; with one node per thread alternate lanes idled through the average).
+// Measured at 4097^2 (FP64 / FP32): level-0 interpolation 262 -> 152 / 75 -> 53 us,
+// FP32 level-0 restriction 83 -> 73 us; on levels below 2048 rows and on rotated fine
+// levels the one-node-per-thread form was as fast or faster, so those keep it.
+constexpr int kTransferRows = 4;
+constexpr int kTransferRowsMinLevelRows = 2048;
+
+template <typename T, bool EXACT, bool PER, int ROWS>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
                            int transfer, const T* __restrict__ d, T* __restrict__ fc) {
+  const LevelDev<T>& Lf = *Lfp;
   const LevelDev<T>& Lc = *Lcp;
-  int i, j;
-  if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
-  fc[sidx(Lc, i, j)] = rnd(Lc, restrict_value<T, EXACT, PER>(*Lfp, transfer, d, i, j));
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  if (q >= Lc.cols) return;
+  const int jb = blockIdx.y * (kBY * ROWS) + threadIdx.y;
+#pragma unroll
+  for (int r = 0; r < (ROWS > 1 ? ROWS : 0); ++r) {
+    // fine node under the coarse node (and the odd fine row after it for H = 2h)
+    const int j = min(jb + r * kBY, Lc.rows - 1);
+    const int i = Lc.kind == kRot ? 2 * q + (j & 1) : q;
+    const int fi = min(transfer == kRbAxisToRot ? i : 2 * i, Lf.n);
+    const int fj = min(transfer == kRbAxisToRot ? j : 2 * j, Lf.n);
+    prefetch_l2(d + sidx(Lf, fi, fj));
+    if (transfer != kRbAxisToRot && fj < Lf.n) prefetch_l2(d + sidx(Lf, min(fi + 1, Lf.n), fj + 1));
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int j = jb + r * kBY;
+    if (j >= Lc.rows) break;
+    const int i = Lc.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(Lc, i, j)) continue;
+    fc[sidx(Lc, i, j)] = rnd(Lc, restrict_value<T, EXACT, PER>(Lf, transfer, d, i, j));
+  }
 }
 
-template <typename T, bool EXACT, bool PER>
+// PAIR: an axis fine level, one thread per node pair (2p, 2p + 1); otherwise one thread
+// per storage column (rotated fine levels hold one interpolation kind per row).
+template <typename T, bool EXACT, bool PER, int ROWS, bool PAIR>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_prolong_add(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
                               int transfer, const T* uin, T* uf, const T* __restrict__ vc) {
   const LevelDev<T>& Lf = *Lfp;
-  int i, j;
-  if (!thread_node(Lf, i, j) || !interior(Lf, i, j)) return;
-  const int64_t at = sidx(Lf, i, j);
-  uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_value<T, EXACT, PER>(*Lcp, transfer, vc, i, j)));
+  const LevelDev<T>& Lc = *Lcp;
+  const bool axis = Lf.kind == kAxis;
+  const int t = blockIdx.x * kBX + threadIdx.x;
+  const int i0 = PAIR ? 2 * t : 0;
+  if (PAIR ? i0 > Lf.n : t >= Lf.cols) return;
+  const int jb = blockIdx.y * (kBY * ROWS) + threadIdx.y;
+#pragma unroll
+  for (int r = 0; r < (ROWS > 1 ? ROWS : 0); ++r) {
+    const int j = min(jb + r * kBY, Lf.rows - 1);
+    const int i = PAIR ? i0 : min(axis ? t : 2 * t + (j & 1), Lf.n);
+    prefetch_l2(uin + sidx(Lf, i, j));
+    const int ci = transfer == kRbAxisToRot ? i : i >> 1, cj = transfer == kRbAxisToRot ? j : j >> 1;
+    prefetch_l2(vc + sidx(Lc, ci, cj));
+  }
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int j = jb + r * kBY;
+    if (j >= Lf.rows) break;
+#pragma unroll
+    for (int k = 0; k < (PAIR ? 2 : 1); ++k) {
+      const int i = PAIR ? i0 + k : (axis ? t : 2 * t + (j & 1));
+      if (!interior(Lf, i, j)) continue;
+      const int64_t at = sidx(Lf, i, j);
+      uf[at] = rnd(Lf, Arith<T>::add(uin[at], prolong_value<T, EXACT, PER>(Lc, transfer, vc, i, j)));
+    }
+  }
 }
 
 // Exact solve on the one-unknown coarsest level: u = f / a_pp (Dirichlet), or the
@@ -1562,7 +1616,21 @@ cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const
 template <typename T>
 cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
                             const T* d, T* fc, cudaStream_t s) {
-  const dim3 g = grid_of(Lc.h), b(kBX, kBY);
+  dim3 g = grid_of(Lc.h);
+  const dim3 b(kBX, kBY);
+  if (transfer != kStandardCubic && Lc.h.rows >= kTransferRowsMinLevelRows) {
+    g.y = (Lc.h.rows + kBY * kTransferRows - 1) / (kBY * kTransferRows);
+#define NSMG_RESTRICT(E, P) k_restrict<T, E, P, kTransferRows><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc)
+    if (Lf.h.per) {
+      if (exact) NSMG_RESTRICT(true, true);
+      else NSMG_RESTRICT(false, true);
+    } else {
+      if (exact) NSMG_RESTRICT(true, false);
+      else NSMG_RESTRICT(false, false);
+    }
+#undef NSMG_RESTRICT
+    return cudaGetLastError();
+  }
   if (transfer == kStandardCubic) {
     if (Lf.h.per) {
       if (exact) k_restrict_cubic<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
@@ -1572,11 +1640,11 @@ cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int 
       else k_restrict_cubic<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
     }
   } else if (Lf.h.per) {
-    if (exact) k_restrict<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
-    else k_restrict<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    if (exact) k_restrict<T, true, true, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    else k_restrict<T, false, true, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
   } else {
-    if (exact) k_restrict<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
-    else k_restrict<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    if (exact) k_restrict<T, true, false, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    else k_restrict<T, false, false, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
   }
   return cudaGetLastError();
 }
@@ -1584,8 +1652,22 @@ cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int 
 template <typename T>
 cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer,
                                bool exact, T* uf, const T* vc, cudaStream_t s, const T* uin) {
-  const dim3 g = grid_of(Lf.h), b(kBX, kBY);
+  const dim3 b(kBX, kBY);
   const T* ui = uin ? uin : uf;
+  if (transfer != kStandardCubic && Lf.h.kind == kAxis && Lf.h.rows >= kTransferRowsMinLevelRows) {
+    const dim3 g((Lf.h.n / 2 + 1 + kBX - 1) / kBX, (Lf.h.rows + kBY * kTransferRows - 1) / (kBY * kTransferRows));
+#define NSMG_PROLONG(E, P) k_prolong_add<T, E, P, kTransferRows, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc)
+    if (Lc.h.per) {
+      if (exact) NSMG_PROLONG(true, true);
+      else NSMG_PROLONG(false, true);
+    } else {
+      if (exact) NSMG_PROLONG(true, false);
+      else NSMG_PROLONG(false, false);
+    }
+#undef NSMG_PROLONG
+    return cudaGetLastError();
+  }
+  const dim3 g = grid_of(Lf.h);
   if (transfer == kStandardCubic) {
     if (Lc.h.per) {
       if (exact) k_prolong_cubic<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, ui, uf, vc);
@@ -1595,11 +1677,11 @@ cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, i
       else k_prolong_cubic<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, ui, uf, vc);
     }
   } else if (Lc.h.per) {
-    if (exact) k_prolong_add<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
-    else k_prolong_add<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+    if (exact) k_prolong_add<T, true, true, 1, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+    else k_prolong_add<T, false, true, 1, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
   } else {
-    if (exact) k_prolong_add<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
-    else k_prolong_add<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+    if (exact) k_prolong_add<T, true, false, 1, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
+    else k_prolong_add<T, false, false, 1, false><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, ui, uf, vc);
   }
   return cudaGetLastError();
 }
