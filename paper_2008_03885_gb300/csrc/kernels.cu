@@ -544,15 +544,25 @@ __global__ void k_apply(const LevelDev<T>* __restrict__ Lp, const T* __restrict_
 }
 
 // Restriction terms (dx, dy) in fine-lattice units, sorted by (dy, dx), with weights.
-struct RTerm {
-  int dx, dy;
-  double w;
-};
-__constant__ RTerm c_rterms_rb_axis[5] = {{0, -1, 0.125}, {-1, 0, 0.125}, {0, 0, 0.5}, {1, 0, 0.125}, {0, 1, 0.125}};
-__constant__ RTerm c_rterms_rb_rot[5] = {{-1, -1, 0.125}, {1, -1, 0.125}, {0, 0, 0.5}, {-1, 1, 0.125}, {1, 1, 0.125}};
-__constant__ RTerm c_rterms_std[9] = {{-1, -1, 0.0625}, {0, -1, 0.125}, {1, -1, 0.0625},
-                                      {-1, 0, 0.125},   {0, 0, 0.25},   {1, 0, 0.125},
-                                      {-1, 1, 0.0625},  {0, 1, 0.125},  {1, 1, 0.0625}};
+// Restriction terms of each transfer in the order of the sum: the red-black transfers'
+// R = 1/2 P^T (centre 1/2, four neighbours 1/8: axis neighbours from an axis level,
+// diagonal ones from a rotated level) and full weighting R = 1/4 P^T for H = 2h
+// (Eq. (transfer_r2), Eq. (transfer_2d)). Compile-time functions, so that inside a
+// kernel specialised on the transfer every weight is a literal.
+__host__ __device__ constexpr int rt_count(int tr) { return tr == kStandard ? 9 : 5; }
+__host__ __device__ constexpr int rt_dx(int tr, int k) {
+  return tr == kStandard ? k % 3 - 1
+         : tr == kRbAxisToRot ? (k >= 1 && k <= 3 ? k - 2 : 0)
+                              : (k == 2 ? 0 : (k == 0 || k == 3) ? -1 : 1);
+}
+__host__ __device__ constexpr int rt_dy(int tr, int k) {
+  return tr == kStandard ? k / 3 - 1
+         : tr == kRbAxisToRot ? (k == 0 ? -1 : k == 4 ? 1 : 0)
+                              : (k < 2 ? -1 : k > 2 ? 1 : 0);
+}
+__host__ __device__ constexpr double rt_w(int tr, int k) {
+  return tr == kStandard ? (rt_dx(tr, k) == 0 ? 2 : 1) * (rt_dy(tr, k) == 0 ? 2 : 1) * 0.0625 : (k == 2 ? 0.5 : 0.125);
+}
 
 // Storage position of lattice node (i, j): in the level's global storage, or in the
 // compact rows x cols layout of the shared-memory tail.
@@ -606,21 +616,28 @@ __device__ __forceinline__ T wrapped_sum(const LevelDev<T>& L, int nt, const int
 }
 
 // Restriction from a periodic level.
-template <typename T, bool EXACT, class Idx>
-__device__ __forceinline__ T restrict_wrapped(const LevelDev<T>& Lf, int transfer, const T* __restrict__ d,
-                                           int fi, int fj, Idx idx) {
-  const RTerm* rt = transfer == kRbAxisToRot ? c_rterms_rb_axis
-                    : transfer == kRbRotToAxis ? c_rterms_rb_rot
-                                               : c_rterms_std;
-  const int nt = transfer == kStandard ? 9 : 5;
+template <typename T, bool EXACT, int TR, class Idx>
+__device__ __forceinline__ T restrict_wrapped(const LevelDev<T>& Lf, const T* __restrict__ d, int fi, int fj,
+                                              Idx idx) {
+  constexpr int nt = rt_count(TR);
   int ti[kMaxTransferTerms], tj[kMaxTransferTerms];
   T w[kMaxTransferTerms];
+#pragma unroll
   for (int k = 0; k < nt; ++k) {
-    ti[k] = fi + rt[k].dx;
-    tj[k] = fj + rt[k].dy;
-    w[k] = T(rt[k].w);
+    ti[k] = fi + rt_dx(TR, k);
+    tj[k] = fj + rt_dy(TR, k);
+    w[k] = T(rt_w(TR, k));
   }
   return wrapped_sum<T, EXACT>(Lf, nt, ti, tj, w, d, idx);
+}
+
+template <typename T, bool EXACT, int TR, class Idx>
+__device__ __forceinline__ T restrict_sum(const LevelDev<T>& Lf, const T* __restrict__ d, int fi, int fj, Idx idx) {
+  T s = Arith<T>::mul(T(rt_w(TR, 0)), d[idx(Lf, fi + rt_dx(TR, 0), fj + rt_dy(TR, 0))]);
+#pragma unroll
+  for (int k = 1; k < rt_count(TR); ++k)
+    s = madd<T, EXACT>(s, T(rt_w(TR, k)), d[idx(Lf, fi + rt_dx(TR, k), fj + rt_dy(TR, k))]);
+  return s;
 }
 
 // Restricted residual at coarse node (i, j) (coarse-level lattice). PER: the levels
@@ -632,14 +649,14 @@ __device__ __forceinline__ T restrict_value(const LevelDev<T>& Lf, int transfer,
   // fine-lattice position of the coarse node
   const int fi = transfer == kRbAxisToRot ? i : 2 * i;
   const int fj = transfer == kRbAxisToRot ? j : 2 * j;
-  if (PER) return restrict_wrapped<T, EXACT>(Lf, transfer, d, fi, fj, idx);
-  const RTerm* rt = transfer == kRbAxisToRot ? c_rterms_rb_axis
-                    : transfer == kRbRotToAxis ? c_rterms_rb_rot
-                                               : c_rterms_std;
-  const int nt = transfer == kStandard ? 9 : 5;
-  T s = Arith<T>::mul(T(rt[0].w), d[idx(Lf, fi + rt[0].dx, fj + rt[0].dy)]);
-  for (int k = 1; k < nt; ++k) s = madd<T, EXACT>(s, T(rt[k].w), d[idx(Lf, fi + rt[k].dx, fj + rt[k].dy)]);
-  return s;
+  if (PER) {
+    if (transfer == kRbAxisToRot) return restrict_wrapped<T, EXACT, kRbAxisToRot>(Lf, d, fi, fj, idx);
+    if (transfer == kRbRotToAxis) return restrict_wrapped<T, EXACT, kRbRotToAxis>(Lf, d, fi, fj, idx);
+    return restrict_wrapped<T, EXACT, kStandard>(Lf, d, fi, fj, idx);
+  }
+  if (transfer == kRbAxisToRot) return restrict_sum<T, EXACT, kRbAxisToRot>(Lf, d, fi, fj, idx);
+  if (transfer == kRbRotToAxis) return restrict_sum<T, EXACT, kRbRotToAxis>(Lf, d, fi, fj, idx);
+  return restrict_sum<T, EXACT, kStandard>(Lf, d, fi, fj, idx);
 }
 
 // Coarse terms (lattice i, j, weight) of the interpolated value at fine node (i, j),
@@ -1098,13 +1115,28 @@ __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const dou
 }
 
 // u += e * inv_scale (FP64 update of the refinement step).
+// kTransferRows rows per thread with the lines prefetched into L2, as in the transfers.
 __global__ void k_ir_update(const LevelDev<double>* __restrict__ Lp, double* __restrict__ u,
                             const float* __restrict__ e, double inv_scale) {
   const LevelDev<double>& L = *Lp;
-  int i, j;
-  if (!thread_node(L, i, j) || !interior(L, i, j)) return;
-  const int64_t at = sidx(L, i, j);
-  u[at] = u[at] + (double)e[at] * inv_scale;
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  if (q >= L.cols) return;
+  const int jb = blockIdx.y * (kBY * kTransferRows) + threadIdx.y;
+#pragma unroll
+  for (int r = 0; r < kTransferRows; ++r) {
+    const int64_t at = (int64_t)min(jb + r * kBY, L.rows - 1) * L.pitch + q;
+    prefetch_l2(u + at);
+    prefetch_l2(e + at);
+  }
+#pragma unroll
+  for (int r = 0; r < kTransferRows; ++r) {
+    const int j = jb + r * kBY;
+    if (j >= L.rows) break;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
+    const int64_t at = sidx(L, i, j);
+    u[at] = u[at] + (double)e[at] * inv_scale;
+  }
 }
 
 // ---- small-level tail ---------------------------------------------------------
@@ -1744,7 +1776,9 @@ cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const dou
 
 cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
                              cudaStream_t s) {
-  k_ir_update<<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, u, e, inv_scale);
+  dim3 g = grid_of(L.h);
+  g.y = (L.h.rows + kBY * kTransferRows - 1) / (kBY * kTransferRows);
+  k_ir_update<<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, e, inv_scale);
   return cudaGetLastError();
 }
 
