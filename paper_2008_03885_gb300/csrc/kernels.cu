@@ -91,7 +91,7 @@ __device__ __forceinline__ int64_t sidx(const LevelDev<T>& L, int i, int j) {
 template <typename T>
 __device__ __forceinline__ bool thread_node(const LevelDev<T>& L, int& i, int& j) {
   const int q = blockIdx.x * kBX + threadIdx.x;
-  j = blockIdx.y * kBY + threadIdx.y;
+  j = blockIdx.y * blockDim.y + threadIdx.y;
   if (j >= L.rows || q >= L.cols) return false;
   i = L.kind == kRot ? 2 * q + (j & 1) : q;
   return true;
@@ -163,7 +163,6 @@ __device__ __forceinline__ T relax_value(const LevelDev<T>& L, const T* __restri
 
 // ---- specialised fast path: NT-point stencils with coefficients in registers and
 // kRows rows per thread (same arithmetic as apply_at / relax_value) --------------
-constexpr int kRowsMax = 4;
 // Rows per thread of the 5/9-point kernels (2 and 4 measured equal for FP32 on GB300).
 template <typename T>
 struct RowsPer {
@@ -312,11 +311,10 @@ struct StencilSmem {
 
 template <typename T>
 __device__ __forceinline__ void stage_stencil(const LevelDev<T>& L, StencilSmem<T>& sm) {
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  if (tid < L.nt) {
-    sm.c[tid] = L.c[tid];
-    sm.d[0][tid] = L.delta[0][tid];
-    sm.d[1][tid] = L.delta[1][tid];
+  for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < L.nt; k += blockDim.x * blockDim.y) {
+    sm.c[k] = L.c[k];
+    sm.d[0][k] = L.delta[0][k];
+    sm.d[1][k] = L.delta[1][k];
   }
   __syncthreads();
 }
@@ -339,7 +337,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_g
   int i, j;
   if (L.kind == kAxis) {
     const int i0 = 2 * (blockIdx.x * kBX + threadIdx.x);
-    j = blockIdx.y * kBY + threadIdx.y;
+    j = blockIdx.y * blockDim.y + threadIdx.y;
     const int lo = L.lo;
     if (j < lo || j >= L.n || i0 > L.n) return;
     i = (((i0 + j) & 1) == red) ? i0 : i0 + 1;
@@ -758,8 +756,13 @@ __device__ __forceinline__ T prolong_value(const LevelDev<T>& Lc, int transfer, 
 // copy their coarse node); 2D weights are products. R = 1/4 P^T: per axis taps
 // (-1, 9, 16, 9, -1) / 32 at fine offsets (-3, -1, 0, 1, 3). All weights and their
 // products are exact in FP32 and FP64.
-__constant__ int c_cubic_off[5] = {-3, -1, 0, 1, 3};
-__constant__ float c_cubic_r1[5] = {-1.0f / 32, 9.0f / 32, 16.0f / 32, 9.0f / 32, -1.0f / 32};
+// (Compile-time functions: inside unrolled loops the weights and their products fold
+// to literals instead of table loads, conversions and multiplies.)
+__host__ __device__ constexpr int cubic_off(int a) { return a == 0 ? -3 : a == 4 ? 3 : a - 2; }
+template <typename T>
+__host__ __device__ constexpr T cubic_r1(int a) {
+  return a == 2 ? T(0.5) : (a == 1 || a == 3) ? T(0.28125) : T(-0.03125);  // 16/32, 9/32, -1/32
+}
 
 // Dirichlet edge terms: coordinates folded into [0, n] by odd reflection (sign -1 per
 // reflection), boundary positions dropped; then as wrapped_sum (ordered by storage
@@ -821,8 +824,8 @@ __device__ __forceinline__ T restrict_cubic_value(const LevelDev<T>& Lf, const T
     for (int b = 0; b < 5; ++b)
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
-        const T w = Arith<T>::mul(T(c_cubic_r1[a]), T(c_cubic_r1[b]));  // exact
-        const T x = d[idx(Lf, fi + c_cubic_off[a], fj + c_cubic_off[b])];
+        const T w = cubic_r1<T>(a) * cubic_r1<T>(b);  // exact
+        const T x = d[idx(Lf, fi + cubic_off(a), fj + cubic_off(b))];
         s = (a == 0 && b == 0) ? Arith<T>::mul(w, x) : madd<T, EXACT>(s, w, x);
       }
     return s;
@@ -832,9 +835,9 @@ __device__ __forceinline__ T restrict_cubic_value(const LevelDev<T>& Lf, const T
   int m = 0;
   for (int b = 0; b < 5; ++b)
     for (int a = 0; a < 5; ++a) {
-      ti[m] = fi + c_cubic_off[a];
-      tj[m] = fj + c_cubic_off[b];
-      w[m++] = Arith<T>::mul(T(c_cubic_r1[a]), T(c_cubic_r1[b]));
+      ti[m] = fi + cubic_off(a);
+      tj[m] = fj + cubic_off(b);
+      w[m++] = Arith<T>::mul(cubic_r1<T>(a), cubic_r1<T>(b));
     }
   return edge_sum<T, EXACT, PER>(Lf, 25, ti, tj, w, d, idx);
 }
@@ -1546,6 +1549,35 @@ dim3 norm_grid(const LevelDev<T>& L) {
 
 }  // namespace
 
+// Rows per block of the wide-stencil kernels. FP64 work is bound by each SM's FP64 pipe
+// (about 2 operations per clock), so a small level whose 256-thread blocks cover only a
+// few SMs is limited by those SMs: there the blocks shrink (down to one warp) until the
+// grid has kSpreadBlocksPerSm blocks per SM or the rows run out. Measured on GB300
+// (FP64 solves to 1e-10, order 4, RBC, Galerkin): 4097^2 64.0 -> 63.1 ms, 1025^2 9.63 ->
+// 9.02 ms, 257^2 6.07 -> 5.78 ms (8 blocks per SM: the same; 2: about half the gain).
+constexpr int kSpreadBlocksPerSm = 4;
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 1;
+  }
+  return n;
+}
+
+template <typename T>
+int gen_block_rows(const LevelDev<T>& L, unsigned gx) {
+  if (sizeof(T) != 8) return kBY;
+  const long target = (long)kSpreadBlocksPerSm * sm_count();
+  int by = kBY;
+  while (by > 1 && (long)gx * ((L.rows + by - 1) / by) < target) by >>= 1;
+  return by;
+}
+
 template <typename T, int NT>
 cudaError_t launch_half_sweep_nt(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout, int red,
                                  cudaStream_t s) {
@@ -1570,8 +1602,10 @@ cudaError_t launch_half_sweep(const LevelPair<T>& L, bool exact, const T* uin, c
   if (L.h.nt == 9) return launch_half_sweep_nt<T, 9>(L, exact, uin, f, uout, red, s);
   dim3 g = grid_of(L.h);
   if (L.h.kind == kAxis) g.x = ((L.h.n + 2) / 2 + kBX - 1) / kBX;  // pairs (2p, 2p+1), 2p <= n
-  if (exact) k_half_sweep_gen<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
-  else k_half_sweep_gen<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, uin, f, uout, red);
+  const int by = gen_block_rows(L.h, g.x);
+  g.y = (L.h.rows + by - 1) / by;
+  if (exact) k_half_sweep_gen<T, true><<<g, dim3(kBX, by), 0, s>>>(L.d, uin, f, uout, red);
+  else k_half_sweep_gen<T, false><<<g, dim3(kBX, by), 0, s>>>(L.d, uin, f, uout, red);
   return cudaGetLastError();
 }
 
@@ -1639,9 +1673,11 @@ cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const
                             cudaStream_t s) {
   if (L.h.nt == 5) return launch_residual_nt<T, 5>(L, exact, u, f, d, s);
   if (L.h.nt == 9) return launch_residual_nt<T, 9>(L, exact, u, f, d, s);
-  const dim3 g = grid_of(L.h);
-  if (exact) k_residual_gen<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
-  else k_residual_gen<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, d);
+  dim3 g = grid_of(L.h);
+  const int by = gen_block_rows(L.h, g.x);
+  g.y = (L.h.rows + by - 1) / by;
+  if (exact) k_residual_gen<T, true><<<g, dim3(kBX, by), 0, s>>>(L.d, u, f, d);
+  else k_residual_gen<T, false><<<g, dim3(kBX, by), 0, s>>>(L.d, u, f, d);
   return cudaGetLastError();
 }
 
