@@ -516,7 +516,7 @@ struct mg_handle {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
   };
-  GraphEntry g_cycle64, g_inner32;
+  GraphEntry g_cycle64, g_cycle64r, g_inner32;  // g_cycle64r: level 0's first red half-sweep done
   cudaStream_t priv = nullptr;  // used when the caller passes the legacy default stream
   double* host_u = nullptr;     // mg_solve_host: device copies of the caller's u and f
   double* host_f = nullptr;
@@ -748,7 +748,7 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P, int bf
 }
 
 void free_all(mg_handle* h) {
-  for (auto* g : {&h->g_cycle64, &h->g_inner32})
+  for (auto* g : {&h->g_cycle64, &h->g_cycle64r, &h->g_inner32})
     if (g->exec) cudaGraphExecDestroy(g->exec);
   if (h->priv) cudaStreamDestroy(h->priv);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -901,8 +901,10 @@ mg_status cycle_sweep(const Ctx& c, int l, T*& cur, T*& oth, const T* F) {
   return MG_OK;
 }
 
+// red_done: the first half-sweep (red) of the first pre-smoothing sweep already left its
+// result in the level's t buffer (the residual-norm kernel did it); start with black.
 template <typename T>
-mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
+mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, bool red_done = false) {
   mg_handle* h = c.h;
   Hier<T>& H = hier<T>(h);
   const int lmax = (int)h->host.size() - 1;
@@ -924,7 +926,13 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init) {
   T* cur = U;
   T* oth = H.t[l];
   const bool flips = fused_sweeps<T>(h);
-  for (int k = 0; k < h->opt.nu1; ++k)
+  int k0 = 0;
+  if (red_done) {
+    Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+    LAUNCH(h, 1, launch_half_sweep<T>(H.L[l], c.exact, H.t[l], F, cur, 0, c.s));
+    k0 = 1;
+  }
+  for (int k = k0; k < h->opt.nu1; ++k)
     if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) return st;
   {
     Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
@@ -966,6 +974,30 @@ mg_status rel_residual(mg_handle* h, const Ctx& c, const double* U, const double
   {
     Bracket b(h, 0, MG_KERNEL_NORM, c.s);
     LAUNCH(h, 2, launch_resnorm<double>(h->h64.L[0], c.exact, U, F, h->partial, h->scalar, c.s));
+  }
+  double r2;
+  mg_status st = read_scalar(h, c.s, &r2);
+  if (st != MG_OK) return st;
+  *out = std::sqrt(r2) / std::sqrt(fn2);
+  if (!std::isfinite(*out)) return MG_ERR_NONFINITE;
+  return MG_OK;
+}
+
+// Whether the FP64 solve lets each residual-norm kernel also do the first half-sweep of
+// the next cycle (k_resnorm_red): red-black smoothing with half-sweep kernels, at least
+// one pre-smoothing sweep, and a finest level outside the small-level tail.
+bool norm_takes_red(const mg_handle* h) {
+  return h->opt.smoother == MG_SMOOTH_REDBLACK && !fused_sweeps<double>(h) && h->opt.nu1 >= 1 &&
+         h->h64.tail_level != 0;
+}
+
+// rel_residual, and t[0] = U with its red nodes relaxed (discarded if no cycle follows).
+mg_status rel_residual_red(mg_handle* h, const Ctx& c, const double* U, const double* F, double fn2,
+                           double* out) {
+  {
+    Bracket b(h, 0, MG_KERNEL_NORM, c.s);
+    LAUNCH(h, 2, launch_resnorm_red<double>(h->h64.L[0], c.exact, U, F, h->h64.t[0], 1, h->partial, h->scalar,
+                                            c.s));
   }
   double r2;
   mg_status st = read_scalar(h, c.s, &r2);
@@ -1361,14 +1393,19 @@ mg_status mg_solve(mg_handle* h, double* u, const double* f, double rtol, int ma
       ++h->cycles;
     }
   } else {
-    if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
+    // Each norm kernel also relaxes the red nodes into t[0]; the cycle graph then starts
+    // with the black half-sweep (same bits as a full first sweep).
+    const bool fuse = norm_takes_red(h);
+    auto norm = [&]() { return fuse ? rel_residual_red(h, c, u, f, fn2, &rr) : rel_residual(h, c, u, f, fn2, &rr); };
+    if ((st = norm()) != MG_OK) return st;
     if (history_out) history_out[0] = rr;
     while (k < max_cycles && rr >= rtol) {
-      st = run_graph(c, h->g_cycle64, u, f, [&]() { return cycle_level<double>(c, 0, u, f, false); });
+      st = run_graph(c, fuse ? h->g_cycle64r : h->g_cycle64, u, f,
+                     [&]() { return cycle_level<double>(c, 0, u, f, false, fuse); });
       if (st != MG_OK) return st;
       ++k;
       ++h->cycles;
-      if ((st = rel_residual(h, c, u, f, fn2, &rr)) != MG_OK) return st;
+      if ((st = norm()) != MG_OK) return st;
       if (history_out) history_out[k] = rr;
     }
   }

@@ -1047,6 +1047,37 @@ __global__ void k_resnorm_partial(const LevelDev<T>* __restrict__ Lp, const T* _
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
 }
 
+// Residual-norm partial sums (as k_resnorm_partial: same nodes, order and sums) fused
+// with the first half-sweep of the next cycle: nodes of colour `red` get the relaxed
+// value u + (f - L u) omega / a_pp from the same residual, the others are copied
+// (u -> uout, out of place as in the half-sweep kernels). Per node the arithmetic is
+// that of the half-sweep, so a cycle that starts with the other colour from uout gives
+// the same bits as one that starts from u.
+template <typename T, bool EXACT>
+__global__ void k_resnorm_red(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
+                              const T* __restrict__ f, T* __restrict__ uout, int red, double* __restrict__ partial,
+                              int tiles_y) {
+  const LevelDev<T>& L = *Lp;
+  double v = 0.0;
+  const int q = blockIdx.x * kBX + threadIdx.x;
+  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+    const int j = ty * kBY + threadIdx.y;
+    if (j >= L.rows || q >= L.cols) continue;
+    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    if (!interior(L, i, j)) continue;
+    const int64_t at = sidx(L, i, j);
+    T wd;
+    const T r = Arith<T>::sub(f[at], apply_at<T, EXACT>(L, u, i, j, at, &wd));
+    const double d = (double)r;
+    v += d * d;
+    uout[at] = is_red(L, i, j) == red
+                   ? rnd(L, EXACT ? Arith<T>::add(u[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, u[at]))
+                   : u[at];
+  }
+  v = block_sum(v);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
 template <typename T>
 __global__ void k_sumsq_partial(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ f,
                                 double* __restrict__ partial, int tiles_y) {
@@ -1778,6 +1809,17 @@ cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const 
 }
 
 template <typename T>
+cudaError_t launch_resnorm_red(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* uout, int red,
+                               double* partial, double* out, cudaStream_t s) {
+  const dim3 g = norm_grid(L.h);
+  const int ty = (int)grid_of(L.h).y;
+  if (exact) k_resnorm_red<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, uout, red, partial, ty);
+  else k_resnorm_red<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, uout, red, partial, ty);
+  k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_sumsq(const LevelPair<T>& L, const T* f, double* partial, double* out,
                          cudaStream_t s) {
   const dim3 g = norm_grid(L.h);
@@ -1942,6 +1984,8 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, con
   template int resnorm_blocks<T>(const LevelPair<T>&);                                                \
   template cudaError_t launch_resnorm<T>(const LevelPair<T>&, bool, const T*, const T*, double*,     \
                                          double*, cudaStream_t);                                      \
+  template cudaError_t launch_resnorm_red<T>(const LevelPair<T>&, bool, const T*, const T*, T*, int,  \
+                                             double*, double*, cudaStream_t);                         \
   template cudaError_t launch_sumsq<T>(const LevelPair<T>&, const T*, double*, double*, cudaStream_t); \
   template cudaError_t launch_zero_boundary<T>(const LevelPair<T>&, T*, cudaStream_t);                \
   template cudaError_t launch_copy_boundary<T>(const LevelPair<T>&, const T*, T*, cudaStream_t);      \

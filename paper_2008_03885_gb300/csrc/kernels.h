@@ -47,6 +47,11 @@ template <typename T>
 cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const T* f,
                            double* partial, double* out, cudaStream_t s);
 // Sum of squares of f over interior nodes (same reduction order).
+// out = ||f - L u||^2 (as launch_resnorm) and, from the same residual, uout = u with the
+// nodes of colour `red` relaxed: the first half-sweep of a following cycle.
+template <typename T>
+cudaError_t launch_resnorm_red(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* uout, int red,
+                               double* partial, double* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_sumsq(const LevelPair<T>& L, const T* f, double* partial, double* out,
                          cudaStream_t s);
