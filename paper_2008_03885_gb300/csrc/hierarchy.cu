@@ -920,7 +920,8 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
     else LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, prog, nops, c.exact, c.s));
     return MG_OK;
   }
-  if (zero_init) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
+  // (after red_done the black half-sweep writes every unknown of U)
+  if (zero_init && !red_done) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
   // Tile-kernel sweeps flip between U and t[l]; an odd number of them is evened out by
   // an out-of-place interpolation so that the level ends in U.
   T* cur = U;
@@ -1152,12 +1153,21 @@ double ir_scale_for(double r2, int64_t m) {
 // One refinement step of the mixed-precision solve: FP64 residual r = f - L u
 // (also returns ||r||^2), then -- unless `norm_only` -- `inner_cycles` FP32 cycles
 // on L e = r * scale from e = 0, and the FP64 update u += e / scale.
+// Whether the refinement residual kernel also does the first (red) half-sweep of the
+// FP32 cycle from e = 0 (conditions as norm_takes_red, on the FP32 hierarchy).
+bool ir_takes_red(const mg_handle* h) {
+  return h->opt.smoother == MG_SMOOTH_REDBLACK && !fused_sweeps<float>(h) && h->opt.nu1 >= 1 &&
+         h->opt.inner_cycles >= 1 && h->h32.tail_level != 0;
+}
+
 mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
   mg_handle* h = c.h;
+  const bool red = ir_takes_red(h);
   {
     Bracket b(h, 0, MG_KERNEL_NORM, c.s);
     LAUNCH(h, 2, launch_ir_residual(h->h64.L[0], c.exact, u, f, h->h32.f[0], h->ir_scale, h->partial,
-                                    h->scalar, c.s, h->opt.bf16_levels > 0 ? 1 : 0));
+                                    h->scalar, c.s, h->opt.bf16_levels > 0 ? 1 : 0, red ? &h->h32.L[0] : nullptr,
+                                    red ? h->h32.t[0] : nullptr));
   }
   return read_scalar(h, c.s, r2);
 }
@@ -1165,10 +1175,11 @@ mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
 mg_status ir_correct(const Ctx& c, double* u) {
   mg_handle* h = c.h;
   mg_status st;
+  const bool red = ir_takes_red(h);
   st = run_graph(c, h->g_inner32, nullptr, nullptr, [&]() -> mg_status {
     mg_status s2;
     for (int k = 0; k < h->opt.inner_cycles; ++k)
-      if ((s2 = cycle_level<float>(c, 0, h->h32.u[0], h->h32.f[0], k == 0)) != MG_OK) return s2;
+      if ((s2 = cycle_level<float>(c, 0, h->h32.u[0], h->h32.f[0], k == 0, red && k == 0)) != MG_OK) return s2;
     return MG_OK;
   });
   if (st != MG_OK) return st;

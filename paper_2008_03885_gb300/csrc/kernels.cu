@@ -1126,10 +1126,17 @@ __global__ void k_zero_boundary(int n, int pitch, T* __restrict__ u) {
 
 // Iterative-refinement residual: r = f - L u in FP64 (evaluation order of EXACT),
 // r32 = fl32(r * scale) for the FP32 inner cycles, and per-block sums of r^2.
+//
+// With t32 (and L32, the FP32 level 0), the kernel also does the first half-sweep of the
+// FP32 cycle that follows from e = 0: red nodes get 0 + r32 omega / a_pp, black nodes 0.
+// On a zero vector the FP32 stencil sum is +0 (every operator row has a positive
+// diagonal, and +0 absorbs -0 in a sum), so the half-sweep's residual is r32 itself and
+// this is the half-sweep's value bit for bit.
 template <bool EXACT>
 __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
                               const double* __restrict__ f, float* __restrict__ r32, double scale,
-                              double* __restrict__ partial, int tiles_y, int bf16) {
+                              double* __restrict__ partial, int tiles_y, int bf16,
+                              const LevelDev<float>* __restrict__ L32p, float* __restrict__ t32) {
   const LevelDev<double>& L = *Lp;
   double v = 0.0;
   const int q = blockIdx.x * kBX + threadIdx.x;
@@ -1141,8 +1148,18 @@ __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const dou
     const int64_t at = sidx(L, i, j);
     const double r = Arith<double>::sub(f[at], apply_at<double, EXACT>(L, u, i, j, at, nullptr));
     const float r32v = (float)(r * scale);
-    r32[at] = bf16 ? __bfloat162float(__float2bfloat16_rn(r32v)) : r32v;
+    const float rv = bf16 ? __bfloat162float(__float2bfloat16_rn(r32v)) : r32v;
+    r32[at] = rv;
     v += r * r;
+    if (t32) {
+      const LevelDev<float>& L32 = *L32p;
+      float e = 0.f;
+      if (is_red(L32, i, j) == 1) {
+        const float wd = fast_node(L32, i, j) ? L32.wd : L32.cls_wd[class_of(L32, i, j)];
+        e = rnd(L32, EXACT ? Arith<float>::add(0.f, Arith<float>::mul(rv, wd)) : Arith<float>::fma(rv, wd, 0.f));
+      }
+      t32[at] = e;
+    }
   }
   v = block_sum(v);
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
@@ -1843,11 +1860,13 @@ cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s) {
 }
 
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
-                               float* r32, double scale, double* partial, double* out, cudaStream_t s, int bf16) {
+                               float* r32, double scale, double* partial, double* out, cudaStream_t s, int bf16,
+                               const LevelPair<float>* L32, float* t32) {
   const dim3 g = norm_grid(L.h);
   const int ty = (int)grid_of(L.h).y;
-  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16);
-  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16);
+  const LevelDev<float>* L32d = L32 ? L32->d : nullptr;
+  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16, L32d, t32);
+  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16, L32d, t32);
   k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
   return cudaGetLastError();
 }

@@ -65,9 +65,10 @@ cudaError_t launch_copy_boundary(const LevelPair<T>& L, const T* src, T* dst, cu
 
 // Refinement step, finest level (FP64 grid, FP32 grid of the same storage layout):
 // r32 = fl32((f - L u) * scale), *out = sum of (f - L u)^2 (two launches).
+// With L32 / t32: also the first half-sweep (red) of the FP32 cycle from e = 0 into t32.
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
                                float* r32, double scale, double* partial, double* out, cudaStream_t s,
-                               int bf16 = 0);
+                               int bf16 = 0, const LevelPair<float>* L32 = nullptr, float* t32 = nullptr);
 // u += e * inv_scale on interior nodes.
 cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
                              cudaStream_t s);

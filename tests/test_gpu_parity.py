@@ -409,3 +409,39 @@ def test_dirichlet_data_rejected_for_wide_stencils():
     with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, 4, REDBLACK, GALERKIN, dirichlet_data=1)
     assert e.value.status == mg.MG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("opts", [dict(order=4, co=REDBLACK, op=GALERKIN, nu1=2),
+                                  dict(order=2, co=REDBLACK, op=GALERKIN, nu1=1),
+                                  dict(order=4, co=STANDARD, op=NONGALERKIN, nu1=1, nu2=2),
+                                  dict(order=4, co=REDBLACK, op=GALERKIN, nu1=2, boundary="periodic"),
+                                  dict(order=2, co=REDBLACK, op=GALERKIN, nu1=1, dirichlet_data=1)])
+def test_solve_with_norm_fused_half_sweep_equals_single_cycles(opts):
+    """mg_solve lets each residual-norm kernel also do the next cycle's first (red)
+    half-sweep and starts the cycle with black; mg_cycle runs whole cycles. K cycles of
+    either must give the same iterate bit for bit and the same relative residuals."""
+    opts = dict(opts)
+    order, co, op = opts.pop("order"), opts.pop("co"), opts.pop("op")
+    n, K = 128, 4
+    F = synth.rhs_normal(n, seed=23)
+    if opts.get("boundary") == "periodic":
+        F = F - F[:n, :n].mean()
+        F[n, :] = 0.0
+        F[:, n] = 0.0
+    h = mg.mg_setup(n, order, co, op, **opts)
+    try:
+        f = torch.tensor(F, dtype=torch.float64, device="cuda")
+        u0 = torch.zeros_like(f)
+        if opts.get("dirichlet_data"):
+            x = torch.linspace(0, 1, n + 1, dtype=torch.float64, device="cuda")
+            g = (x[None, :] ** 2 + 2 * x[:, None]).contiguous()
+            u0[0, :], u0[n, :], u0[:, 0], u0[:, n] = g[0, :], g[n, :], g[:, 0], g[:, n]
+        us = u0.clone()
+        k, hist = mg.mg_solve(h, us, f, rtol=0.0, max_cycles=K, raise_not_converged=False)
+        assert k == K
+        uc = u0.clone()
+        rr = [mg.mg_cycle(h, uc, f) for _ in range(K)]
+        assert torch.equal(us, uc)
+        assert np.allclose(hist[1:], rr, rtol=1e-13, atol=0.0)
+    finally:
+        h.close()
