@@ -920,8 +920,17 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
     else LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, prog, nops, c.exact, c.s));
     return MG_OK;
   }
-  // (after red_done the black half-sweep writes every unknown of U)
-  if (zero_init && !red_done) CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
+  // From u = 0 the first red half-sweep needs no stencil (k_first_half_zero); after it,
+  // or after red_done, the black half-sweep writes every unknown of U.
+  if (zero_init && !red_done) {
+    if (h->opt.smoother == MG_SMOOTH_REDBLACK && !fused_sweeps<T>(h) && h->opt.nu1 >= 1) {
+      Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+      LAUNCH(h, 1, launch_first_half_zero<T>(H.L[l], F, H.t[l], 1, c.s));
+      red_done = true;
+    } else {
+      CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
+    }
+  }
   // Tile-kernel sweeps flip between U and t[l]; an odd number of them is evened out by
   // an out-of-place interpolation so that the level ends in U.
   T* cur = U;

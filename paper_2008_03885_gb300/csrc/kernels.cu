@@ -1053,6 +1053,27 @@ __global__ void k_resnorm_partial(const LevelDev<T>* __restrict__ Lp, const T* _
 // (u -> uout, out of place as in the half-sweep kernels). Per node the arithmetic is
 // that of the half-sweep, so a cycle that starts with the other colour from uout gives
 // the same bits as one that starts from u.
+// First half-sweep (colour `red`) of a cycle on a coarse level, whose correction starts
+// from u = 0, into t: on a zero vector every stencil sum is +0 (each operator row has a
+// positive diagonal, and +0 absorbs -0), so the half-sweep's residual is f and its new
+// value 0 + f omega / a_pp; the other colour keeps its 0. This writes exactly those bits
+// without the stencil gathers (and replaces zeroing u, since the black half-sweep that
+// follows writes every unknown of u).
+template <typename T>
+__global__ void k_first_half_zero(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ f, T* __restrict__ t,
+                                  int red) {
+  const LevelDev<T>& L = *Lp;
+  int i, j;
+  if (!thread_node(L, i, j) || !interior(L, i, j)) return;
+  const int64_t at = sidx(L, i, j);
+  T e = T(0);
+  if (is_red(L, i, j) == red) {
+    const T wd = fast_node(L, i, j) ? L.wd : L.cls_wd[class_of(L, i, j)];
+    e = rnd(L, Arith<T>::add(T(0), Arith<T>::mul(f[at], wd)));
+  }
+  t[at] = e;
+}
+
 template <typename T, bool EXACT>
 __global__ void k_resnorm_red(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
                               const T* __restrict__ f, T* __restrict__ uout, int red, double* __restrict__ partial,
@@ -1826,6 +1847,12 @@ cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const 
 }
 
 template <typename T>
+cudaError_t launch_first_half_zero(const LevelPair<T>& L, const T* f, T* t, int red, cudaStream_t s) {
+  k_first_half_zero<T><<<grid_of(L.h), dim3(kBX, kBY), 0, s>>>(L.d, f, t, red);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_resnorm_red(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* uout, int red,
                                double* partial, double* out, cudaStream_t s) {
   const dim3 g = norm_grid(L.h);
@@ -2003,6 +2030,7 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, con
   template int resnorm_blocks<T>(const LevelPair<T>&);                                                \
   template cudaError_t launch_resnorm<T>(const LevelPair<T>&, bool, const T*, const T*, double*,     \
                                          double*, cudaStream_t);                                      \
+  template cudaError_t launch_first_half_zero<T>(const LevelPair<T>&, const T*, T*, int, cudaStream_t); \
   template cudaError_t launch_resnorm_red<T>(const LevelPair<T>&, bool, const T*, const T*, T*, int,  \
                                              double*, double*, cudaStream_t);                         \
   template cudaError_t launch_sumsq<T>(const LevelPair<T>&, const T*, double*, double*, cudaStream_t); \

@@ -47,6 +47,9 @@ template <typename T>
 cudaError_t launch_resnorm(const LevelPair<T>& L, bool exact, const T* u, const T* f,
                            double* partial, double* out, cudaStream_t s);
 // Sum of squares of f over interior nodes (same reduction order).
+// t = the first half-sweep (colour red) from u = 0: red unknowns 0 + f omega / a_pp, others 0.
+template <typename T>
+cudaError_t launch_first_half_zero(const LevelPair<T>& L, const T* f, T* t, int red, cudaStream_t s);
 // out = ||f - L u||^2 (as launch_resnorm) and, from the same residual, uout = u with the
 // nodes of colour `red` relaxed: the first half-sweep of a following cycle.
 template <typename T>
