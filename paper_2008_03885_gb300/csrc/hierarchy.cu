@@ -1743,9 +1743,13 @@ mg_status batch_cycle(mg_batch* b, std::vector<BatchList<T>>& lv, bool zero0, cu
   for (int l = 0; l + 1 < b->nl; ++l) {
     BatchList<T>& B = lv[l];
     if (B.ne == 0) continue;
-    if (l > 0 || zero0) BLAUNCH(b, launch_batch_step<T>(kBZero, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+    // from u = 0 the first red half-sweep needs no stencil and replaces zeroing u
+    const bool from_zero = l > 0 || zero0;
+    if (from_zero && b->nu1 == 0)
+      BLAUNCH(b, launch_batch_step<T>(kBZero, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
     for (int k = 0; k < b->nu1; ++k) {
-      BLAUNCH(b, launch_batch_step<T>(kBHalfRed, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
+      const int red_op = from_zero && k == 0 ? kBHalfRedZero : kBHalfRed;
+      BLAUNCH(b, launch_batch_step<T>(red_op, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
       BLAUNCH(b, launch_batch_step<T>(kBHalfBlack, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
     }
     BLAUNCH(b, launch_batch_step<T>(kBResidual, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));

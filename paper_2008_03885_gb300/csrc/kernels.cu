@@ -1349,6 +1349,11 @@ __global__ void __launch_bounds__(kBX * kBY)
         case kBHalfRed:
           B.t[at] = is_red(L, i, j) ? relax_value<T, EXACT, 1>(L, B.u, B.f, i, j, at) : B.u[at];
           break;
+        case kBHalfRedZero: {  // as k_first_half_zero
+          const T wd = fast_node(L, i, j) ? L.wd : L.cls_wd[class_of(L, i, j)];
+          B.t[at] = is_red(L, i, j) ? Arith<T>::add(T(0), Arith<T>::mul(B.f[at], wd)) : T(0);
+          break;
+        }
         case kBHalfBlack:
           B.u[at] = is_red(L, i, j) ? B.t[at] : relax_value<T, EXACT, 1>(L, B.t, B.f, i, j, at);
           break;

@@ -144,7 +144,8 @@ struct BatchLevel {
 };
 
 enum BatchOp : int32_t {
-  kBZero = 0, kBHalfRed = 1, kBHalfBlack = 2, kBResidual = 3, kBRestrict = 4, kBProlong = 5, kBCoarsest = 6
+  kBZero = 0, kBHalfRed = 1, kBHalfBlack = 2, kBResidual = 3, kBRestrict = 4, kBProlong = 5, kBCoarsest = 6,
+  kBHalfRedZero = 7  // kBHalfRed from u = 0 (no stencil; replaces kBZero + kBHalfRed, same bits)
 };
 
 // A tile is 64 storage columns (2 per thread, so a thread holds one red and one black
