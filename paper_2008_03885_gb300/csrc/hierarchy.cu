@@ -1054,11 +1054,14 @@ mg_status alloc_hier(mg_handle* h, bool caller_level0) {
 }
 
 // Tail program for cycle_level(l, zero_init = true): the same op sequence the
-// per-level launches would make.
-void emit_tail(const mg_handle* h, int l, bool zero, std::vector<int4>& prog) {
+// per-level launches would make. Nested levels start from u = 0 with the stencil-free
+// first half-sweep (kOpSmooth, z = 1); the top level keeps its zeroing op, which the
+// launch skips to continue from u.
+void emit_tail(const mg_handle* h, int l, bool zero, std::vector<int4>& prog, bool top = false) {
   const int lmax = (int)h->host.size() - 1;
-  if (zero) prog.push_back(make_int4(kOpZero, l, 0, 0));
-  for (int k = 0; k < h->opt.nu1; ++k) prog.push_back(make_int4(kOpSmooth, l, 0, 0));
+  const bool zs = zero && !top && h->opt.smoother == MG_SMOOTH_REDBLACK && h->opt.nu1 >= 1;
+  if (zero && !zs) prog.push_back(make_int4(kOpZero, l, 0, 0));
+  for (int k = 0; k < h->opt.nu1; ++k) prog.push_back(make_int4(kOpSmooth, l, zs && k == 0 ? 1 : 0, 0));
   prog.push_back(make_int4(kOpResRestrict, l, 0, 0));
   if (l + 1 == lmax) {
     prog.push_back(make_int4(kOpCoarsest, lmax, 0, 0));
@@ -1122,7 +1125,7 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
   td.coarsest_a = H.coarsest_a;
   td.coarsest_zero = H.coarsest_zero;
   std::vector<int4> prog;
-  emit_tail(h, lt, true, prog);
+  emit_tail(h, lt, true, prog, true);
   mg_status st;
   if ((st = device_alloc(h, (void**)&H.d_tail, sizeof(td))) != MG_OK) return st;
   if ((st = device_alloc(h, (void**)&H.d_prog, prog.size() * sizeof(int4))) != MG_OK) return st;

@@ -122,6 +122,18 @@ __device__ __forceinline__ bool fast_node(const LevelDev<T>& L, int i, int j) {
   return i >= L.rx && i <= L.fxe && j >= L.ry && j <= L.fye;
 }
 
+// omega / a_pp of node (i, j).
+template <typename T>
+__device__ __forceinline__ T node_wd(const LevelDev<T>& L, int i, int j) {
+  return fast_node(L, i, j) ? L.wd : L.cls_wd[class_of(L, i, j)];
+}
+
+// First half-sweep value from u = 0 (see k_first_half_zero): 0 + f omega / a_pp.
+template <typename T>
+__device__ __forceinline__ T relax_from_zero(T f, T wd) {
+  return Arith<T>::add(T(0), Arith<T>::mul(f, wd));
+}
+
 // (L u)(i, j) and the node's omega / a_pp.
 // CU: unroll factor of the boundary-class term loop (its loads then run ahead of the
 // ordered sum); 1 in the register-tight NT kernels.
@@ -1067,10 +1079,7 @@ __global__ void k_first_half_zero(const LevelDev<T>* __restrict__ Lp, const T* _
   if (!thread_node(L, i, j) || !interior(L, i, j)) return;
   const int64_t at = sidx(L, i, j);
   T e = T(0);
-  if (is_red(L, i, j) == red) {
-    const T wd = fast_node(L, i, j) ? L.wd : L.cls_wd[class_of(L, i, j)];
-    e = rnd(L, Arith<T>::add(T(0), Arith<T>::mul(f[at], wd)));
-  }
+  if (is_red(L, i, j) == red) e = rnd(L, relax_from_zero(f[at], node_wd(L, i, j)));
   t[at] = e;
 }
 
@@ -1175,10 +1184,7 @@ __global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const dou
     if (t32) {
       const LevelDev<float>& L32 = *L32p;
       float e = 0.f;
-      if (is_red(L32, i, j) == 1) {
-        const float wd = fast_node(L32, i, j) ? L32.wd : L32.cls_wd[class_of(L32, i, j)];
-        e = rnd(L32, EXACT ? Arith<float>::add(0.f, Arith<float>::mul(rv, wd)) : Arith<float>::fma(rv, wd, 0.f));
-      }
+      if (is_red(L32, i, j) == 1) e = rnd(L32, relax_from_zero(rv, node_wd(L32, i, j)));
       t32[at] = e;
     }
   }
@@ -1254,7 +1260,10 @@ __global__ void __launch_bounds__(kTailThreads, 1)
           for (int k = tid; k < total; k += nth) {
             if (!tail_node(L, k, i, j)) continue;
             const int64_t at = sidx(L, i, j);
-            dst[at] = is_red(L, i, j) == half ? relax_value<T, EXACT>(L, src, F, i, j, at) : src[at];
+            if (op.z && half)  // first half-sweep from u = 0 (op.z: U not zeroed)
+              dst[at] = is_red(L, i, j) ? relax_from_zero(F[at], node_wd(L, i, j)) : T(0);
+            else
+              dst[at] = is_red(L, i, j) == half ? relax_value<T, EXACT>(L, src, F, i, j, at) : src[at];
           }
           cluster.sync();
         }
@@ -1349,11 +1358,9 @@ __global__ void __launch_bounds__(kBX * kBY)
         case kBHalfRed:
           B.t[at] = is_red(L, i, j) ? relax_value<T, EXACT, 1>(L, B.u, B.f, i, j, at) : B.u[at];
           break;
-        case kBHalfRedZero: {  // as k_first_half_zero
-          const T wd = fast_node(L, i, j) ? L.wd : L.cls_wd[class_of(L, i, j)];
-          B.t[at] = is_red(L, i, j) ? Arith<T>::add(T(0), Arith<T>::mul(B.f[at], wd)) : T(0);
+        case kBHalfRedZero:  // as k_first_half_zero
+          B.t[at] = is_red(L, i, j) ? relax_from_zero(B.f[at], node_wd(L, i, j)) : T(0);
           break;
-        }
         case kBHalfBlack:
           B.u[at] = is_red(L, i, j) ? B.t[at] : relax_value<T, EXACT, 1>(L, B.t, B.f, i, j, at);
           break;
@@ -1545,7 +1552,9 @@ __global__ void __launch_bounds__(kTailThreads, 1)
           T* dst = half ? Tb : U;
           for (int k = tid; k < total; k += kTailThreads) {
             if (!tail_node(L, k, i, j)) continue;
-            if (is_red(L, i, j) == half) {
+            if (op.z && half) {  // first half-sweep from u = 0 (op.z: U not zeroed)
+              dst[k] = is_red(L, i, j) ? relax_from_zero(F[k], node_wd(L, i, j)) : T(0);
+            } else if (is_red(L, i, j) == half) {
               T wd;
               const T r = Arith<T>::sub(F[k], smem_apply<T, EXACT>(L, src, i, j, &wd, cs, os2));
               dst[k] = EXACT ? Arith<T>::add(src[k], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, src[k]);

@@ -78,6 +78,8 @@ cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float*
 
 // ---- small-level tail: one thread block runs a whole sub-cycle ---------------
 constexpr int kTailMaxLevels = 40;
+// kOpSmooth with z = 1: the first red-black sweep from u = 0 (the level's u is not zeroed
+// first; its red half-sweep needs no stencil).
 enum TailOp : int32_t { kOpZero = 0, kOpSmooth = 1, kOpResRestrict = 2, kOpCoarsest = 3, kOpProlong = 4 };
 
 // Levels and buffers the tail program refers to (device-resident).
