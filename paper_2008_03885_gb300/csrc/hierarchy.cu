@@ -948,15 +948,20 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
     Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
     LAUNCH(h, 1, launch_residual<T>(H.L[l], c.exact, cur, F, H.d[l], c.s));
   }
+  // The restriction also writes the coarse level's first (zero-start) half-sweep when
+  // that level runs as separate launches.
+  const bool coarse_red = l + 1 != lmax && l + 1 != H.tail_level && h->opt.smoother == MG_SMOOTH_REDBLACK &&
+                          !fused_sweeps<T>(h) && h->opt.nu1 >= 1;
   {
     Bracket b(h, l, MG_KERNEL_RESTRICT, c.s);
-    LAUNCH(h, 1, launch_restrict<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, H.d[l], H.f[l + 1], c.s));
+    LAUNCH(h, 1, launch_restrict<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, H.d[l], H.f[l + 1], c.s,
+                                    coarse_red ? H.t[l + 1] : nullptr));
   }
   if (l + 1 == lmax) {
     LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.coarsest_zero, H.f[lmax], H.u[lmax], c.s));
   } else {
     for (int g = 0; g < gamma_at(h, l); ++g)
-      if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0)) != MG_OK) return st;
+      if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0, coarse_red && g == 0)) != MG_OK) return st;
   }
   {
     Bracket b(h, l, MG_KERNEL_PROLONG, c.s);

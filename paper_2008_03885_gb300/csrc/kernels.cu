@@ -933,14 +933,24 @@ __device__ __forceinline__ T prolong_any(const LevelDev<T>& Lc, int transfer, co
                 : prolong_value<T, EXACT, false>(Lc, transfer, vc, i, j, idx);
 }
 
+// Stores the restricted value v of coarse node (i, j); with tc also the coarse level's
+// first half-sweep from u = 0 (the value k_first_half_zero would write from this f).
+template <typename T>
+__device__ __forceinline__ void store_restricted(const LevelDev<T>& Lc, T* __restrict__ fc, T* __restrict__ tc,
+                                                 int i, int j, T v) {
+  const int64_t at = sidx(Lc, i, j);
+  fc[at] = v;
+  if (tc) tc[at] = is_red(Lc, i, j) == 1 ? rnd(Lc, relax_from_zero(v, node_wd(Lc, i, j))) : T(0);
+}
+
 template <typename T, bool EXACT, bool PER>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value)
     k_restrict_cubic(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp, const T* __restrict__ d,
-                     T* __restrict__ fc) {
+                     T* __restrict__ fc, T* __restrict__ tc) {
   const LevelDev<T>& Lc = *Lcp;
   int i, j;
   if (!thread_node(Lc, i, j) || !interior(Lc, i, j)) return;
-  fc[sidx(Lc, i, j)] = rnd(Lc, restrict_cubic_value<T, EXACT, PER>(*Lfp, d, i, j));
+  store_restricted(Lc, fc, tc, i, j, rnd(Lc, restrict_cubic_value<T, EXACT, PER>(*Lfp, d, i, j)));
 }
 
 template <typename T, bool EXACT, bool PER>
@@ -967,7 +977,7 @@ constexpr int kTransferRowsMinLevelRows = 2048;
 
 template <typename T, bool EXACT, bool PER, int ROWS>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_restrict(const LevelDev<T>* __restrict__ Lfp, const LevelDev<T>* __restrict__ Lcp,
-                           int transfer, const T* __restrict__ d, T* __restrict__ fc) {
+                           int transfer, const T* __restrict__ d, T* __restrict__ fc, T* __restrict__ tc) {
   const LevelDev<T>& Lf = *Lfp;
   const LevelDev<T>& Lc = *Lcp;
   const int q = blockIdx.x * kBX + threadIdx.x;
@@ -989,7 +999,7 @@ __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_restrict(con
     if (j >= Lc.rows) break;
     const int i = Lc.kind == kRot ? 2 * q + (j & 1) : q;
     if (!interior(Lc, i, j)) continue;
-    fc[sidx(Lc, i, j)] = rnd(Lc, restrict_value<T, EXACT, PER>(Lf, transfer, d, i, j));
+    store_restricted(Lc, fc, tc, i, j, rnd(Lc, restrict_value<T, EXACT, PER>(Lf, transfer, d, i, j)));
   }
 }
 
@@ -1792,12 +1802,12 @@ cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const
 
 template <typename T>
 cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
-                            const T* d, T* fc, cudaStream_t s) {
+                            const T* d, T* fc, cudaStream_t s, T* tc) {
   dim3 g = grid_of(Lc.h);
   const dim3 b(kBX, kBY);
   if (transfer != kStandardCubic && Lc.h.rows >= kTransferRowsMinLevelRows) {
     g.y = (Lc.h.rows + kBY * kTransferRows - 1) / (kBY * kTransferRows);
-#define NSMG_RESTRICT(E, P) k_restrict<T, E, P, kTransferRows><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc)
+#define NSMG_RESTRICT(E, P) k_restrict<T, E, P, kTransferRows><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc, tc)
     if (Lf.h.per) {
       if (exact) NSMG_RESTRICT(true, true);
       else NSMG_RESTRICT(false, true);
@@ -1810,18 +1820,18 @@ cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int 
   }
   if (transfer == kStandardCubic) {
     if (Lf.h.per) {
-      if (exact) k_restrict_cubic<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
-      else k_restrict_cubic<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
+      if (exact) k_restrict_cubic<T, true, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc, tc);
+      else k_restrict_cubic<T, false, true><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc, tc);
     } else {
-      if (exact) k_restrict_cubic<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
-      else k_restrict_cubic<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc);
+      if (exact) k_restrict_cubic<T, true, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc, tc);
+      else k_restrict_cubic<T, false, false><<<g, b, 0, s>>>(Lf.d, Lc.d, d, fc, tc);
     }
   } else if (Lf.h.per) {
-    if (exact) k_restrict<T, true, true, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
-    else k_restrict<T, false, true, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    if (exact) k_restrict<T, true, true, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc, tc);
+    else k_restrict<T, false, true, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc, tc);
   } else {
-    if (exact) k_restrict<T, true, false, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
-    else k_restrict<T, false, false, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc);
+    if (exact) k_restrict<T, true, false, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc, tc);
+    else k_restrict<T, false, false, 1><<<g, b, 0, s>>>(Lf.d, Lc.d, transfer, d, fc, tc);
   }
   return cudaGetLastError();
 }
@@ -2062,7 +2072,7 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, con
   template cudaError_t launch_residual<T>(const LevelPair<T>&, bool, const T*, const T*, T*,          \
                                           cudaStream_t);                                              \
   template cudaError_t launch_restrict<T>(const LevelPair<T>&, const LevelPair<T>&, int, bool,        \
-                                          const T*, T*, cudaStream_t);                                \
+                                          const T*, T*, cudaStream_t, T*);                            \
   template cudaError_t launch_prolong_add<T>(const LevelPair<T>&, const LevelPair<T>&, int, bool, T*, \
                                              const T*, cudaStream_t, const T*);                       \
   template cudaError_t launch_sweep_fused<T>(const LevelPair<T>&, bool, const T*, const T*, T*, cudaStream_t); \

@@ -24,9 +24,10 @@ cudaError_t launch_apply(const LevelPair<T>& L, bool exact, const T* u, T* out, 
 template <typename T>
 cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d,
                             cudaStream_t s);
+// With tc: also the coarse level's first half-sweep from u = 0 (as launch_first_half_zero).
 template <typename T>
 cudaError_t launch_restrict(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer, bool exact,
-                            const T* d, T* fc, cudaStream_t s);
+                            const T* d, T* fc, cudaStream_t s, T* tc = nullptr);
 // uf = uin + P vc (uin = nullptr: in place, uf += P vc).
 template <typename T>
 cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, int transfer,
