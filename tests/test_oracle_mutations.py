@@ -2,17 +2,22 @@
 
 Each case plants one mistake in the oracle (on the CPU, through monkeypatch: a
 dropped stencil term, a wrong sign, a wrong transfer weight, a swapped colour order,
-a wrong residual sign, a wrong coarsest solve, a wrong relaxation scaling) and runs
-a battery of the pins of `test_oracle.py` (printed stencils, the paper's symbol,
-printed Galerkin operators and transfers, the two-level direct-solver theorem, the
-Schur-complement identity, printed rates and the LFA rate, agreement with a direct
-solve). At least one pin must fail for every mistake, and none without one.
+a wrong residual sign, a wrong coarsest solve, a wrong relaxation scaling, ghosts
+without the odd-reflection sign; for periodic grids a coarsest solution off zero mean or a
+missing wrap-around; for cubic transfers bilinear or wrong taps) and runs a battery of the
+pins of `test_oracle.py`, `test_oracle_periodic.py` or `test_oracle_cubic.py`
+(printed stencils, the paper's symbols, printed Galerkin operators and transfers, the
+two-level direct-solver theorem, the Schur-complement identity, printed rates and LFA
+rates, agreement with a direct solve). At least one pin must fail for every mistake,
+and none without one.
 """
 import numpy as np
 import pytest
 
 import oracle.mg as omg
 import test_oracle as pins
+import test_oracle_cubic as cpins
+import test_oracle_periodic as ppins
 
 BATTERY = [
     ("fine stencil (order 4)", lambda: pins.test_fine_operator_matches_printed_stencil(4, 8)),
@@ -30,9 +35,28 @@ BATTERY = [
 ]
 
 
-def failures():
+PERIODIC_BATTERY = [
+    ("printed block circulant", ppins.test_five_point_matrix_is_the_printed_block_circulant),
+    ("periodic Schur complement", ppins.test_red_black_reduction_schur_complement_is_twice_galerkin),
+    ("Fourier eigenvectors", lambda: ppins.test_fourier_modes_are_exact_eigenvectors(4, 3, 5)),
+    ("two-level direct solver (periodic)", ppins.test_two_level_rbc_galerkin_is_direct_solver),
+    ("discrete LFA rate", lambda: ppins.test_two_level_rate_equals_discrete_lfa("nongalerkin", 1.0)),
+    ("zero-mean converged solution", ppins.test_converged_solution_is_the_zero_mean_solution),
+    ("printed periodic rates", ppins.test_printed_three_level_and_two_level_sc_rates),
+]
+
+CUBIC_BATTERY = [
+    ("printed cubic transfers", cpins.test_cubic_transfers_match_printed_stencils),
+    ("printed restriction symbol", lambda: cpins.test_restriction_symbol_is_the_printed_one(2, 3)),
+    ("tensor cubics reproduced", cpins.test_interpolation_reproduces_tensor_cubics_away_from_the_boundary),
+    ("fourth order up to the boundary", cpins.test_interpolation_is_fourth_order_up_to_the_boundary),
+    ("cubic transfers converge faster", cpins.test_fourth_order_transfers_and_coarse_operator_converge_faster),
+]
+
+
+def failures(battery=None):
     out = []
-    for name, pin in BATTERY:
+    for name, pin in battery or BATTERY:
         try:
             with np.errstate(all="ignore"):
                 pin()
@@ -125,7 +149,61 @@ def restriction_transposed_weight(monkeypatch):
     monkeypatch.setattr(omg.Oracle, "__init__", bad)
 
 
+def even_reflection(monkeypatch):
+    orig = omg.fold
+
+    def bad(t, n):
+        tp, sign, on_boundary = orig(t, n)
+        return tp, np.ones_like(sign), on_boundary  # ghosts mirrored without the sign flip
+
+    monkeypatch.setattr(omg, "fold", bad)
+
+
+def periodic_not_zero_mean(monkeypatch):
+    orig = omg.Oracle.coarse_solve
+
+    def bad(self, d):
+        v = orig(self, d)
+        if self.periodic:  # the singular coarse solve left with a constant in its solution
+            v = v + 1.0
+        return v
+
+    monkeypatch.setattr(omg.Oracle, "coarse_solve", bad)
+
+
+def periodic_wrap_dropped(monkeypatch):
+    orig = omg.stencil_weights
+
+    def bad(level, stencil, factor):
+        if not level.periodic:
+            return orig(level, stencil, factor)
+        level.periodic = False  # wrap-around terms treated as Dirichlet ghosts
+        try:
+            return orig(level, stencil, factor)
+        finally:
+            level.periodic = True
+
+    monkeypatch.setattr(omg, "stencil_weights", bad)
+
+
+def cubic_as_bilinear(monkeypatch):
+    monkeypatch.setattr(omg, "_cubic_interpolation",
+                        lambda fine, coarse: omg.interpolation(fine, coarse, omg.STANDARD, 2))
+
+
+def cubic_taps_swapped(monkeypatch):
+    orig = omg._cubic_interpolation
+
+    def bad(fine, coarse):
+        P = orig(fine, coarse).tocsr(copy=True)
+        P.data = np.where(np.abs(P.data) == 9.0 / 16, P.data * 0.5, P.data)  # 9/32 for 9/16
+        return P
+
+    monkeypatch.setattr(omg, "_cubic_interpolation", bad)
+
+
 MUTATIONS = {
+    "even instead of odd reflection at the boundary": even_reflection,
     "dropped stencil term": drop_term,
     "wrong sign of a stencil term": flip_sign,
     "interpolation weights summed": interpolation_weight,
@@ -147,3 +225,35 @@ def test_planted_mistake_is_caught(name, monkeypatch):
     MUTATIONS[name](monkeypatch)
     caught = failures()
     assert caught, f"no pin caught: {name}"
+
+
+def test_periodic_and_cubic_batteries_pass_on_the_oracle_as_written():
+    assert failures(PERIODIC_BATTERY) == []
+    assert failures(CUBIC_BATTERY) == []
+
+
+PERIODIC_MUTATIONS = {
+    "periodic coarsest solution not normalised to zero mean": periodic_not_zero_mean,
+    "periodic wrap-around dropped": periodic_wrap_dropped,
+    "dropped stencil term (periodic)": drop_term,
+    "black half-sweep first (periodic)": black_first,
+}
+
+
+@pytest.mark.parametrize("name", sorted(PERIODIC_MUTATIONS))
+def test_planted_periodic_mistake_is_caught(name, monkeypatch):
+    PERIODIC_MUTATIONS[name](monkeypatch)
+    assert failures(PERIODIC_BATTERY), f"no periodic pin caught: {name}"
+
+
+CUBIC_MUTATIONS = {
+    "cubic transfers built as bilinear": cubic_as_bilinear,
+    "cubic tap 9/16 halved": cubic_taps_swapped,
+    "even instead of odd reflection (cubic ghosts)": even_reflection,
+}
+
+
+@pytest.mark.parametrize("name", sorted(CUBIC_MUTATIONS))
+def test_planted_cubic_mistake_is_caught(name, monkeypatch):
+    CUBIC_MUTATIONS[name](monkeypatch)
+    assert failures(CUBIC_BATTERY), f"no cubic pin caught: {name}"
