@@ -62,7 +62,7 @@ extern "C" {
 typedef enum {
   MG_OK = 0,
   MG_ERR_INVALID = 1,       /* bad argument: size, enum, NULL pointer, level index */
-  MG_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement */
+  MG_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement */
   MG_ERR_OOM = 3,           /* device allocation failed */
   MG_ERR_BUDGET = 4,        /* request exceeds a caller-set memory budget */
   MG_ERR_CUDA = 5,          /* a CUDA runtime call failed; the handle must be destroyed */
