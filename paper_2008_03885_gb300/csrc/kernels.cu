@@ -1664,15 +1664,15 @@ dim3 norm_grid(const LevelDev<T>& L) {
 // 9.02 ms, 257^2 6.07 -> 5.78 ms (8 blocks per SM: the same; 2: about half the gain).
 constexpr int kSpreadBlocksPerSm = 4;
 
+// SM count of the current device when first asked (one GPU model per process here;
+// initialised once, thread-safe).
 int sm_count() {
-  static int n = 0;
-  if (n == 0) {
+  static const int n = [] {
     int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-      n = v;
-    else
-      return 1;
-  }
+    const bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0;
+    return ok ? v : 1;
+  }();
   return n;
 }
 
