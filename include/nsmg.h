@@ -284,10 +284,9 @@ mg_status mg_solve_batched(mg_handle* const* handles, double* const* u, const do
 
 /* ---- relative residual without device allocation ----------------------------
    The paper has no counterpart to this call; it serves callers that must not
-   allocate device memory at the point where they need a residual norm: code that
-   runs while a stream is being captured into a CUDA graph (cudaMalloc cannot be
-   captured), loops that cannot afford the implicit device synchronisation of
-   cudaMalloc / cudaFree, or hosts that fix the library's memory at set-up.
+   allocate device memory at the point where they need a residual norm: loops that
+   cannot afford the implicit device synchronisation of cudaMalloc / cudaFree, or hosts
+   that fix the library's memory at set-up (a budget, or an arena they manage).
    Writes ||f - L_h u||_2 / ||f||_2 over the finest level's interior nodes (same
    evaluation order as mg_cycle's rel_res_out, partial sums added in a different
    fixed order) to the DEVICE double *rel_res_dev, asynchronously on `stream`.
@@ -296,7 +295,9 @@ mg_status mg_solve_batched(mg_handle* const* handles, double* const* u, const do
    32 KB device array inside the library (2 x 2048 doubles), which every GPU that
    loads the library holds until the process exits. The first call on a device looks
    up that array's device address (and may make the CUDA runtime load the library's
-   device code), so make the first call on each device before any stream capture.
+   device code), so make the first call on each device before any stream capture. The
+   looked-up address is kept for the life of the process: after a cudaDeviceReset, do not
+   call it again on that device.
    All calls share the array and each call overwrites the partials it reads, so no
    state carries over; calls whose work overlaps on the GPU (different streams, or
    several host threads) race on the array and must be serialised by the caller.

@@ -25,6 +25,7 @@ import numpy as np
 import torch
 
 import paper_2008_03885_gb300 as mg
+import synth
 
 
 @dataclasses.dataclass
@@ -34,14 +35,16 @@ class Request:
     order: int
     coarse_op: str  # "galerkin" or "nongalerkin"
     rtol: float
-    f: np.ndarray  # (n+1, n+1) float64 right-hand side
+    f: np.ndarray | None  # (n+1, n+1) float64 right-hand side in host memory, or None:
+    #                       N(0,1) from `seed`, generated on the device (synth.rhs_normal_torch)
     arrival: float = 0.0  # seconds after the stream starts
+    seed: int = 0
 
 
 @dataclasses.dataclass
 class Result:
     rid: int
-    u: np.ndarray
+    u: np.ndarray | None  # None when the server runs with keep_u=False
     cycles: int
     rel_res: float
     arrival: float
@@ -164,8 +167,10 @@ class Server:
             self.cache.release(hi)
         torch.cuda.synchronize()
 
-    def run(self, requests, realtime: bool = True):
-        """Serve `requests` (sorted by arrival). Returns (results by rid, stats)."""
+    def run(self, requests, realtime: bool = True, keep_u: bool = True):
+        """Serve `requests` (sorted by arrival). Returns (results by rid, stats).
+        keep_u=False: each solution is still copied back to host memory (the latency
+        includes it) but into a buffer the worker reuses, and not kept."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         q: queue.Queue = queue.Queue()
         results = {}
@@ -175,12 +180,13 @@ class Server:
 
         def worker():
             stream = torch.cuda.Stream()
+            host_bufs = {}  # n -> pinned buffer reused for the copy-back (keep_u=False)
             while True:
                 r = q.get()
                 if r is None:
                     return
                 try:
-                    res = self._solve(r, stream, t0)
+                    res = self._solve(r, stream, t0, None if keep_u else host_bufs)
                     with lock:
                         results[r.rid] = res
                 except Exception as e:  # reported after the run
@@ -219,33 +225,44 @@ class Server:
         }
         return results, stats
 
-    def _solve(self, r: Request, stream, t0: float) -> Result:
+    def _solve(self, r: Request, stream, t0: float, host_bufs=None) -> Result:
         hi = self.cache.acquire((r.n, r.order, r.coarse_op))
         start = time.perf_counter() - t0
         try:
             with torch.cuda.stream(stream):
-                f_host = torch.from_numpy(r.f).pin_memory()
-                hi.f.copy_(f_host, non_blocking=True)
+                if r.f is None:
+                    synth.rhs_normal_torch(r.n, r.seed, out=hi.f)
+                else:
+                    f_host = torch.from_numpy(r.f).pin_memory()
+                    hi.f.copy_(f_host, non_blocking=True)
                 hi.u.zero_()
                 k, hist = mg.mg_solve(hi.handle, hi.u, hi.f, rtol=r.rtol, max_cycles=self.max_cycles,
                                       stream=stream, raise_not_converged=False)
-                u_host = torch.empty_like(f_host).pin_memory()
+                if host_bufs is None:
+                    u_host = torch.empty(hi.u.shape, dtype=torch.float64).pin_memory()
+                else:
+                    u_host = host_bufs.get(r.n)
+                    if u_host is None:
+                        u_host = host_bufs[r.n] = torch.empty(hi.u.shape, dtype=torch.float64).pin_memory()
                 u_host.copy_(hi.u, non_blocking=True)
                 stream.synchronize()
         finally:
             self.cache.release(hi)
-        return Result(r.rid, u_host.numpy(), k, hist[-1], r.arrival, start, time.perf_counter() - t0)
+        return Result(r.rid, u_host.numpy() if host_bufs is None else None, k, hist[-1], r.arrival, start,
+                      time.perf_counter() - t0)
 
     def close(self):
         self.cache.close()
 
 
 def poisson_stream(seed: int, count: int, rate: float, k_lo: int, k_hi: int, rtol: float = 1e-8,
-                   rhs=None):
+                   rhs=None, device_rhs: bool = False):
     """Seeded request stream: exponential inter-arrival times at `rate` per second,
     sides 2^k + 1 with k uniform in [k_lo, k_hi], order 2/4 and Galerkin/non-Galerkin
-    50/50, right-hand sides from `rhs(n, seed)` (default N(0,1))."""
-    import synth
+    50/50, one right-hand side per request from `rhs(n, seed)` (default N(0,1)), seeded
+    by the request id. device_rhs=True: the requests carry only the seed and the server
+    generates each N(0,1) right-hand side on the device (a 20 000-request stream of
+    sides up to 4097 would need ~0.7 TB of host memory for its right-hand sides)."""
     rhs = rhs or synth.rhs_normal
     u = synth.uniform01(seed, 4 * count)
     t = 0.0
@@ -256,5 +273,6 @@ def poisson_stream(seed: int, count: int, rate: float, k_lo: int, k_hi: int, rto
         order = 2 if u[4 * i + 2] < 0.5 else 4
         op = "galerkin" if u[4 * i + 3] < 0.5 else "nongalerkin"
         n = 2 ** k
-        out.append(Request(i, n, order, op, rtol, rhs(n, seed * 100003 + i), t))
+        rs = seed * 100003 + i
+        out.append(Request(i, n, order, op, rtol, None if device_rhs else rhs(n, rs), t, rs))
     return out

@@ -137,3 +137,52 @@ def rhs_periodic_mode(n: int, k: int, l: int) -> np.ndarray:
     f = np.zeros((n + 1, n + 1))
     f[:n, :n] = np.outer(np.cos(2 * math.pi * l * x), np.cos(2 * math.pi * k * x))
     return f
+
+
+# ---- the same generator with torch tensors (on any device) --------------------------
+# Used where a right-hand side is made on the GPU next to the solve (e.g. one per
+# served request), so no host generation or host-to-device copy sits in the request
+# path. SplitMix64 with 64-bit wrap-around arithmetic in signed int64 (two's
+# complement gives the same bits as unsigned arithmetic; right shifts are made
+# logical by masking). The uniforms are bit-identical to `uniform01`; the normals
+# agree with `normal` to within the rounding of log / cos / sin on the device.
+def _i64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _lsr(z, s: int):
+    import torch
+    return torch.bitwise_and(torch.bitwise_right_shift(z, s), (1 << (64 - s)) - 1)
+
+
+def uniform01_torch(seed: int, count: int, device="cpu", offset: int = 0):
+    import torch
+    k = torch.arange(offset + 1, offset + count + 1, dtype=torch.int64, device=device)
+    base = _i64((int(seed) << 32) & 0xFFFFFFFFFFFFFFFF)
+    z = base + k * _i64(int(_GOLDEN))
+    z = torch.bitwise_xor(z, _lsr(z, 30)) * _i64(int(_M1))
+    z = torch.bitwise_xor(z, _lsr(z, 27)) * _i64(int(_M2))
+    z = torch.bitwise_xor(z, _lsr(z, 31))
+    return _lsr(z, 11).to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal_torch(seed: int, count: int, device="cpu"):
+    import torch
+    m = (count + 1) // 2
+    u = uniform01_torch(seed, 2 * m, device)
+    r = torch.sqrt(-2.0 * torch.log(1.0 - u[0::2]))
+    t = (2.0 * math.pi) * u[1::2]
+    z = torch.stack((r * torch.cos(t), r * torch.sin(t)), dim=1).reshape(-1)
+    return z[:count]
+
+
+def rhs_normal_torch(n: int, seed: int = 0, device="cpu", out=None):
+    """`rhs_normal` generated on `device` (into `out` if given, an (n+1) x (n+1) float64
+    tensor): i.i.d. N(0,1) on interior nodes, row-major, zero boundary."""
+    import torch
+    if out is None:
+        out = torch.zeros((n + 1, n + 1), dtype=torch.float64, device=device)
+    else:
+        out.zero_()
+    out[1:-1, 1:-1] = normal_torch(seed, (n - 1) * (n - 1), out.device).reshape(n - 1, n - 1)
+    return out

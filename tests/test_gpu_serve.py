@@ -1,7 +1,10 @@
 """Serving with continuous batching: every result equals the same request solved
-alone, and the budget is respected."""
+alone, every result is checked against the FP64 oracle, and the budget is respected."""
 import numpy as np
 import pytest
+
+from oracle import spectral
+from oracle.mg import REDBLACK, Options, Oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +43,51 @@ def test_results_identical_alone_and_in_the_mix(opts):
         u, k = alone(r, **opts)
         assert res.cycles == k
         assert np.array_equal(res.u, u), r.rid
+
+
+class OracleCache:
+    """One oracle hierarchy per problem shape (the served requests repeat shapes)."""
+
+    def __init__(self, **opts):
+        self.opts, self.cache = opts, {}
+
+    def __call__(self, r):
+        key = (r.n, r.order, r.coarse_op)
+        if key not in self.cache:
+            self.cache[key] = Oracle(r.n, r.order, REDBLACK, r.coarse_op, Options(**self.opts))
+        return self.cache[key]
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_served_results_against_the_oracle(mixed):
+    """Every served solution meets the tolerance by the oracle's own FP64 residual and is
+    close to the exact discrete solution (oracle/spectral.py). FP64 with the exact
+    evaluation order: every served solution equals the oracle's iterate after the same
+    number of cycles bit for bit (Algorithm "MG", Sec. 2.2, stopped by its while-test)."""
+    opts = dict(nu1=2, nu2=1)
+    if mixed:
+        opts.update(precision=mg.MG_PREC_MIXED_FP32, fma_contract=1)
+    reqs = serve.poisson_stream(seed=21, count=32, rate=3000.0, k_lo=4, k_hi=8, rtol=1e-8)
+    srv = serve.Server(slots=5, budget_bytes=8e9, **opts)
+    try:
+        results, stats = srv.run(reqs, realtime=True)
+    finally:
+        srv.close()
+    oracles = OracleCache(nu1=2, nu2=1)
+    for r in reqs:
+        res = results[r.rid]
+        o = oracles(r)
+        ug = o.to_vec(res.u)
+        fv = o.to_vec(r.f)
+        rr = o.rel_residual(ug, fv)
+        assert rr < 1.5e-8, (r.rid, rr)
+        assert abs(rr - res.rel_res) <= 1e-6 * rr, (r.rid, rr, res.rel_res)
+        U = o.to_vec(spectral.solve(r.f, r.order))
+        assert np.linalg.norm(ug - U) <= 1e-6 * np.linalg.norm(U), r.rid
+        if not mixed:
+            uo, ho = o.solve(fv, rtol=r.rtol, max_cycles=60)
+            assert res.cycles == len(ho) - 1, r.rid
+            assert np.array_equal(ug, uo), r.rid
 
 
 def test_small_budget_evicts_and_stays_correct():
