@@ -36,14 +36,16 @@ WORKLOAD = ("2D Poisson -Lap u = f, 4th-order 9-point Laplacian, 4097x4097 nodes
             "Galerkin G^(2) coarse operators, V(2,1) red-black smoothing, omega=1, solve from u=0 to 1e-10")
 
 # DRAM bytes (read + write) per launch of the dominant kernel, k_half_sweep_nt<double,
-# exact, 9> on level 0, from one ncu capture of `bench.py --profile-case`
-# (profiles/k_half_sweep_nt_fp64_order4_N4096.md); None whenever that kernel changes.
+# exact, 9> on level 0, from one ncu capture of `bench.py --profile-case` (the summary
+# under profiles/ names the kernel and workload); None whenever that kernel changes.
 DOMINANT_KERNEL_TRAFFIC_BYTES = 373.26e6
 
-# FP64 ALU peak for non-fused FP64 operations: GB300 FP64 1.25 TFLOP/s counts an FMA as
-# two flops, i.e. 0.625 T FP64 instructions/s; a kernel that rounds every product
-# separately issues one instruction per flop.
-FP64_SEPARATE_OP_PEAK_TFLOPS = 0.625
+# FP64 peak of GB300: 1.25 TFLOP/s nominal (an FMA counts two flops). MEASURED_PEAKS.json
+# carries no FP64 figure; the measured DFMA issue rate (600 G/s, 1.20 TFLOP/s) is quoted
+# beside it. Flops per updated node of a half-sweep: 2 s for the stencil application of
+# s terms plus 3 (f - L u, the multiply by omega / a_pp, the add to u): 21 for s = 9.
+FP64_PEAK_TFLOPS = 1.25
+FP64_DFMA_MEASURED_TFLOPS = 1.1998
 
 
 def load_peaks():
@@ -136,50 +138,101 @@ def max_over_ranks(ws, x: float) -> float:
     return float(t.item())
 
 
-def oracle_sample(cycles_to_tol: int, n_sample: int = 2048):
-    """Time one V(2,1) cycle of the oracle on an (n_sample+1)^2 grid of the same workload
-    and scale it to the full grid and the cycle count: a bounded CPU baseline."""
+def host_cores():
+    """Cores this process may run on, and the machine's core count."""
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:
+        usable = os.cpu_count()
+    return usable, os.cpu_count()
+
+
+def build_oracle(n: int = N):
+    """The FP64 oracle of the bench workload on an (n+1)^2 grid, its right-hand side, and
+    the seconds the build took."""
     import synth
     from oracle.mg import GALERKIN, REDBLACK, Options, Oracle
-    import numpy as np
-    o = Oracle(n_sample, ORDER, REDBLACK, GALERKIN, Options(nu1=NU1, nu2=NU2))
-    f = o.to_vec(synth.rhs_sine_modes(n_sample, SEED))
     t0 = time.perf_counter()
-    o.cycle(np.zeros_like(f), f)
-    dt = time.perf_counter() - t0
-    scale = (N - 1) ** 2 / (n_sample - 1) ** 2
-    return dt * scale * cycles_to_tol * 1e3, dt
+    o = Oracle(n, ORDER, REDBLACK, GALERKIN, Options(nu1=NU1, nu2=NU2))
+    setup_s = time.perf_counter() - t0
+    return o, o.to_vec(synth.rhs_sine_modes(n, SEED)), setup_s
 
 
-def oracle_cycles_to_tol(n_small: int = 256) -> int:
-    """Cycles the oracle needs for this workload on a small grid (the count is
-    nearly independent of the grid size for multigrid)."""
-    import synth
-    from oracle.mg import GALERKIN, REDBLACK, Options, Oracle
-    o = Oracle(n_small, ORDER, REDBLACK, GALERKIN, Options(nu1=NU1, nu2=NU2))
-    _, hist = o.solve(o.to_vec(synth.rhs_sine_modes(n_small, SEED)), rtol=RTOL, max_cycles=60)
-    return len(hist) - 1
+def oracle_cycle_times(o, f, cycles: int, residuals: int = 0):
+    """Time `cycles` consecutive V(2,1) cycles of the oracle from u = 0 (each from the
+    previous iterate); the relative residual after each of the first `residuals` cycles
+    is evaluated outside the timed region. Returns (seconds per cycle, residual history)."""
+    import numpy as np
+    u = np.zeros_like(f)
+    hist = [o.rel_residual(u, f)]
+    times = []
+    for k in range(cycles):
+        t0 = time.perf_counter()
+        u = o.cycle(u, f)
+        times.append(time.perf_counter() - t0)
+        if k < residuals:
+            hist.append(o.rel_residual(u, f))
+    # the cycle count to the tolerance, if the timed cycles did not reach it (not timed)
+    while residuals and hist[-1] >= RTOL and len(hist) <= 30:
+        u = o.cycle(u, f)
+        hist.append(o.rel_residual(u, f))
+    return times, hist
+
+
+def _all_cores_worker(n):
+    o, f, _ = build_oracle(n)
+    times, _ = oracle_cycle_times(o, f, 1)
+    return times[0]
+
+
+def oracle_all_cores(n: int = 1024):
+    """Every usable core runs its own oracle (one V(2,1) cycle on an (n+1)^2 grid of the
+    workload, processes started with spawn): aggregate grid-point-cycles/s against one
+    process alone. The oracle itself is single-threaded numpy/scipy."""
+    import multiprocessing as mp
+    usable, _ = host_cores()
+    one = _all_cores_worker(n)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(usable) as pool:
+        t0 = time.perf_counter()
+        per = pool.map(_all_cores_worker, [n] * usable)
+        wall = time.perf_counter() - t0
+    pts = (n + 1) ** 2
+    return {"processes": usable, "grid": f"{n + 1}^2", "cycle_s_one_process": one,
+            "cycle_s_median_all_cores": statistics.median(per),
+            "grid_point_cycles_per_s_one_process": pts / one,
+            "grid_point_cycles_per_s_all_cores": usable * pts / statistics.median(per),
+            "wall_s_including_setup": wall}
 
 
 def run_reference(args, ws, rank):
-    """The FP64 oracle on the host cores, each step one bounded sample (see oracle_sample)."""
+    """The FP64 oracle on the host cores, on the bench workload itself (4097^2): built once
+    (not timed), then every step is one oracle V(2,1) cycle continuing from the previous
+    iterate. value = median cycle time x the cycles the oracle needs to reach 1e-10 (its
+    own residual history, evaluated outside the timed cycles)."""
     if rank != 0:
         return
-    cycles = oracle_cycles_to_tol()
-    vals = []
-    for k in range(args.warmup + args.steps):
-        v, _ = oracle_sample(cycles, args.ref_n)
-        if k >= args.warmup:
-            vals.append(v)
-    value = statistics.median(vals)
-    sample = (f"one V(2,1) cycle of the oracle on a {args.ref_n + 1}^2 grid of the same workload, "
-              f"scaled by the point ratio to 4097^2 and by {cycles} cycles to 1e-10 (the oracle's count on 257^2)")
+    o, f, setup_s = build_oracle(args.ref_n)
+    times, hist = oracle_cycle_times(o, f, args.warmup + args.steps, residuals=min(12, args.warmup + args.steps))
+    timed = times[args.warmup:]
+    cyc_ms = statistics.median(timed) * 1e3
+    below = [k for k, r in enumerate(hist) if r < RTOL]
+    cycles = below[0] if below else None
+    value = cyc_ms * cycles if cycles else None
+    usable, total = host_cores()
+    allc = None if args.no_all_cores else oracle_all_cores()
+    sample = (f"one V(2,1) cycle of the oracle per step on the {args.ref_n + 1}^2 workload itself "
+              f"(build {setup_s:.1f} s, not timed); value = median cycle time x {cycles} cycles to 1e-10 "
+              f"(the oracle's own residual history)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": cyc_ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": WORKLOAD, "parallelism": "replicas", "step": "one oracle V(2,1) cycle",
+                   "cycles_to_tol": cycles, "history": hist, "cycle_ms_all": [t * 1e3 for t in timed],
+                   "setup_s": setup_s},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "host_cores": total, "usable_cores": usable,
+                         "kind": "oracle", "sample": sample, "all_cores": allc},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -254,6 +307,23 @@ def run_ours(args, ws, rank, local):
     e2e_ms = max_over_ranks(ws, e2.elapsed_time(e3) / args.steps)
     assert torch.equal(u_steps[-1], u.cpu()), "host-buffer solve differs from the device solve"
     final_rr = hist[-1]
+    # the same host <-> device copies alone (pinned memory, the call's stream), to split
+    # the end-to-end time into copies and solve
+    dev_f, dev_u = torch.empty_like(f), torch.empty_like(u)
+    cp = []
+    for k in range(args.steps):
+        a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a0.record(stream)
+        dev_f.copy_(f_host, non_blocking=True)
+        dev_u.copy_(u_steps[k], non_blocking=True)
+        a1.record(stream)
+        u_steps[k].copy_(dev_u, non_blocking=True)
+        a2.record(stream)
+        torch.cuda.synchronize()
+        cp.append((a0.elapsed_time(a1), a1.elapsed_time(a2)))
+    h2d_ms = statistics.median(c[0] for c in cp)
+    d2h_ms = statistics.median(c[1] for c in cp)
+    del dev_f, dev_u
 
     # ---- variants of the same workload (one timed solve each after one warm-up)
     variants = {}
@@ -310,12 +380,12 @@ def run_ours(args, ws, rank, local):
     batched = run_batched(args) if not args.quick and not args.no_extras else None
     served = run_serving(args) if not args.quick and not args.no_extras else None
 
-    # ---- roofline of the dominant kernel (finest-level red-black half-sweep)
+    # ---- roofline of the dominant kernel (finest-level red-black half-sweep, FP64)
     sm_ms, sm_n = kt[mg.MG_KERNEL_SMOOTH]
     per_launch_ms = sm_ms / max(sm_n, 1)
     pts = (N - 1) ** 2
-    flops_per_launch = pts / 2 * 20  # 9 mul + 8 add + sub + mul + add per updated node
-    bytes_per_launch = 3 * (N + 1) ** 2 * 8  # read u, f; write u (whole grid)
+    flops_per_launch = pts / 2 * (2 * 9 + 3)  # updated nodes x (2 s + 3), s = 9 terms
+    bytes_per_launch = 12 * (N + 1) ** 2  # half of a sweep's 24 B per node (read u, f; write u)
     achieved_tflops = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
     hbm_peak, peak_kind = load_peaks()
     achieved_gbs = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
@@ -329,16 +399,28 @@ def run_ours(args, ws, rank, local):
                    "cycles_to_tol": cycles, "final_rel_res": final_rr, "fma_contract": 0,
                    "l2": "inputs larger than L2: f alone is 134 MB and the hierarchy ~1.1 GB per solve",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_SEPARATE_OP_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_SEPARATE_OP_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS,
                      "traffic": DOMINANT_KERNEL_TRAFFIC_BYTES, "algorithmic_bytes": bytes_per_launch,
+                     "traffic_over_algorithmic": (DOMINANT_KERNEL_TRAFFIC_BYTES / bytes_per_launch
+                                                  if DOMINANT_KERNEL_TRAFFIC_BYTES else None),
+                     "algorithmic_flops": flops_per_launch,
                      "kernel": "k_half_sweep_nt<double, exact, 9> on level 0",
                      "per_launch_ms": per_launch_ms, "launches": sm_n,
-                     "hbm_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm_peak,
+                     "peak_kind": "FP64 1.25 TFLOP/s nominal (FMA = 2 flops); no FP64 figure in "
+                                  "MEASURED_PEAKS.json",
+                     "frac_of_measured_dfma_rate": achieved_tflops / FP64_DFMA_MEASURED_TFLOPS,
+                     "note": "exact evaluation order (no FMA): DADD/DMUL issue at 0.506 T/s measured, so "
+                             "this kernel cannot exceed 0.40 of the nominal FP64 peak",
+                     "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_algorithmic": achieved_gbs / hbm_peak,
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
-                     "peak_kind": "FP64 1.25 TFLOP/s nominal counted per separately rounded op",
                      "share_of_finest_level_kernel_time": sm_ms / total_kernel_ms if total_kernel_ms else None},
-        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * bytes_grid, "d2h_bytes_per_step": bytes_grid},
+        "roofline_fp32_smoothing": fp32_smoothing_roofline(variants.get("mixed_fp32_inner"), hbm_peak, peak_kind),
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * bytes_grid, "d2h_bytes_per_step": bytes_grid,
+                "breakdown_ms": {"h2d_copies": h2d_ms, "d2h_copy": d2h_ms, "device_solve": ms_max,
+                                 "rest": e2e_ms - h2d_ms - d2h_ms - ms_max},
+                "copy_gbs": {"h2d": 2 * bytes_grid / (h2d_ms * 1e-3) / 1e9,
+                             "d2h": bytes_grid / (d2h_ms * 1e-3) / 1e9}},
         "throughput": solve_throughput(ms_max, cycles, variants.get("mixed_fp32_inner")),
         "gpu_launches": launches,
         "clocks": clocks,
@@ -350,30 +432,62 @@ def run_ours(args, ws, rank, local):
                                enumerate(("smooth", "residual", "restrict", "prolong", "norm"))},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, dt = oracle_sample(cycles, args.ref_n)
-        out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                               "sample": f"one V(2,1) cycle of the oracle on a {args.ref_n + 1}^2 grid "
-                                         f"({dt:.2f} s), scaled by the point ratio to 4097^2 and by "
-                                         f"{cycles} cycles to 1e-10"}
+        del u, f
+        torch.cuda.empty_cache()
+        o, fo, setup_s = build_oracle(N)
+        times, _ = oracle_cycle_times(o, fo, 1)
+        del o, fo
+        usable, total = host_cores()
+        out["cpu_baseline"] = {"value": times[0] * cycles * 1e3, "unit": "ms", "cores": 1, "host_cores": total,
+                               "usable_cores": usable, "kind": "oracle",
+                               "sample": f"one V(2,1) cycle of the oracle on the 4097^2 workload itself "
+                                         f"({times[0]:.2f} s; build {setup_s:.1f} s, not timed) x {cycles} "
+                                         f"cycles to 1e-10 (the oracle's iterates are bitwise the GPU's, so "
+                                         f"it needs the same count)"}
     if rank == 0:
         print(json.dumps(out))
+
+
+def fp32_smoothing_roofline(mixed, hbm_peak, peak_kind):
+    """HBM roofline of the mixed path's level-0 FP32 red-black smoothing, on the method's
+    algorithmic bytes: 12 B per node per full sweep (read u and f, write u once), i.e.
+    6 B per node per half-sweep. Per refinement step V(2,1) makes 2 (nu1 + nu2) = 6
+    half-sweeps on level 0, one of them inside the FP64 refinement residual (timed with
+    the norm class), so the smoothing launches carry 5 of them."""
+    if not mixed:
+        return None
+    sm_ms, sm_n = mixed["finest_kernel_ms"]["smooth"], mixed["finest_kernel_launches"]["smooth"]
+    steps = mixed["cycles"]
+    alg = steps * (2 * (NU1 + NU2) - 1) * 6 * (N + 1) ** 2
+    gbs = alg / (sm_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_solve": alg, "launches_per_solve": sm_n,
+            "ms_per_solve": sm_ms, "kernel": "level-0 FP32 smoothing of the mixed path (4097^2, order 4)"}
 
 
 def run_mixed_large(args):
     """8193^2 (N = 8192), orders 2 and 4, N(0,1) right-hand side: time to 1e-10 of the
     FP64 path (exact evaluation order, bitwise equal to the oracle's iterates) and of
-    the mixed path (FP32 inner cycles, FP64 refinement), and the mixed solution's
-    relative error against the FP64 solution."""
+    the mixed path (FP32 inner cycles, FP64 refinement); each solution's relative error
+    against the FP64 oracle's exact discrete solution (Fourier diagonalisation with the
+    operator's symbol, oracle/spectral.py, computed on the host outside the timing) and
+    the mixed solution's difference from the FP64 one."""
     import torch
     import paper_2008_03885_gb300 as mg
     import synth
+    from oracle import spectral
     n = args.large_n
-    f = torch.tensor(synth.rhs_normal(n, SEED + 3), dtype=torch.float64, device="cuda")
+    F = synth.rhs_normal(n, SEED + 3)
+    f = torch.tensor(F, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    out = {"n": n, "rhs": "N(0,1) i.i.d.", "rtol": RTOL}
+    out = {"n": n, "rhs": "N(0,1) i.i.d.", "rtol": RTOL,
+           "error_reference": "oracle exact discrete solution (oracle/spectral.py: DST-I with the symbol)"}
     for order in (2, 4):
         res = {}
         sols = {}
+        t0 = time.perf_counter()
+        U = torch.tensor(spectral.solve(F, order, workers=-1), dtype=torch.float64, device="cuda")
+        oracle_s = time.perf_counter() - t0
         for name, extra in (("fp64", {}), ("mixed", {"precision": mg.MG_PREC_MIXED_FP32, "fma_contract": 1})):
             h = mg.mg_setup(n, order, "redblack", "galerkin", nu1=NU1 if order == 4 else 1, nu2=1, **extra)
             u = torch.zeros_like(f)
@@ -390,9 +504,12 @@ def run_mixed_large(args):
             sols[name] = u
         err = float(torch.linalg.norm(sols["mixed"] - sols["fp64"]) / torch.linalg.norm(sols["fp64"]))
         res["mixed"]["rel_error_vs_fp64_solution"] = err
+        for name in ("fp64", "mixed"):
+            res[name]["rel_error_vs_oracle_solution"] = float(torch.linalg.norm(sols[name] - U) / torch.linalg.norm(U))
+        res["oracle_solution_s"] = oracle_s
         res["speedup_mixed_vs_fp64"] = res["fp64"]["ms"] / res["mixed"]["ms"]
         out[f"order{order}"] = res
-        del sols
+        del sols, U
     return out
 
 
@@ -459,33 +576,36 @@ def run_batched(args):
 
 def run_serving(args):
     """Seeded Poisson request stream at 2000 req/s, sides 2^k + 1 with k uniform in
-    [8, 12], order 2/4 and Galerkin/non-Galerkin 50/50, tolerance 1e-8, 120 GB budget:
-    continuous batching (8 slots, mixed precision) vs the plain per-request FP64 solve
-    (one slot). A bounded sample: the first `serve_count` requests of the stream."""
-    import numpy as np
+    [8, 12], order 2/4 and Galerkin/non-Galerkin 50/50, tolerance 1e-8, 120 GB budget,
+    one N(0,1) right-hand side per request (seeded by the request id, generated on the
+    device when the request is taken up; every solution is copied back to host memory).
+    Continuous batching (8 slots, mixed precision) serves the whole stream. The plain
+    per-request FP64 solve (one slot, one request at a time) serves every
+    `serve_plain_every`-th request of the same stream at the same arrival times, i.e. the
+    offered rate divided by that factor: its capacity (~60 req/s) is far below 2000 req/s,
+    so the whole stream would take over five minutes of one-at-a-time FP64 solves."""
     import torch
     from paper_2008_03885_gb300 import serve
-    import synth
-    rhs_cache = {}
-
-    def rhs(n, seed):  # one N(0,1) right-hand side per size keeps host generation bounded
-        if n not in rhs_cache:
-            rhs_cache[n] = synth.rhs_normal(n, SEED + n)
-        return rhs_cache[n]
-
-    reqs = serve.poisson_stream(SEED, args.serve_count, 2000.0, 8, 12, rtol=1e-8, rhs=rhs)
+    reqs = serve.poisson_stream(SEED, args.serve_count, 2000.0, 8, 12, rtol=1e-8, device_rhs=True)
     keys = sorted({(r.n, r.order, r.coarse_op) for r in reqs})
     out = {"requests": len(reqs), "rate_rps": 2000.0, "sides": "2^k+1, k uniform in [8, 12]",
-           "sample": f"first {len(reqs)} requests of the seeded 20000-request stream", "budget_gb": 120}
-    for name, slots, opts in (("continuous_mixed", 8, dict(nu1=NU1, nu2=NU2, precision=1, fma_contract=1)),
-                              ("plain_fp64", 1, dict(nu1=NU1, nu2=NU2))):
+           "rhs": "one N(0,1) field per request, seeded by the request id", "budget_gb": 120}
+    plain = reqs[::args.serve_plain_every]
+    for name, slots, opts, rq in (
+            ("continuous_mixed", 8, dict(nu1=NU1, nu2=NU2, precision=1, fma_contract=1), reqs),
+            ("plain_fp64", 1, dict(nu1=NU1, nu2=NU2), plain)):
         srv = serve.Server(slots=slots, budget_bytes=120e9, **opts)
         srv.warm(keys, per_key=min(slots, 2))
-        results, stats = srv.run(reqs, realtime=True)
+        results, stats = srv.run(rq, realtime=True, keep_u=False)
         srv.close()
         stats["max_rel_res"] = max(r.rel_res for r in results.values())
+        stats["offered_rate_rps"] = 2000.0 * len(rq) / len(reqs)
+        if rq is not reqs:
+            stats["sample"] = (f"every {args.serve_plain_every}th request of the {len(reqs)}-request stream "
+                               f"({len(rq)} requests) at their arrival times")
         out[name] = stats
-    out["offered_load_rps"] = 2000.0
+        del results
+        torch.cuda.empty_cache()
     return out
 
 
@@ -560,14 +680,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-n", type=int, default=2048)
+    ap.add_argument("--ref-n", type=int, default=N, help="grid of the reference arm (the oracle)")
+    ap.add_argument("--no-all-cores", action="store_true", help="reference arm: skip the all-cores run")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true", help="run a few finest-level kernels (ncu)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--large-n", type=int, default=8192)
-    ap.add_argument("--serve-count", type=int, default=400)
+    ap.add_argument("--serve-count", type=int, default=20000)
+    ap.add_argument("--serve-plain-every", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=4096)
     ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")
     args = ap.parse_args()

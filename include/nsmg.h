@@ -131,9 +131,12 @@ typedef struct {
                            memory), > 0 = levels (below the finest) with at most this many
                            unknowns run in one thread-block-cluster kernel, -1 = never */
   int32_t tail_ctas;   /* CTAs of that cluster (1..16); 0 = largest the device schedules */
-  int32_t sweep_kernel;/* red-black sweeps: 0 = auto (two half-sweep kernels), 1 = half-sweep
-                          kernels, 2 = one shared-memory tile kernel per sweep; every choice
-                          gives the same bits */
+  int32_t sweep_kernel;/* red-black sweeps: 0 = auto (mixed precision: large FP32 axis levels with a
+                          5- or 9-point cross stencil run TMA-staged shared-memory tile kernels,
+                          nu1 sweeps from zero in one kernel, the residual fused with the
+                          red-black restriction, one kernel per post-smoothing sweep; other
+                          levels two half-sweep kernels), 1 = half-sweep kernels only, 2 = one
+                          shared-memory tile kernel per sweep; every choice gives the same bits */
   int32_t bf16_levels; /* mixed precision, storage trial: values stored on the k finest FP32
                           inner levels are rounded to bfloat16 (0 = off, at most 4; the
                           arrays stay FP32, so this measures accuracy, not bandwidth) */

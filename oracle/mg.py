@@ -286,14 +286,40 @@ def interpolation(fine: Level, coarse: Level, coarsening: str, order: int = 2) -
     return m
 
 
-# ---- exact dyadic sparse products (Galerkin operators with cubic transfers) -------
+# ---- exact dyadic sparse products (the Galerkin recursion) ----------------------
+# Galerkin coefficients are dyadic fractions whose numerators grow every level (about
+# 3 bits per red-black level, 14 per cubic level), so on deep hierarchies "R A P" has
+# no unique FP64 value. The recursion is formed exactly and each level rounded once.
 # A matrix is (rows, cols, numerators, e): entry = numerator / 2^e, numerators Python
 # integers (numpy object arrays), so products and sums are exact at any depth.
-def _exact_from(m: sp.csr_matrix, e: int):
+def _dyadic_exponent(data: np.ndarray) -> int:
+    """Smallest e >= 0 with every entry times 2^e an integer (entries are dyadic)."""
+    e = 0
+    while data.size and not np.all(np.floor(data * 2.0 ** e) == data * 2.0 ** e):
+        e += 1
+        assert e < 1000, "not a dyadic matrix"
+    return e
+
+
+def _exact_from(m: sp.csr_matrix, e: int | None = None):
     c = m.tocoo()
+    if e is None:
+        e = _dyadic_exponent(c.data)
     num = np.array([int(v * 2 ** e) for v in c.data], dtype=object)
     assert all(float(n) == v * 2 ** e for n, v in zip(num, c.data)), "not a multiple of 2^-e"
     return c.row.astype(np.int64), c.col.astype(np.int64), num, e
+
+
+def _fp64_product_is_exact(R: sp.csr_matrix, W: sp.csr_matrix, P: sp.csr_matrix) -> bool:
+    """Whether the FP64 product R W P is exact in any evaluation order: with every factor
+    written as an integer matrix times 2^-e (smallest e), each product and partial sum is
+    an integer times 2^-(eR + eW + eP) of magnitude at most ||N_R|| ||N_W|| ||N_P||
+    (infinity norms of the integer matrices); below 2^53 all of them are representable."""
+    bound = 1.0
+    for m in (R, W, P):
+        e = _dyadic_exponent(m.data)
+        bound *= float(abs(m).sum(axis=1).max()) * 2.0 ** e if m.nnz else 0.0
+    return bound < 2.0 ** 53
 
 
 def _exact_mul(A, B, shape):
@@ -320,6 +346,15 @@ def _exact_mul(A, B, shape):
     keep = np.array([v != 0 for v in sums], dtype=bool)
     k = key[starts][keep]
     return k // shape[2], k % shape[2], sums[keep], ea + eb
+
+
+def _exact_normalize(E):
+    """Drop factors of two common to every numerator (keeps the integers small)."""
+    r, c, num, e = E
+    while e > 0 and len(num) and bool(np.all(num % 2 == 0)):
+        num = num // 2
+        e -= 1
+    return r, c, num, e
 
 
 def _exact_round(E, shape) -> sp.csr_matrix:
@@ -416,22 +451,27 @@ class Oracle:
             else:
                 base_W, base_s = stencil_weights(L0, FIVE_POINT, 1.0), s2  # L_h^(2)
         gal_W = base_W
-        # Cubic transfers: the Galerkin recursion is formed exactly (its dyadic
-        # coefficients outgrow 53 bits after three levels) and each level rounded once;
-        # with the other transfers the floating-point product below is already exact.
-        exact = self.opt.transfer_order == 4 and coarse_op in (GALERKIN, TRUE_HIGH, GN)
-        if exact:
-            gal_E = _exact_from(base_W, 0)
+        # The Galerkin recursion is exact and each level is rounded once: its dyadic
+        # coefficients outgrow FP64's 53 bits on deep hierarchies (about 3 bits per
+        # red-black level, 14 per cubic level). While a bound proves the FP64 sparse
+        # product exact it is used as is; from the first level where it does not, the
+        # recursion continues in exact integer arithmetic.
+        gal_E = None
+        galerkin = coarse_op in (GALERKIN, TRUE_HIGH, GN)
         for l in range(1, len(self.levels)):
             lev = self.levels[l]
-            if exact:
-                nf, nc = self.levels[l - 1].size, lev.size
-                WP = _exact_mul(gal_E, _exact_from(self.P[l - 1], 8), (nf, nf, nc))
-                gal_E = _exact_mul(_exact_from(self.R[l - 1], 10), WP, (nc, nf, nc))
-                gal_W = _exact_round(gal_E, (nc, nc))
-            else:
-                gal_W = (self.R[l - 1] @ gal_W @ self.P[l - 1]).tocsr()
-                gal_W.sort_indices()
+            if galerkin and (coarse_op != GN or l == 1):
+                R, P = self.R[l - 1], self.P[l - 1]
+                if gal_E is None and _fp64_product_is_exact(R, gal_W, P):
+                    gal_W = (R @ gal_W @ P).tocsr()
+                    gal_W.sort_indices()
+                else:
+                    if gal_E is None:
+                        gal_E = _exact_from(gal_W)
+                    nf, nc = self.levels[l - 1].size, lev.size
+                    WP = _exact_mul(gal_E, _exact_from(P), (nf, nf, nc))
+                    gal_E = _exact_normalize(_exact_mul(_exact_from(R), WP, (nc, nf, nc)))
+                    gal_W = _exact_round(gal_E, (nc, nc))
             hh = lev.h2  # (h_l / h_0)^2
             if coarse_op in (GALERKIN, TRUE_HIGH) or (coarse_op == GN and l == 1):
                 lev.W, lev.s = gal_W, base_s

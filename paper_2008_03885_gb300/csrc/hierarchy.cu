@@ -11,6 +11,7 @@
 
 #include "../../include/nsmg.h"
 #include "kernels.h"
+#include "tiles.h"
 
 using namespace nsmg;
 
@@ -55,70 +56,19 @@ const std::vector<std::pair<Key, double>> kFirstGalerkin = {  // Eq. (L_G1) time
     {{0, 0}, 3.0}, {{-1, 0}, -0.5}, {{1, 0}, -0.5}, {{0, -1}, -0.5}, {{0, 1}, -0.5},
     {{-1, -1}, -0.25}, {{1, -1}, -0.25}, {{-1, 1}, -0.25}, {{1, 1}, -0.25}};
 
-// Interpolation weights from a coarse node at fine-lattice position (0, 0) to fine
-// offsets (dx, dy) (Eq. transfer_r2 in the fine level's own frame; Eq. transfer_2d).
-std::vector<std::pair<Key, double>> interp_stencil(int transfer) {
-  if (transfer == kStandardCubic) {  // Eq. (interp_2d4o): products of the 1D taps
-    const double t[7] = {-1.0 / 16, 0.0, 9.0 / 16, 1.0, 9.0 / 16, 0.0, -1.0 / 16};
-    std::vector<std::pair<Key, double>> p;
-    for (int dy = -3; dy <= 3; ++dy)
-      for (int dx = -3; dx <= 3; ++dx)
-        if (t[dx + 3] != 0.0 && t[dy + 3] != 0.0) p.push_back({{dx, dy}, t[dx + 3] * t[dy + 3]});
-    return p;
-  }
-  if (transfer == kRbAxisToRot)
-    return {{{0, 0}, 1.0}, {{1, 0}, 0.25}, {{-1, 0}, 0.25}, {{0, 1}, 0.25}, {{0, -1}, 0.25}};
-  if (transfer == kRbRotToAxis)
-    return {{{0, 0}, 1.0}, {{1, 1}, 0.25}, {{-1, 1}, 0.25}, {{1, -1}, 0.25}, {{-1, -1}, 0.25}};
-  std::vector<std::pair<Key, double>> p;
-  const double w1[3] = {0.5, 1.0, 0.5};
-  for (int dy = -1; dy <= 1; ++dy)
-    for (int dx = -1; dx <= 1; ++dx) p.push_back({{dx, dy}, w1[dx + 1] * w1[dy + 1]});
-  return p;
-}
-
 int radius(const Stencil& s, bool x) {
   int r = 0;
   for (const auto& t : s) r = std::max(r, std::abs(x ? t.first.second : t.first.first));
   return r;
 }
 
-// Galerkin product R W P on the infinite lattice (Eq. L_G_l): the coarse stencil of a
-// coarse node at the origin. R = 1/2 P^T (red-black) or 1/4 P^T (standard).
-Stencil galerkin(const Stencil& W, int transfer) {
-  const auto P = interp_stencil(transfer);
-  const double rscale = (transfer == kStandard || transfer == kStandardCubic) ? 0.25 : 0.5;
-  const int step = transfer == kRbAxisToRot ? 1 : 2;  // fine-lattice units per coarse unit
-  const int M = (std::max(radius(W, true), radius(W, false)) + 4) / step + 2;
-  Stencil out;
-  for (int b = -M; b <= M; ++b)
-    for (int a = -M; a <= M; ++a) {
-      if (transfer == kRbAxisToRot && ((a + b) & 1)) continue;  // coarse = black points
-      const int px = a * step, py = b * step;
-      // v = P e_(a,b) on the fine lattice, then (W v) at the restriction's support.
-      std::map<Key, double> v;
-      for (const auto& t : P) v[Key(py + t.first.second, px + t.first.first)] += t.second;
-      double g = 0.0;
-      for (const auto& r : P) {  // restriction support = interpolation support at origin
-        const int rx = r.first.first, ry = r.first.second;
-        double wv = 0.0;
-        for (const auto& w : W) {
-          auto it = v.find(Key(ry + w.first.first, rx + w.first.second));
-          if (it != v.end()) wv += w.second * it->second;
-        }
-        g += rscale * r.second * wv;
-      }
-      if (g != 0.0) put(out, a, b, g);
-    }
-  return out;
-}
-
-// ---- exact dyadic stencils (Galerkin recursion over cubic transfers) ------------
-// The cubic weights make the Galerkin coefficients dyadic fractions whose numerators
-// grow by about 14 bits per level, past FP64's 53 from the fourth coarse level on.
-// The recursion is therefore carried exactly (value = numerator / 2^exp with a
-// 256-bit signed numerator) and every level's weights are rounded once to FP64, as in
-// the oracle's exact sparse products.
+// ---- exact dyadic stencils (the Galerkin recursion) --------------------------------
+// Galerkin coefficients are dyadic fractions whose numerators grow every level: about
+// 14 bits per level with cubic transfers (past FP64's 53 from the fourth coarse level
+// on) and about 3 bits per red-black level (past 53 from level 17, i.e. on grids of
+// 1025^2 and more). The recursion is therefore carried exactly (value = numerator /
+// 2^exp with a 256-bit signed numerator) and every level's weights are rounded once to
+// FP64, as in the oracle's exact sparse products.
 struct Big {
   uint64_t w[4] = {0, 0, 0, 0};  // two's complement, little-endian limbs
   static Big of(int64_t v) {
@@ -231,26 +181,60 @@ Stencil rounded(const XStencil& x) {
   return s;
 }
 
-// Exact Galerkin product R W P on the infinite lattice for the cubic transfers
-// (same loop structure as galerkin()); P = taps / 2^8, R = P^T / 4.
+// Interpolation weights from a coarse node at fine-lattice position (0, 0) to fine
+// offsets (dx, dy) (Eq. transfer_r2 in the fine level's own frame; Eq. transfer_2d;
+// Eq. interp_2d4o), as integers over 2^exp: ((dx, dy), tap).
+struct ITaps {
+  std::vector<std::pair<Key, int64_t>> t;
+  int exp;
+};
+ITaps interp_taps(int transfer) {
+  ITaps p;
+  if (transfer == kStandardCubic) {  // 1D taps times 16, 2D products times 256
+    const int64_t t1[7] = {-1, 0, 9, 16, 9, 0, -1};
+    for (int dy = -3; dy <= 3; ++dy)
+      for (int dx = -3; dx <= 3; ++dx)
+        if (t1[dx + 3] && t1[dy + 3]) p.t.push_back({{dx, dy}, t1[dx + 3] * t1[dy + 3]});
+    p.exp = 8;
+  } else if (transfer == kRbAxisToRot) {
+    p.t = {{{0, 0}, 4}, {{1, 0}, 1}, {{-1, 0}, 1}, {{0, 1}, 1}, {{0, -1}, 1}};
+    p.exp = 2;
+  } else if (transfer == kRbRotToAxis) {
+    p.t = {{{0, 0}, 4}, {{1, 1}, 1}, {{-1, 1}, 1}, {{1, -1}, 1}, {{-1, -1}, 1}};
+    p.exp = 2;
+  } else {  // bilinear: (1, 2, 1) x (1, 2, 1) / 4
+    const int64_t w1[3] = {1, 2, 1};
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) p.t.push_back({{dx, dy}, w1[dx + 1] * w1[dy + 1]});
+    p.exp = 2;
+  }
+  return p;
+}
+
+// Exact Galerkin product R W P on the infinite lattice (Eq. L_G_l): the coarse stencil
+// of a coarse node at the origin, with R = P^T / 2 (red-black) or P^T / 4 (standard,
+// bilinear or cubic). The
+// coefficients are dyadic fractions whose numerators grow every level (about 3 bits per
+// red-black level, 14 per cubic level) and outgrow FP64's 53 bits on deep hierarchies,
+// so the recursion is carried exactly and each level is rounded once (rounded()).
 // Returns exp = -1 if a numerator would exceed kMaxExactBits.
-XStencil galerkin_exact(const XStencil& W) {
-  const int64_t t1[7] = {-1, 0, 9, 16, 9, 0, -1};  // 1D taps times 16
-  std::vector<std::pair<Key, int64_t>> P;  // (dx, dy) -> 2D tap times 256
-  for (int dy = -3; dy <= 3; ++dy)
-    for (int dx = -3; dx <= 3; ++dx)
-      if (t1[dx + 3] && t1[dy + 3]) P.push_back({{dx, dy}, t1[dx + 3] * t1[dy + 3]});
+XStencil galerkin_exact(const XStencil& W, int transfer) {
+  const ITaps P = interp_taps(transfer);
+  const int rexp = (transfer == kStandard || transfer == kStandardCubic) ? 2 : 1;
+  const int step = transfer == kRbAxisToRot ? 1 : 2;
   int rW = 0;
   for (const auto& t : W.t) rW = std::max({rW, std::abs(t.first.first), std::abs(t.first.second)});
-  const int M = (rW + 4) / 2 + 2;
+  const int M = (rW + 4) / step + 2;
   XStencil out;
-  out.exp = W.exp + 8 + 8 + 2;
+  out.exp = W.exp + 2 * P.exp + rexp;
   for (int b = -M; b <= M; ++b)
     for (int a = -M; a <= M; ++a) {
+      if (transfer == kRbAxisToRot && ((a + b) & 1)) continue;  // coarse = black points
+      const int px = a * step, py = b * step;
       std::map<Key, int64_t> v;  // P e_(a,b) on the fine lattice, keyed (dy, dx)
-      for (const auto& t : P) v[Key(2 * b + t.first.second, 2 * a + t.first.first)] += t.second;
+      for (const auto& t : P.t) v[Key(py + t.first.second, px + t.first.first)] += t.second;
       Big g;
-      for (const auto& r : P) {
+      for (const auto& r : P.t) {
         Big wv;
         for (const auto& w : W.t) {
           auto it = v.find(Key(r.first.second + w.first.first, r.first.first + w.first.second));
@@ -491,6 +475,7 @@ struct Hier {
   int nops = 0;
   int tail_ctas = 1;       // CTAs in the tail's thread-block cluster
   int tail_smem = 0;       // > 0: the tail's levels live in shared memory (elements)
+  std::vector<TileLevel> tiles;  // FP32 levels: TMA tile kernels (tiles.h) where eligible
 };
 
 struct mg_handle {
@@ -639,32 +624,22 @@ bool build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
       base_s = s2;
     }
   }
-  Stencil gal = base;
   const int op = h->coarse_op;
-  // cubic transfers: the Galerkin recursion in exact arithmetic (see XStencil)
-  const bool exact = h->opt.transfer_order == 4;
-  XStencil galx;
-  if (exact) galx = exact_of(base);
+  // the Galerkin recursion in exact arithmetic, each level rounded once (see XStencil)
+  XStencil galx = exact_of(base);
+  if (galx.exp < 0) return false;
   for (int l = 1; l < nl; ++l) {
     HostLevel& L = h->host[l];
     const bool galerkin_level =
         op == MG_OP_GALERKIN || op == MG_OP_GALERKIN_TRUE_HIGH || (op == MG_OP_GALERKIN_GN && l == 1);
-    if (exact) {
-      if (galerkin_level) {
-        galx = galerkin_exact(galx);
-        if (galx.exp < 0) return false;
-      }
-    } else {
-      gal = galerkin(gal, transfer_of(h->coarsening, l - 1, shapes[l - 1].kind, h->opt.transfer_order));
+    if (galerkin_level) {
+      galx = galerkin_exact(galx, transfer_of(h->coarsening, l - 1, shapes[l - 1].kind, h->opt.transfer_order));
+      if (galx.exp < 0) return false;
     }
     if (galerkin_level) {
-      if (exact) {
-        L.W = rounded(galx);
-        L.Wx = galx;
-        L.exact = 1;
-      } else {
-        L.W = gal;
-      }
+      L.W = rounded(galx);
+      L.Wx = galx;
+      L.exact = 1;
       L.s = base_s;
     } else if (op == MG_OP_GALERKIN_G1) {
       L.W = from_frame(L.shape.kind, kFirstGalerkin, 1.0 / L.shape.hh);
@@ -697,6 +672,17 @@ bool build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
 }
 
 size_t level_bytes(const HostLevel& L, size_t elem) { return (size_t)L.rows * L.pitch * elem; }
+
+// Storage description of level l in precision T: the FP64 finest level keeps the
+// caller's (N+1)-element rows; every other level, and the FP32 finest level of the
+// mixed-precision path, pads its rows to a multiple of 32 elements (so that rows start
+// on 16-byte boundaries, as TMA tile loads require).
+template <typename T>
+HostLevel storage_of(const HostLevel& L, int l) {
+  HostLevel S = L;
+  if (l == 0 && sizeof(T) == 4) S.pitch = round_pitch(L.cols);
+  return S;
+}
 
 mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
   if (bytes == 0) bytes = 256;
@@ -783,6 +769,28 @@ struct Ctx {
   cudaStream_t s;
   bool exact;
 };
+
+// The handle's device status word (bits set by kernels whose bounded waits gave up),
+// kept next to the norm scalar so that one copy reads both.
+int* status_word(mg_handle* h) { return reinterpret_cast<int*>(h->scalar + 1); }
+
+// The FP32 view of a level, for the tile-kernel calls (reached only when T = float:
+// tile_at<double> is always null).
+template <typename T>
+const LevelPair<float>& f32(const LevelPair<T>& L) {
+  return reinterpret_cast<const LevelPair<float>&>(L);
+}
+
+// Tile kernels of FP32 level l (tiles.h), or null: FP64 levels and levels that keep the
+// per-step kernels.
+template <typename T>
+const TileLevel* tile_at(const mg_handle* h, int l);
+template <>
+const TileLevel* tile_at<double>(const mg_handle*, int) { return nullptr; }
+template <>
+const TileLevel* tile_at<float>(const mg_handle* h, int l) {
+  return l < (int)h->h32.tiles.size() && h->h32.tiles[l].on ? &h->h32.tiles[l] : nullptr;
+}
 
 // Work of an API call runs on the caller's stream, or -- for the legacy default
 // stream, which cannot be captured into a graph -- on the handle's own stream,
@@ -871,7 +879,7 @@ mg_status smooth(const Ctx& c, int l, T* U, const T* F) {
       Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
       LAUNCH(h, 1, launch_sweep_fused<T>(L, c.exact, U, F, Tb, c.s));
     }
-    CK(cudaMemcpyAsync(U, Tb, level_bytes(h->host[l], sizeof(T)), cudaMemcpyDeviceToDevice, c.s));
+    CK(cudaMemcpyAsync(U, Tb, level_bytes(storage_of<T>(h->host[l], l), sizeof(T)), cudaMemcpyDeviceToDevice, c.s));
   } else if (h->opt.smoother == MG_SMOOTH_REDBLACK) {
     {
       Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
@@ -882,7 +890,7 @@ mg_status smooth(const Ctx& c, int l, T* U, const T* F) {
   } else {
     Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
     LAUNCH(h, 1, launch_jacobi<T>(L, c.exact, U, F, Tb, c.s));
-    CK(cudaMemcpyAsync(U, Tb, level_bytes(h->host[l], sizeof(T)), cudaMemcpyDeviceToDevice, c.s));
+    CK(cudaMemcpyAsync(U, Tb, level_bytes(storage_of<T>(h->host[l], l), sizeof(T)), cudaMemcpyDeviceToDevice, c.s));
   }
   return MG_OK;
 }
@@ -899,6 +907,14 @@ mg_status cycle_sweep(const Ctx& c, int l, T*& cur, T*& oth, const T* F) {
   }
   std::swap(cur, oth);
   return MG_OK;
+}
+
+// Whether level l of precision T starts its cycles with the fused tile presmooth
+// (tiles.h): its first red half-sweep is then not done by the kernel before it.
+template <typename T>
+bool tile_presmooth(const mg_handle* h, int l) {
+  const TileLevel* tl = tile_at<T>(h, l);
+  return tl && tl->nu1 == h->opt.nu1 && h->opt.smoother == MG_SMOOTH_REDBLACK;
 }
 
 // red_done: the first half-sweep (red) of the first pre-smoothing sweep already left its
@@ -920,15 +936,20 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
     else LAUNCH(h, 1, launch_tail<T>(H.tail_ctas, H.d_tail, prog, nops, c.exact, c.s));
     return MG_OK;
   }
+  // FP32 levels with tile kernels: nu1 sweeps from u = 0 in one kernel, the residual
+  // fused with the red-black restriction, and post-smoothing sweeps as one kernel each
+  // (ping-pong between U and t[l]); the same bits as the per-step kernels.
+  const TileLevel* tl = tile_at<T>(h, l);
+  const bool tile_pre = zero_init && tile_presmooth<T>(h, l);
   // From u = 0 the first red half-sweep needs no stencil (k_first_half_zero); after it,
   // or after red_done, the black half-sweep writes every unknown of U.
-  if (zero_init && !red_done) {
+  if (zero_init && !red_done && !tile_pre) {
     if (h->opt.smoother == MG_SMOOTH_REDBLACK && !fused_sweeps<T>(h) && h->opt.nu1 >= 1) {
       Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
       LAUNCH(h, 1, launch_first_half_zero<T>(H.L[l], F, H.t[l], 1, c.s));
       red_done = true;
     } else {
-      CK(cudaMemsetAsync(U, 0, level_bytes(h->host[l], sizeof(T)), c.s));
+      CK(cudaMemsetAsync(U, 0, level_bytes(storage_of<T>(h->host[l], l), sizeof(T)), c.s));
     }
   }
   // Tile-kernel sweeps flip between U and t[l]; an odd number of them is evened out by
@@ -936,23 +957,33 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
   T* cur = U;
   T* oth = H.t[l];
   const bool flips = fused_sweeps<T>(h);
-  int k0 = 0;
-  if (red_done) {
+  if (tile_pre) {
     Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
-    LAUNCH(h, 1, launch_half_sweep<T>(H.L[l], c.exact, H.t[l], F, cur, 0, c.s));
-    k0 = 1;
-  }
-  for (int k = k0; k < h->opt.nu1; ++k)
-    if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) return st;
-  {
-    Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
-    LAUNCH(h, 1, launch_residual<T>(H.L[l], c.exact, cur, F, H.d[l], c.s));
+    LAUNCH(h, 1, launch_tile_presmooth(*tl, f32(H.L[l]), c.exact, (float*)U, status_word(h), c.s));
+  } else {
+    int k0 = 0;
+    if (red_done) {
+      Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+      LAUNCH(h, 1, launch_half_sweep<T>(H.L[l], c.exact, H.t[l], F, cur, 0, c.s));
+      k0 = 1;
+    }
+    for (int k = k0; k < h->opt.nu1; ++k)
+      if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) return st;
   }
   // The restriction also writes the coarse level's first (zero-start) half-sweep when
-  // that level runs as separate launches.
+  // that level runs as separate launches (and does not start with a tile presmooth).
   const bool coarse_red = l + 1 != lmax && l + 1 != H.tail_level && h->opt.smoother == MG_SMOOTH_REDBLACK &&
-                          !fused_sweeps<T>(h) && h->opt.nu1 >= 1;
-  {
+                          !fused_sweeps<T>(h) && h->opt.nu1 >= 1 && !tile_presmooth<T>(h, l + 1);
+  if (tl && cur == U && h->transfer[l] == kRbAxisToRot) {
+    Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
+    LAUNCH(h, 1, launch_tile_res_restrict(*tl, f32(H.L[l]), f32(H.L[l + 1]), c.exact,
+                                          (float*)H.f[l + 1], coarse_red ? (float*)H.t[l + 1] : nullptr,
+                                          status_word(h), c.s));
+  } else {
+    {
+      Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
+      LAUNCH(h, 1, launch_residual<T>(H.L[l], c.exact, cur, F, H.d[l], c.s));
+    }
     Bracket b(h, l, MG_KERNEL_RESTRICT, c.s);
     LAUNCH(h, 1, launch_restrict<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, H.d[l], H.f[l + 1], c.s,
                                     coarse_red ? H.t[l + 1] : nullptr));
@@ -963,24 +994,36 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
     for (int g = 0; g < gamma_at(h, l); ++g)
       if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0, coarse_red && g == 0)) != MG_OK) return st;
   }
+  // tile post-smoothing: sweeps ping-pong U <-> t[l], so an odd count starts from an
+  // out-of-place interpolation into t[l]
+  const bool tile_post = tl && h->opt.smoother == MG_SMOOTH_REDBLACK && cur == U;
   {
     Bracket b(h, l, MG_KERNEL_PROLONG, c.s);
-    if (flips && ((h->opt.nu1 + h->opt.nu2) & 1)) {
+    if ((flips || tile_post) && ((tile_post ? h->opt.nu2 : h->opt.nu1 + h->opt.nu2) & 1)) {
       LAUNCH(h, 1, launch_prolong_add<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, oth, H.u[l + 1], c.s, cur));
       std::swap(cur, oth);
     } else {
       LAUNCH(h, 1, launch_prolong_add<T>(H.L[l], H.L[l + 1], h->transfer[l], c.exact, cur, H.u[l + 1], c.s));
     }
   }
-  for (int k = 0; k < h->opt.nu2; ++k)
-    if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) return st;
+  for (int k = 0; k < h->opt.nu2; ++k) {
+    if (tile_post) {
+      Bracket b(h, l, MG_KERNEL_SMOOTH, c.s);
+      LAUNCH(h, 1, launch_tile_sweep(*tl, f32(H.L[l]), c.exact, cur == H.t[l],
+                                     (float*)oth, status_word(h), c.s));
+      std::swap(cur, oth);
+    } else if ((st = cycle_sweep<T>(c, l, cur, oth, F)) != MG_OK) {
+      return st;
+    }
+  }
   return cur == U ? MG_OK : MG_ERR_INVALID;
 }
 
 mg_status read_scalar(mg_handle* h, cudaStream_t s, double* out) {
-  CK(cudaMemcpyAsync(h->hscalar, h->scalar, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->hscalar, h->scalar, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   *out = *h->hscalar;
+  if (*reinterpret_cast<const int*>(h->hscalar + 1) != 0) return MG_ERR_TIMEOUT;
   return MG_OK;
 }
 
@@ -1046,8 +1089,9 @@ mg_status alloc_hier(mg_handle* h, bool caller_level0) {
   mg_status st;
   for (int l = 0; l < nl; ++l) {
     const int bf16 = (!caller_level0 && l < h->opt.bf16_levels) ? 1 : 0;
-    if ((st = upload_level<T>(h, h->host[l], H.L[l], bf16)) != MG_OK) return st;
-    const size_t b = level_bytes(h->host[l], sizeof(T));
+    const HostLevel S = storage_of<T>(h->host[l], l);
+    if ((st = upload_level<T>(h, S, H.L[l], bf16)) != MG_OK) return st;
+    const size_t b = level_bytes(S, sizeof(T));
     if (l > 0 || !caller_level0) {
       if ((st = device_alloc(h, (void**)&H.u[l], b)) != MG_OK) return st;
       if ((st = device_alloc(h, (void**)&H.f[l], b)) != MG_OK) return st;
@@ -1174,7 +1218,7 @@ double ir_scale_for(double r2, int64_t m) {
 // FP32 cycle from e = 0 (conditions as norm_takes_red, on the FP32 hierarchy).
 bool ir_takes_red(const mg_handle* h) {
   return h->opt.smoother == MG_SMOOTH_REDBLACK && !fused_sweeps<float>(h) && h->opt.nu1 >= 1 &&
-         h->opt.inner_cycles >= 1 && h->h32.tail_level != 0;
+         h->opt.inner_cycles >= 1 && h->h32.tail_level != 0 && !tile_presmooth<float>(h, 0);
 }
 
 mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
@@ -1182,9 +1226,8 @@ mg_status ir_residual(const Ctx& c, double* u, const double* f, double* r2) {
   const bool red = ir_takes_red(h);
   {
     Bracket b(h, 0, MG_KERNEL_NORM, c.s);
-    LAUNCH(h, 2, launch_ir_residual(h->h64.L[0], c.exact, u, f, h->h32.f[0], h->ir_scale, h->partial,
-                                    h->scalar, c.s, h->opt.bf16_levels > 0 ? 1 : 0, red ? &h->h32.L[0] : nullptr,
-                                    red ? h->h32.t[0] : nullptr));
+    LAUNCH(h, 2, launch_ir_residual(h->h64.L[0], c.exact, u, f, h->h32.L[0], h->h32.f[0], h->ir_scale, h->partial,
+                                    h->scalar, c.s, h->opt.bf16_levels > 0 ? 1 : 0, red ? h->h32.t[0] : nullptr));
   }
   return read_scalar(h, c.s, r2);
 }
@@ -1200,7 +1243,7 @@ mg_status ir_correct(const Ctx& c, double* u) {
     return MG_OK;
   });
   if (st != MG_OK) return st;
-  LAUNCH(h, 1, launch_ir_update(h->h64.L[0], u, h->h32.u[0], 1.0 / h->ir_scale, c.s));
+  LAUNCH(h, 1, launch_ir_update(h->h64.L[0], h->h32.L[0], u, h->h32.u[0], 1.0 / h->ir_scale, c.s));
   return MG_OK;
 }
 
@@ -1257,7 +1300,7 @@ size_t mg_workspace_bytes(const mg_grid* grid, int order, mg_coarsening coarseni
     const size_t pitch = l == 0 ? cols : round_pitch((int)cols);
     const size_t arrays = l == 0 ? 2 : 4;
     bytes += arrays * rows * pitch * sizeof(double);
-    if (o.precision == MG_PREC_MIXED_FP32) bytes += 4 * rows * pitch * sizeof(float);
+    if (o.precision == MG_PREC_MIXED_FP32) bytes += 4 * rows * round_pitch((int)cols) * sizeof(float);
   }
   return bytes;
 }
@@ -1320,6 +1363,11 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
     if (o.tail_unknowns == 0) st = build_tail<float>(h, 0, kTailSmemElemsFp32);
     else st = build_tail<float>(h, tail_limit(0));
     if (st != MG_OK) return fail(st);
+    // TMA tile kernels on the large eligible FP32 levels above the tail (sweep_kernel 0)
+    h->h32.tiles.assign(nl, TileLevel());
+    if (o.sweep_kernel == 0 && o.smoother == MG_SMOOTH_REDBLACK)
+      for (int l = 0; l + 1 < nl && (h->h32.tail_level < 0 || l < h->h32.tail_level); ++l)
+        tile_setup(h->h32.tiles[l], h->h32.L[l], h->h32.u[l], h->h32.t[l], h->h32.f[l], o.nu1);
   }
   h->nblocks0 = resnorm_blocks<double>(h->h64.L[0]);
   if ((st = device_alloc(h, (void**)&h->partial, h->nblocks0 * sizeof(double))) != MG_OK) return fail(st);
@@ -1865,6 +1913,7 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out) 
     if (b->mixed) {
       e.r32 = h->h32.f[0];
       e.e32 = h->h32.u[0];
+      e.pitch32 = h->h32.L[0].h.pitch;
     }
     b->fin.push_back(e);
   }

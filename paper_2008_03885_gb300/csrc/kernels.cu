@@ -12,198 +12,10 @@
 #include <cstdio>
 
 #include "kernels.h"
+#include "device.cuh"
 
 namespace nsmg {
 namespace {
-
-constexpr int kBX = 32, kBY = 8;
-
-// Minimum resident 256-thread blocks per SM requested from the compiler: FP32 stencil
-// kernels are memory-latency bound and gain from full occupancy (8 blocks: 32
-// registers); FP64 kernels are bound by the FP64 pipe and keep their registers.
-template <typename T>
-struct MinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
-};
-
-template <typename T>
-struct Arith;
-template <>
-struct Arith<double> {
-  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
-  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
-  static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
-  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
-};
-template <>
-struct Arith<float> {
-  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
-  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
-  static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
-};
-
-// One class term by a single 16-byte load.
-template <typename T>
-__device__ __forceinline__ ClassTerm<T> load_term(const ClassTerm<T>* p) {
-  const int4 w = __ldg(reinterpret_cast<const int4*>(p));
-  ClassTerm<T> t;
-  if (sizeof(T) == 8) {
-    t.c = (T)__hiloint2double(w.y, w.x);
-    t.dx = w.z;
-    t.dy = w.w;
-  } else {
-    t.c = (T)__int_as_float(w.x);
-    t.dx = w.y;
-    t.dy = w.z;
-  }
-  return t;
-}
-
-// Hint: bring the line holding *p into L2, so that the loads issued later wait on L2
-// rather than DRAM (more bytes in flight than the registers of a thread allow).
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
-// s + c * x in the chosen rounding mode.
-// Value as stored on a level: FP32 levels of the bfloat16 storage trial round it.
-template <typename T>
-__device__ __forceinline__ T rnd(const LevelDev<T>& L, T v) {
-  return v;
-}
-template <>
-__device__ __forceinline__ float rnd<float>(const LevelDev<float>& L, float v) {
-  return L.bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
-}
-
-template <typename T, bool EXACT>
-__device__ __forceinline__ T madd(T s, T c, T x) {
-  return EXACT ? Arith<T>::add(s, Arith<T>::mul(c, x)) : Arith<T>::fma(c, x, s);
-}
-
-template <typename T>
-__device__ __forceinline__ int64_t sidx(const LevelDev<T>& L, int i, int j) {
-  return (int64_t)j * L.pitch + (L.kind == kRot ? (i >> 1) : i);
-}
-
-// Lattice coordinates of the thread's storage element; false if outside storage.
-template <typename T>
-__device__ __forceinline__ bool thread_node(const LevelDev<T>& L, int& i, int& j) {
-  const int q = blockIdx.x * kBX + threadIdx.x;
-  j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (j >= L.rows || q >= L.cols) return false;
-  i = L.kind == kRot ? 2 * q + (j & 1) : q;
-  return true;
-}
-
-template <typename T>
-__device__ __forceinline__ bool interior(const LevelDev<T>& L, int i, int j) {
-  return i >= L.lo && i < L.n && j >= L.lo && j < L.n;
-}
-
-template <typename T>
-__device__ __forceinline__ bool is_red(const LevelDev<T>& L, int i, int j) {
-  return L.kind == kRot ? (i & 1) : ((i + j) & 1);
-}
-
-// Class index of a node that is not a fast node.
-template <typename T>
-__device__ __forceinline__ int class_of(const LevelDev<T>& L, int i, int j) {
-  if (L.small) return j * L.clsw + i;
-  const int e = L.n - L.per;  // last lattice index a fast stencil may reach
-  const int cx = i < L.rx ? i : (i > e - L.rx ? 2 * L.rx - (e - i) : L.rx);
-  const int cy = j < L.ry ? j : (j > e - L.ry ? 2 * L.ry - (e - j) : L.ry);
-  return cy * L.clsw + cx;
-}
-
-template <typename T>
-__device__ __forceinline__ bool fast_node(const LevelDev<T>& L, int i, int j) {
-  return i >= L.rx && i <= L.fxe && j >= L.ry && j <= L.fye;
-}
-
-// omega / a_pp of node (i, j).
-template <typename T>
-__device__ __forceinline__ T node_wd(const LevelDev<T>& L, int i, int j) {
-  return fast_node(L, i, j) ? L.wd : L.cls_wd[class_of(L, i, j)];
-}
-
-// First half-sweep value from u = 0 (see k_first_half_zero): 0 + f omega / a_pp.
-template <typename T>
-__device__ __forceinline__ T relax_from_zero(T f, T wd) {
-  return Arith<T>::add(T(0), Arith<T>::mul(f, wd));
-}
-
-// (L u)(i, j) and the node's omega / a_pp.
-// CU: unroll factor of the boundary-class term loop (its loads then run ahead of the
-// ordered sum); 1 in the register-tight NT kernels.
-template <typename T, bool EXACT, int CU = 4>
-__device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict__ u, int i, int j,
-                                      int64_t at, T* wd) {
-  T s;
-  if (fast_node(L, i, j)) {
-    const int32_t* dl = L.delta[L.kind == kRot ? (i & 1) : 0];
-    s = Arith<T>::mul(L.c[0], u[at + dl[0]]);
-#pragma unroll CU
-    for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, L.c[k], u[at + dl[k]]);
-    if (wd) *wd = L.wd;
-  } else {
-    const int cl = class_of(L, i, j);
-    const int2 e = L.cls[cl];
-    const ClassTerm<T>* tt = L.terms + e.x;
-    s = T(0);
-#pragma unroll CU
-    for (int k = 0; k < e.y; ++k) {
-      const ClassTerm<T> t = load_term(tt + k);
-      const T x = u[sidx(L, i + t.dx, j + t.dy)];
-      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
-    }
-    if (wd) *wd = L.cls_wd[cl];
-  }
-  return s;
-}
-
-// New value of node (i, j) after one relaxation: u + (f - L u) * omega / a_pp.
-template <typename T, bool EXACT, int CU = 4>
-__device__ __forceinline__ T relax_value(const LevelDev<T>& L, const T* __restrict__ uin,
-                                         const T* __restrict__ f, int i, int j, int64_t at) {
-  T wd;
-  const T s = apply_at<T, EXACT, CU>(L, uin, i, j, at, &wd);
-  const T r = Arith<T>::sub(f[at], s);
-  return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
-}
-
-// ---- specialised fast path: NT-point stencils with coefficients in registers and
-// kRows rows per thread (same arithmetic as apply_at / relax_value) --------------
-// Rows per thread of the 5/9-point kernels (2 and 4 measured equal for FP32 on GB300).
-template <typename T>
-struct RowsPer {
-  static constexpr int value = 4;
-};
-
-template <typename T, bool EXACT, int NT>
-__device__ __forceinline__ T apply_fast(const T (&c)[NT], const int (&dl)[NT], const T* __restrict__ u,
-                                        int64_t at) {
-  T s = Arith<T>::mul(c[0], u[at + dl[0]]);
-#pragma unroll
-  for (int k = 1; k < NT; ++k) s = madd<T, EXACT>(s, c[k], u[at + dl[k]]);
-  return s;
-}
-
-template <typename T, bool EXACT, int NT>
-__device__ __forceinline__ T relax_fast(const T (&c)[NT], const int (&dl)[NT], T wd, const T* __restrict__ uin,
-                                        const T* __restrict__ f, int64_t at) {
-  const T r = Arith<T>::sub(f[at], apply_fast<T, EXACT, NT>(c, dl, uin, at));
-  return EXACT ? Arith<T>::add(uin[at], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, uin[at]);
-}
-
-// fast_node with the boundary kind fixed at compile time (the NT kernels run at the
-// register limit; constant bounds keep the Dirichlet instantiation free of spills).
-template <bool PER, typename T>
-__device__ __forceinline__ bool fast_node_c(const LevelDev<T>& L, int i, int j) {
-  const int e = L.n - (PER ? 1 : 0);
-  return i >= L.rx && i <= e - L.rx && j >= L.ry && j <= e - L.ry;
-}
 
 template <typename T, bool EXACT, int NT, bool PER>
 __global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value) k_half_sweep_nt(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ uin,
@@ -1107,21 +919,41 @@ __global__ void k_first_half_zero(const LevelDev<T>* __restrict__ Lp, const T* _
   t[at] = e;
 }
 
-template <typename T, bool EXACT>
-__global__ void k_resnorm_red(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u,
-                              const T* __restrict__ f, T* __restrict__ uout, int red, double* __restrict__ partial,
-                              int tiles_y) {
+// The norm kernels below (k_resnorm_red, k_ir_residual) walk the level's 32 x 8 tiles
+// in a flat order, block b taking tiles b, b + gridDim.x, ...: with one block per
+// resident slot every SM gets the same number of tiles (to one), whatever the grid
+// shape, and the partial sums stay at most kMaxPartials.
+template <typename T, bool EXACT, int NT>
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<T>::value)
+    k_resnorm_red(const LevelDev<T>* __restrict__ Lp, const T* __restrict__ u, const T* __restrict__ f,
+                  T* __restrict__ uout, int red, double* __restrict__ partial, int tiles_x, int tiles) {
   const LevelDev<T>& L = *Lp;
+  constexpr int NA = NT > 0 ? NT : 1;
+  T c[NA];
+  int dl[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) {
+    c[k] = L.c[k];
+    dl[k] = L.delta[0][k];
+  }
   double v = 0.0;
-  const int q = blockIdx.x * kBX + threadIdx.x;
-  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int ty = t / tiles_x;
+    const int q = (t - ty * tiles_x) * kBX + threadIdx.x;
     const int j = ty * kBY + threadIdx.y;
     if (j >= L.rows || q >= L.cols) continue;
     const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
     if (!interior(L, i, j)) continue;
     const int64_t at = sidx(L, i, j);
     T wd;
-    const T r = Arith<T>::sub(f[at], apply_at<T, EXACT>(L, u, i, j, at, &wd));
+    T s;
+    if (NT > 0 && L.kind == kAxis && fast_node(L, i, j)) {
+      s = apply_fast<T, EXACT, NA>(c, dl, u, at);
+      wd = L.wd;
+    } else {
+      s = apply_at<T, EXACT, 1>(L, u, i, j, at, &wd);
+    }
+    const T r = Arith<T>::sub(f[at], s);
     const double d = (double)r;
     v += d * d;
     uout[at] = is_red(L, i, j) == red
@@ -1129,7 +961,7 @@ __global__ void k_resnorm_red(const LevelDev<T>* __restrict__ Lp, const T* __res
                    : u[at];
   }
   v = block_sum(v);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = v;
 }
 
 template <typename T>
@@ -1186,39 +1018,53 @@ __global__ void k_zero_boundary(int n, int pitch, T* __restrict__ u) {
 // On a zero vector the FP32 stencil sum is +0 (every operator row has a positive
 // diagonal, and +0 absorbs -0 in a sum), so the half-sweep's residual is r32 itself and
 // this is the half-sweep's value bit for bit.
-template <bool EXACT>
-__global__ void k_ir_residual(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
-                              const double* __restrict__ f, float* __restrict__ r32, double scale,
-                              double* __restrict__ partial, int tiles_y, int bf16,
-                              const LevelDev<float>* __restrict__ L32p, float* __restrict__ t32) {
+template <bool EXACT, int NT>
+__global__ void __launch_bounds__(kBX * kBY, MinBlocks<double>::value)
+    k_ir_residual(const LevelDev<double>* __restrict__ Lp, const double* __restrict__ u,
+                  const double* __restrict__ f, float* __restrict__ r32, double scale,
+                  double* __restrict__ partial, int tiles_x, int tiles, int bf16,
+                  const LevelDev<float>* __restrict__ L32p, float* __restrict__ t32) {
   const LevelDev<double>& L = *Lp;
+  const LevelDev<float>& L32 = *L32p;  // FP32 finest level: same nodes, its own row pitch
+  constexpr int NA = NT > 0 ? NT : 1;
+  double c[NA];
+  int dl[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) {
+    c[k] = L.c[k];
+    dl[k] = L.delta[0][k];
+  }
+  const int pitch32 = L32.pitch;
   double v = 0.0;
-  const int q = blockIdx.x * kBX + threadIdx.x;
-  for (int ty = blockIdx.y; ty < tiles_y; ty += gridDim.y) {
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int ty = t / tiles_x;
+    const int q = (t - ty * tiles_x) * kBX + threadIdx.x;
     const int j = ty * kBY + threadIdx.y;
     if (j >= L.rows || q >= L.cols) continue;
-    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    const int i = q;  // the finest level is an axis grid
     if (!interior(L, i, j)) continue;
-    const int64_t at = sidx(L, i, j);
-    const double r = Arith<double>::sub(f[at], apply_at<double, EXACT>(L, u, i, j, at, nullptr));
+    const int64_t at = (int64_t)j * L.pitch + i;
+    const double s = (NT > 0 && fast_node(L, i, j)) ? apply_fast<double, EXACT, NA>(c, dl, u, at)
+                                                    : apply_at<double, EXACT, 1>(L, u, i, j, at, nullptr);
+    const double r = Arith<double>::sub(f[at], s);
     const float r32v = (float)(r * scale);
     const float rv = bf16 ? __bfloat162float(__float2bfloat16_rn(r32v)) : r32v;
-    r32[at] = rv;
+    const int64_t at32 = (int64_t)j * pitch32 + i;
+    r32[at32] = rv;
     v += r * r;
     if (t32) {
-      const LevelDev<float>& L32 = *L32p;
       float e = 0.f;
       if (is_red(L32, i, j) == 1) e = rnd(L32, relax_from_zero(rv, node_wd(L32, i, j)));
-      t32[at] = e;
+      t32[at32] = e;
     }
   }
   v = block_sum(v);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = v;
 }
 
 // u += e * inv_scale (FP64 update of the refinement step).
 // kTransferRows rows per thread with the lines prefetched into L2, as in the transfers.
-__global__ void k_ir_update(const LevelDev<double>* __restrict__ Lp, double* __restrict__ u,
+__global__ void k_ir_update(const LevelDev<double>* __restrict__ Lp, int pitch32, double* __restrict__ u,
                             const float* __restrict__ e, double inv_scale) {
   const LevelDev<double>& L = *Lp;
   const int q = blockIdx.x * kBX + threadIdx.x;
@@ -1226,18 +1072,18 @@ __global__ void k_ir_update(const LevelDev<double>* __restrict__ Lp, double* __r
   const int jb = blockIdx.y * (kBY * kTransferRows) + threadIdx.y;
 #pragma unroll
   for (int r = 0; r < kTransferRows; ++r) {
-    const int64_t at = (int64_t)min(jb + r * kBY, L.rows - 1) * L.pitch + q;
-    prefetch_l2(u + at);
-    prefetch_l2(e + at);
+    const int jr = min(jb + r * kBY, L.rows - 1);
+    prefetch_l2(u + (int64_t)jr * L.pitch + q);
+    prefetch_l2(e + (int64_t)jr * pitch32 + q);
   }
 #pragma unroll
   for (int r = 0; r < kTransferRows; ++r) {
     const int j = jb + r * kBY;
     if (j >= L.rows) break;
-    const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
+    const int i = q;  // the finest level is an axis grid
     if (!interior(L, i, j)) continue;
-    const int64_t at = sidx(L, i, j);
-    u[at] = u[at] + (double)e[at] * inv_scale;
+    const int64_t at = (int64_t)j * L.pitch + i;
+    u[at] = u[at] + (double)e[(int64_t)j * pitch32 + i] * inv_scale;
   }
 }
 
@@ -1435,7 +1281,7 @@ __global__ void __launch_bounds__(kBX * kBY)
       const int64_t at = (int64_t)j * L.pitch + q;
       if (mode != 1) {
         const double r = Arith<double>::sub(B.f[at], apply_at<double, EXACT>(L, B.u, i, j, at, nullptr));
-        if (mode == 0) B.r32[at] = (float)(r * sc);
+        if (mode == 0) B.r32[(int64_t)j * B.pitch32 + q] = (float)(r * sc);
         v += r * r;
       } else {
         v += B.f[at] * B.f[at];
@@ -1479,7 +1325,7 @@ __global__ void __launch_bounds__(kBX * kBY)
     const int i = L.kind == kRot ? 2 * q + (j & 1) : q;
     if (!interior(L, i, j)) continue;
     const int64_t at = (int64_t)j * L.pitch + q;
-    B.u[at] = B.u[at] + (double)B.e32[at] * inv;
+    B.u[at] = B.u[at] + (double)B.e32[(int64_t)j * B.pitch32 + q] * inv;
   }
 }
 
@@ -1879,6 +1725,22 @@ cudaError_t launch_coarsest(int64_t idx, T a, int zero_mean, const T* f, T* u, c
   return cudaGetLastError();
 }
 
+// Blocks of a kernel resident on the whole GPU at once (256-thread blocks), looked up
+// once per kernel.
+template <auto KERNEL>
+int resident_blocks() {
+  static const int v = [] {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, KERNEL, kBX * kBY, 0) != cudaSuccess || nb < 1) {
+      cudaGetLastError();
+      nb = 1;
+    }
+    return nb * sm_count();
+  }();
+  return v;
+}
+
+// Partial sums a norm reduction of level L may need: at most kMaxPartials.
 template <typename T>
 int resnorm_blocks(const LevelPair<T>& L) {
   const dim3 g = norm_grid(L.h);
@@ -1902,15 +1764,29 @@ cudaError_t launch_first_half_zero(const LevelPair<T>& L, const T* f, T* t, int 
   return cudaGetLastError();
 }
 
+template <typename T, bool EXACT, int NT>
+cudaError_t launch_resnorm_red_as(const LevelPair<T>& L, const T* u, const T* f, T* uout, int red, double* partial,
+                                  double* out, cudaStream_t s) {
+  const dim3 t = grid_of(L.h);
+  const int tiles = (int)(t.x * t.y);
+  const int blocks = std::min({tiles, kMaxPartials, resident_blocks<k_resnorm_red<T, EXACT, NT>>()});
+  k_resnorm_red<T, EXACT, NT><<<blocks, dim3(kBX, kBY), 0, s>>>(L.d, u, f, uout, red, partial, (int)t.x, tiles);
+  k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, blocks, out);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_resnorm_red(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* uout, int red,
                                double* partial, double* out, cudaStream_t s) {
-  const dim3 g = norm_grid(L.h);
-  const int ty = (int)grid_of(L.h).y;
-  if (exact) k_resnorm_red<T, true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, uout, red, partial, ty);
-  else k_resnorm_red<T, false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, uout, red, partial, ty);
-  k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
-  return cudaGetLastError();
+  const int nt = L.h.kind == kAxis ? L.h.nt : 0;
+  if (nt == 9)
+    return exact ? launch_resnorm_red_as<T, true, 9>(L, u, f, uout, red, partial, out, s)
+                 : launch_resnorm_red_as<T, false, 9>(L, u, f, uout, red, partial, out, s);
+  if (nt == 5)
+    return exact ? launch_resnorm_red_as<T, true, 5>(L, u, f, uout, red, partial, out, s)
+                 : launch_resnorm_red_as<T, false, 5>(L, u, f, uout, red, partial, out, s);
+  return exact ? launch_resnorm_red_as<T, true, 0>(L, u, f, uout, red, partial, out, s)
+               : launch_resnorm_red_as<T, false, 0>(L, u, f, uout, red, partial, out, s);
 }
 
 template <typename T>
@@ -1936,23 +1812,37 @@ cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
-                               float* r32, double scale, double* partial, double* out, cudaStream_t s, int bf16,
-                               const LevelPair<float>* L32, float* t32) {
-  const dim3 g = norm_grid(L.h);
-  const int ty = (int)grid_of(L.h).y;
-  const LevelDev<float>* L32d = L32 ? L32->d : nullptr;
-  if (exact) k_ir_residual<true><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16, L32d, t32);
-  else k_ir_residual<false><<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, ty, bf16, L32d, t32);
-  k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, (int)(g.x * g.y), out);
+template <bool EXACT, int NT>
+cudaError_t launch_ir_residual_as(const LevelPair<double>& L, const double* u, const double* f,
+                                  const LevelPair<float>& L32, float* r32, double scale, double* partial, double* out,
+                                  cudaStream_t s, int bf16, float* t32) {
+  const dim3 t = grid_of(L.h);
+  const int tiles = (int)(t.x * t.y);
+  const int blocks = std::min({tiles, kMaxPartials, resident_blocks<k_ir_residual<EXACT, NT>>()});
+  k_ir_residual<EXACT, NT><<<blocks, dim3(kBX, kBY), 0, s>>>(L.d, u, f, r32, scale, partial, (int)t.x, tiles, bf16,
+                                                             L32.d, t32);
+  k_sum_partials<<<1, dim3(kBX, kBY), 0, s>>>(partial, blocks, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
-                             cudaStream_t s) {
+cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
+                               const LevelPair<float>& L32, float* r32, double scale, double* partial,
+                               double* out, cudaStream_t s, int bf16, float* t32) {
+  if (L.h.nt == 9)
+    return exact ? launch_ir_residual_as<true, 9>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32)
+                 : launch_ir_residual_as<false, 9>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32);
+  if (L.h.nt == 5)
+    return exact ? launch_ir_residual_as<true, 5>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32)
+                 : launch_ir_residual_as<false, 5>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32);
+  return exact ? launch_ir_residual_as<true, 0>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32)
+               : launch_ir_residual_as<false, 0>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32);
+}
+
+cudaError_t launch_ir_update(const LevelPair<double>& L, const LevelPair<float>& L32, double* u, const float* e,
+                             double inv_scale, cudaStream_t s) {
   dim3 g = grid_of(L.h);
   g.y = (L.h.rows + kBY * kTransferRows - 1) / (kBY * kTransferRows);
-  k_ir_update<<<g, dim3(kBX, kBY), 0, s>>>(L.d, u, e, inv_scale);
+  k_ir_update<<<g, dim3(kBX, kBY), 0, s>>>(L.d, L32.h.pitch, u, e, inv_scale);
   return cudaGetLastError();
 }
 

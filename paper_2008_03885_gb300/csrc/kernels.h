@@ -67,15 +67,15 @@ cudaError_t launch_zero_boundary(const LevelPair<T>& L, T* u, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_boundary(const LevelPair<T>& L, const T* src, T* dst, cudaStream_t s);
 
-// Refinement step, finest level (FP64 grid, FP32 grid of the same storage layout):
-// r32 = fl32((f - L u) * scale), *out = sum of (f - L u)^2 (two launches).
-// With L32 / t32: also the first half-sweep (red) of the FP32 cycle from e = 0 into t32.
+// Refinement step, finest level (FP64 grid L, FP32 grid L32 of the same nodes with its
+// own row pitch): r32 = fl32((f - L u) * scale), *out = sum of (f - L u)^2 (two launches).
+// With t32: also the first half-sweep (red) of the FP32 cycle from e = 0 into t32.
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
-                               float* r32, double scale, double* partial, double* out, cudaStream_t s,
-                               int bf16 = 0, const LevelPair<float>* L32 = nullptr, float* t32 = nullptr);
-// u += e * inv_scale on interior nodes.
-cudaError_t launch_ir_update(const LevelPair<double>& L, double* u, const float* e, double inv_scale,
-                             cudaStream_t s);
+                               const LevelPair<float>& L32, float* r32, double scale, double* partial,
+                               double* out, cudaStream_t s, int bf16 = 0, float* t32 = nullptr);
+// u += e * inv_scale on interior nodes (e in the FP32 finest level's storage).
+cudaError_t launch_ir_update(const LevelPair<double>& L, const LevelPair<float>& L32, double* u, const float* e,
+                             double inv_scale, cudaStream_t s);
 
 // ---- small-level tail: one thread block runs a whole sub-cycle ---------------
 constexpr int kTailMaxLevels = 40;
@@ -144,6 +144,7 @@ struct BatchLevel {
   T coarsest_a;
   float* r32;             // finest level, mixed precision: FP32 residual (inner right-hand side)
   float* e32;             //   and FP32 correction
+  int32_t pitch32;        //   row pitch of those FP32 arrays (padded to 32 elements)
 };
 
 enum BatchOp : int32_t {

@@ -1,0 +1,759 @@
+// Shared-memory tile kernels for the large axis levels of the FP32 inner cycle (see
+// tiles.h). A block owns a tile of kTQ storage columns x kTJ rows (kTQ / 2 node pairs
+// per row, each pair one red and one black node). One TMA load per input array brings
+// the tile and its halo into shared memory (zero fill outside the array); the block then
+// runs its relaxation phases on shared-memory copies, recomputing on the halo what the
+// next phase needs (red nodes of one phase on a margin of the stencil reach around the
+// nodes the following phase updates), and writes only the tile's result. Values of one
+// colour are kept compactly, one per node pair, so that consecutive lanes touch
+// consecutive shared-memory words.
+//
+// Arithmetic per node is exactly that of the per-step kernels (kernels.cu): the same
+// fast stencil in registers (a 5-point or 9-point cross, terms in (dy, dx) order) or the
+// same boundary-class term list, the same multiply / fused-multiply-add sequence, and
+// the same relaxation u + r * omega / a_pp; so a fused group of steps gives the same bits
+// as the separate launches.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "device.cuh"
+#include "tiles.h"
+
+namespace nsmg {
+namespace {
+
+constexpr int kTQ = 128;  // tile storage columns
+constexpr int kTP = kTQ / 2;  // node pairs per tile row
+constexpr int kTJ = 32;   // tile rows
+constexpr int kTT = 256;  // threads per block
+constexpr int kTileMinRows = 256;  // smaller levels keep the per-step kernels
+
+__host__ __device__ constexpr int round4(int x) { return (x + 3) / 4 * 4; }
+
+// A compact one-colour array over the tile plus a margin of M rows and MP node pairs.
+template <int M>
+struct Reg {
+  static constexpr int mp = (M + 1) / 2;
+  static constexpr int w = kTP + 2 * mp;
+  static constexpr int h = kTJ + 2 * M;
+  static constexpr int n = w * h;
+};
+
+// Halo of the TMA box (x multiple of 4 elements: the box must start on 16 bytes).
+template <int R, int NS>
+struct PreGeo {  // presmooth: red(0) values on the tile plus (2 NS - 1) R
+  static constexpr int M0 = (2 * NS - 1) * R;
+  static constexpr int HX = round4(2 * Reg<M0>::mp), HY = M0;
+};
+template <int R>
+struct SweepGeo {  // one sweep: red on the tile plus R, reading u a further R away
+  static constexpr int HX = round4(2 * Reg<R>::mp + R), HY = 2 * R;
+};
+template <int R>
+struct RrGeo {  // residual + restriction: red residuals on the tile plus 1
+  static constexpr int HX = round4(2 * Reg<1>::mp + R), HY = 1 + R;
+};
+
+// ---- mbarrier and TMA --------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load(float* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bound of the waits on a load barrier (each try_wait suspends the thread for a short
+// system-dependent time; the limit is far beyond any real load).
+constexpr long kWaitTries = 1L << 22;
+
+// ---- node arithmetic -------------------------------------------------------------
+// omega / a_pp of node (i, j).
+__device__ __forceinline__ float wd_at(const LevelDev<float>& L, float wdf, int i, int j) {
+  return fast_node_c<false>(L, i, j) ? wdf : L.cls_wd[class_of(L, i, j)];
+}
+
+// Relaxed value u + (f - s) omega / a_pp (as relax_fast / relax_value).
+template <bool EXACT>
+__device__ __forceinline__ float relax(float s, float f, float u, float wd) {
+  const float r = Arith<float>::sub(f, s);
+  return EXACT ? Arith<float>::add(u, Arith<float>::mul(r, wd)) : Arith<float>::fma(r, wd, u);
+}
+
+// (L x)(i, j): the fast cross stencil with coefficients c (terms in (dy, dx) order) or
+// the node's boundary-class term list. x(i, j) returns the value of lattice node (i, j).
+template <bool EXACT, int NT, class X>
+__device__ __forceinline__ float stencil(const LevelDev<float>& L, const float (&c)[NT], int i, int j, X x) {
+  if (fast_node_c<false>(L, i, j)) {
+    if (NT == 9) {
+      float s = Arith<float>::mul(c[0], x(i, j - 2));
+      s = madd<float, EXACT>(s, c[1], x(i, j - 1));
+      s = madd<float, EXACT>(s, c[2], x(i - 2, j));
+      s = madd<float, EXACT>(s, c[3], x(i - 1, j));
+      s = madd<float, EXACT>(s, c[4], x(i, j));
+      s = madd<float, EXACT>(s, c[5], x(i + 1, j));
+      s = madd<float, EXACT>(s, c[6], x(i + 2, j));
+      s = madd<float, EXACT>(s, c[7], x(i, j + 1));
+      return madd<float, EXACT>(s, c[8], x(i, j + 2));
+    }
+    float s = Arith<float>::mul(c[0], x(i, j - 1));
+    s = madd<float, EXACT>(s, c[1], x(i - 1, j));
+    s = madd<float, EXACT>(s, c[2], x(i, j));
+    s = madd<float, EXACT>(s, c[3], x(i + 1, j));
+    return madd<float, EXACT>(s, c[4], x(i, j + 1));
+  }
+  const int2 e = L.cls[class_of(L, i, j)];
+  const ClassTerm<float>* tt = L.terms + e.x;
+  float s = 0.f;
+  for (int k = 0; k < e.y; ++k) {
+    const ClassTerm<float> t = load_term(tt + k);
+    const float v = x(i + t.dx, j + t.dy);
+    s = k == 0 ? Arith<float>::mul(t.c, v) : madd<float, EXACT>(s, t.c, v);
+  }
+  return s;
+}
+
+// Tile origin of the block.
+struct Tile {
+  int J0, Q0, P0;
+  __device__ Tile(int bx, int by) : J0(by * kTJ), Q0(bx * kTQ), P0(bx * kTP) {}
+  // index of lattice node (i, j) in a compact one-colour array of margin M
+  template <int M>
+  __device__ __forceinline__ int at(int i, int j) const {
+    return (j - J0 + M) * Reg<M>::w + ((i >> 1) - P0 + Reg<M>::mp);
+  }
+  // index of lattice node (i, j) in a staged box with halo (HX, HY)
+  template <int HX, int HY>
+  __device__ __forceinline__ int box(int i, int j) const {
+    return (j - J0 + HY) * (kTQ + 2 * HX) + (i - Q0 + HX);
+  }
+};
+
+__device__ __forceinline__ bool inner(int n, int i, int j) { return i >= 1 && i < n && j >= 1 && j < n; }
+
+// TMA destinations start on 128-byte boundaries: the dynamic shared memory is rounded
+// up to one (the launch adds 128 bytes for it) and every staged box is padded to a
+// multiple of 32 floats.
+__host__ __device__ constexpr int pad32(int n) { return (n + 31) / 32 * 32; }
+__device__ __forceinline__ float* smem_base(unsigned char* raw) {
+  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~(uintptr_t)127);
+}
+
+// Store the tile's result: node pair (2p, 2p + 1) of row j as one 8-byte store.
+__device__ __forceinline__ void store_pair(float* out, int pitch, int n, int j, int p, float red, float black) {
+  if (j > n || 2 * p > n) return;
+  const float2 v = (j & 1) ? make_float2(red, black) : make_float2(black, red);  // red: i + j odd
+  *reinterpret_cast<float2*>(out + (int64_t)j * pitch + 2 * p) = v;
+}
+
+// ---- fast path: tiles whose nodes (with the halo) are all fast interior nodes ------
+// Then every node uses the level's cross stencil with the coefficients in registers,
+// omega / a_pp is the level's constant, and no node needs a boundary test: each value
+// is read at a compile-time offset from a per-node base index. A source is where a
+// phase reads one colour (or both) from:
+struct SZero {  // the zero start: every value of this colour is 0
+  template <int M>
+  __device__ __forceinline__ int base(int, int, int) const { return 0; }
+  template <int DX, int DY>
+  __device__ __forceinline__ float get(int, int) const { return 0.f; }
+};
+template <int MS>
+struct SCompact {  // one colour, one value per node pair, tile plus margin MS
+  const float* p;
+  // base of the node at (row rr, pair pp) of a region of margin M
+  template <int M>
+  __device__ __forceinline__ int base(int rr, int pp, int) const {
+    return (rr - M + MS) * Reg<MS>::w + (pp - Reg<M>::mp + Reg<MS>::mp);
+  }
+  // lattice offset (DX, DY) from a node whose column parity within its pair is a
+  template <int DX, int DY>
+  __device__ __forceinline__ float get(int b, int a) const {
+    return p[b + DY * Reg<MS>::w + ((a + DX) >> 1)];
+  }
+};
+template <int HX, int HY>
+struct SBox {  // a staged TMA box (both colours), halo (HX, HY)
+  const float* p;
+  static constexpr int BW = kTQ + 2 * HX;
+  template <int M>
+  __device__ __forceinline__ int base(int rr, int pp, int a) const {
+    return (rr - M + HY) * BW + (2 * (pp - Reg<M>::mp) + a + HX);
+  }
+  template <int DX, int DY>
+  __device__ __forceinline__ float get(int b, int) const {
+    return p[b + DY * BW + DX];
+  }
+};
+
+// (L x) at a fast node: terms in (dy, dx) order; odd offsets (DX + DY) read the other
+// colour's source `so` (base bo), even ones the node's own colour `ss` (base bs).
+template <bool EXACT, int NT, class SO, class SS>
+__device__ __forceinline__ float cross(const float (&c)[NT], const SO& so, int bo, const SS& ss, int bs, int a) {
+  if constexpr (NT == 9) {
+    float s = Arith<float>::mul(c[0], ss.template get<0, -2>(bs, a));
+    s = madd<float, EXACT>(s, c[1], so.template get<0, -1>(bo, a));
+    s = madd<float, EXACT>(s, c[2], ss.template get<-2, 0>(bs, a));
+    s = madd<float, EXACT>(s, c[3], so.template get<-1, 0>(bo, a));
+    s = madd<float, EXACT>(s, c[4], ss.template get<0, 0>(bs, a));
+    s = madd<float, EXACT>(s, c[5], so.template get<1, 0>(bo, a));
+    s = madd<float, EXACT>(s, c[6], ss.template get<2, 0>(bs, a));
+    s = madd<float, EXACT>(s, c[7], so.template get<0, 1>(bo, a));
+    return madd<float, EXACT>(s, c[8], ss.template get<0, 2>(bs, a));
+  } else {
+    float s = Arith<float>::mul(c[0], so.template get<0, -1>(bo, a));
+    s = madd<float, EXACT>(s, c[1], so.template get<-1, 0>(bo, a));
+    s = madd<float, EXACT>(s, c[2], ss.template get<0, 0>(bs, a));
+    s = madd<float, EXACT>(s, c[3], so.template get<1, 0>(bo, a));
+    return madd<float, EXACT>(s, c[4], so.template get<0, 1>(bo, a));
+  }
+}
+
+// One fast relaxation phase: every node of colour RED in the tile plus margin M gets
+// relax(L x, f, old) (old, so and ss as above; with ZERO_START the stencil-free value
+// 0 + f omega / a_pp), handed to sink(e, rr, pp, a, value). Each thread evaluates kIlp
+// nodes before it hands any of them over, so that their dependency chains (shared-memory
+// loads, then a chain of fused multiply-adds) overlap.
+// (Measured on GB300, 4097^2 FP32 fourth order, one tile per block: 2 and 4 nodes per
+// thread at a time were slower than 1 -- presmooth 107 / 134 vs 106 us, sweep 70 / 86 vs
+// 67 us -- with more registers per node and more idle lanes in each phase's last pass.)
+constexpr int kIlp = 1;
+static_assert((kTJ * kTP) % (kIlp * kTT) == 0, "the tile's node pairs split evenly over the block");
+
+template <bool EXACT, int NT, bool RED, int M, bool ZERO_START, class SO, class SS, class SOLD, class FB, class SINK>
+__device__ __forceinline__ void phase(const float (&c)[NT], float wd, const SO& so, const SS& ss, const SOLD& sold,
+                                      const FB& fb, SINK sink) {
+  constexpr int N = Reg<M>::n;
+  for (int e0 = threadIdx.x; e0 < N; e0 += kIlp * kTT) {
+    float v[kIlp];
+    int rr[kIlp], pp[kIlp], a[kIlp];
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u) {
+      const int e = min(e0 + u * kTT, N - 1);  // past the end: recompute the last node, not stored
+      rr[u] = e / Reg<M>::w;
+      pp[u] = e - rr[u] * Reg<M>::w;
+      a[u] = (rr[u] + M + (RED ? 1 : 0)) & 1;  // column parity of the node (tile rows start even)
+      const float f = fb.template get<0, 0>(fb.template base<M>(rr[u], pp[u], a[u]), a[u]);
+      if constexpr (ZERO_START) {
+        v[u] = relax_from_zero(f, wd);
+      } else {
+        const float st = cross<EXACT, NT>(c, so, so.template base<M>(rr[u], pp[u], a[u]), ss,
+                                          ss.template base<M>(rr[u], pp[u], a[u]), a[u]);
+        v[u] = relax<EXACT>(st, f, sold.template get<0, 0>(sold.template base<M>(rr[u], pp[u], a[u]), a[u]), wd);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kIlp; ++u)
+      if (e0 + u * kTT < N) sink(e0 + u * kTT, rr[u], pp[u], a[u], v[u]);
+  }
+}
+
+// Whether the tile's nodes within margin m (rows) / 2 mp (columns) are all fast
+// interior nodes of L (Dirichlet levels: rx <= i <= n - rx, ry <= j <= n - ry).
+template <int M>
+__device__ __forceinline__ bool fast_tile(const LevelDev<float>& L, const Tile& T) {
+  return T.Q0 - 2 * Reg<M>::mp >= L.rx && T.Q0 + kTQ + 2 * Reg<M>::mp - 1 <= L.fxe && T.J0 - M >= L.ry &&
+         T.J0 + kTJ - 1 + M <= L.fye;
+}
+
+// Unchecked store of a fast tile's node pair (2p, 2p + 1) of row j.
+__device__ __forceinline__ void put_pair(float* out, int pitch, int j, int p, float red, float black) {
+  const float2 v = (j & 1) ? make_float2(red, black) : make_float2(black, red);
+  *reinterpret_cast<float2*>(out + (int64_t)j * pitch + 2 * p) = v;
+}
+
+// ---- one tile per block ---------------------------------------------------------
+// Block (bx, by) stages its tile with one TMA load per input array and runs body(T,
+// box) on it. (Measured on GB300, 4097^2 FP32 fourth order: a persistent form with two
+// shared-memory stages, the next tile's loads in flight during the current one, was
+// slower: sweep 78 vs 67 us, presmooth 126 vs 106 us; it holds two blocks per SM
+// instead of three.) A wait that gives up sets the status word and leaves the block
+// once its load has landed (or a second bounded wait ran out).
+__device__ __forceinline__ bool wait_tile(uint64_t* bar, int* status) {
+  bool ok = false;
+  for (long q = 0; q < kWaitTries && !ok; ++q) ok = mbar_try(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, kStatusTmaTimeout);
+      for (long q = 0; q < kWaitTries && !mbar_try(bar, 0); ++q) {
+      }
+    }
+    __syncthreads();
+    return false;
+  }
+  return true;
+}
+
+template <int NB, class BODY>
+__device__ __forceinline__ void tile_block(float* box0, int box_floats, const CUtensorMap* const (&maps)[NB], int hx,
+                                           int hy, int* status, BODY body) {
+  __shared__ uint64_t bar;
+  const Tile T(blockIdx.x, blockIdx.y);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    mbar_expect(&bar, (uint32_t)(NB * (kTQ + 2 * hx) * (kTJ + 2 * hy) * sizeof(float)));
+#pragma unroll
+    for (int m = 0; m < NB; ++m) tma_load(box0 + m * box_floats, maps[m], T.Q0 - hx, T.J0 - hy, &bar);
+  }
+  __syncthreads();
+  if (!wait_tile(&bar, status)) return;
+  body(T, box0);
+}
+
+// ---- presmooth: NS red-black sweeps from u = 0 ---------------------------------
+template <bool EXACT, int NT, int NS>
+__global__ void __launch_bounds__(kTT, 3) k_tile_presmooth(const LevelDev<float>* __restrict__ Lp,
+                                                        const __grid_constant__ CUtensorMap mapF,
+                                                        float* __restrict__ out, int* __restrict__ status) {
+  constexpr int R = NT == 9 ? 2 : 1;
+  using G = PreGeo<R, NS>;
+  constexpr int M0 = G::M0, M1 = (2 * NS - 2) * R, M2 = NS == 2 ? R : 0;
+  constexpr int FN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float* box0 = smem_base(tile_smem);
+  float* sR0 = box0 + pad32(FN);
+  float* sB1 = sR0 + Reg<M0>::n;
+  float* sR2 = sB1 + (NS == 2 ? Reg<M1>::n : 0);
+  const LevelDev<float>& L = *Lp;
+  float c[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) c[k] = L.c[k];
+  const float wdf = L.wd;
+  const int n = L.n, pitch = L.pitch;
+  const CUtensorMap* const maps[1] = {&mapF};
+  tile_block<1>(box0, pad32(FN), maps, G::HX, G::HY, status, [&](const Tile& T, float* sF) {
+    const int tid = threadIdx.x;
+    if (fast_tile<M0>(L, T)) {
+      const SBox<G::HX, G::HY> fb{sF};
+      phase<EXACT, NT, true, M0, true>(c, wdf, SZero{}, SZero{}, SZero{}, fb,
+                                       [=](int e, int, int, int, float v) { sR0[e] = v; });
+      __syncthreads();
+      const SCompact<M0> r0{sR0};
+      if constexpr (NS == 2) {
+        const SCompact<M1> b1{sB1};
+        const SCompact<M2> r2{sR2};
+        phase<EXACT, NT, false, M1, false>(c, wdf, r0, SZero{}, SZero{}, fb,
+                                           [=](int e, int, int, int, float v) { sB1[e] = v; });
+        __syncthreads();
+        phase<EXACT, NT, true, M2, false>(c, wdf, b1, r0, r0, fb, [=](int e, int, int, int, float v) { sR2[e] = v; });
+        __syncthreads();
+        phase<EXACT, NT, false, 0, false>(c, wdf, r2, b1, b1, fb, [=](int, int rr, int pp, int a, float v) {
+          put_pair(out, pitch, T.J0 + rr, T.P0 + pp, sR2[r2.template base<0>(rr, pp, a)], v);
+        });
+      } else {
+        phase<EXACT, NT, false, 0, false>(c, wdf, r0, SZero{}, SZero{}, fb, [=](int, int rr, int pp, int a, float v) {
+          put_pair(out, pitch, T.J0 + rr, T.P0 + pp, sR0[r0.template base<0>(rr, pp, a)], v);
+        });
+      }
+      return;
+    }
+    auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
+    // red nodes from zero: 0 + f omega / a_pp
+    for (int e = tid; e < Reg<M0>::n; e += kTT) {
+      const int rr = e / Reg<M0>::w, pp = e - rr * Reg<M0>::w;
+      const int j = T.J0 - M0 + rr, i = 2 * (T.P0 - Reg<M0>::mp + pp) + ((j + 1) & 1);
+      sR0[e] = inner(n, i, j) ? relax_from_zero(F(i, j), wd_at(L, wdf, i, j)) : 0.f;
+    }
+    __syncthreads();
+    auto xR0 = [=](int i, int j) { return sR0[T.at<M0>(i, j)]; };
+    if constexpr (NS == 2) {
+      // black nodes of sweep 1 (their old values and black neighbours are 0)
+      for (int e = tid; e < Reg<M1>::n; e += kTT) {
+        const int rr = e / Reg<M1>::w, pp = e - rr * Reg<M1>::w;
+        const int j = T.J0 - M1 + rr, i = 2 * (T.P0 - Reg<M1>::mp + pp) + (j & 1);
+        float v = 0.f;
+        if (inner(n, i, j)) {
+          const float s =
+              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR0(a, b) : 0.f; });
+          v = relax<EXACT>(s, F(i, j), 0.f, wd_at(L, wdf, i, j));
+        }
+        sB1[e] = v;
+      }
+      __syncthreads();
+      auto xB1 = [=](int i, int j) { return sB1[T.at<M1>(i, j)]; };
+      // red nodes of sweep 2
+      for (int e = tid; e < Reg<M2>::n; e += kTT) {
+        const int rr = e / Reg<M2>::w, pp = e - rr * Reg<M2>::w;
+        const int j = T.J0 - M2 + rr, i = 2 * (T.P0 - Reg<M2>::mp + pp) + ((j + 1) & 1);
+        float v = 0.f;
+        if (inner(n, i, j)) {
+          const float s =
+              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR0(a, b) : xB1(a, b); });
+          v = relax<EXACT>(s, F(i, j), xR0(i, j), wd_at(L, wdf, i, j));
+        }
+        sR2[e] = v;
+      }
+      __syncthreads();
+      auto xR2 = [=](int i, int j) { return sR2[T.at<M2>(i, j)]; };
+      // black nodes of sweep 2 on the tile, stored with their red partners
+      for (int e = tid; e < kTJ * kTP; e += kTT) {
+        const int rr = e / kTP, pp = e - rr * kTP;
+        const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);
+        float v = 0.f;
+        if (inner(n, i, j)) {
+          const float s =
+              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR2(a, b) : xB1(a, b); });
+          v = relax<EXACT>(s, F(i, j), xB1(i, j), wd_at(L, wdf, i, j));
+        }
+        store_pair(out, pitch, n, j, p, xR2(2 * p + ((j + 1) & 1), j), v);
+      }
+    } else {
+      for (int e = tid; e < kTJ * kTP; e += kTT) {
+        const int rr = e / kTP, pp = e - rr * kTP;
+        const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);
+        float v = 0.f;
+        if (inner(n, i, j)) {
+          const float s =
+              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR0(a, b) : 0.f; });
+          v = relax<EXACT>(s, F(i, j), 0.f, wd_at(L, wdf, i, j));
+        }
+        store_pair(out, pitch, n, j, p, xR0(2 * p + ((j + 1) & 1), j), v);
+      }
+    }
+  });
+}
+
+// ---- one red-black sweep, u -> out -----------------------------------------------
+template <bool EXACT, int NT>
+__global__ void __launch_bounds__(kTT, 3) k_tile_sweep(const LevelDev<float>* __restrict__ Lp,
+                                                    const __grid_constant__ CUtensorMap mapU,
+                                                    const __grid_constant__ CUtensorMap mapF, float* __restrict__ out,
+                                                    int* __restrict__ status) {
+  constexpr int R = NT == 9 ? 2 : 1;
+  using G = SweepGeo<R>;
+  constexpr int BN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float* box0 = smem_base(tile_smem);
+  float* sR = box0 + 2 * pad32(BN);
+  const LevelDev<float>& L = *Lp;
+  float c[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) c[k] = L.c[k];
+  const float wdf = L.wd;
+  const int n = L.n, pitch = L.pitch;
+  const CUtensorMap* const maps[2] = {&mapU, &mapF};
+  tile_block<2>(box0, pad32(BN), maps, G::HX, G::HY, status, [&](const Tile& T, float* sU) {
+    const int tid = threadIdx.x;
+    float* sF = sU + pad32(BN);
+    if (fast_tile<R>(L, T)) {
+      const SBox<G::HX, G::HY> ub{sU}, fb{sF};
+      const SCompact<R> rn{sR};
+      phase<EXACT, NT, true, R, false>(c, wdf, ub, ub, ub, fb, [=](int e, int, int, int, float v) { sR[e] = v; });
+      __syncthreads();
+      phase<EXACT, NT, false, 0, false>(c, wdf, rn, ub, ub, fb, [=](int, int rr, int pp, int a, float v) {
+        put_pair(out, pitch, T.J0 + rr, T.P0 + pp, sR[rn.template base<0>(rr, pp, a)], v);
+      });
+      return;
+    }
+    auto U = [=](int i, int j) { return sU[T.box<G::HX, G::HY>(i, j)]; };
+    auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
+    // red half-sweep on the tile plus R
+    for (int e = tid; e < Reg<R>::n; e += kTT) {
+      const int rr = e / Reg<R>::w, pp = e - rr * Reg<R>::w;
+      const int j = T.J0 - R + rr, i = 2 * (T.P0 - Reg<R>::mp + pp) + ((j + 1) & 1);
+      float v = U(i, j);
+      if (inner(n, i, j)) v = relax<EXACT>(stencil<EXACT, NT>(L, c, i, j, U), F(i, j), v, wd_at(L, wdf, i, j));
+      sR[e] = v;
+    }
+    __syncthreads();
+    auto xR = [=](int i, int j) { return sR[T.at<R>(i, j)]; };
+    // black half-sweep on the tile
+    for (int e = tid; e < kTJ * kTP; e += kTT) {
+      const int rr = e / kTP, pp = e - rr * kTP;
+      const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);
+      float v = U(i, j);
+      if (inner(n, i, j)) {
+        const float s =
+            stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR(a, b) : U(a, b); });
+        v = relax<EXACT>(s, F(i, j), v, wd_at(L, wdf, i, j));
+      }
+      store_pair(out, pitch, n, j, p, xR(2 * p + ((j + 1) & 1), j), v);
+    }
+  });
+}
+
+// ---- residual + red-black restriction (axis level -> its black points) ------------
+template <bool EXACT, int NT, bool TC>
+__global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<float>* __restrict__ Lp,
+                                                           const LevelDev<float>* __restrict__ Lcp,
+                                                           const __grid_constant__ CUtensorMap mapU,
+                                                           const __grid_constant__ CUtensorMap mapF,
+                                                           float* __restrict__ fc, float* __restrict__ tc,
+                                                           int* __restrict__ status) {
+  constexpr int R = NT == 9 ? 2 : 1;
+  using G = RrGeo<R>;
+  constexpr int BN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float* box0 = smem_base(tile_smem);
+  float* sD = box0 + 2 * pad32(BN);  // residuals of the red nodes, tile plus 1
+  const LevelDev<float>& L = *Lp;
+  const LevelDev<float>& Lc = *Lcp;
+  float c[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) c[k] = L.c[k];
+  const int n = L.n, pc = Lc.pitch;
+  const CUtensorMap* const maps[2] = {&mapU, &mapF};
+  tile_block<2>(box0, pad32(BN), maps, G::HX, G::HY, status, [&](const Tile& T, float* sU) {
+    const int tid = threadIdx.x;
+    float* sF = sU + pad32(BN);
+    if (fast_tile<1>(L, T)) {
+      const SBox<G::HX, G::HY> ub{sU}, fb{sF};
+      const SCompact<1> dr{sD};
+      // red residuals on the tile plus 1 (kIlp nodes per thread at a time, as in phase)
+      for (int e0 = tid; e0 < Reg<1>::n; e0 += kIlp * kTT) {
+        float d[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+          const int e = min(e0 + u * kTT, Reg<1>::n - 1);
+          const int rr = e / Reg<1>::w, pp = e - rr * Reg<1>::w;
+          const int a = rr & 1;  // red node of row J0 - 1 + rr
+          const int b = ub.template base<1>(rr, pp, a);
+          d[u] = Arith<float>::sub(fb.template get<0, 0>(b, a), cross<EXACT, NT>(c, ub, b, ub, b, a));
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u)
+          if (e0 + u * kTT < Reg<1>::n) sD[e0 + u * kTT] = d[u];
+      }
+      __syncthreads();
+      for (int e0 = tid; e0 < kTJ * kTP; e0 += kIlp * kTT) {
+        float v[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+          const int e = e0 + u * kTT;  // kTJ * kTP is a multiple of kIlp * kTT
+          const int rr = e / kTP, pp = e - rr * kTP;
+          const int a = rr & 1;  // black node = coarse node
+          const int b = ub.template base<0>(rr, pp, a);
+          const float d = Arith<float>::sub(fb.template get<0, 0>(b, a), cross<EXACT, NT>(c, ub, b, ub, b, a));
+          const int bd = dr.template base<0>(rr, pp, a);
+          // R = 1/2 P^T, Eq. (transfer_r2): terms (0,-1), (-1,0), (0,0), (1,0), (0,1)
+          float w = Arith<float>::mul(0.125f, dr.template get<0, -1>(bd, a));
+          w = madd<float, EXACT>(w, 0.125f, dr.template get<-1, 0>(bd, a));
+          w = madd<float, EXACT>(w, 0.5f, d);
+          w = madd<float, EXACT>(w, 0.125f, dr.template get<1, 0>(bd, a));
+          v[u] = madd<float, EXACT>(w, 0.125f, dr.template get<0, 1>(bd, a));
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+          const int e = e0 + u * kTT;
+          const int rr = e / kTP, pp = e - rr * kTP;
+          const int j = T.J0 + rr, i = 2 * (T.P0 + pp) + (rr & 1);
+          const int64_t at = (int64_t)j * pc + (i >> 1);
+          fc[at] = v[u];
+          if (TC) tc[at] = (i & 1) ? relax_from_zero(v[u], node_wd(Lc, i, j)) : 0.f;
+        }
+      }
+      return;
+    }
+    auto U = [=](int i, int j) { return sU[T.box<G::HX, G::HY>(i, j)]; };
+    auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
+    for (int e = tid; e < Reg<1>::n; e += kTT) {
+      const int rr = e / Reg<1>::w, pp = e - rr * Reg<1>::w;
+      const int j = T.J0 - 1 + rr, i = 2 * (T.P0 - Reg<1>::mp + pp) + ((j + 1) & 1);
+      sD[e] = inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, NT>(L, c, i, j, U)) : 0.f;
+    }
+    __syncthreads();
+    auto D = [=](int i, int j) { return sD[T.at<1>(i, j)]; };
+    for (int e = tid; e < kTJ * kTP; e += kTT) {
+      const int rr = e / kTP, pp = e - rr * kTP;
+      const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);  // black node = coarse node
+      if (!inner(n, i, j)) continue;
+      const float d = Arith<float>::sub(F(i, j), stencil<EXACT, NT>(L, c, i, j, U));
+      float v = Arith<float>::mul(0.125f, D(i, j - 1));
+      v = madd<float, EXACT>(v, 0.125f, D(i - 1, j));
+      v = madd<float, EXACT>(v, 0.5f, d);
+      v = madd<float, EXACT>(v, 0.125f, D(i + 1, j));
+      v = madd<float, EXACT>(v, 0.125f, D(i, j + 1));
+      const int64_t at = (int64_t)j * pc + (i >> 1);
+      fc[at] = v;
+      if (TC) tc[at] = (i & 1) ? relax_from_zero(v, node_wd(Lc, i, j)) : 0.f;
+    }
+  });
+}
+
+// ---- host side -----------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// 2D map over a level's (n + 1) x (n + 1) nodes (row stride pitch) with a box of
+// (kTQ + 2 hx) x (kTJ + 2 hy) elements.
+bool make_map(CUtensorMap* m, const float* base, const LevelDev<float>& L, int hx, int hy) {
+  const auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  std::memset(m, 0, sizeof(*m));
+  const cuuint64_t dims[2] = {(cuuint64_t)L.cols, (cuuint64_t)L.rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)L.pitch * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)(kTQ + 2 * hx), (cuuint32_t)(kTJ + 2 * hy)};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Dynamic shared memory of each kernel: its staged boxes (each padded to 32 floats), its
+// one-colour arrays, and 128 bytes to align the base.
+template <int R, int NS>
+size_t pre_smem() {
+  using G = PreGeo<R, NS>;
+  size_t n = (size_t)pad32((kTQ + 2 * G::HX) * (kTJ + 2 * G::HY)) + Reg<G::M0>::n;
+  if (NS == 2) n += Reg<2 * R>::n + Reg<R>::n;
+  return n * sizeof(float) + 128;
+}
+template <int R>
+size_t sweep_smem() {
+  using G = SweepGeo<R>;
+  return (2 * (size_t)pad32((kTQ + 2 * G::HX) * (kTJ + 2 * G::HY)) + Reg<R>::n) * sizeof(float) + 128;
+}
+template <int R>
+size_t rr_smem() {
+  using G = RrGeo<R>;
+  return (2 * (size_t)pad32((kTQ + 2 * G::HX) * (kTJ + 2 * G::HY)) + Reg<1>::n) * sizeof(float) + 128;
+}
+
+// Raise a kernel's dynamic shared-memory limit once per process (the sizes are fixed
+// per instantiation).
+template <auto KERNEL>
+cudaError_t allow_smem(size_t bytes) {
+  static const cudaError_t e = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return e;
+}
+
+}  // namespace
+
+bool tile_eligible(const LevelPair<float>& P) {
+  const LevelDev<float>& L = P.h;
+  if (L.kind != kAxis || L.per || L.bf16 || L.rows < kTileMinRows) return false;
+  if (L.pitch % 4 != 0) return false;  // TMA row stride: 16 bytes
+  // the fast stencil must be the 5-point or 9-point cross with terms in (dy, dx) order
+  static const int x5[5] = {0, -1, 0, 1, 0}, y5[5] = {-1, 0, 0, 0, 1};
+  static const int x9[9] = {0, 0, -2, -1, 0, 1, 2, 0, 0}, y9[9] = {-2, -1, 0, 0, 0, 0, 0, 1, 2};
+  const int* xs = L.nt == 5 ? x5 : L.nt == 9 ? x9 : nullptr;
+  const int* ys = L.nt == 5 ? y5 : y9;
+  if (!xs) return false;
+  for (int k = 0; k < L.nt; ++k)
+    if (L.sdx[0][k] != xs[k] || L.sdy[k] != ys[k]) return false;
+  return true;
+}
+
+bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, float* f, int nu1) {
+  T.on = false;
+  if (!tile_eligible(P)) return false;
+  const LevelDev<float>& L = P.h;
+  T.nt = L.nt;
+  T.reach = L.nt == 9 ? 2 : 1;
+  T.nu1 = (nu1 == 1 || nu1 == 2) ? nu1 : 0;
+  T.grid = dim3((L.cols + kTQ - 1) / kTQ, (L.rows + kTJ - 1) / kTJ);
+  bool ok = true;
+  if (T.reach == 2) {
+    if (T.nu1 == 2) ok &= make_map(&T.f_pre, f, L, PreGeo<2, 2>::HX, PreGeo<2, 2>::HY);
+    if (T.nu1 == 1) ok &= make_map(&T.f_pre, f, L, PreGeo<2, 1>::HX, PreGeo<2, 1>::HY);
+    ok &= make_map(&T.u_sw, u, L, SweepGeo<2>::HX, SweepGeo<2>::HY);
+    ok &= make_map(&T.t_sw, t, L, SweepGeo<2>::HX, SweepGeo<2>::HY);
+    ok &= make_map(&T.f_sw, f, L, SweepGeo<2>::HX, SweepGeo<2>::HY);
+    ok &= make_map(&T.u_rr, u, L, RrGeo<2>::HX, RrGeo<2>::HY);
+    ok &= make_map(&T.f_rr, f, L, RrGeo<2>::HX, RrGeo<2>::HY);
+  } else {
+    if (T.nu1 == 2) ok &= make_map(&T.f_pre, f, L, PreGeo<1, 2>::HX, PreGeo<1, 2>::HY);
+    if (T.nu1 == 1) ok &= make_map(&T.f_pre, f, L, PreGeo<1, 1>::HX, PreGeo<1, 1>::HY);
+    ok &= make_map(&T.u_sw, u, L, SweepGeo<1>::HX, SweepGeo<1>::HY);
+    ok &= make_map(&T.t_sw, t, L, SweepGeo<1>::HX, SweepGeo<1>::HY);
+    ok &= make_map(&T.f_sw, f, L, SweepGeo<1>::HX, SweepGeo<1>::HY);
+    ok &= make_map(&T.u_rr, u, L, RrGeo<1>::HX, RrGeo<1>::HY);
+    ok &= make_map(&T.f_rr, f, L, RrGeo<1>::HX, RrGeo<1>::HY);
+  }
+  T.on = ok;
+  return ok;
+}
+
+namespace {
+template <bool EXACT, int NT, int NS>
+cudaError_t presmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u, int* status, cudaStream_t s) {
+  const size_t smem = pre_smem<NT == 9 ? 2 : 1, NS>();
+  cudaError_t e = allow_smem<k_tile_presmooth<EXACT, NT, NS>>(smem);
+  if (e != cudaSuccess) return e;
+  k_tile_presmooth<EXACT, NT, NS><<<T.grid, kTT, smem, s>>>(L.d, T.f_pre, u, status);
+  return cudaGetLastError();
+}
+template <bool EXACT, int NT>
+cudaError_t sweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t, float* out, int* status,
+                     cudaStream_t s) {
+  const size_t smem = sweep_smem<NT == 9 ? 2 : 1>();
+  cudaError_t e = allow_smem<k_tile_sweep<EXACT, NT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_tile_sweep<EXACT, NT><<<T.grid, kTT, smem, s>>>(L.d, from_t ? T.t_sw : T.u_sw, T.f_sw, out, status);
+  return cudaGetLastError();
+}
+template <bool EXACT, int NT, bool TC>
+cudaError_t rr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc, float* fc, float* tc,
+                  int* status, cudaStream_t s) {
+  const size_t smem = rr_smem<NT == 9 ? 2 : 1>();
+  cudaError_t e = allow_smem<k_tile_res_restrict<EXACT, NT, TC>>(smem);
+  if (e != cudaSuccess) return e;
+  k_tile_res_restrict<EXACT, NT, TC><<<T.grid, kTT, smem, s>>>(L.d, Lc.d, T.u_rr, T.f_rr, fc, tc, status);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L, bool exact, float* u, int* status,
+                                  cudaStream_t s) {
+  if (!T.on || !T.nu1) return cudaErrorInvalidValue;
+  if (T.nt == 9) {
+    if (T.nu1 == 2) return exact ? presmooth_as<true, 9, 2>(T, L, u, status, s) : presmooth_as<false, 9, 2>(T, L, u, status, s);
+    return exact ? presmooth_as<true, 9, 1>(T, L, u, status, s) : presmooth_as<false, 9, 1>(T, L, u, status, s);
+  }
+  if (T.nu1 == 2) return exact ? presmooth_as<true, 5, 2>(T, L, u, status, s) : presmooth_as<false, 5, 2>(T, L, u, status, s);
+  return exact ? presmooth_as<true, 5, 1>(T, L, u, status, s) : presmooth_as<false, 5, 1>(T, L, u, status, s);
+}
+
+cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, bool exact, bool from_t, float* uout,
+                              int* status, cudaStream_t s) {
+  if (!T.on) return cudaErrorInvalidValue;
+  if (T.nt == 9)
+    return exact ? sweep_as<true, 9>(T, L, from_t, uout, status, s) : sweep_as<false, 9>(T, L, from_t, uout, status, s);
+  return exact ? sweep_as<true, 5>(T, L, from_t, uout, status, s) : sweep_as<false, 5>(T, L, from_t, uout, status, s);
+}
+
+cudaError_t launch_tile_res_restrict(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc,
+                                     bool exact, float* fc, float* tc, int* status, cudaStream_t s) {
+  if (!T.on || Lc.h.kind != kRot || Lc.h.bf16) return cudaErrorInvalidValue;
+  if (T.nt == 9) {
+    if (tc) return exact ? rr_as<true, 9, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, true>(T, L, Lc, fc, tc, status, s);
+    return exact ? rr_as<true, 9, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, false>(T, L, Lc, fc, tc, status, s);
+  }
+  if (tc) return exact ? rr_as<true, 5, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 5, true>(T, L, Lc, fc, tc, status, s);
+  return exact ? rr_as<true, 5, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 5, false>(T, L, Lc, fc, tc, status, s);
+}
+
+}  // namespace nsmg

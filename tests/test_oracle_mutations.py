@@ -257,3 +257,13 @@ CUBIC_MUTATIONS = {
 def test_planted_cubic_mistake_is_caught(name, monkeypatch):
     CUBIC_MUTATIONS[name](monkeypatch)
     assert failures(CUBIC_BATTERY), f"no cubic pin caught: {name}"
+
+
+def test_fp64_galerkin_products_fail_the_deep_level_pin(monkeypatch):
+    """Planted mistake: the Galerkin recursion in plain FP64 sparse products (no exact
+    recursion once the coefficients outgrow 53 bits). The deep-level pin must fail."""
+    import test_oracle_deep_galerkin as deep
+    monkeypatch.setattr(omg, "_fp64_product_is_exact", lambda *a: True)
+    o = omg.Oracle(deep.N, 2, omg.REDBLACK, omg.GALERKIN)
+    with pytest.raises(AssertionError):
+        deep.test_deep_galerkin_rows_are_the_exact_product_rounded_once(o, 19)
