@@ -1102,13 +1102,12 @@ __device__ __forceinline__ bool tail_node(const LevelDev<T>& L, int k, int& i, i
   return interior(L, i, j);
 }
 
-template <typename T, bool EXACT>
-__global__ void __launch_bounds__(kTailThreads, 1)
-    k_tail(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog, int nops) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int tid = (int)cluster.block_rank() * kTailThreads + threadIdx.x;
-  const int nth = (int)cluster.num_blocks() * kTailThreads;
+// The tail's op program (see TailOp) run by `nth` threads (thread index tid) with
+// sync() between dependent phases; sync() returns false when the threads must stop (a
+// bounded barrier gave up), and the program is abandoned.
+template <typename T, bool EXACT, class SYNC>
+__device__ __forceinline__ void tail_program(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog,
+                                             int nops, int tid, int nth, SYNC sync) {
   for (int p = 0; p < nops; ++p) {
     const int4 op = prog[p];
     const int l = op.y;
@@ -1135,7 +1134,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
             else
               dst[at] = is_red(L, i, j) == half ? relax_value<T, EXACT>(L, src, F, i, j, at) : src[at];
           }
-          cluster.sync();
+          if (!sync()) return;
         }
       } else {
         for (int k = tid; k < total; k += nth) {
@@ -1143,7 +1142,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
           const int64_t at = sidx(L, i, j);
           Tb[at] = relax_value<T, EXACT>(L, U, F, i, j, at);
         }
-        cluster.sync();
+        if (!sync()) return;
         for (int k = tid; k < total; k += nth) {
           if (!tail_node(L, k, i, j)) continue;
           const int64_t at = sidx(L, i, j);
@@ -1159,7 +1158,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         const int64_t at = sidx(L, i, j);
         Dd[at] = Arith<T>::sub(F[at], apply_at<T, EXACT>(L, U, i, j, at, nullptr));
       }
-      cluster.sync();
+      if (!sync()) return;
       const LevelDev<T>& Lc = *D->L[l + 1];
       T* Fc = D->f[l + 1];
       const int ctot = Lc.rows * Lc.cols;
@@ -1181,8 +1180,20 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         U[at] = Arith<T>::add(U[at], prolong_any<T, EXACT>(Lc, D->transfer[l], V, i, j));
       }
     }
-    cluster.sync();
+    if (!sync()) return;
   }
+}
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(kTailThreads, 1)
+    k_tail(const TailDesc<T>* __restrict__ D, const int4* __restrict__ prog, int nops) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  tail_program<T, EXACT>(D, prog, nops, (int)cluster.block_rank() * kTailThreads + threadIdx.x,
+                         (int)cluster.num_blocks() * kTailThreads, [&]() {
+                           cluster.sync();
+                           return true;
+                         });
 }
 
 // ---- batched level-synchronous step kernels ------------------------------------
@@ -1992,10 +2003,10 @@ NSMG_INSTANTIATE(float)
 // Relative residual of the finest level without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// residual norm: code running while a CUDA stream is being captured into a graph
-// (cudaMalloc is not capturable), real-time loops that must not hit the implicit
-// device synchronisation of cudaMalloc / cudaFree, or hosts that hand the library a
-// fixed memory budget and forbid allocation after set-up. For them the partial sums
+// residual norm: real-time loops that must not hit the implicit device
+// synchronisation of cudaMalloc / cudaFree, or hosts that hand the library a fixed
+// memory budget (or an arena they manage) and forbid allocation after set-up. For
+// them the partial sums
 // of the reduction live in a file-scope device array instead of in memory obtained
 // from the allocator: every GPU that loads this library holds
 // kStaticNormPartials x 2 doubles (32 KB) until the process exits.
