@@ -44,10 +44,13 @@
  * - Relative residual = ||f - L_h u||_2 / ||f||_2 over interior nodes (the h^d
  *   weight of the paper's grid norm, Sec. 2.1, cancels).
  * - Floating-point evaluation order (precision MG_PREC_FP64, fma_contract = 0):
- *   every operator application sums its nonzeros in increasing row-major
- *   position of the column, each product rounded separately; relaxation is
- *   u + r * fl(omega / a_pp) with r = f - (A u). Two implementations that follow
- *   this order produce the same iterates bit for bit.
+ *   every operator row (a_pq fixed) is split into groups of nonzeros of equal value;
+ *   the groups are ordered by the row-major position of their first column and each
+ *   group's columns in increasing row-major position; the row's value is
+ *   sum_g a_g * (x_g1 + x_g2 + ...), every sum left to right and every product and
+ *   sum rounded separately. Grid transfers sum their products in increasing position
+ *   of the column. Relaxation is u + r * fl(omega / a_pp) with r = f - (A u). Two
+ *   implementations that follow this order produce the same iterates bit for bit.
  */
 #ifndef NSMG_H
 #define NSMG_H

@@ -53,12 +53,16 @@ nonstandard coarsening", arXiv:2008.03885):
   rounding of deep Galerkin products) and whose zero-mean solution is 0.
 
 Floating-point evaluation order (so that any implementation following the same
-order reproduces every iterate bit for bit): each operator application
-y_p = sum_q a_pq x_q sums its nonzeros in increasing column order of a row-major
-(j, then i) numbering of the level's unknowns, starting from the first product,
-every product rounded separately (no fused multiply-add); coefficients are exact
-dyadic weights w times one scale s per level (a_pq = fl(w_pq * s)); a relaxation
-is u + r * fl(omega / a_pp) with r = f - (A u); a correction is u + (P v).
+order reproduces every iterate bit for bit): in each operator application
+y_p = sum_q a_pq x_q the row's nonzeros are split into groups of equal value a_g, the
+groups ordered by their first column and each group's columns in increasing order of
+a row-major (j, then i) numbering of the level's unknowns; y_p = sum_g a_g (x_g1 +
+x_g2 + ...), every sum left to right and every product and sum rounded separately (no
+fused multiply-add). The paper writes its stencils in this factored form (a weight
+times a sum of equally weighted neighbours, e.g. Eq. L_h_2d_4o), which this reading
+follows; the grid transfers R and P sum their products in column order. Coefficients
+are exact dyadic weights w times one scale s per level (a_pq = fl(w_pq * s)); a
+relaxation is u + r * fl(omega / a_pp) with r = f - (A u); a correction is u + (P v).
 """
 from __future__ import annotations
 
@@ -293,11 +297,17 @@ def interpolation(fine: Level, coarse: Level, coarsening: str, order: int = 2) -
 # A matrix is (rows, cols, numerators, e): entry = numerator / 2^e, numerators Python
 # integers (numpy object arrays), so products and sums are exact at any depth.
 def _dyadic_exponent(data: np.ndarray) -> int:
-    """Smallest e >= 0 with every entry times 2^e an integer (entries are dyadic)."""
-    e = 0
-    while data.size and not np.all(np.floor(data * 2.0 ** e) == data * 2.0 ** e):
-        e += 1
-        assert e < 1000, "not a dyadic matrix"
+    """Smallest e >= 0 with every entry times 2^e an integer (every double is a dyadic
+    fraction: mantissa m / 2^53 times 2^ex, so it needs 53 - ex - (trailing zero bits
+    of m) fraction bits)."""
+    d = data[data != 0]
+    if d.size == 0:
+        return 0
+    m, ex = np.frexp(np.abs(d))
+    M = (m * 2.0 ** 53).astype(np.int64)
+    tz = np.log2((M & -M).astype(np.float64)).astype(np.int64)
+    e = int(max(0, int((53 - ex - tz).max())))
+    assert np.all(np.floor(d * 2.0 ** e) == d * 2.0 ** e)
     return e
 
 
@@ -368,8 +378,9 @@ def _exact_round(E, shape) -> sp.csr_matrix:
     return m
 
 
-class Ell:
-    """A CSR matrix as padded rows with sorted columns, applied in column order."""
+class ColumnEll:
+    """A CSR matrix as padded rows with sorted columns, applied in column order: the
+    grid transfers, y = sum_k a_k x_k from the first product, left to right."""
 
     def __init__(self, m: sp.csr_matrix):
         m = m.tocsr()
@@ -393,6 +404,107 @@ class Ell:
         y = self.vals[0] * x[self.cols[0]]
         for k in range(1, self.width):
             y = y + self.vals[k] * x[self.cols[k]]
+        return y
+
+
+class Ell:
+    """A level operator applied row by row in the evaluation order of the header: each
+    row's nonzeros are split into groups of equal value, the groups ordered by the
+    column of their first nonzero and each group's nonzeros by column; the row's value
+    is sum_g c_g * (x_g1 + x_g2 + ...), every sum left to right and every operation
+    rounded separately (numpy FP64 ufuncs, one per operation, never fused). Stored as
+    padded slots [group, position in group, row]."""
+
+    def __init__(self, m: sp.csr_matrix):
+        m = m.tocsr()
+        m.sort_indices()
+        nrow = m.shape[0]
+        self.shape = m.shape
+        counts = np.diff(m.indptr)
+        W = int(counts.max()) if nrow else 0
+        if m.nnz == 0:
+            self.G = self.K = 0
+            return
+        # dense [row, column rank] copies of the rows (NaN-padded values never compare equal)
+        rows = np.repeat(np.arange(nrow), counts)
+        pos = np.arange(m.nnz) - np.repeat(m.indptr[:-1], counts)
+        V = np.full((nrow, W), np.nan)
+        C = np.zeros((nrow, W), dtype=np.int64)
+        V[rows, pos] = m.data
+        C[rows, pos] = m.indices
+        valid = ~np.isnan(V)
+        # first[r, k]: column rank of the first nonzero of row r equal in value to nonzero k.
+        # Rows repeat (every interior row of a level is the same stencil), so it is worked
+        # out once per distinct row: rows are bucketed by two hashes of their values' bit
+        # patterns and each bucket is checked to hold one distinct row.
+        Vh = np.where(valid, V, 0.0)
+        bits = Vh.view(np.uint64) ^ valid.astype(np.uint64)  # exact: the values' bit patterns
+
+        def mix(z):  # SplitMix64's finaliser: every output bit depends on every input bit
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            return z ^ (z >> np.uint64(31))
+
+        with np.errstate(over="ignore"):
+            # each word mixed together with its position, so that rearranged rows differ
+            posk = np.arange(1, W + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+            m1 = mix(bits ^ posk[None, :])
+            h1 = m1.sum(axis=1, dtype=np.uint64)
+            h2 = mix(m1 + posk[None, :]).sum(axis=1, dtype=np.uint64)
+        keys = np.stack([h1, h2, counts.astype(np.uint64)], axis=1)
+        _, rep, inv = np.unique(keys, axis=0, return_index=True, return_inverse=True)
+        inv = inv.reshape(-1)
+        assert np.array_equal(Vh, Vh[rep][inv]) and np.array_equal(counts, counts[rep][inv]), \
+            "two distinct operator rows share a bucket"
+        Vu = V[rep]
+        fu = np.tile(np.arange(W), (len(rep), 1))
+        for j in range(W):
+            for k in range(j + 1, W):
+                hit = (fu[:, k] == k) & (Vu[:, k] == Vu[:, j])
+                fu[hit, k] = j
+        first = fu[inv]
+        key = np.where(valid, first * (W + 1) + np.arange(W)[None, :], W * (W + 1) + np.arange(W)[None, :])
+        order = np.argsort(key, axis=1, kind="stable")
+        Vs = np.take_along_axis(V, order, axis=1)
+        Cs = np.take_along_axis(C, order, axis=1)
+        Fs = np.take_along_axis(first, order, axis=1)
+        vs = np.take_along_axis(valid, order, axis=1)
+        gstart = np.ones((nrow, W), dtype=bool)
+        gstart[:, 1:] = Fs[:, 1:] != Fs[:, :-1]
+        gstart &= vs
+        g_in_row = np.cumsum(gstart, axis=1) - 1
+        idx = np.tile(np.arange(W), (nrow, 1))
+        k_in_g = idx - np.maximum.accumulate(np.where(gstart, idx, 0), axis=1)
+        self.G = int(g_in_row[vs].max()) + 1
+        self.K = int(k_in_g[vs].max()) + 1
+        rr = np.tile(np.arange(nrow)[:, None], (1, W))
+        self.cols = np.zeros((self.G, self.K, nrow), dtype=np.int64)
+        self.valid = np.zeros((self.G, self.K, nrow), dtype=bool)
+        self.gval = np.zeros((self.G, nrow))
+        self.cols[g_in_row[vs], k_in_g[vs], rr[vs]] = Cs[vs]
+        self.valid[g_in_row[vs], k_in_g[vs], rr[vs]] = True
+        self.gval[g_in_row[gstart], rr[gstart]] = Vs[gstart]  # value of the group's first nonzero
+        self.gvalid = self.valid[:, 0, :]
+        self.full = [[bool(self.valid[g, k].all()) for k in range(self.K)] for g in range(self.G)]
+        self.any = [[bool(self.valid[g, k].any()) for k in range(self.K)] for g in range(self.G)]
+
+    def __matmul__(self, x: np.ndarray) -> np.ndarray:
+        if self.G == 0:
+            return np.zeros(self.shape[0])
+        y = None
+        for g in range(self.G):
+            S = x[self.cols[g, 0]]
+            for k in range(1, self.K):
+                if not self.any[g][k]:
+                    continue
+                t = S + x[self.cols[g, k]]
+                S = t if self.full[g][k] else np.where(self.valid[g, k], t, S)
+            P = self.gval[g] * S
+            if y is None:
+                y = np.where(self.gvalid[0], P, 0.0)
+            else:
+                t = y + P
+                y = t if self.full[g][0] else np.where(self.gvalid[g], t, y)
         return y
 
 
@@ -486,8 +598,8 @@ class Oracle:
             lev.A = (lev.W * lev.s).tocsr()  # elementwise fl(w * s)
             lev.A.sort_indices()
         self._A = [Ell(lev.A) for lev in self.levels]
-        self._P = [Ell(P) for P in self.P]
-        self._R = [Ell(R) for R in self.R]
+        self._P = [ColumnEll(P) for P in self.P]
+        self._R = [ColumnEll(R) for R in self.R]
         with np.errstate(divide="ignore"):  # a periodic single-node level has a_pp = 0 (never smoothed)
             self.wd = [self.opt.omega / lev.A.diagonal() for lev in self.levels]
         last = self.levels[-1]

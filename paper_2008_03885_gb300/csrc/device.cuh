@@ -40,20 +40,30 @@ struct Arith<float> {
   static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
 };
 
-// One class term by a single 16-byte load.
+// One class term by a single 16-byte load; `start` is set on the first term of a group
+// of equal coefficients (the flag travels in dx, see kTermStart).
 template <typename T>
-__device__ __forceinline__ ClassTerm<T> load_term(const ClassTerm<T>* p) {
+struct Term {
+  T c;
+  int dx, dy;
+  bool start;
+};
+template <typename T>
+__device__ __forceinline__ Term<T> load_term(const ClassTerm<T>* p) {
   const int4 w = __ldg(reinterpret_cast<const int4*>(p));
-  ClassTerm<T> t;
+  Term<T> t;
+  int dx;
   if (sizeof(T) == 8) {
     t.c = (T)__hiloint2double(w.y, w.x);
-    t.dx = w.z;
+    dx = w.z;
     t.dy = w.w;
   } else {
     t.c = (T)__int_as_float(w.x);
-    t.dx = w.y;
+    dx = w.y;
     t.dy = w.z;
   }
+  t.start = dx >= (kTermStart >> 1);
+  t.dx = t.start ? dx - kTermStart : dx;
   return t;
 }
 
@@ -76,6 +86,48 @@ template <typename T, bool EXACT>
 __device__ __forceinline__ T madd(T s, T c, T x) {
   return EXACT ? Arith<T>::add(s, Arith<T>::mul(c, x)) : Arith<T>::fma(c, x, s);
 }
+
+// One operator row in the evaluation order: terms arrive in evaluation order (groups of
+// equal coefficient, see LevelDev::c), `start` on the first term of each group.
+// EXACT: sum_g c_g * (x_g1 + x_g2 + ...), the group sums and the outer sum left to right,
+// every operation rounded separately. Otherwise one fused multiply-add per term, from
+// the first product.
+template <typename T, bool EXACT>
+struct RowSum {
+  T s = T(0);   // sum of the closed groups (EXACT) or running sum
+  T g = T(0);   // open group's sum of values
+  T cg = T(0);  // open group's coefficient
+  bool any = false, open = false;
+  __device__ __forceinline__ void add(T c, T x, bool start) {
+    if (EXACT) {
+      if (start) {
+        close();
+        g = x;
+        cg = c;
+        open = true;
+      } else {
+        g = Arith<T>::add(g, x);
+      }
+    } else {
+      s = any ? Arith<T>::fma(c, x, s) : Arith<T>::mul(c, x);
+      any = true;
+    }
+  }
+  __device__ __forceinline__ void close() {
+    if (EXACT && open) {
+      const T p = Arith<T>::mul(cg, g);
+      s = any ? Arith<T>::add(s, p) : p;
+      any = true;
+      open = false;
+    }
+  }
+  __device__ __forceinline__ T value() {
+    close();
+    return s;
+  }
+};
+
+__device__ __forceinline__ bool gbit(const uint32_t* m, int k) { return (m[k >> 5] >> (k & 31)) & 1u; }
 
 template <typename T>
 __device__ __forceinline__ int64_t sidx(const LevelDev<T>& L, int i, int j) {
@@ -135,27 +187,24 @@ __device__ __forceinline__ T relax_from_zero(T f, T wd) {
 template <typename T, bool EXACT, int CU = 4>
 __device__ __forceinline__ T apply_at(const LevelDev<T>& L, const T* __restrict__ u, int i, int j,
                                       int64_t at, T* wd) {
-  T s;
+  RowSum<T, EXACT> acc;
   if (fast_node(L, i, j)) {
     const int32_t* dl = L.delta[L.kind == kRot ? (i & 1) : 0];
-    s = Arith<T>::mul(L.c[0], u[at + dl[0]]);
 #pragma unroll CU
-    for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, L.c[k], u[at + dl[k]]);
+    for (int k = 0; k < L.nt; ++k) acc.add(L.c[k], u[at + dl[k]], gbit(L.gmask, k));
     if (wd) *wd = L.wd;
   } else {
     const int cl = class_of(L, i, j);
     const int2 e = L.cls[cl];
     const ClassTerm<T>* tt = L.terms + e.x;
-    s = T(0);
 #pragma unroll CU
     for (int k = 0; k < e.y; ++k) {
-      const ClassTerm<T> t = load_term(tt + k);
-      const T x = u[sidx(L, i + t.dx, j + t.dy)];
-      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
+      const Term<T> t = load_term(tt + k);
+      acc.add(t.c, u[sidx(L, i + t.dx, j + t.dy)], t.start);
     }
     if (wd) *wd = L.cls_wd[cl];
   }
-  return s;
+  return acc.value();
 }
 
 // New value of node (i, j) after one relaxation: u + (f - L u) * omega / a_pp.
@@ -176,13 +225,34 @@ struct RowsPer {
   static constexpr int value = 4;
 };
 
+// The NT-term fast stencils come in fixed group shapes (checked on the host, see
+// fast_groups_ok): 5 terms = four equal neighbours, then the centre; 9 terms = two
+// groups of four, then the centre (fourth-order cross, first Galerkin stencils).
+__host__ __device__ constexpr uint32_t fast_gmask(int nt) { return nt == 9 ? 0x111u : nt == 5 ? 0x11u : 0u; }
+
 template <typename T, bool EXACT, int NT>
 __device__ __forceinline__ T apply_fast(const T (&c)[NT], const int (&dl)[NT], const T* __restrict__ u,
                                         int64_t at) {
-  T s = Arith<T>::mul(c[0], u[at + dl[0]]);
+  if constexpr (EXACT && (NT == 5 || NT == 9)) {
+    T g0 = u[at + dl[0]];
 #pragma unroll
-  for (int k = 1; k < NT; ++k) s = madd<T, EXACT>(s, c[k], u[at + dl[k]]);
-  return s;
+    for (int k = 1; k < 4; ++k) g0 = Arith<T>::add(g0, u[at + dl[k]]);
+    T s = Arith<T>::mul(c[0], g0);
+    if (NT == 9) {
+      T g1 = u[at + dl[4]];
+#pragma unroll
+      for (int k = 5; k < 8; ++k) g1 = Arith<T>::add(g1, u[at + dl[k]]);
+      s = Arith<T>::add(s, Arith<T>::mul(c[4], g1));
+    }
+    return Arith<T>::add(s, Arith<T>::mul(c[NT - 1], u[at + dl[NT - 1]]));
+  } else {
+    // (fused multiply-adds; the EXACT form of other term counts is never instantiated for
+    // use: the launchers take the NT kernels only for 5 and 9 terms)
+    T s = Arith<T>::mul(c[0], u[at + dl[0]]);
+#pragma unroll
+    for (int k = 1; k < NT; ++k) s = Arith<T>::fma(c[k], u[at + dl[k]], s);
+    return s;
+  }
 }
 
 template <typename T, bool EXACT, int NT>

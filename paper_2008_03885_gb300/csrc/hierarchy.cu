@@ -355,6 +355,7 @@ int transfer_of(int coarsening, int l, int fine_kind, int transfer_order) {
 struct HostLevel {
   LevelShape shape;
   int per = 0;  // periodic level: unknowns 0 <= i, j < n, stencils wrap
+  int boundary_data = 0;  // level 0 with Dirichlet data g: fast stencils read the boundary
   int exact = 0;  // W is the rounding of the exact stencil Wx (boundary rows from Wx)
   XStencil Wx;
   int rows, cols, pitch;
@@ -368,23 +369,63 @@ struct HostLevel {
   std::vector<double> tc;
   double wd_fast = 0.0;
   int rx = 0, ry = 0;
-  std::vector<double> c;  // fast coefficients, (dy, dx) order
+  std::vector<double> c;  // fast coefficients, in evaluation order (group_terms)
   std::vector<int> dxs, dys;
+  std::vector<uint8_t> gstart;  // 1: the fast term starts a group
+  std::vector<uint8_t> tstart;  // class terms: 1 starts a group
   int64_t unknowns = 0;
 };
 
 int storage_cols(int kind, int n) { return kind == kAxis ? n + 1 : n / 2 + 1; }
 int round_pitch(int cols) { return (cols + 31) / 32 * 32; }
 
+// Evaluation order of an operator row (terms given in (dy, dx), i.e. storage column,
+// order): the terms are split into groups of equal coefficient, the groups ordered by
+// their first term and each group's terms kept in column order; `start` flags the first
+// term of every group. The row is then evaluated as sum_g c_g * (x_g1 + x_g2 + ...).
+void group_terms(std::vector<int>& dx, std::vector<int>& dy, std::vector<double>& c, std::vector<uint8_t>& start) {
+  const size_t m = c.size();
+  std::vector<int> grp(m, -1), first;  // group of each term; first term of each group
+  for (size_t k = 0; k < m; ++k) {
+    for (size_t g = 0; g < first.size() && grp[k] < 0; ++g)
+      if (c[first[g]] == c[k]) grp[k] = (int)g;
+    if (grp[k] < 0) {
+      grp[k] = (int)first.size();
+      first.push_back((int)k);
+    }
+  }
+  std::vector<int> dx2, dy2;
+  std::vector<double> c2;
+  start.clear();
+  for (size_t g = 0; g < first.size(); ++g)
+    for (size_t k = 0; k < m; ++k)
+      if (grp[k] == (int)g) {
+        start.push_back((int)k == first[g] ? 1 : 0);
+        dx2.push_back(dx[k]);
+        dy2.push_back(dy[k]);
+        c2.push_back(c[k]);
+      }
+  dx.swap(dx2);
+  dy.swap(dy2);
+  c.swap(c2);
+}
+
 void build_classes(HostLevel& L, double omega) {
   const int n = L.shape.n;
-  L.rx = radius(L.W, true);
-  L.ry = radius(L.W, false);
+  // Fast nodes use the plain stencil. With homogeneous Dirichlet data a fast stencil must
+  // not reach a boundary line either: the operator's rows drop boundary columns, and a
+  // term of value 0 kept in a row would change its groups of equal coefficient (the
+  // evaluation order). So the fast range starts one node further in (radius + 1);
+  // periodic rows wrap, and with Dirichlet data g the stencil reads the boundary values.
+  const int ext = (L.per || L.boundary_data) ? 0 : 1;
+  L.rx = radius(L.W, true) + ext;
+  L.ry = radius(L.W, false) + ext;
   for (const auto& t : L.W) {
     L.c.push_back(t.second * L.s);
     L.dxs.push_back(t.first.second);
     L.dys.push_back(t.first.first);
   }
+  group_terms(L.dxs, L.dys, L.c, L.gstart);
   L.wd_fast = omega / (L.W.at(Key(0, 0)) * L.s);
   const int R = std::max(L.rx, L.ry);
   const int e = n - L.per;  // last lattice index a fast stencil may reach
@@ -411,12 +452,20 @@ void build_classes(HostLevel& L, double omega) {
                                   : (L.per ? wrap_row(L.W, n, i, j) : fold_row(L.W, n, i, j));
       L.cls[k] = make_int2((int)L.tdx.size(), (int)row.size());
       double diag = 0.0;
+      std::vector<int> rdx, rdy;
+      std::vector<double> rc;
+      std::vector<uint8_t> rst;
       for (const auto& t : row) {
-        L.tdx.push_back(t.first.second);
-        L.tdy.push_back(t.first.first);
-        L.tc.push_back(t.second * L.s);
+        rdx.push_back(t.first.second);
+        rdy.push_back(t.first.first);
+        rc.push_back(t.second * L.s);
         if (t.first.first == 0 && t.first.second == 0) diag = t.second * L.s;
       }
+      group_terms(rdx, rdy, rc, rst);
+      L.tdx.insert(L.tdx.end(), rdx.begin(), rdx.end());
+      L.tdy.insert(L.tdy.end(), rdy.begin(), rdy.end());
+      L.tc.insert(L.tc.end(), rc.begin(), rc.end());
+      L.tstart.insert(L.tstart.end(), rst.begin(), rst.end());
       L.cls_wd[k] = omega / diag;
     }
 }
@@ -453,6 +502,7 @@ LevelDev<T> to_dev(const HostLevel& L) {
     d.sdy[k] = dy;
     d.delta[0][k] = dy * L.pitch + d.sdx[0][k];
     d.delta[1][k] = dy * L.pitch + d.sdx[1][k];
+    if (L.gstart[k]) d.gmask[k >> 5] |= 1u << (k & 31);
   }
   return d;
 }
@@ -604,6 +654,7 @@ bool build_operators(mg_handle* h, const std::vector<LevelShape>& shapes) {
   h->host.resize(nl);
   for (int l = 0; l < nl; ++l) h->host[l].shape = shapes[l];
   HostLevel& L0 = h->host[0];
+  L0.boundary_data = h->opt.dirichlet_data;
   Stencil base;
   double base_s;
   if (h->order == 2) {
@@ -718,7 +769,7 @@ mg_status upload_level(mg_handle* h, const HostLevel& L, LevelPair<T>& P, int bf
   for (size_t k = 0; k < tt.size(); ++k) {
     std::memset(&tt[k], 0, sizeof(tt[k]));
     tt[k].c = (T)L.tc[k];
-    tt[k].dx = L.tdx[k];
+    tt[k].dx = L.tdx[k] + (L.tstart[k] ? kTermStart : 0);
     tt[k].dy = L.tdy[k];
   }
   CK(cudaMemcpyAsync(cls, L.cls.data(), L.cls.size() * sizeof(int2), cudaMemcpyHostToDevice, h->priv));

@@ -2,10 +2,12 @@
 // red-black and Jacobi relaxation, residual, restriction, interpolation with
 // correction, coarsest solve, and a deterministic residual-norm reduction.
 //
-// Evaluation order (EXACT = true): each sum starts from its first product and
-// adds the following products in the order of the term list (sorted by (dy, dx)),
-// every product and sum rounded separately (__dmul_rn / __dadd_rn keep nvcc from
-// contracting them into FMAs). EXACT = false lets products fuse into FMAs.
+// Evaluation order (EXACT = true): an operator row is sum_g c_g * (x_g1 + x_g2 + ...)
+// over its groups of equal coefficient (groups ordered by their first term in (dy, dx)
+// order, each group's terms in (dy, dx) order), every sum left to right and every
+// product and sum rounded separately (__dmul_rn / __dadd_rn keep nvcc from contracting
+// them into FMAs); grid transfers sum their products in the order of their term lists.
+// EXACT = false lets products fuse into FMAs (one per term, in the same term order).
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
@@ -131,6 +133,7 @@ template <typename T>
 struct StencilSmem {
   T c[kMaxTerms];
   int d[2][kMaxTerms];
+  uint32_t gm[kMaxTerms / 32];
 };
 
 template <typename T>
@@ -140,6 +143,8 @@ __device__ __forceinline__ void stage_stencil(const LevelDev<T>& L, StencilSmem<
     sm.d[0][k] = L.delta[0][k];
     sm.d[1][k] = L.delta[1][k];
   }
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  if (t < kMaxTerms / 32) sm.gm[t] = L.gmask[t];
   __syncthreads();
 }
 
@@ -147,10 +152,10 @@ __device__ __forceinline__ void stage_stencil(const LevelDev<T>& L, StencilSmem<
 template <typename T, bool EXACT, int U = 4>
 __device__ __forceinline__ T apply_smem(const StencilSmem<T>& sm, int nt, int par, const T* __restrict__ u, int64_t at) {
   const int* dl = sm.d[par];
-  T s = Arith<T>::mul(sm.c[0], u[at + dl[0]]);
+  RowSum<T, EXACT> acc;
 #pragma unroll U
-  for (int k = 1; k < nt; ++k) s = madd<T, EXACT>(s, sm.c[k], u[at + dl[k]]);
-  return s;
+  for (int k = 0; k < nt; ++k) acc.add(sm.c[k], u[at + dl[k]], gbit(sm.gm, k));
+  return acc.value();
 }
 
 // Wide-stencil kernels. DEEP (FP32, levels below kGenDeepRows rows): the term loop
@@ -235,32 +240,31 @@ template <typename T, bool EXACT, int NT>
 __device__ __forceinline__ T relax_tile(const LevelDev<T>& L, const TileGeom& G, T wdf, const T* __restrict__ su,
                                         const T* __restrict__ sf, const T* sc, const int* soff, int e, int i, int j,
                                         int q0, int j0, int SW) {
-  T s, wd;
+  T wd;
+  RowSum<T, EXACT> acc;
   if (i >= G.rx && i <= G.n - G.rx && j >= G.ry && j <= G.n - G.ry) {
-    s = Arith<T>::mul(sc[0], su[e + soff[0]]);
     if (NT > 0) {
 #pragma unroll
-      for (int k = 1; k < NT; ++k) s = madd<T, EXACT>(s, sc[k], su[e + soff[k]]);
+      for (int k = 0; k < NT; ++k) acc.add(sc[k], su[e + soff[k]], gbit(L.gmask, k));
     } else {
 #pragma unroll 4
-      for (int k = 1; k < G.nt; ++k) s = madd<T, EXACT>(s, sc[k], su[e + soff[k]]);
+      for (int k = 0; k < G.nt; ++k) acc.add(sc[k], su[e + soff[k]], gbit(L.gmask, k));
     }
     wd = wdf;
   } else {
     const int cl = class_of(L, i, j);
     const int2 ce = L.cls[cl];
     const ClassTerm<T>* tt = L.terms + ce.x;
-    s = T(0);
 #pragma unroll 4
     for (int k = 0; k < ce.y; ++k) {
-      const ClassTerm<T> t = load_term(tt + k);
+      const Term<T> t = load_term(tt + k);
       const int ti = i + t.dx, tj = j + t.dy;
       const int tq = G.kind == kRot ? (ti >> 1) : ti;
-      const T x = su[(tj - j0) * SW + (tq - q0)];
-      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
+      acc.add(t.c, su[(tj - j0) * SW + (tq - q0)], t.start);
     }
     wd = L.cls_wd[cl];
   }
+  const T s = acc.value();
   const T r = Arith<T>::sub(sf[e], s);
   return EXACT ? Arith<T>::add(su[e], Arith<T>::mul(r, wd)) : Arith<T>::fma(r, wd, su[e]);
 }
@@ -1357,28 +1361,25 @@ struct TailStencil {
 template <typename T, bool EXACT>
 __device__ __forceinline__ T smem_apply(const LevelDev<T>& L, const T* u, int i, int j, T* wd, const T* __restrict__ cs,
                                         const int* __restrict__ os2) {
-  T s;
+  RowSum<T, EXACT> acc;
   if (fast_node(L, i, j)) {
     const int* os = os2 + (L.kind == kRot ? (i & 1) : 0) * kMaxTerms;
     const int e = smem_idx(L, i, j);
-    s = Arith<T>::mul(cs[0], u[e + os[0]]);
 #pragma unroll 8
-    for (int k = 1; k < L.nt; ++k) s = madd<T, EXACT>(s, cs[k], u[e + os[k]]);
+    for (int k = 0; k < L.nt; ++k) acc.add(cs[k], u[e + os[k]], gbit(L.gmask, k));
     if (wd) *wd = L.wd;
   } else {
     const int cl = class_of(L, i, j);
     const int2 ce = L.cls[cl];
     const ClassTerm<T>* tt = L.terms + ce.x;
-    s = T(0);
 #pragma unroll 4
     for (int k = 0; k < ce.y; ++k) {
-      const ClassTerm<T> t = load_term(tt + k);
-      const T x = u[smem_idx(L, i + t.dx, j + t.dy)];
-      s = k == 0 ? Arith<T>::mul(t.c, x) : madd<T, EXACT>(s, t.c, x);
+      const Term<T> t = load_term(tt + k);
+      acc.add(t.c, u[smem_idx(L, i + t.dx, j + t.dy)], t.start);
     }
     if (wd) *wd = L.cls_wd[cl];
   }
-  return s;
+  return acc.value();
 }
 
 template <typename T, bool EXACT>
@@ -1504,6 +1505,17 @@ dim3 grid_of(const LevelDev<T>& L) {
   return dim3((L.cols + kBX - 1) / kBX, (L.rows + kBY - 1) / kBY);
 }
 
+// Term count of the level's fast stencil if the register-coefficient (NT) kernels can
+// take it: 5 or 9 terms in the group shape apply_fast evaluates; 0 otherwise.
+template <typename T>
+int fast_nt(const LevelDev<T>& L) {
+  if (L.nt != 5 && L.nt != 9) return 0;
+  if (L.gmask[0] != fast_gmask(L.nt)) return 0;
+  for (int w = 1; w < kMaxTerms / 32; ++w)
+    if (L.gmask[w]) return 0;
+  return L.nt;
+}
+
 // Bounded grid of the norm reductions (see kMaxPartials).
 template <typename T>
 dim3 norm_grid(const LevelDev<T>& L) {
@@ -1562,8 +1574,9 @@ cudaError_t launch_half_sweep_nt(const LevelPair<T>& L, bool exact, const T* uin
 template <typename T>
 cudaError_t launch_half_sweep(const LevelPair<T>& L, bool exact, const T* uin, const T* f, T* uout,
                               int red, cudaStream_t s) {
-  if (L.h.nt == 5) return launch_half_sweep_nt<T, 5>(L, exact, uin, f, uout, red, s);
-  if (L.h.nt == 9) return launch_half_sweep_nt<T, 9>(L, exact, uin, f, uout, red, s);
+  const int ntf = fast_nt(L.h);
+  if (ntf == 5) return launch_half_sweep_nt<T, 5>(L, exact, uin, f, uout, red, s);
+  if (ntf == 9) return launch_half_sweep_nt<T, 9>(L, exact, uin, f, uout, red, s);
   dim3 g = grid_of(L.h);
   if (L.h.kind == kAxis) g.x = ((L.h.n + 2) / 2 + kBX - 1) / kBX;  // pairs (2p, 2p+1), 2p <= n
   const int by = gen_block_rows(L.h, g.x);
@@ -1641,8 +1654,9 @@ cudaError_t launch_residual_nt(const LevelPair<T>& L, bool exact, const T* u, co
 template <typename T>
 cudaError_t launch_residual(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* d,
                             cudaStream_t s) {
-  if (L.h.nt == 5) return launch_residual_nt<T, 5>(L, exact, u, f, d, s);
-  if (L.h.nt == 9) return launch_residual_nt<T, 9>(L, exact, u, f, d, s);
+  const int ntf = fast_nt(L.h);
+  if (ntf == 5) return launch_residual_nt<T, 5>(L, exact, u, f, d, s);
+  if (ntf == 9) return launch_residual_nt<T, 9>(L, exact, u, f, d, s);
   dim3 g = grid_of(L.h);
   const int by = gen_block_rows(L.h, g.x);
   g.y = (L.h.rows + by - 1) / by;
@@ -1789,7 +1803,7 @@ cudaError_t launch_resnorm_red_as(const LevelPair<T>& L, const T* u, const T* f,
 template <typename T>
 cudaError_t launch_resnorm_red(const LevelPair<T>& L, bool exact, const T* u, const T* f, T* uout, int red,
                                double* partial, double* out, cudaStream_t s) {
-  const int nt = L.h.kind == kAxis ? L.h.nt : 0;
+  const int nt = L.h.kind == kAxis ? fast_nt(L.h) : 0;
   if (nt == 9)
     return exact ? launch_resnorm_red_as<T, true, 9>(L, u, f, uout, red, partial, out, s)
                  : launch_resnorm_red_as<T, false, 9>(L, u, f, uout, red, partial, out, s);
@@ -1839,10 +1853,11 @@ cudaError_t launch_ir_residual_as(const LevelPair<double>& L, const double* u, c
 cudaError_t launch_ir_residual(const LevelPair<double>& L, bool exact, const double* u, const double* f,
                                const LevelPair<float>& L32, float* r32, double scale, double* partial,
                                double* out, cudaStream_t s, int bf16, float* t32) {
-  if (L.h.nt == 9)
+  const int ntf = fast_nt(L.h);
+  if (ntf == 9)
     return exact ? launch_ir_residual_as<true, 9>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32)
                  : launch_ir_residual_as<false, 9>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32);
-  if (L.h.nt == 5)
+  if (ntf == 5)
     return exact ? launch_ir_residual_as<true, 5>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32)
                  : launch_ir_residual_as<false, 5>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32);
   return exact ? launch_ir_residual_as<true, 0>(L, u, f, L32, r32, scale, partial, out, s, bf16, t32)

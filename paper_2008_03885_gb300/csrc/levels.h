@@ -20,7 +20,9 @@ enum Transfer : int32_t {
 };
 
 // A merged boundary-class term: coefficient and lattice offset in one aligned 16-byte
-// record, so that one vector load fetches it.
+// record, so that one vector load fetches it. The first term of each group of equal
+// coefficients (see LevelDev::gmask) carries kTermStart added to dx.
+constexpr int32_t kTermStart = 1 << 20;
 template <typename T>
 struct __align__(16) ClassTerm {
   T c;
@@ -35,7 +37,7 @@ struct __align__(16) ClassTerm {
 // boundary entries of every array are 0. Periodic (per = 1): nodes 0 <= i, j < n are
 // the unknowns (node n is node 0); row and column n are never read.
 //
-// The operator is a constant stencil (dx, dy, c) sorted by (dy, dx) for "fast"
+// The operator is a constant stencil (dx, dy, c) for "fast"
 // nodes, rx <= i <= n - per - rx (the same for j with ry): their stencil reaches no
 // ghost (Dirichlet) and does not wrap (periodic). Other nodes use a per-class merged
 // term list: the stencil folded by odd reflection at the boundary lines with
@@ -51,7 +53,10 @@ struct LevelDev {
   int32_t nt, rx, ry;
   int32_t small, clsw;
   T wd;                       // omega / a_pp at fast nodes
-  T c[kMaxTerms];             // fast-node coefficients
+  T c[kMaxTerms];             // fast-node coefficients, in evaluation order: groups of equal
+                              // coefficient (ordered by their first term in (dy, dx) order),
+                              // each group's terms in (dy, dx) order
+  uint32_t gmask[kMaxTerms / 32];  // bit k: fast term k starts a group
   int32_t delta[2][kMaxTerms];  // storage offsets of the fast terms for i even / odd
   int32_t sdx[2][kMaxTerms];    // storage-column shift of the fast terms for i even / odd
   int32_t sdy[kMaxTerms];       // row shift of the fast terms

@@ -9,8 +9,8 @@
 // consecutive shared-memory words.
 //
 // Arithmetic per node is exactly that of the per-step kernels (kernels.cu): the same
-// fast stencil in registers (a 5-point or 9-point cross, terms in (dy, dx) order) or the
-// same boundary-class term list, the same multiply / fused-multiply-add sequence, and
+// fast stencil in registers (a 5-point or 9-point cross, terms in evaluation order) or
+// the same boundary-class term list, the same grouped sums (or fused multiply-adds), and
 // the same relaxation u + r * omega / a_pp; so a fused group of steps gives the same bits
 // as the separate launches.
 #include <cudaTypedefs.h>
@@ -103,37 +103,41 @@ __device__ __forceinline__ float relax(float s, float f, float u, float wd) {
   return EXACT ? Arith<float>::add(u, Arith<float>::mul(r, wd)) : Arith<float>::fma(r, wd, u);
 }
 
-// (L x)(i, j): the fast cross stencil with coefficients c (terms in (dy, dx) order) or
-// the node's boundary-class term list. x(i, j) returns the value of lattice node (i, j).
+// (L x)(i, j): the fast cross stencil with coefficients c (in evaluation order) or the
+// node's boundary-class term list. x(i, j) returns the value of lattice node (i, j).
 template <bool EXACT, int NT, class X>
 __device__ __forceinline__ float stencil(const LevelDev<float>& L, const float (&c)[NT], int i, int j, X x) {
   if (fast_node_c<false>(L, i, j)) {
+    // terms in evaluation order: 9 points = +-2 neighbours, +-1 neighbours, centre;
+    // 5 points = the four neighbours, the centre
+    RowSum<float, EXACT> acc;
     if (NT == 9) {
-      float s = Arith<float>::mul(c[0], x(i, j - 2));
-      s = madd<float, EXACT>(s, c[1], x(i, j - 1));
-      s = madd<float, EXACT>(s, c[2], x(i - 2, j));
-      s = madd<float, EXACT>(s, c[3], x(i - 1, j));
-      s = madd<float, EXACT>(s, c[4], x(i, j));
-      s = madd<float, EXACT>(s, c[5], x(i + 1, j));
-      s = madd<float, EXACT>(s, c[6], x(i + 2, j));
-      s = madd<float, EXACT>(s, c[7], x(i, j + 1));
-      return madd<float, EXACT>(s, c[8], x(i, j + 2));
+      acc.add(c[0], x(i, j - 2), true);
+      acc.add(c[1], x(i - 2, j), false);
+      acc.add(c[2], x(i + 2, j), false);
+      acc.add(c[3], x(i, j + 2), false);
+      acc.add(c[4], x(i, j - 1), true);
+      acc.add(c[5], x(i - 1, j), false);
+      acc.add(c[6], x(i + 1, j), false);
+      acc.add(c[7], x(i, j + 1), false);
+      acc.add(c[8], x(i, j), true);
+    } else {
+      acc.add(c[0], x(i, j - 1), true);
+      acc.add(c[1], x(i - 1, j), false);
+      acc.add(c[2], x(i + 1, j), false);
+      acc.add(c[3], x(i, j + 1), false);
+      acc.add(c[4], x(i, j), true);
     }
-    float s = Arith<float>::mul(c[0], x(i, j - 1));
-    s = madd<float, EXACT>(s, c[1], x(i - 1, j));
-    s = madd<float, EXACT>(s, c[2], x(i, j));
-    s = madd<float, EXACT>(s, c[3], x(i + 1, j));
-    return madd<float, EXACT>(s, c[4], x(i, j + 1));
+    return acc.value();
   }
   const int2 e = L.cls[class_of(L, i, j)];
   const ClassTerm<float>* tt = L.terms + e.x;
-  float s = 0.f;
+  RowSum<float, EXACT> acc;
   for (int k = 0; k < e.y; ++k) {
-    const ClassTerm<float> t = load_term(tt + k);
-    const float v = x(i + t.dx, j + t.dy);
-    s = k == 0 ? Arith<float>::mul(t.c, v) : madd<float, EXACT>(s, t.c, v);
+    const Term<float> t = load_term(tt + k);
+    acc.add(t.c, x(i + t.dx, j + t.dy), t.start);
   }
-  return s;
+  return acc.value();
 }
 
 // Tile origin of the block.
@@ -212,22 +216,45 @@ struct SBox {  // a staged TMA box (both colours), halo (HX, HY)
 // colour's source `so` (base bo), even ones the node's own colour `ss` (base bs).
 template <bool EXACT, int NT, class SO, class SS>
 __device__ __forceinline__ float cross(const float (&c)[NT], const SO& so, int bo, const SS& ss, int bs, int a) {
+  // terms in evaluation order (group-major, see LevelDev::c): 9 points = the four
+  // +-2 neighbours, the four +-1 neighbours, the centre; 5 points = the four neighbours,
+  // the centre
   if constexpr (NT == 9) {
-    float s = Arith<float>::mul(c[0], ss.template get<0, -2>(bs, a));
-    s = madd<float, EXACT>(s, c[1], so.template get<0, -1>(bo, a));
-    s = madd<float, EXACT>(s, c[2], ss.template get<-2, 0>(bs, a));
-    s = madd<float, EXACT>(s, c[3], so.template get<-1, 0>(bo, a));
-    s = madd<float, EXACT>(s, c[4], ss.template get<0, 0>(bs, a));
-    s = madd<float, EXACT>(s, c[5], so.template get<1, 0>(bo, a));
-    s = madd<float, EXACT>(s, c[6], ss.template get<2, 0>(bs, a));
-    s = madd<float, EXACT>(s, c[7], so.template get<0, 1>(bo, a));
-    return madd<float, EXACT>(s, c[8], ss.template get<0, 2>(bs, a));
+    const float x0 = ss.template get<0, -2>(bs, a), x1 = ss.template get<-2, 0>(bs, a);
+    const float x2 = ss.template get<2, 0>(bs, a), x3 = ss.template get<0, 2>(bs, a);
+    const float x4 = so.template get<0, -1>(bo, a), x5 = so.template get<-1, 0>(bo, a);
+    const float x6 = so.template get<1, 0>(bo, a), x7 = so.template get<0, 1>(bo, a);
+    const float x8 = ss.template get<0, 0>(bs, a);
+    if constexpr (EXACT) {
+      const float g0 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x0, x1), x2), x3);
+      const float g1 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x4, x5), x6), x7);
+      return Arith<float>::add(Arith<float>::add(Arith<float>::mul(c[0], g0), Arith<float>::mul(c[4], g1)),
+                               Arith<float>::mul(c[8], x8));
+    } else {
+      float s = Arith<float>::mul(c[0], x0);
+      s = Arith<float>::fma(c[1], x1, s);
+      s = Arith<float>::fma(c[2], x2, s);
+      s = Arith<float>::fma(c[3], x3, s);
+      s = Arith<float>::fma(c[4], x4, s);
+      s = Arith<float>::fma(c[5], x5, s);
+      s = Arith<float>::fma(c[6], x6, s);
+      s = Arith<float>::fma(c[7], x7, s);
+      return Arith<float>::fma(c[8], x8, s);
+    }
   } else {
-    float s = Arith<float>::mul(c[0], so.template get<0, -1>(bo, a));
-    s = madd<float, EXACT>(s, c[1], so.template get<-1, 0>(bo, a));
-    s = madd<float, EXACT>(s, c[2], ss.template get<0, 0>(bs, a));
-    s = madd<float, EXACT>(s, c[3], so.template get<1, 0>(bo, a));
-    return madd<float, EXACT>(s, c[4], so.template get<0, 1>(bo, a));
+    const float x0 = so.template get<0, -1>(bo, a), x1 = so.template get<-1, 0>(bo, a);
+    const float x2 = so.template get<1, 0>(bo, a), x3 = so.template get<0, 1>(bo, a);
+    const float x4 = ss.template get<0, 0>(bs, a);
+    if constexpr (EXACT) {
+      const float g0 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x0, x1), x2), x3);
+      return Arith<float>::add(Arith<float>::mul(c[0], g0), Arith<float>::mul(c[4], x4));
+    } else {
+      float s = Arith<float>::mul(c[0], x0);
+      s = Arith<float>::fma(c[1], x1, s);
+      s = Arith<float>::fma(c[2], x2, s);
+      s = Arith<float>::fma(c[3], x3, s);
+      return Arith<float>::fma(c[4], x4, s);
+    }
   }
 }
 
@@ -657,13 +684,17 @@ bool tile_eligible(const LevelPair<float>& P) {
   if (L.kind != kAxis || L.per || L.bf16 || L.rows < kTileMinRows) return false;
   if (L.pitch % 4 != 0) return false;  // TMA row stride: 16 bytes
   // the fast stencil must be the 5-point or 9-point cross with terms in (dy, dx) order
-  static const int x5[5] = {0, -1, 0, 1, 0}, y5[5] = {-1, 0, 0, 0, 1};
-  static const int x9[9] = {0, 0, -2, -1, 0, 1, 2, 0, 0}, y9[9] = {-2, -1, 0, 0, 0, 0, 0, 1, 2};
+  // (offsets in evaluation order: groups of equal coefficient, see LevelDev::c)
+  static const int x5[5] = {0, -1, 1, 0, 0}, y5[5] = {-1, 0, 0, 1, 0};
+  static const int x9[9] = {0, -2, 2, 0, 0, -1, 1, 0, 0}, y9[9] = {-2, 0, 0, 2, -1, 0, 0, 1, 0};
   const int* xs = L.nt == 5 ? x5 : L.nt == 9 ? x9 : nullptr;
   const int* ys = L.nt == 5 ? y5 : y9;
   if (!xs) return false;
   for (int k = 0; k < L.nt; ++k)
     if (L.sdx[0][k] != xs[k] || L.sdy[k] != ys[k]) return false;
+  if (L.gmask[0] != fast_gmask(L.nt)) return false;
+  for (int w = 1; w < kMaxTerms / 32; ++w)
+    if (L.gmask[w]) return false;
   return true;
 }
 

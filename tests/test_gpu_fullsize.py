@@ -6,7 +6,9 @@ cycle (operator, residual, one red-black sweep, restriction, interpolation) are
 checked bit for bit on sampled nodes whose values are computed here one at a time from
 the definition: the level's stencil weights (independent of N; read off an interior
 row of a small oracle hierarchy), folded by odd reflection with the oracle's `fold`,
-merged, summed in column order with every product rounded separately. Whole solves at
+merged, evaluated in the library's order (groups of equal coefficient, each group's
+values summed, then multiplied; transfers in column order), every operation rounded
+separately. Whole solves at
 4097^2 (FP64) and 8193^2 (mixed precision) are checked by an independent plain-PyTorch
 FP64 residual of the returned solution.
 """
@@ -51,6 +53,28 @@ def node_row(st, n, i, j, scale):
         key = (int(tj[0]), int(ti[0]))
         acc[key] = acc.get(key, 0.0) + float(si[0] * sj[0]) * w
     return [(tj, ti, w * scale) for (tj, ti), w in sorted(acc.items())]
+
+
+def grouped_sum(terms, val):
+    """An operator row in the evaluation order: the terms (column order) split into groups
+    of equal coefficient, groups ordered by their first term; sum_g c_g * (x_g1 + ...),
+    every operation rounded (plain Python floats)."""
+    groups = []
+    for tj, ti, c in terms:
+        for g in groups:
+            if g[0] == c:
+                g[1].append(val(ti, tj))
+                break
+        else:
+            groups.append([c, [val(ti, tj)]])
+    s = None
+    for c, xs in groups:
+        g = xs[0]
+        for x in xs[1:]:
+            g = g + x
+        p = c * g
+        s = p if s is None else s + p
+    return s
 
 
 def ordered_sum(terms, val):
@@ -134,7 +158,7 @@ def test_operator_residual_and_sweep_on_sampled_nodes(hier, l):
     def relax(i, j, val):
         r = row(i, j)
         diag = [c for tj, ti, c in r if ti == i and tj == j][0]
-        return val(i, j) + (F(i, j) - ordered_sum(r, val)) * (1.0 / diag)
+        return val(i, j) + (F(i, j) - grouped_sum(r, val)) * (1.0 / diag)
 
     half = {}
 
@@ -146,7 +170,7 @@ def test_operator_residual_and_sweep_on_sampled_nodes(hier, l):
         return half[(i, j)]
 
     for i, j in sample_nodes(n, kind, 300 + l):
-        s = ordered_sum(row(i, j), U)
+        s = grouped_sum(row(i, j), U)
         assert ga(i, j) == s, ("apply", l, i, j)
         assert gr(i, j) == F(i, j) - s, ("residual", l, i, j)
         want = after_red(i, j) if red(i, j) else relax(i, j, after_red)
