@@ -38,7 +38,7 @@ WORKLOAD = ("2D Poisson -Lap u = f, 4th-order 9-point Laplacian, 4097x4097 nodes
 # DRAM bytes (read + write) per launch of the dominant kernel, k_half_sweep_nt<double,
 # exact, 9> on level 0, from one ncu capture of `bench.py --profile-case` (the summary
 # under profiles/ names the kernel and workload); None whenever that kernel changes.
-DOMINANT_KERNEL_TRAFFIC_BYTES = 373.26e6
+DOMINANT_KERNEL_TRAFFIC_BYTES = 373.25e6
 
 # FP64 peak of GB300: 1.25 TFLOP/s nominal (an FMA counts two flops). MEASURED_PEAKS.json
 # carries no FP64 figure; the measured DFMA issue rate (600 G/s, 1.20 TFLOP/s) is quoted
@@ -371,10 +371,6 @@ def run_ours(args, ws, rank, local):
                               "transfer_order": extra.get("transfer_order", 2),
                               "finest_kernel_ms": {k: v[0] for k, v in vt.items()},
                               "finest_kernel_launches": {k: v[1] for k, v in vt.items()}}
-            if extra.get("precision") == mg.MG_PREC_MIXED_FP32:
-                # FP32 half-sweep on level 0: 12 bytes per node (read u, f; write u)
-                sm_ms, sm_n = vt["smooth"]
-                variants[name]["fp32_half_sweep_gbs"] = 3 * (N + 1) ** 2 * 4 / (sm_ms / max(sm_n, 1) * 1e-3) / 1e9
             hv.close()
     large = run_mixed_large(args) if not args.quick and not args.no_extras else None
     batched = run_batched(args) if not args.quick and not args.no_extras else None
@@ -410,8 +406,11 @@ def run_ours(args, ws, rank, local):
                      "peak_kind": "FP64 1.25 TFLOP/s nominal (FMA = 2 flops); no FP64 figure in "
                                   "MEASURED_PEAKS.json",
                      "frac_of_measured_dfma_rate": achieved_tflops / FP64_DFMA_MEASURED_TFLOPS,
-                     "note": "exact evaluation order (no FMA): DADD/DMUL issue at 0.506 T/s measured, so "
-                             "this kernel cannot exceed 0.40 of the nominal FP64 peak",
+                     "note": "exact evaluation order (no FMA; each row's groups of equal coefficient summed "
+                             "then multiplied): 14 DADD/DMUL per updated node for the method's 21 flops, issued "
+                             "at most 0.506 T/s (measured), so this kernel cannot exceed 0.61 of the nominal "
+                             "FP64 peak",
+                     "fp64_ops_per_updated_node": 14,
                      "hbm_gbs_algorithmic": achieved_gbs, "hbm_frac_algorithmic": achieved_gbs / hbm_peak,
                      "hbm_peak_gbs": hbm_peak, "hbm_peak_kind": peak_kind,
                      "share_of_finest_level_kernel_time": sm_ms / total_kernel_ms if total_kernel_ms else None},
@@ -451,18 +450,24 @@ def run_ours(args, ws, rank, local):
 def fp32_smoothing_roofline(mixed, hbm_peak, peak_kind):
     """HBM roofline of the mixed path's level-0 FP32 red-black smoothing, on the method's
     algorithmic bytes: 12 B per node per full sweep (read u and f, write u once), i.e.
-    6 B per node per half-sweep. Per refinement step V(2,1) makes 2 (nu1 + nu2) = 6
-    half-sweeps on level 0, one of them inside the FP64 refinement residual (timed with
-    the norm class), so the smoothing launches carry 5 of them."""
+    6 B per node per half-sweep; V(2,1) makes 2 (nu1 + nu2) = 6 half-sweeps per
+    refinement step on level 0. With the TMA tile kernels (4097^2) they run as two
+    launches per step: the presmooth (nu1 sweeps from zero) and one post-smoothing
+    sweep. Without them (per-half-sweep launches) the first red half-sweep runs inside
+    the FP64 refinement residual (timed with the norm class), so the smoothing launches
+    carry 5 of the 6."""
     if not mixed:
         return None
     sm_ms, sm_n = mixed["finest_kernel_ms"]["smooth"], mixed["finest_kernel_launches"]["smooth"]
     steps = mixed["cycles"]
-    alg = steps * (2 * (NU1 + NU2) - 1) * 6 * (N + 1) ** 2
+    tiles = sm_n == 2 * steps
+    half_sweeps = 2 * (NU1 + NU2) - (0 if tiles else 1)
+    alg = steps * half_sweeps * 6 * (N + 1) ** 2
     gbs = alg / (sm_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
             "peak_kind": peak_kind, "algorithmic_bytes_per_solve": alg, "launches_per_solve": sm_n,
-            "ms_per_solve": sm_ms, "kernel": "level-0 FP32 smoothing of the mixed path (4097^2, order 4)"}
+            "half_sweeps_per_step": half_sweeps, "tile_kernels": tiles, "ms_per_solve": sm_ms,
+            "kernel": "level-0 FP32 smoothing of the mixed path (4097^2, order 4)"}
 
 
 def run_mixed_large(args):
