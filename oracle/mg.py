@@ -51,6 +51,13 @@ nonstandard coarsening", arXiv:2008.03885):
   zero-mean solution, computed with the constant mode removed explicitly. Periodic
   hierarchies coarsen down to a single node, whose operator row is zero (up to the
   rounding of deep Galerkin products) and whose zero-mean solution is 0.
+* Exact coarsest solve with more than one unknown (Dirichlet, n_min > 2 or a
+  truncated hierarchy; Algorithm "MG" asks only for an exact solve, so this is a
+  reading): the coarsest operator A (symmetric positive definite) is factored once as
+  A = L L^T by Cholesky, its inverse factor G = L^-1 is formed, and each solve is
+  x = G^T (G d): two triangular products with no sequential dependence between rows.
+  The operation order is fixed (see dense_coarse_factor) so that an implementation
+  following it reproduces x bit for bit. One unknown keeps x = d / a_pp.
 
 Floating-point evaluation order (so that any implementation following the same
 order reproduces every iterate bit for bit): in each operator application
@@ -378,6 +385,58 @@ def _exact_round(E, shape) -> sp.csr_matrix:
     return m
 
 
+DENSE_MAX_UNKNOWNS = 1024  # coarsest systems up to this size use the factored solve
+
+
+def dense_coarse_factor(A: np.ndarray) -> np.ndarray:
+    """Inverse Cholesky factor G = L^-1 of a symmetric positive definite A (FP64), in a
+    fixed order, every product and sum rounded separately:
+
+    Cholesky by columns j = 0, 1, ...: s = A_jj - L_j0 L_j0 - L_j1 L_j1 - ... (k
+    ascending), L_jj = sqrt(s), r_j = 1 / L_jj; for i > j, t = A_ij - L_i0 L_j0 - ...
+    - L_i,j-1 L_j,j-1 and L_ij = t r_j.
+    Inverse factor by rows i: G_ii = r_i and, for c < i, G_ic = -((L_ic G_cc +
+    L_i,c+1 G_c+1,c + ... + L_i,i-1 G_i-1,c) r_i), the sum from its first product with
+    k ascending. G L = I follows from the forward substitution L G = I read row by row."""
+    m = A.shape[0]
+    L = np.zeros((m, m))
+    r = np.zeros(m)
+    for j in range(m):
+        s = A[j, j]
+        col = A[j + 1:, j].copy()
+        for k in range(j):
+            s = s - L[j, k] * L[j, k]
+            col = col - L[j + 1:, k] * L[j, k]
+        assert s > 0.0, "coarsest operator is not positive definite"
+        L[j, j] = math.sqrt(s)
+        r[j] = 1.0 / L[j, j]
+        L[j + 1:, j] = col * r[j]
+    G = np.zeros((m, m))
+    for i in range(m):
+        G[i, i] = r[i]
+        acc = np.zeros(i)
+        for k in range(i):
+            acc[k] = L[i, k] * G[k, k]  # first product of column k's sum
+            acc[:k] = acc[:k] + L[i, k] * G[k, :k]
+        G[i, :i] = -(acc * r[i])
+    return G
+
+
+def dense_coarse_solve(G: np.ndarray, d: np.ndarray) -> np.ndarray:
+    """x = G^T (G d) with G lower triangular: y_i = G_i0 d_0 + ... + G_ii d_i and
+    x_i = G_ii y_i + G_i+1,i y_i+1 + ... + G_m-1,i y_m-1, each sum from its first product
+    with k ascending, products and sums rounded separately."""
+    m = d.size
+    y = G[:, 0] * d[0]
+    for k in range(1, m):
+        y[k:] = y[k:] + G[k:, k] * d[k]
+    x = np.zeros(m)
+    for k in range(m):
+        x[k] = G[k, k] * y[k]
+        x[:k] = x[:k] + G[k, :k] * y[k]
+    return x
+
+
 class ColumnEll:
     """A CSR matrix as padded rows with sorted columns, applied in column order: the
     grid transfers, y = sum_k a_k x_k from the first product, left to right."""
@@ -604,6 +663,9 @@ class Oracle:
             self.wd = [self.opt.omega / lev.A.diagonal() for lev in self.levels]
         last = self.levels[-1]
         self._coarse_dense = last.A.toarray()
+        self._coarse_G = None
+        if not self.periodic and 1 < last.size <= DENSE_MAX_UNKNOWNS:
+            self._coarse_G = dense_coarse_factor(self._coarse_dense)
         self._g = None  # nonzero Dirichlet data (set_boundary), level 0 only
 
     # ---- nonzero Dirichlet data (second order) ------------------------------
@@ -686,6 +748,9 @@ class Oracle:
             return np.linalg.solve(self._coarse_dense + np.full((m, m), 1.0 / m), d - d.mean())
         if d.size == 1:
             return d / self._coarse_dense[0, 0]
+        if self._coarse_G is not None:
+            return dense_coarse_solve(self._coarse_G, d)
+        # larger truncated hierarchies (printed-rate pins only): LAPACK's solve
         return np.linalg.solve(self._coarse_dense, d)
 
     def cycle_level(self, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:

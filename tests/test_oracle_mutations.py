@@ -267,3 +267,66 @@ def test_fp64_galerkin_products_fail_the_deep_level_pin(monkeypatch):
     o = omg.Oracle(deep.N, 2, omg.REDBLACK, omg.GALERKIN)
     with pytest.raises(AssertionError):
         deep.test_deep_galerkin_rows_are_the_exact_product_rounded_once(o, 19)
+
+
+import test_oracle_dense_coarse as dpins
+
+DENSE_BATTERY = [
+    ("exact rational solution", lambda: dpins.test_dense_solve_matches_exact_rational_solution(
+        4, omg.REDBLACK, omg.GALERKIN, 8)),
+    ("library Cholesky factor", lambda: dpins.test_inverse_factor_inverts_the_library_cholesky_factor(8)),
+    ("single-level closed form", lambda: dpins.test_single_level_hierarchy_is_the_closed_form_solve(4)),
+    ("two-level direct solver (dense)", dpins.test_two_level_direct_solver_with_dense_coarsest_level),
+]
+
+
+def dense_not_transposed(monkeypatch):
+    """Back substitution with G instead of G^T."""
+    orig = omg.Oracle.coarse_solve
+
+    def bad_solve(self, d):
+        if self._coarse_G is None:
+            return orig(self, d)
+        y = self._coarse_G @ d
+        return self._coarse_G @ y
+    monkeypatch.setattr(omg.Oracle, "coarse_solve", bad_solve)
+
+
+def dense_inverse_sign(monkeypatch):
+    """The inverse factor's off-diagonal entries without their minus sign."""
+    orig = omg.dense_coarse_factor
+
+    def bad(A):
+        G = orig(A)
+        return np.diag(np.diag(G)) - np.tril(G, -1)
+    monkeypatch.setattr(omg, "dense_coarse_factor", bad)
+
+
+def dense_pivot_not_inverted(monkeypatch):
+    """L_ij = t / r_j written as t * L_jj (the pivot not inverted) in the factor."""
+    def bad(A):
+        m = A.shape[0]
+        L = np.zeros((m, m))
+        for j in range(m):
+            s = A[j, j] - np.dot(L[j, :j], L[j, :j])
+            L[j, j] = np.sqrt(s)
+            L[j + 1:, j] = (A[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) * L[j, j]
+        return np.linalg.inv(L)
+    monkeypatch.setattr(omg, "dense_coarse_factor", bad)
+
+
+DENSE_MUTATIONS = {
+    "dense coarsest: back substitution with G, not G^T": dense_not_transposed,
+    "dense coarsest: inverse factor sign dropped": dense_inverse_sign,
+    "dense coarsest: pivot not inverted": dense_pivot_not_inverted,
+}
+
+
+def test_dense_battery_passes_on_the_oracle_as_written():
+    assert failures(DENSE_BATTERY) == []
+
+
+@pytest.mark.parametrize("name", sorted(DENSE_MUTATIONS))
+def test_planted_dense_coarsest_mistake_is_caught(name, monkeypatch):
+    DENSE_MUTATIONS[name](monkeypatch)
+    assert failures(DENSE_BATTERY), f"no dense-coarsest pin caught: {name}"
