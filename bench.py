@@ -40,6 +40,11 @@ WORKLOAD = ("2D Poisson -Lap u = f, 4th-order 9-point Laplacian, 4097x4097 nodes
 # under profiles/ names the kernel and workload); None whenever that kernel changes.
 DOMINANT_KERNEL_TRAFFIC_BYTES = 373.25e6
 
+# The batched and served problems stop coarsening at a 16-cell axis grid and solve its
+# 225 unknowns exactly with the dense factor (fewer near-empty small levels); the
+# headline workload coarsens to one unknown.
+N_MIN_SMALL = 16
+
 # FP64 peak of GB300: 1.25 TFLOP/s nominal (an FMA counts two flops). MEASURED_PEAKS.json
 # carries no FP64 figure; the measured DFMA issue rate (600 G/s, 1.20 TFLOP/s) is quoted
 # beside it. Flops per updated node of a half-sweep: 2 s for the stencil application of
@@ -333,6 +338,9 @@ def run_ours(args, ws, rank, local):
                 ("redblack_nongalerkin", "redblack", "nongalerkin", 1.0, {}),
                 ("standard_galerkin_omega1.1", "standard", "galerkin", 1.1, {}),
                 ("fp64_fma_contract", "redblack", "galerkin", 1.0, {"fma_contract": 1}),
+                ("fp64_dense_coarsest_nmin16", "redblack", "galerkin", 1.0, {"n_min": 16}),
+                ("mixed_dense_coarsest_nmin16", "redblack", "galerkin", 1.0,
+                 {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1, "fma_contract": 1, "n_min": 16}),
                 ("mixed_fp32_inner", "redblack", "galerkin", 1.0,
                  {"precision": mg.MG_PREC_MIXED_FP32, "inner_cycles": 1, "fma_contract": 1}),
                 ("mixed_fp32_inner_nongalerkin_coarse", "redblack", "nongalerkin", 1.0,
@@ -533,7 +541,7 @@ def run_batched(args):
     for n, _ in specs:
         if n not in rhs:
             rhs[n] = torch.tensor(synth.rhs_normal(n, SEED + n), dtype=torch.float64, device="cuda")
-    opts = dict(nu1=NU1, nu2=NU2, precision=mg.MG_PREC_MIXED_FP32, fma_contract=1)
+    opts = dict(nu1=NU1, nu2=NU2, precision=mg.MG_PREC_MIXED_FP32, fma_contract=1, n_min=N_MIN_SMALL)
     t0 = time.perf_counter()
     hs = [mg.mg_setup(n, order, "redblack", "galerkin", **opts) for n, order in specs]
     fs = [rhs[n] for n, _ in specs]
@@ -574,6 +582,7 @@ def run_batched(args):
     points = sum((n - 1) ** 2 for n, _ in specs)
     return {"problems": count, "sides": "2^k+1, k uniform in {7..11}", "unknowns": points,
             "precision": "mixed FP32 inner / FP64 refinement", "rtol": 1e-8,
+            "n_min": N_MIN_SMALL, "coarsest": f"dense solve of {(N_MIN_SMALL - 1) ** 2} unknowns",
             "batch_ms": batch_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms,
             "max_cycles": max(cyc), "max_rel_res": max(rr), "batch_kernel_launches": batch_launches,
             "unknowns_per_s": points / (batch_ms * 1e-3), "setup_s": setup_s, "batch_create_s": create_s}
@@ -594,11 +603,12 @@ def run_serving(args):
     reqs = serve.poisson_stream(SEED, args.serve_count, 2000.0, 8, 12, rtol=1e-8, device_rhs=True)
     keys = sorted({(r.n, r.order, r.coarse_op) for r in reqs})
     out = {"requests": len(reqs), "rate_rps": 2000.0, "sides": "2^k+1, k uniform in [8, 12]",
-           "rhs": "one N(0,1) field per request, seeded by the request id", "budget_gb": 120}
+           "rhs": "one N(0,1) field per request, seeded by the request id", "budget_gb": 120,
+           "n_min": N_MIN_SMALL}
     plain = reqs[::args.serve_plain_every]
     for name, slots, opts, rq in (
-            ("continuous_mixed", 8, dict(nu1=NU1, nu2=NU2, precision=1, fma_contract=1), reqs),
-            ("plain_fp64", 1, dict(nu1=NU1, nu2=NU2), plain)):
+            ("continuous_mixed", 8, dict(nu1=NU1, nu2=NU2, precision=1, fma_contract=1, n_min=N_MIN_SMALL), reqs),
+            ("plain_fp64", 1, dict(nu1=NU1, nu2=NU2, n_min=N_MIN_SMALL), plain)):
         srv = serve.Server(slots=slots, budget_bytes=120e9, **opts)
         srv.warm(keys, per_key=min(slots, 2))
         results, stats = srv.run(rq, realtime=True, keep_u=False)

@@ -121,9 +121,18 @@ typedef struct {
   int32_t gamma;       /* 1 = V cycle, 2 = W cycle, 3 = "Wn" cycle: 2 coarse cycles on
                           levels 0 and 1, 1 below (Sec. 4.4) (default 1) */
   int32_t smoother;    /* mg_smoother (default MG_SMOOTH_REDBLACK) */
-  int32_t n_min;       /* coarsest axis grid cells per side (default 2: one unknown; only 2 is
-                          accepted; periodic hierarchies go on to one node, N_l = 1) */
-  int32_t max_levels;  /* 0 = no limit */
+  int32_t n_min;       /* coarsest axis grid cells per side: a power of two, 2 <= n_min <= n / 2
+                          (default 2: one unknown, solved by one division; periodic
+                          hierarchies go on to one node, N_l = 1, and accept only 2).
+                          n_min > 2 (Dirichlet): the coarsest level's (n_min - 1)^2 unknowns
+                          are solved exactly (Algorithm "MG", Sec. 2.2) by a dense factor
+                          formed at set-up: Cholesky A = L L^T by columns, G = L^-1 by rows,
+                          then x = G^T (G d), every sum in a fixed order (k ascending from
+                          the first product), so the iterates are reproducible bit for bit */
+  int32_t max_levels;  /* 0 = no limit; otherwise at least 2 (Dirichlet only): the hierarchy
+                          stops after that many levels and its coarsest level (axis or
+                          rotated, at most 1024 unknowns, else MG_ERR_UNSUPPORTED) takes the
+                          dense solve */
   int32_t precision;   /* mg_precision (default MG_PREC_FP64) */
   int32_t fma_contract;/* 0 = separate rounding of every product (default), 1 = FMA allowed */
   int32_t inner_cycles;/* mixed precision: FP32 cycles per refinement step (default 1: FP32

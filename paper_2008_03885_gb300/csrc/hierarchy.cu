@@ -518,6 +518,7 @@ struct Hier {
   int64_t coarsest_idx = 0;
   T coarsest_a = T(1);
   int coarsest_zero = 0;  // periodic: the coarsest single node's zero-mean solution is 0
+  DenseCoarse<T> dense{};  // m > 0: the coarsest level has m > 1 unknowns (dense solve)
   // small-level tail (one thread block runs the sub-cycle from tail_level down)
   int tail_level = -1;
   TailDesc<T>* d_tail = nullptr;
@@ -639,8 +640,11 @@ mg_status validate(const mg_grid* grid, int order, int coarsening, int coarse_op
   if (o.dirichlet_data == 1 && (order != 2 || o.boundary != MG_BOUNDARY_DIRICHLET)) return MG_ERR_UNSUPPORTED;
   if (o.transfer_order == 4 && coarsening != MG_COARSEN_STANDARD) return MG_ERR_UNSUPPORTED;
   if (o.boundary == MG_BOUNDARY_PERIODIC && o.sweep_kernel == 2) return MG_ERR_UNSUPPORTED;
-  if (o.n_min != 2) return MG_ERR_UNSUPPORTED;  // coarsest level must hold one unknown
-  if (o.max_levels != 0) return MG_ERR_UNSUPPORTED;
+  if (!pow2(o.n_min) || o.n_min < 2 || o.max_levels < 0) return MG_ERR_INVALID;
+  // at least two levels; a coarsest level with several unknowns takes the dense solve,
+  // which is built for Dirichlet boundaries
+  if (o.n_min > grid->n / 2 || o.max_levels == 1) return MG_ERR_UNSUPPORTED;
+  if (o.boundary == MG_BOUNDARY_PERIODIC && (o.n_min != 2 || o.max_levels != 0)) return MG_ERR_UNSUPPORTED;
   return MG_OK;
 }
 
@@ -735,6 +739,64 @@ HostLevel storage_of(const HostLevel& L, int l) {
   return S;
 }
 
+// Largest coarsest system solved by the dense factor (2 x m^2 values per precision).
+constexpr int kDenseMaxUnknowns = 1024;
+
+// Inverse Cholesky factor G = L^-1 of the coarsest operator (level C, Dirichlet), in
+// the unknown order row-major (j, then i), every product and sum rounded separately:
+// Cholesky by columns j (s = A_jj - L_j0 L_j0 - ... with k ascending, L_jj = sqrt(s),
+// r_j = 1 / L_jj, L_ij = (A_ij - L_i0 L_j0 - ...) r_j), then G by rows i (G_ii = r_i,
+// G_ic = -((L_ic G_cc + L_i,c+1 G_c+1,c + ... + L_i,i-1 G_i-1,c) r_i)). A's entries
+// are the level's coefficients fl(w s), as in its stencil kernels. Returns false if
+// the operator is not positive definite.
+bool dense_factor(const HostLevel& C, std::vector<double>& G, std::vector<int2>& ij) {
+  const int n = C.shape.n;
+  std::vector<int> index((size_t)(n + 1) * (n + 1), -1);
+  ij.clear();
+  for (int j = 1; j < n; ++j)
+    for (int i = 1; i < n; ++i) {
+      if (C.shape.kind == kRot && ((i + j) & 1)) continue;
+      index[(size_t)j * (n + 1) + i] = (int)ij.size();
+      ij.push_back(make_int2(i, j));
+    }
+  const size_t m = ij.size();
+  std::vector<double> A(m * m, 0.0);
+  for (size_t p = 0; p < m; ++p) {
+    const int i = ij[p].x, j = ij[p].y;
+    const Stencil row = C.exact ? fold_row_x(C.Wx, n, i, j) : fold_row(C.W, n, i, j);
+    for (const auto& t : row) {
+      const int q = index[(size_t)(j + t.first.first) * (n + 1) + (i + t.first.second)];
+      if (q < 0) return false;
+      A[p * m + q] = t.second * C.s;
+    }
+  }
+  std::vector<double> L(m * m, 0.0), r(m);
+  for (size_t j = 0; j < m; ++j) {
+    double sd = A[j * m + j];
+    for (size_t k = 0; k < j; ++k) sd = sd - L[j * m + k] * L[j * m + k];
+    if (!(sd > 0.0)) return false;
+    L[j * m + j] = std::sqrt(sd);
+    r[j] = 1.0 / L[j * m + j];
+    for (size_t i = j + 1; i < m; ++i) {
+      double t = A[i * m + j];
+      for (size_t k = 0; k < j; ++k) t = t - L[i * m + k] * L[j * m + k];
+      L[i * m + j] = t * r[j];
+    }
+  }
+  G.assign(m * m, 0.0);
+  std::vector<double> acc(m);
+  for (size_t i = 0; i < m; ++i) {
+    G[i * m + i] = r[i];
+    for (size_t k = 0; k < i; ++k) {
+      const double lik = L[i * m + k];
+      acc[k] = lik * G[k * m + k];  // the first product of column k's sum
+      for (size_t c = 0; c < k; ++c) acc[c] = acc[c] + lik * G[k * m + c];
+    }
+    for (size_t c = 0; c < i; ++c) G[i * m + c] = -(acc[c] * r[i]);
+  }
+  return true;
+}
+
 mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
   if (bytes == 0) bytes = 256;
   if (h->opt.dev_alloc) {  // caller's allocator
@@ -749,6 +811,33 @@ mg_status device_alloc(mg_handle* h, void** p, size_t bytes) {
   }
   h->allocs.push_back(*p);
   if (cudaMemsetAsync(*p, 0, bytes, h->priv) != cudaSuccess) return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+// Device copies of the dense coarsest factor in precision T (FP32: G rounded once).
+template <typename T>
+mg_status upload_dense(mg_handle* h, const std::vector<double>& G, const std::vector<int2>& ij, DenseCoarse<T>& D) {
+  const size_t m = ij.size();
+  std::vector<T> ga(m * m), gb(m * m);
+  for (size_t k = 0; k < m; ++k)
+    for (size_t i = 0; i < m; ++i) {
+      ga[k * m + i] = (T)G[i * m + k];
+      gb[k * m + i] = (T)G[k * m + i];
+    }
+  T *dga, *dgb;
+  int2* dij;
+  mg_status st;
+  if ((st = device_alloc(h, (void**)&dga, m * m * sizeof(T))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&dgb, m * m * sizeof(T))) != MG_OK) return st;
+  if ((st = device_alloc(h, (void**)&dij, m * sizeof(int2))) != MG_OK) return st;
+  CK(cudaMemcpyAsync(dga, ga.data(), m * m * sizeof(T), cudaMemcpyHostToDevice, h->priv));
+  CK(cudaMemcpyAsync(dgb, gb.data(), m * m * sizeof(T), cudaMemcpyHostToDevice, h->priv));
+  CK(cudaMemcpyAsync(dij, ij.data(), m * sizeof(int2), cudaMemcpyHostToDevice, h->priv));
+  CK(cudaStreamSynchronize(h->priv));  // the host vectors go out of scope
+  D.ga = dga;
+  D.gb = dgb;
+  D.ij = dij;
+  D.m = (int)m;
   return MG_OK;
 }
 
@@ -1040,7 +1129,10 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
                                     coarse_red ? H.t[l + 1] : nullptr));
   }
   if (l + 1 == lmax) {
-    LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.coarsest_zero, H.f[lmax], H.u[lmax], c.s));
+    if (H.dense.m > 0)
+      LAUNCH(h, 1, launch_coarsest_dense<T>(H.dense, H.L[lmax], c.exact, H.f[lmax], H.d[lmax], H.u[lmax], c.s));
+    else
+      LAUNCH(h, 1, launch_coarsest<T>(H.coarsest_idx, H.coarsest_a, H.coarsest_zero, H.f[lmax], H.u[lmax], c.s));
   } else {
     for (int g = 0; g < gamma_at(h, l); ++g)
       if ((st = cycle_level<T>(c, l + 1, H.u[l + 1], H.f[l + 1], g == 0, coarse_red && g == 0)) != MG_OK) return st;
@@ -1224,6 +1316,7 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
   td.coarsest_idx = H.coarsest_idx;
   td.coarsest_a = H.coarsest_a;
   td.coarsest_zero = H.coarsest_zero;
+  td.dense = H.dense;
   std::vector<int4> prog;
   emit_tail(h, lt, true, prog, true);
   mg_status st;
@@ -1353,6 +1446,16 @@ size_t mg_workspace_bytes(const mg_grid* grid, int order, mg_coarsening coarseni
     bytes += arrays * rows * pitch * sizeof(double);
     if (o.precision == MG_PREC_MIXED_FP32) bytes += 4 * rows * round_pitch((int)cols) * sizeof(float);
   }
+  // dense coarsest factor (two m x m copies per precision) when the coarsest level has
+  // several unknowns
+  const LevelShape& c = shapes.back();
+  const size_t mc = o.boundary == MG_BOUNDARY_PERIODIC ? 1
+                    : c.kind == kAxis ? (size_t)(c.n - 1) * (c.n - 1)
+                                      : ((size_t)(c.n - 1) * (c.n - 1) + 1) / 2;
+  if (mc > 1) {
+    bytes += 2 * mc * mc * sizeof(double) + mc * sizeof(int2);
+    if (o.precision == MG_PREC_MIXED_FP32) bytes += 2 * mc * mc * sizeof(float) + mc * sizeof(int2);
+  }
   return bytes;
 }
 
@@ -1390,7 +1493,12 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
       cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess)
     return fail(MG_ERR_CUDA);
   const HostLevel& C = h->host.back();
-  if (C.unknowns != 1) return fail(MG_ERR_UNSUPPORTED);
+  // several coarsest unknowns (n_min > 2, or a truncated hierarchy): the dense solve
+  std::vector<double> cG;
+  std::vector<int2> cij;
+  if (C.unknowns != 1 &&
+      (C.per || C.unknowns > kDenseMaxUnknowns || !dense_factor(C, cG, cij) || (int64_t)cij.size() != C.unknowns))
+    return fail(MG_ERR_UNSUPPORTED);
   // Dirichlet: node (1, 1) with a_pp from its folded row; periodic: node (0, 0), whose
   // row is zero (the zero-mean solution is 0)
   const int64_t cidx = C.per ? 0 : (int64_t)1 * C.pitch + (C.shape.kind == kRot ? 0 : 1);
@@ -1400,6 +1508,7 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
   h->h64.coarsest_idx = cidx;
   h->h64.coarsest_a = ca;
   h->h64.coarsest_zero = C.per;
+  if (!cij.empty() && (st = upload_dense<double>(h, cG, cij, h->h64.dense)) != MG_OK) return fail(st);
   auto tail_limit = [&](int64_t dflt) -> int64_t {
     return o.tail_unknowns < 0 ? 0 : (o.tail_unknowns > 0 ? (int64_t)o.tail_unknowns : dflt);
   };
@@ -1411,6 +1520,7 @@ mg_status mg_setup(const mg_grid* grid, int order, mg_coarsening coarsening, mg_
     h->h32.coarsest_idx = cidx;
     h->h32.coarsest_a = (float)ca;
     h->h32.coarsest_zero = C.per;
+    if (!cij.empty() && (st = upload_dense<float>(h, cG, cij, h->h32.dense)) != MG_OK) return fail(st);
     if (o.tail_unknowns == 0) st = build_tail<float>(h, 0, kTailSmemElemsFp32);
     else st = build_tail<float>(h, tail_limit(0));
     if (st != MG_OK) return fail(st);
@@ -1660,8 +1770,10 @@ struct BatchList {
   int* d_prefix = nullptr;              // tiles over level l
   int* d_cprefix = nullptr;             // tiles over level l + 1 (restriction)
   int ne = 0, tiles = 0, ctiles = 0, rpt = 1;
-  BatchLevel<T>* d_coarsest = nullptr;  // problems whose level l + 1 is the coarsest
+  BatchLevel<T>* d_coarsest = nullptr;  // problems whose level l + 1 is the coarsest (one unknown)
   int nc = 0;
+  BatchLevel<T>* d_coarsest_dense = nullptr;  // ... with several unknowns (dense solve)
+  int ncd = 0;
   std::vector<BatchLevel<T>> host;
 };
 
@@ -1745,7 +1857,7 @@ mg_status build_lists(mg_batch* b, std::vector<BatchList<T>>& lv) {
   lv.assign(b->nl, BatchList<T>());
   for (int l = 0; l + 1 < b->nl; ++l) {
     BatchList<T>& B = lv[l];
-    std::vector<BatchLevel<T>> coarsest;
+    std::vector<BatchLevel<T>> coarsest, coarsest_dense;
     for (int p = 0; p < b->count; ++p) {
       mg_handle* h = b->hs[p];
       Hier<T>& H = hier<T>(h);
@@ -1772,14 +1884,18 @@ mg_status build_lists(mg_batch* b, std::vector<BatchList<T>>& lv) {
       e.ctiles_x = (h->host[l + 1].cols + kBatchCols - 1) / kBatchCols;
       e.coarsest_idx = H.coarsest_idx;
       e.coarsest_a = H.coarsest_a;
+      e.dense = H.dense;
+      e.dc = H.d[l + 1];
       B.host.push_back(e);
-      if (l + 2 == nlp) coarsest.push_back(e);
+      if (l + 2 == nlp) (H.dense.m > 0 ? coarsest_dense : coarsest).push_back(e);
     }
     B.ne = (int)B.host.size();
     B.nc = (int)coarsest.size();
+    B.ncd = (int)coarsest_dense.size();
     mg_status st;
     if ((st = upload_vec(b, B.host, &B.d_entries)) != MG_OK) return st;
     if ((st = upload_vec(b, coarsest, &B.d_coarsest)) != MG_OK) return st;
+    if ((st = upload_vec(b, coarsest_dense, &B.d_coarsest_dense)) != MG_OK) return st;
   }
   return MG_OK;
 }
@@ -1862,6 +1978,8 @@ mg_status batch_cycle(mg_batch* b, std::vector<BatchList<T>>& lv, bool zero0, cu
     BLAUNCH(b, launch_batch_step<T>(kBResidual, B.d_entries, B.d_prefix, B.ne, B.tiles, B.rpt, act, b->exact, s));
     BLAUNCH(b, launch_batch_step<T>(kBRestrict, B.d_entries, B.d_cprefix, B.ne, B.ctiles, B.rpt, act, b->exact, s));
     if (B.nc > 0) BLAUNCH(b, launch_batch_step<T>(kBCoarsest, B.d_coarsest, nullptr, B.nc, 0, 1, act, b->exact, s));
+    if (B.ncd > 0)
+      BLAUNCH(b, launch_batch_step<T>(kBCoarsestDense, B.d_coarsest_dense, nullptr, B.ncd, 0, 1, act, b->exact, s));
   }
   for (int l = b->nl - 2; l >= 0; --l) {
     BatchList<T>& B = lv[l];

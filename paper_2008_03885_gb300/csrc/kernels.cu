@@ -860,6 +860,55 @@ __global__ void k_coarsest(int64_t idx, T a, int zero_mean, const T* __restrict_
   if (threadIdx.x == 0 && blockIdx.x == 0) u[idx] = zero_mean ? T(0) : Arith<T>::div(f[idx], a);
 }
 
+// Exact coarsest solve with m > 1 unknowns: y = G f, then u = G^T y (DenseCoarse).
+// Thread i (strided by nth) forms y_i, then x_i, each a sum from its first product with
+// k ascending; SYNC separates the two products (returns false if the caller must stop).
+template <typename T, bool EXACT, class IDX, class SYNC>
+__device__ __forceinline__ bool dense_coarse(const DenseCoarse<T>& C, const LevelDev<T>& L, const T* F, T* Y,
+                                             T* U, IDX idx, int tid, int nth, SYNC sync) {
+  const int m = C.m;
+  const int2 q0 = C.ij[0];
+  const T f0 = F[idx(L, q0.x, q0.y)];
+  for (int i = tid; i < m; i += nth) {
+    T s = Arith<T>::mul(C.ga[i], f0);
+    for (int k = 1; k <= i; ++k) {
+      const int2 q = C.ij[k];
+      const T g = C.ga[(int64_t)k * m + i];
+      const T x = F[idx(L, q.x, q.y)];
+      s = EXACT ? Arith<T>::add(s, Arith<T>::mul(g, x)) : Arith<T>::fma(g, x, s);
+    }
+    const int2 p = C.ij[i];
+    Y[idx(L, p.x, p.y)] = s;
+  }
+  if (!sync()) return false;
+  for (int i = tid; i < m; i += nth) {
+    const int2 p = C.ij[i];
+    T s = Arith<T>::mul(C.gb[(int64_t)i * m + i], Y[idx(L, p.x, p.y)]);
+    for (int k = i + 1; k < m; ++k) {
+      const int2 q = C.ij[k];
+      const T g = C.gb[(int64_t)k * m + i];
+      const T x = Y[idx(L, q.x, q.y)];
+      s = EXACT ? Arith<T>::add(s, Arith<T>::mul(g, x)) : Arith<T>::fma(g, x, s);
+    }
+    U[idx(L, p.x, p.y)] = s;
+  }
+  return true;
+}
+
+struct BlockSync {
+  __device__ __forceinline__ bool operator()() const {
+    __syncthreads();
+    return true;
+  }
+};
+
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(1024) k_coarsest_dense(DenseCoarse<T> C, const LevelDev<T>* __restrict__ Lp,
+                                                         const T* __restrict__ f, T* __restrict__ y,
+                                                         T* __restrict__ u) {
+  dense_coarse<T, EXACT>(C, *Lp, f, y, u, GlobalIdx(), (int)threadIdx.x, (int)blockDim.x, BlockSync());
+}
+
 // Block-wide sum of a double (blockDim = kBX * kBY = 256 threads).
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double warp_part[32];
@@ -1171,9 +1220,12 @@ __device__ __forceinline__ void tail_program(const TailDesc<T>* __restrict__ D, 
         Fc[sidx(Lc, i, j)] = restrict_any<T, EXACT>(L, D->transfer[l], Dd, i, j);
       }
     } else if (op.x == kOpCoarsest) {
-      if (tid == 0)
+      if (D->dense.m > 0) {
+        if (!dense_coarse<T, EXACT>(D->dense, L, D->f[l], D->d[l], D->u[l], GlobalIdx(), tid, nth, sync)) return;
+      } else if (tid == 0) {
         D->u[l][D->coarsest_idx] =
             D->coarsest_zero ? T(0) : Arith<T>::div(D->f[l][D->coarsest_idx], D->coarsest_a);
+      }
     } else {  // kOpProlong
       const LevelDev<T>& Lc = *D->L[l + 1];
       T* U = D->u[l];
@@ -1270,6 +1322,16 @@ __global__ void k_batch_coarsest(const BatchLevel<T>* __restrict__ E, int ne, co
   const BatchLevel<T>& B = E[e];
   if (!active[B.problem]) return;
   B.uc[B.coarsest_idx] = Arith<T>::div(B.fc[B.coarsest_idx], B.coarsest_a);
+}
+
+// Problems whose coarsest level has a dense solve: one block per entry.
+template <typename T, bool EXACT>
+__global__ void __launch_bounds__(256) k_batch_coarsest_dense(const BatchLevel<T>* __restrict__ E,
+                                                              const int* __restrict__ active) {
+  const BatchLevel<T>& B = E[blockIdx.x];
+  if (!active[B.problem]) return;  // uniform over the block
+  dense_coarse<T, EXACT>(B.dense, *B.Lc, B.fc, B.dc, B.uc, GlobalIdx(), (int)threadIdx.x, (int)blockDim.x,
+                         BlockSync());
 }
 
 template <bool EXACT>
@@ -1474,7 +1536,9 @@ __global__ void __launch_bounds__(kTailThreads, 1)
         Fc[k] = restrict_any<T, EXACT>(L, tr, Dd, i, j, SmemIdx());
       }
     } else if (op.x == kOpCoarsest) {
-      if (tid == 0) {
+      if (D->dense.m > 0) {
+        dense_coarse<T, EXACT>(D->dense, L, F, sm + D->sm_d[l], U, SmemIdx(), tid, kTailThreads, BlockSync());
+      } else if (tid == 0) {
         const int c = D->coarsest_zero ? smem_idx(L, 0, 0) : smem_idx(L, 1, 1);
         U[c] = D->coarsest_zero ? T(0) : Arith<T>::div(F[c], D->coarsest_a);
       }
@@ -1745,6 +1809,15 @@ cudaError_t launch_prolong_add(const LevelPair<T>& Lf, const LevelPair<T>& Lc, i
 }
 
 template <typename T>
+cudaError_t launch_coarsest_dense(const DenseCoarse<T>& C, const LevelPair<T>& L, bool exact, const T* f, T* y, T* u,
+                                  cudaStream_t s) {
+  const int threads = std::min(1024, (C.m + 31) / 32 * 32);
+  if (exact) k_coarsest_dense<T, true><<<1, threads, 0, s>>>(C, L.d, f, y, u);
+  else k_coarsest_dense<T, false><<<1, threads, 0, s>>>(C, L.d, f, y, u);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_coarsest(int64_t idx, T a, int zero_mean, const T* f, T* u, cudaStream_t s) {
   k_coarsest<T><<<1, 32, 0, s>>>(idx, a, zero_mean, f, u);
   return cudaGetLastError();
@@ -1930,6 +2003,11 @@ cudaError_t launch_batch_step(int op, const BatchLevel<T>* entries, const int* p
     k_batch_coarsest<T><<<(ne + 127) / 128, 128, 0, s>>>(entries, ne, active);
     return cudaGetLastError();
   }
+  if (op == kBCoarsestDense) {
+    if (exact) k_batch_coarsest_dense<T, true><<<ne, 256, 0, s>>>(entries, active);
+    else k_batch_coarsest_dense<T, false><<<ne, 256, 0, s>>>(entries, active);
+    return cudaGetLastError();
+  }
   if (total_tiles <= 0) return cudaSuccess;
   const dim3 blk(kBX, kBY);
 #define NSMG_BSTEP(R)                                                                                   \
@@ -1993,6 +2071,8 @@ cudaError_t launch_tail_smem(const TailDesc<T>* desc, int sm_elems, int nst, con
                                              const T*, cudaStream_t, const T*);                       \
   template cudaError_t launch_sweep_fused<T>(const LevelPair<T>&, bool, const T*, const T*, T*, cudaStream_t); \
   template cudaError_t launch_coarsest<T>(int64_t, T, int, const T*, T*, cudaStream_t);                    \
+  template cudaError_t launch_coarsest_dense<T>(const DenseCoarse<T>&, const LevelPair<T>&, bool, const T*, T*, T*, \
+                                                cudaStream_t);                                                     \
   template int resnorm_blocks<T>(const LevelPair<T>&);                                                \
   template cudaError_t launch_resnorm<T>(const LevelPair<T>&, bool, const T*, const T*, double*,     \
                                          double*, cudaStream_t);                                      \

@@ -39,6 +39,23 @@ cudaError_t launch_sweep_fused(const LevelPair<T>& L, bool exact, const T* uin, 
 template <typename T>
 cudaError_t launch_coarsest(int64_t idx, T a, int zero_mean, const T* f, T* u, cudaStream_t s);
 
+// Exact coarsest solve with m > 1 unknowns (Dirichlet): x = G^T (G d), G = L^-1 the
+// inverse Cholesky factor of the coarsest operator, formed on the host at set-up in a
+// fixed order. y_i = G_i0 d_0 + ... + G_ii d_i, then x_i = G_ii y_i + ... + G_m-1,i y_m-1,
+// each sum from its first product with k ascending (separately rounded when exact).
+template <typename T>
+struct DenseCoarse {
+  const T* ga;     // ga[k * m + i] = G_ik (k <= i): reads coalesced over i
+  const T* gb;     // gb[k * m + i] = G_ki (k >= i)
+  const int2* ij;  // lattice coordinates (i, j) of unknown k, row-major (j, then i)
+  int32_t m;       // unknowns; 0: one unknown, solved by the division
+};
+// Dense coarsest solve on level L's storage: u = G^T (G f), y (the level's d array)
+// holds G f in between. One block.
+template <typename T>
+cudaError_t launch_coarsest_dense(const DenseCoarse<T>& C, const LevelPair<T>& L, bool exact, const T* f, T* y, T* u,
+                                  cudaStream_t s);
+
 // Sum of squares of d = f - L u over interior nodes of an axis level, in FP64:
 // per-block partial sums into `partial` (size >= resnorm_blocks(L)), then one
 // block adds the partials in a fixed order into *out. Deterministic.
@@ -96,6 +113,7 @@ struct TailDesc {
   int64_t coarsest_idx;
   T coarsest_a;
   int32_t coarsest_zero;  // periodic single node: the zero-mean solution 0
+  DenseCoarse<T> dense;   // m > 0: the coarsest level's dense solve
   // shared-memory-resident variant: per level, element offsets of u, t, f, d in the
   // block's shared memory (compact rows x cols layout) and the number of levels held
   int32_t sm_u[kTailMaxLevels], sm_t[kTailMaxLevels], sm_f[kTailMaxLevels], sm_d[kTailMaxLevels];
@@ -142,6 +160,8 @@ struct BatchLevel {
   int32_t tiles_x, ctiles_x;  // tiles per row of tiles on level l / level l + 1
   int64_t coarsest_idx;   // of level l + 1 when it is the problem's coarsest level
   T coarsest_a;
+  DenseCoarse<T> dense;   //   m > 0: its dense solve (y in dc)
+  T* dc;                  // level l + 1's d array
   float* r32;             // finest level, mixed precision: FP32 residual (inner right-hand side)
   float* e32;             //   and FP32 correction
   int32_t pitch32;        //   row pitch of those FP32 arrays (padded to 32 elements)
@@ -149,7 +169,8 @@ struct BatchLevel {
 
 enum BatchOp : int32_t {
   kBZero = 0, kBHalfRed = 1, kBHalfBlack = 2, kBResidual = 3, kBRestrict = 4, kBProlong = 5, kBCoarsest = 6,
-  kBHalfRedZero = 7  // kBHalfRed from u = 0 (no stencil; replaces kBZero + kBHalfRed, same bits)
+  kBHalfRedZero = 7,  // kBHalfRed from u = 0 (no stencil; replaces kBZero + kBHalfRed, same bits)
+  kBCoarsestDense = 8  // kBCoarsest for coarsest levels with several unknowns (one block per problem)
 };
 
 // A tile is 64 storage columns (2 per thread, so a thread holds one red and one black

@@ -58,6 +58,9 @@ def test_workspace_bytes_validates_without_gpu(lib):
     # FP64 red-black V: roughly 2 arrays on level 0 plus 4 per coarse level
     b = mg.mg_workspace_bytes(1024)
     assert 2 * 1025 * 1025 * 8 <= b <= 12 * 1025 * 1025 * 8
+    # n_min = 16: fewer levels, plus the dense coarsest factor (2 x 225^2 doubles)
+    b16 = mg.mg_workspace_bytes(1024, n_min=16)
+    assert b16 - b >= 2 * 225 * 225 * 8 - 4 * 17 * 17 * 8 * 8
 
 
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
@@ -69,9 +72,16 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, omega=2.5)
     assert e.value.status == mg.MG_ERR_INVALID
-    with pytest.raises(mg.MGError) as e:
-        mg.mg_setup(64, n_min=8)
-    assert e.value.status == mg.MG_ERR_UNSUPPORTED
+    # n_min: a power of two from 2 to N / 2; above 2 (several coarsest unknowns, the
+    # dense solve) Dirichlet only; at least two levels
+    for kwargs, status in ((dict(n_min=3), mg.MG_ERR_INVALID), (dict(n_min=0), mg.MG_ERR_INVALID),
+                           (dict(n_min=64), mg.MG_ERR_UNSUPPORTED), (dict(max_levels=-1), mg.MG_ERR_INVALID),
+                           (dict(max_levels=1), mg.MG_ERR_UNSUPPORTED),
+                           (dict(n_min=8, boundary="periodic"), mg.MG_ERR_UNSUPPORTED),
+                           (dict(max_levels=3, boundary="periodic"), mg.MG_ERR_UNSUPPORTED)):
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_setup(64, **kwargs)
+        assert e.value.status == status, kwargs
     with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, length=-1.0)
     assert e.value.status == mg.MG_ERR_INVALID
