@@ -647,22 +647,23 @@ def run_profile_case(args):
     print(json.dumps({"profile_case": n, "ok": True}))
 
 
-def run_profile_mixed(args):
-    """Two mixed-precision solves of the bench workload (warm-up + one), for ncu."""
+def run_profile_solves(args, mixed: bool):
+    """Two solves of the bench workload (warm-up + one), for ncu: mixed precision
+    (FP32 inner cycles) or the FP64 headline solve."""
     import torch
     import paper_2008_03885_gb300 as mg
     import synth
     n = args.profile_n
     f = torch.tensor(synth.rhs_sine_modes(n, SEED), dtype=torch.float64, device="cuda")
     u = torch.zeros_like(f)
-    h = mg.mg_setup(n, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2,
-                    precision=mg.MG_PREC_MIXED_FP32, inner_cycles=1, fma_contract=1)
+    extra = dict(precision=mg.MG_PREC_MIXED_FP32, inner_cycles=1, fma_contract=1) if mixed else {}
+    h = mg.mg_setup(n, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2, **extra)
     for _ in range(2):
         u.zero_()
         k, hist = mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)
     torch.cuda.synchronize()
     h.close()
-    print(json.dumps({"profile_mixed": n, "steps": k, "final": hist[-1]}))
+    print(json.dumps({"profile_mixed" if mixed else "profile_fp64": n, "cycles": k, "final": hist[-1]}))
 
 
 # Algorithmic HBM bytes per fine grid point per cycle (every kernel reading its inputs
@@ -707,12 +708,13 @@ def main():
     ap.add_argument("--serve-plain-every", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=4096)
     ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")
+    ap.add_argument("--profile-fp64", action="store_true", help="two FP64 solves of the bench workload (ncu)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args)
         return
-    if args.profile_mixed:
-        run_profile_mixed(args)
+    if args.profile_mixed or args.profile_fp64:
+        run_profile_solves(args, mixed=args.profile_mixed)
         return
     ws, rank, local = dist_env()
     if ws > 1:
