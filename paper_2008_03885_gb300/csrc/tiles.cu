@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "device.cuh"
 #include "tiles.h"
@@ -133,6 +134,7 @@ __device__ __forceinline__ float stencil(const LevelDev<float>& L, const float (
   const int2 e = L.cls[class_of(L, i, j)];
   const ClassTerm<float>* tt = L.terms + e.x;
   RowSum<float, EXACT> acc;
+#pragma unroll 4
   for (int k = 0; k < e.y; ++k) {
     const Term<float> t = load_term(tt + k);
     acc.add(t.c, x(i + t.dx, j + t.dy), t.start);
@@ -258,42 +260,105 @@ __device__ __forceinline__ float cross(const float (&c)[NT], const SO& so, int b
   }
 }
 
-// One fast relaxation phase: every node of colour RED in the tile plus margin M gets
+// Fast value of element (rr, pp) (column parity a) of a relaxation phase of margin M:
 // relax(L x, f, old) (old, so and ss as above; with ZERO_START the stencil-free value
-// 0 + f omega / a_pp), handed to sink(e, rr, pp, a, value). Each thread evaluates kIlp
-// nodes before it hands any of them over, so that their dependency chains (shared-memory
-// loads, then a chain of fused multiply-adds) overlap.
+// 0 + f omega / a_pp).
+template <bool EXACT, int NT, int M, bool ZERO_START, class SO, class SS, class SOLD, class FB>
+__device__ __forceinline__ float fast_value(const float (&c)[NT], float wd, const SO& so, const SS& ss,
+                                            const SOLD& sold, const FB& fb, int rr, int pp, int a) {
+  const float f = fb.template get<0, 0>(fb.template base<M>(rr, pp, a), a);
+  if constexpr (ZERO_START) {
+    return relax_from_zero(f, wd);
+  } else {
+    const float st = cross<EXACT, NT>(c, so, so.template base<M>(rr, pp, a), ss, ss.template base<M>(rr, pp, a), a);
+    return relax<EXACT>(st, f, sold.template get<0, 0>(sold.template base<M>(rr, pp, a), a), wd);
+  }
+}
+
+// One fast relaxation phase: every node of colour RED in the tile plus margin M gets its
+// fast value, handed to sink(e, rr, pp, a, value) (e = rr * w + pp).
 // (Measured on GB300, 4097^2 FP32 fourth order, one tile per block: 2 and 4 nodes per
 // thread at a time were slower than 1 -- presmooth 107 / 134 vs 106 us, sweep 70 / 86 vs
 // 67 us -- with more registers per node and more idle lanes in each phase's last pass.)
-constexpr int kIlp = 1;
-static_assert((kTJ * kTP) % (kIlp * kTT) == 0, "the tile's node pairs split evenly over the block");
-
 template <bool EXACT, int NT, bool RED, int M, bool ZERO_START, class SO, class SS, class SOLD, class FB, class SINK>
 __device__ __forceinline__ void phase(const float (&c)[NT], float wd, const SO& so, const SS& ss, const SOLD& sold,
                                       const FB& fb, SINK sink) {
-  constexpr int N = Reg<M>::n;
-  for (int e0 = threadIdx.x; e0 < N; e0 += kIlp * kTT) {
-    float v[kIlp];
-    int rr[kIlp], pp[kIlp], a[kIlp];
-#pragma unroll
-    for (int u = 0; u < kIlp; ++u) {
-      const int e = min(e0 + u * kTT, N - 1);  // past the end: recompute the last node, not stored
-      rr[u] = e / Reg<M>::w;
-      pp[u] = e - rr[u] * Reg<M>::w;
-      a[u] = (rr[u] + M + (RED ? 1 : 0)) & 1;  // column parity of the node (tile rows start even)
-      const float f = fb.template get<0, 0>(fb.template base<M>(rr[u], pp[u], a[u]), a[u]);
-      if constexpr (ZERO_START) {
-        v[u] = relax_from_zero(f, wd);
-      } else {
-        const float st = cross<EXACT, NT>(c, so, so.template base<M>(rr[u], pp[u], a[u]), ss,
-                                          ss.template base<M>(rr[u], pp[u], a[u]), a[u]);
-        v[u] = relax<EXACT>(st, f, sold.template get<0, 0>(sold.template base<M>(rr[u], pp[u], a[u]), a[u]), wd);
-      }
+  for (int e = threadIdx.x; e < Reg<M>::n; e += kTT) {
+    const int rr = e / Reg<M>::w, pp = e - rr * Reg<M>::w;
+    const int a = (rr + M + (RED ? 1 : 0)) & 1;  // column parity of the node (tile rows start even)
+    sink(e, rr, pp, a, fast_value<EXACT, NT, M, ZERO_START>(c, wd, so, ss, sold, fb, rr, pp, a));
+  }
+}
+
+// Lattice coordinates of element (rr, pp) (column parity a) of a region of margin M.
+template <int M>
+__device__ __forceinline__ void node_of(const Tile& T, int rr, int pp, int a, int& i, int& j) {
+  j = T.J0 - M + rr;
+  i = 2 * (T.P0 - Reg<M>::mp + pp) + a;
+}
+
+// Strips of a region of margin M (tile T of level L) that may hold nodes outside the
+// fast range (rx <= i <= fxe, ry <= j <= fye): rows [0, rt) and [rb, h), and in the rows
+// between them the pairs [0, pl) and [pr, w). A superset of those nodes, without overlap.
+template <int M>
+struct Strips {
+  int rt, rb, pl, pr, mw, count;
+  __device__ __forceinline__ Strips(const LevelDev<float>& L, const Tile& T) {
+    constexpr int W = Reg<M>::w, H = Reg<M>::h;
+    const int j0 = T.J0 - M, q0 = T.P0 - Reg<M>::mp;  // lattice row / pair index of element (0, 0)
+    rt = min(max(L.ry - j0, 0), H);
+    rb = max(rt, min(max(L.fye + 1 - j0, 0), H));
+    pl = min(max(L.rx / 2 + 1 - q0, 0), W);        // pair q holds i = 2q + a < rx only if q <= rx / 2
+    pr = max(pl, min(max(L.fxe / 2 - q0, 0), W));  // ... i > fxe only if q >= fxe / 2
+    mw = pl + (W - pr);
+    count = (rt + H - rb) * W + (rb - rt) * mw;
+  }
+  // element k of the strips
+  __device__ __forceinline__ void at(int k, int& rr, int& pp) const {
+    constexpr int W = Reg<M>::w;
+    const int k1 = rt * W, k2 = k1 + (Reg<M>::h - rb) * W;
+    if (k < k1) {
+      rr = k / W;
+      pp = k - rr * W;
+    } else if (k < k2) {
+      const int q = (k - k1) / W;
+      rr = rb + q;
+      pp = k - k1 - q * W;
+    } else {
+      const int q = (k - k2) / mw, r = k - k2 - q * mw;
+      rr = rt + q;
+      pp = r < pl ? r : pr + (r - pl);
     }
-#pragma unroll
-    for (int u = 0; u < kIlp; ++u)
-      if (e0 + u * kTT < N) sink(e0 + u * kTT, rr[u], pp[u], a[u], v[u]);
+  }
+};
+
+// The same phase in a tile that reaches the level's boundary strip: the nodes of the
+// fast range get their fast value; every other node of the region (a boundary-class
+// node, or a node off the interior) gets gen(i, j), the value the per-step kernels give
+// it (class terms, omega / a_pp of its class; 0 or the old value off the interior).
+// The second pass walks only the strips, so that those nodes share warps.
+template <bool EXACT, int NT, bool RED, int M, bool ZERO_START, class SO, class SS, class SOLD, class FB, class SINK,
+          class GEN>
+__device__ __forceinline__ void phase_edge(const float (&c)[NT], float wd, const SO& so, const SS& ss,
+                                           const SOLD& sold, const FB& fb, SINK sink, const LevelDev<float>& L,
+                                           const Tile& T, GEN gen) {
+  for (int e = threadIdx.x; e < Reg<M>::n; e += kTT) {
+    const int rr = e / Reg<M>::w, pp = e - rr * Reg<M>::w;
+    const int a = (rr + M + (RED ? 1 : 0)) & 1;
+    int i, j;
+    node_of<M>(T, rr, pp, a, i, j);
+    if (!fast_node_c<false>(L, i, j)) continue;
+    sink(e, rr, pp, a, fast_value<EXACT, NT, M, ZERO_START>(c, wd, so, ss, sold, fb, rr, pp, a));
+  }
+  const Strips<M> st(L, T);
+  for (int k = threadIdx.x; k < st.count; k += kTT) {
+    int rr, pp;
+    st.at(k, rr, pp);
+    const int a = (rr + M + (RED ? 1 : 0)) & 1;
+    int i, j;
+    node_of<M>(T, rr, pp, a, i, j);
+    if (fast_node_c<false>(L, i, j)) continue;
+    sink(rr * Reg<M>::w + pp, rr, pp, a, gen(i, j));
   }
 }
 
@@ -371,94 +436,76 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_presmooth(const LevelDev<float>
   const int n = L.n, pitch = L.pitch;
   const CUtensorMap* const maps[1] = {&mapF};
   tile_block<1>(box0, pad32(FN), maps, G::HX, G::HY, status, [&](const Tile& T, float* sF) {
-    const int tid = threadIdx.x;
-    if (fast_tile<M0>(L, T)) {
-      const SBox<G::HX, G::HY> fb{sF};
-      phase<EXACT, NT, true, M0, true>(c, wdf, SZero{}, SZero{}, SZero{}, fb,
-                                       [=](int e, int, int, int, float v) { sR0[e] = v; });
+    const SBox<G::HX, G::HY> fb{sF};
+    const SCompact<M0> r0{sR0};
+    auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
+    auto xR0 = [=](int i, int j) { return sR0[T.at<M0>(i, j)]; };
+    auto xB1 = [=](int i, int j) { return sB1[T.at<M1>(i, j)]; };
+    auto xR2 = [=](int i, int j) { return sR2[T.at<M2>(i, j)]; };
+    // values of the nodes outside the fast range, phase by phase (as the per-step kernels)
+    auto g0 = [=](int i, int j) {  // red from zero: 0 + f omega / a_pp
+      return inner(n, i, j) ? relax_from_zero(F(i, j), wd_at(L, wdf, i, j)) : 0.f;
+    };
+    auto g1 = [=](int i, int j) {  // black of sweep 1 (old values 0)
+      if (!inner(n, i, j)) return 0.f;
+      const float st = stencil<EXACT, NT>(L, c, i, j, [=](int x, int y) { return ((x + y) & 1) ? xR0(x, y) : 0.f; });
+      return relax<EXACT>(st, F(i, j), 0.f, wd_at(L, wdf, i, j));
+    };
+    auto g2 = [=](int i, int j) {  // red of sweep 2
+      if (!inner(n, i, j)) return 0.f;
+      const float st =
+          stencil<EXACT, NT>(L, c, i, j, [=](int x, int y) { return ((x + y) & 1) ? xR0(x, y) : xB1(x, y); });
+      return relax<EXACT>(st, F(i, j), xR0(i, j), wd_at(L, wdf, i, j));
+    };
+    auto g3 = [=](int i, int j) {  // black of the last sweep, on the tile
+      if (!inner(n, i, j)) return 0.f;
+      if constexpr (NS == 2) {
+        const float st =
+            stencil<EXACT, NT>(L, c, i, j, [=](int x, int y) { return ((x + y) & 1) ? xR2(x, y) : xB1(x, y); });
+        return relax<EXACT>(st, F(i, j), xB1(i, j), wd_at(L, wdf, i, j));
+      } else {
+        const float st = stencil<EXACT, NT>(L, c, i, j, [=](int x, int y) { return ((x + y) & 1) ? xR0(x, y) : 0.f; });
+        return relax<EXACT>(st, F(i, j), 0.f, wd_at(L, wdf, i, j));
+      }
+    };
+    // a phase over the fast range (every node in a fast tile), else with the others from gen
+    auto run = [&](auto check) {
+      constexpr bool EDGE = decltype(check)::value;
+      auto go = [&](auto red, auto m, auto zero, const auto& so, const auto& ss, const auto& sold, auto sink, auto gen) {
+        constexpr bool RED = decltype(red)::value, ZERO = decltype(zero)::value;
+        constexpr int MM = decltype(m)::value;
+        if constexpr (EDGE) phase_edge<EXACT, NT, RED, MM, ZERO>(c, wdf, so, ss, sold, fb, sink, L, T, gen);
+        else phase<EXACT, NT, RED, MM, ZERO>(c, wdf, so, ss, sold, fb, sink);
+      };
+      using T1 = std::true_type;
+      using F0 = std::false_type;
+      go(T1{}, std::integral_constant<int, M0>{}, T1{}, SZero{}, SZero{}, SZero{},
+         [=](int e, int, int, int, float v) { sR0[e] = v; }, g0);
       __syncthreads();
-      const SCompact<M0> r0{sR0};
+      // the last phase's result with its red partner, one 8-byte store per node pair
+      // (bounds-checked in tiles that reach the level's edge)
+      auto put = [=](int rr, int pp, float red, float black) {
+        if constexpr (EDGE) store_pair(out, pitch, n, T.J0 + rr, T.P0 + pp, red, black);
+        else put_pair(out, pitch, T.J0 + rr, T.P0 + pp, red, black);
+      };
       if constexpr (NS == 2) {
         const SCompact<M1> b1{sB1};
         const SCompact<M2> r2{sR2};
-        phase<EXACT, NT, false, M1, false>(c, wdf, r0, SZero{}, SZero{}, fb,
-                                           [=](int e, int, int, int, float v) { sB1[e] = v; });
+        go(F0{}, std::integral_constant<int, M1>{}, F0{}, r0, SZero{}, SZero{},
+           [=](int e, int, int, int, float v) { sB1[e] = v; }, g1);
         __syncthreads();
-        phase<EXACT, NT, true, M2, false>(c, wdf, b1, r0, r0, fb, [=](int e, int, int, int, float v) { sR2[e] = v; });
+        go(T1{}, std::integral_constant<int, M2>{}, F0{}, b1, r0, r0, [=](int e, int, int, int, float v) { sR2[e] = v; },
+           g2);
         __syncthreads();
-        phase<EXACT, NT, false, 0, false>(c, wdf, r2, b1, b1, fb, [=](int, int rr, int pp, int a, float v) {
-          put_pair(out, pitch, T.J0 + rr, T.P0 + pp, sR2[r2.template base<0>(rr, pp, a)], v);
-        });
+        go(F0{}, std::integral_constant<int, 0>{}, F0{}, r2, b1, b1,
+           [=](int, int rr, int pp, int a, float v) { put(rr, pp, sR2[r2.template base<0>(rr, pp, a)], v); }, g3);
       } else {
-        phase<EXACT, NT, false, 0, false>(c, wdf, r0, SZero{}, SZero{}, fb, [=](int, int rr, int pp, int a, float v) {
-          put_pair(out, pitch, T.J0 + rr, T.P0 + pp, sR0[r0.template base<0>(rr, pp, a)], v);
-        });
+        go(F0{}, std::integral_constant<int, 0>{}, F0{}, r0, SZero{}, SZero{},
+           [=](int, int rr, int pp, int a, float v) { put(rr, pp, sR0[r0.template base<0>(rr, pp, a)], v); }, g3);
       }
-      return;
-    }
-    auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
-    // red nodes from zero: 0 + f omega / a_pp
-    for (int e = tid; e < Reg<M0>::n; e += kTT) {
-      const int rr = e / Reg<M0>::w, pp = e - rr * Reg<M0>::w;
-      const int j = T.J0 - M0 + rr, i = 2 * (T.P0 - Reg<M0>::mp + pp) + ((j + 1) & 1);
-      sR0[e] = inner(n, i, j) ? relax_from_zero(F(i, j), wd_at(L, wdf, i, j)) : 0.f;
-    }
-    __syncthreads();
-    auto xR0 = [=](int i, int j) { return sR0[T.at<M0>(i, j)]; };
-    if constexpr (NS == 2) {
-      // black nodes of sweep 1 (their old values and black neighbours are 0)
-      for (int e = tid; e < Reg<M1>::n; e += kTT) {
-        const int rr = e / Reg<M1>::w, pp = e - rr * Reg<M1>::w;
-        const int j = T.J0 - M1 + rr, i = 2 * (T.P0 - Reg<M1>::mp + pp) + (j & 1);
-        float v = 0.f;
-        if (inner(n, i, j)) {
-          const float s =
-              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR0(a, b) : 0.f; });
-          v = relax<EXACT>(s, F(i, j), 0.f, wd_at(L, wdf, i, j));
-        }
-        sB1[e] = v;
-      }
-      __syncthreads();
-      auto xB1 = [=](int i, int j) { return sB1[T.at<M1>(i, j)]; };
-      // red nodes of sweep 2
-      for (int e = tid; e < Reg<M2>::n; e += kTT) {
-        const int rr = e / Reg<M2>::w, pp = e - rr * Reg<M2>::w;
-        const int j = T.J0 - M2 + rr, i = 2 * (T.P0 - Reg<M2>::mp + pp) + ((j + 1) & 1);
-        float v = 0.f;
-        if (inner(n, i, j)) {
-          const float s =
-              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR0(a, b) : xB1(a, b); });
-          v = relax<EXACT>(s, F(i, j), xR0(i, j), wd_at(L, wdf, i, j));
-        }
-        sR2[e] = v;
-      }
-      __syncthreads();
-      auto xR2 = [=](int i, int j) { return sR2[T.at<M2>(i, j)]; };
-      // black nodes of sweep 2 on the tile, stored with their red partners
-      for (int e = tid; e < kTJ * kTP; e += kTT) {
-        const int rr = e / kTP, pp = e - rr * kTP;
-        const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);
-        float v = 0.f;
-        if (inner(n, i, j)) {
-          const float s =
-              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR2(a, b) : xB1(a, b); });
-          v = relax<EXACT>(s, F(i, j), xB1(i, j), wd_at(L, wdf, i, j));
-        }
-        store_pair(out, pitch, n, j, p, xR2(2 * p + ((j + 1) & 1), j), v);
-      }
-    } else {
-      for (int e = tid; e < kTJ * kTP; e += kTT) {
-        const int rr = e / kTP, pp = e - rr * kTP;
-        const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);
-        float v = 0.f;
-        if (inner(n, i, j)) {
-          const float s =
-              stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR0(a, b) : 0.f; });
-          v = relax<EXACT>(s, F(i, j), 0.f, wd_at(L, wdf, i, j));
-        }
-        store_pair(out, pitch, n, j, p, xR0(2 * p + ((j + 1) & 1), j), v);
-      }
-    }
+    };
+    if (fast_tile<M0>(L, T)) run(std::false_type{});
+    else run(std::true_type{});
   });
 }
 
@@ -482,42 +529,42 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_sweep(const LevelDev<float>* __
   const int n = L.n, pitch = L.pitch;
   const CUtensorMap* const maps[2] = {&mapU, &mapF};
   tile_block<2>(box0, pad32(BN), maps, G::HX, G::HY, status, [&](const Tile& T, float* sU) {
-    const int tid = threadIdx.x;
     float* sF = sU + pad32(BN);
-    if (fast_tile<R>(L, T)) {
-      const SBox<G::HX, G::HY> ub{sU}, fb{sF};
-      const SCompact<R> rn{sR};
-      phase<EXACT, NT, true, R, false>(c, wdf, ub, ub, ub, fb, [=](int e, int, int, int, float v) { sR[e] = v; });
-      __syncthreads();
-      phase<EXACT, NT, false, 0, false>(c, wdf, rn, ub, ub, fb, [=](int, int rr, int pp, int a, float v) {
-        put_pair(out, pitch, T.J0 + rr, T.P0 + pp, sR[rn.template base<0>(rr, pp, a)], v);
-      });
-      return;
-    }
+    const SBox<G::HX, G::HY> ub{sU}, fb{sF};
+    const SCompact<R> rn{sR};
     auto U = [=](int i, int j) { return sU[T.box<G::HX, G::HY>(i, j)]; };
     auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
-    // red half-sweep on the tile plus R
-    for (int e = tid; e < Reg<R>::n; e += kTT) {
-      const int rr = e / Reg<R>::w, pp = e - rr * Reg<R>::w;
-      const int j = T.J0 - R + rr, i = 2 * (T.P0 - Reg<R>::mp + pp) + ((j + 1) & 1);
-      float v = U(i, j);
-      if (inner(n, i, j)) v = relax<EXACT>(stencil<EXACT, NT>(L, c, i, j, U), F(i, j), v, wd_at(L, wdf, i, j));
-      sR[e] = v;
-    }
-    __syncthreads();
     auto xR = [=](int i, int j) { return sR[T.at<R>(i, j)]; };
-    // black half-sweep on the tile
-    for (int e = tid; e < kTJ * kTP; e += kTT) {
-      const int rr = e / kTP, pp = e - rr * kTP;
-      const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);
-      float v = U(i, j);
-      if (inner(n, i, j)) {
-        const float s =
-            stencil<EXACT, NT>(L, c, i, j, [=](int a, int b) { return ((a + b) & 1) ? xR(a, b) : U(a, b); });
-        v = relax<EXACT>(s, F(i, j), v, wd_at(L, wdf, i, j));
+    auto gr = [=](int i, int j) {  // red half-sweep on the tile plus R, nodes outside the fast range
+      const float v = U(i, j);
+      return inner(n, i, j) ? relax<EXACT>(stencil<EXACT, NT>(L, c, i, j, U), F(i, j), v, wd_at(L, wdf, i, j)) : v;
+    };
+    auto gb = [=](int i, int j) {  // black half-sweep on the tile, nodes outside the fast range
+      const float v = U(i, j);
+      if (!inner(n, i, j)) return v;
+      const float st = stencil<EXACT, NT>(L, c, i, j, [=](int x, int y) { return ((x + y) & 1) ? xR(x, y) : U(x, y); });
+      return relax<EXACT>(st, F(i, j), v, wd_at(L, wdf, i, j));
+    };
+    auto run = [&](auto check) {
+      constexpr bool EDGE = decltype(check)::value;
+      auto sink_r = [=](int e, int, int, int, float v) { sR[e] = v; };
+      auto sink_b = [=](int, int rr, int pp, int a, float v) {
+        const float red = sR[rn.template base<0>(rr, pp, a)];
+        if constexpr (EDGE) store_pair(out, pitch, n, T.J0 + rr, T.P0 + pp, red, v);
+        else put_pair(out, pitch, T.J0 + rr, T.P0 + pp, red, v);
+      };
+      if constexpr (EDGE) {
+        phase_edge<EXACT, NT, true, R, false>(c, wdf, ub, ub, ub, fb, sink_r, L, T, gr);
+        __syncthreads();
+        phase_edge<EXACT, NT, false, 0, false>(c, wdf, rn, ub, ub, fb, sink_b, L, T, gb);
+      } else {
+        phase<EXACT, NT, true, R, false>(c, wdf, ub, ub, ub, fb, sink_r);
+        __syncthreads();
+        phase<EXACT, NT, false, 0, false>(c, wdf, rn, ub, ub, fb, sink_b);
       }
-      store_pair(out, pitch, n, j, p, xR(2 * p + ((j + 1) & 1), j), v);
-    }
+    };
+    if (fast_tile<R>(L, T)) run(std::false_type{});
+    else run(std::true_type{});
   });
 }
 
@@ -545,77 +592,84 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
   tile_block<2>(box0, pad32(BN), maps, G::HX, G::HY, status, [&](const Tile& T, float* sU) {
     const int tid = threadIdx.x;
     float* sF = sU + pad32(BN);
-    if (fast_tile<1>(L, T)) {
-      const SBox<G::HX, G::HY> ub{sU}, fb{sF};
-      const SCompact<1> dr{sD};
-      // red residuals on the tile plus 1 (kIlp nodes per thread at a time, as in phase)
-      for (int e0 = tid; e0 < Reg<1>::n; e0 += kIlp * kTT) {
-        float d[kIlp];
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-          const int e = min(e0 + u * kTT, Reg<1>::n - 1);
-          const int rr = e / Reg<1>::w, pp = e - rr * Reg<1>::w;
-          const int a = rr & 1;  // red node of row J0 - 1 + rr
-          const int b = ub.template base<1>(rr, pp, a);
-          d[u] = Arith<float>::sub(fb.template get<0, 0>(b, a), cross<EXACT, NT>(c, ub, b, ub, b, a));
-        }
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u)
-          if (e0 + u * kTT < Reg<1>::n) sD[e0 + u * kTT] = d[u];
-      }
-      __syncthreads();
-      for (int e0 = tid; e0 < kTJ * kTP; e0 += kIlp * kTT) {
-        float v[kIlp];
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-          const int e = e0 + u * kTT;  // kTJ * kTP is a multiple of kIlp * kTT
-          const int rr = e / kTP, pp = e - rr * kTP;
-          const int a = rr & 1;  // black node = coarse node
-          const int b = ub.template base<0>(rr, pp, a);
-          const float d = Arith<float>::sub(fb.template get<0, 0>(b, a), cross<EXACT, NT>(c, ub, b, ub, b, a));
-          const int bd = dr.template base<0>(rr, pp, a);
-          // R = 1/2 P^T, Eq. (transfer_r2): terms (0,-1), (-1,0), (0,0), (1,0), (0,1)
-          float w = Arith<float>::mul(0.125f, dr.template get<0, -1>(bd, a));
-          w = madd<float, EXACT>(w, 0.125f, dr.template get<-1, 0>(bd, a));
-          w = madd<float, EXACT>(w, 0.5f, d);
-          w = madd<float, EXACT>(w, 0.125f, dr.template get<1, 0>(bd, a));
-          v[u] = madd<float, EXACT>(w, 0.125f, dr.template get<0, 1>(bd, a));
-        }
-#pragma unroll
-        for (int u = 0; u < kIlp; ++u) {
-          const int e = e0 + u * kTT;
-          const int rr = e / kTP, pp = e - rr * kTP;
-          const int j = T.J0 + rr, i = 2 * (T.P0 + pp) + (rr & 1);
-          const int64_t at = (int64_t)j * pc + (i >> 1);
-          fc[at] = v[u];
-          if (TC) tc[at] = (i & 1) ? relax_from_zero(v[u], node_wd(Lc, i, j)) : 0.f;
-        }
-      }
-      return;
-    }
+    const SBox<G::HX, G::HY> ub{sU}, fb{sF};
+    const SCompact<1> dr{sD};
     auto U = [=](int i, int j) { return sU[T.box<G::HX, G::HY>(i, j)]; };
     auto F = [=](int i, int j) { return sF[T.box<G::HX, G::HY>(i, j)]; };
-    for (int e = tid; e < Reg<1>::n; e += kTT) {
-      const int rr = e / Reg<1>::w, pp = e - rr * Reg<1>::w;
-      const int j = T.J0 - 1 + rr, i = 2 * (T.P0 - Reg<1>::mp + pp) + ((j + 1) & 1);
-      sD[e] = inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, NT>(L, c, i, j, U)) : 0.f;
-    }
-    __syncthreads();
-    auto D = [=](int i, int j) { return sD[T.at<1>(i, j)]; };
-    for (int e = tid; e < kTJ * kTP; e += kTT) {
-      const int rr = e / kTP, pp = e - rr * kTP;
-      const int j = T.J0 + rr, p = T.P0 + pp, i = 2 * p + (j & 1);  // black node = coarse node
-      if (!inner(n, i, j)) continue;
-      const float d = Arith<float>::sub(F(i, j), stencil<EXACT, NT>(L, c, i, j, U));
-      float v = Arith<float>::mul(0.125f, D(i, j - 1));
-      v = madd<float, EXACT>(v, 0.125f, D(i - 1, j));
-      v = madd<float, EXACT>(v, 0.5f, d);
-      v = madd<float, EXACT>(v, 0.125f, D(i + 1, j));
-      v = madd<float, EXACT>(v, 0.125f, D(i, j + 1));
+    // red residual at element e = (rr, pp) of the tile plus 1: fast, or as the per-step
+    // kernels (0 off the interior)
+    auto red_fast = [=](int e, int rr, int pp) {
+      const int a = rr & 1;  // red node of row J0 - 1 + rr
+      const int b = ub.template base<1>(rr, pp, a);
+      sD[e] = Arith<float>::sub(fb.template get<0, 0>(b, a), cross<EXACT, NT>(c, ub, b, ub, b, a));
+    };
+    // black node (rr, pp) of the tile = coarse node, residual d: R = 1/2 P^T,
+    // Eq. (transfer_r2): terms (0,-1), (-1,0), (0,0), (1,0), (0,1)
+    auto coarse = [=](int rr, int pp, float d) {
+      const int a = rr & 1;
+      const int j = T.J0 + rr, i = 2 * (T.P0 + pp) + a;
+      const int bd = dr.template base<0>(rr, pp, a);
+      float w = Arith<float>::mul(0.125f, dr.template get<0, -1>(bd, a));
+      w = madd<float, EXACT>(w, 0.125f, dr.template get<-1, 0>(bd, a));
+      w = madd<float, EXACT>(w, 0.5f, d);
+      w = madd<float, EXACT>(w, 0.125f, dr.template get<1, 0>(bd, a));
+      const float v = madd<float, EXACT>(w, 0.125f, dr.template get<0, 1>(bd, a));
       const int64_t at = (int64_t)j * pc + (i >> 1);
       fc[at] = v;
       if (TC) tc[at] = (i & 1) ? relax_from_zero(v, node_wd(Lc, i, j)) : 0.f;
-    }
+    };
+    auto black_d = [=](int rr, int pp) {
+      const int a = rr & 1;
+      const int b = ub.template base<0>(rr, pp, a);
+      return Arith<float>::sub(fb.template get<0, 0>(b, a), cross<EXACT, NT>(c, ub, b, ub, b, a));
+    };
+    auto run = [&](auto check) {
+      constexpr bool EDGE = decltype(check)::value;
+      for (int e = tid; e < Reg<1>::n; e += kTT) {
+        const int rr = e / Reg<1>::w, pp = e - rr * Reg<1>::w;
+        if constexpr (EDGE) {
+          int i, j;
+          node_of<1>(T, rr, pp, rr & 1, i, j);
+          if (!fast_node_c<false>(L, i, j)) continue;
+        }
+        red_fast(e, rr, pp);
+      }
+      if constexpr (EDGE) {  // the nodes outside the fast range, in the strips
+        const Strips<1> st(L, T);
+        for (int k = tid; k < st.count; k += kTT) {
+          int rr, pp;
+          st.at(k, rr, pp);
+          int i, j;
+          node_of<1>(T, rr, pp, rr & 1, i, j);
+          if (fast_node_c<false>(L, i, j)) continue;
+          sD[rr * Reg<1>::w + pp] =
+              inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, NT>(L, c, i, j, U)) : 0.f;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < kTJ * kTP; e += kTT) {
+        const int rr = e / kTP, pp = e - rr * kTP;
+        if constexpr (EDGE) {
+          int i, j;
+          node_of<0>(T, rr, pp, rr & 1, i, j);
+          if (!fast_node_c<false>(L, i, j)) continue;
+        }
+        coarse(rr, pp, black_d(rr, pp));
+      }
+      if constexpr (EDGE) {
+        const Strips<0> st(L, T);
+        for (int k = tid; k < st.count; k += kTT) {
+          int rr, pp;
+          st.at(k, rr, pp);
+          int i, j;
+          node_of<0>(T, rr, pp, rr & 1, i, j);
+          if (fast_node_c<false>(L, i, j) || !inner(n, i, j)) continue;
+          coarse(rr, pp, Arith<float>::sub(F(i, j), stencil<EXACT, NT>(L, c, i, j, U)));
+        }
+      }
+    };
+    if (fast_tile<1>(L, T)) run(std::false_type{});
+    else run(std::true_type{});
   });
 }
 
