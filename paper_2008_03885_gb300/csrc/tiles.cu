@@ -297,40 +297,59 @@ __device__ __forceinline__ void node_of(const Tile& T, int rr, int pp, int a, in
   i = 2 * (T.P0 - Reg<M>::mp + pp) + a;
 }
 
-// Strips of a region of margin M (tile T of level L) that may hold nodes outside the
-// fast range (rx <= i <= fxe, ry <= j <= fye): rows [0, rt) and [rb, h), and in the rows
-// between them the pairs [0, pl) and [pr, w). A superset of those nodes, without overlap.
+// Strips of a region of margin M (tile T of level L) that hold its nodes outside the
+// fast range (rx <= i <= fxe, ry <= j <= fye) within rows 0 <= j <= n and columns
+// 0 <= i <= n + 1: rows [r0, rt) and [rb, r1), and in the rows between them the pairs
+// [p0, pl) and [pr, p1). A superset of those nodes, without overlap. Nodes beyond those
+// rows and columns are never read (fast stencils stay two nodes inside the boundary,
+// boundary-class rows drop boundary columns) nor stored, so they are left unset.
 template <int M>
 struct Strips {
-  int rt, rb, pl, pr, mw, count;
+  int r0, rt, rb, r1, p0, pl, pr, p1, pw, mw, count;
   __device__ __forceinline__ Strips(const LevelDev<float>& L, const Tile& T) {
     constexpr int W = Reg<M>::w, H = Reg<M>::h;
     const int j0 = T.J0 - M, q0 = T.P0 - Reg<M>::mp;  // lattice row / pair index of element (0, 0)
-    rt = min(max(L.ry - j0, 0), H);
-    rb = max(rt, min(max(L.fye + 1 - j0, 0), H));
-    pl = min(max(L.rx / 2 + 1 - q0, 0), W);        // pair q holds i = 2q + a < rx only if q <= rx / 2
-    pr = max(pl, min(max(L.fxe / 2 - q0, 0), W));  // ... i > fxe only if q >= fxe / 2
-    mw = pl + (W - pr);
-    count = (rt + H - rb) * W + (rb - rt) * mw;
+    r0 = min(max(-j0, 0), H);
+    r1 = max(r0, min(L.n + 1 - j0, H));
+    rt = min(max(L.ry - j0, r0), r1);
+    rb = max(rt, min(max(L.fye + 1 - j0, r0), r1));
+    p0 = min(max(-q0, 0), W);
+    p1 = max(p0, min((L.n + 1) / 2 + 1 - q0, W));      // pairs q <= (n + 1) / 2
+    pl = min(max(L.rx / 2 + 1 - q0, p0), p1);           // pair q holds i = 2q + a < rx only if q <= rx / 2
+    pr = max(pl, min(max(L.fxe / 2 - q0, p0), p1));    // ... i > fxe only if q >= fxe / 2
+    pw = p1 - p0;
+    mw = (pl - p0) + (p1 - pr);
+    count = (rt - r0 + r1 - rb) * pw + (rb - rt) * mw;
   }
   // element k of the strips
   __device__ __forceinline__ void at(int k, int& rr, int& pp) const {
-    constexpr int W = Reg<M>::w;
-    const int k1 = rt * W, k2 = k1 + (Reg<M>::h - rb) * W;
+    const int k1 = (rt - r0) * pw, k2 = k1 + (r1 - rb) * pw;
     if (k < k1) {
-      rr = k / W;
-      pp = k - rr * W;
+      const int q = k / pw;
+      rr = r0 + q;
+      pp = p0 + (k - q * pw);
     } else if (k < k2) {
-      const int q = (k - k1) / W;
+      const int q = (k - k1) / pw;
       rr = rb + q;
-      pp = k - k1 - q * W;
+      pp = p0 + (k - k1 - q * pw);
     } else {
       const int q = (k - k2) / mw, r = k - k2 - q * mw;
       rr = rt + q;
-      pp = r < pl ? r : pr + (r - pl);
+      pp = r < pl - p0 ? p0 + r : pr + (r - (pl - p0));
     }
   }
 };
+
+// Rows [fast_row0, fast_row0 + fast_rows) of a region of margin M: those that hold
+// nodes of the fast range (ry <= j <= fye).
+template <int M>
+__device__ __forceinline__ int fast_row0(const LevelDev<float>& L, const Tile& T) {
+  return min(max(L.ry - (T.J0 - M), 0), Reg<M>::h);
+}
+template <int M>
+__device__ __forceinline__ int fast_rows(const LevelDev<float>& L, const Tile& T, int r0) {
+  return max(min(L.fye + 1 - (T.J0 - M), Reg<M>::h) - r0, 0);
+}
 
 // The same phase in a tile that reaches the level's boundary strip: the nodes of the
 // fast range get their fast value; every other node of the region (a boundary-class
@@ -342,13 +361,14 @@ template <bool EXACT, int NT, bool RED, int M, bool ZERO_START, class SO, class 
 __device__ __forceinline__ void phase_edge(const float (&c)[NT], float wd, const SO& so, const SS& ss,
                                            const SOLD& sold, const FB& fb, SINK sink, const LevelDev<float>& L,
                                            const Tile& T, GEN gen) {
-  for (int e = threadIdx.x; e < Reg<M>::n; e += kTT) {
-    const int rr = e / Reg<M>::w, pp = e - rr * Reg<M>::w;
+  const int fr0 = fast_row0<M>(L, T), nf = fast_rows<M>(L, T, fr0) * Reg<M>::w;
+  for (int e = threadIdx.x; e < nf; e += kTT) {
+    const int rq = e / Reg<M>::w, pp = e - rq * Reg<M>::w, rr = fr0 + rq;
     const int a = (rr + M + (RED ? 1 : 0)) & 1;
     int i, j;
     node_of<M>(T, rr, pp, a, i, j);
     if (!fast_node_c<false>(L, i, j)) continue;
-    sink(e, rr, pp, a, fast_value<EXACT, NT, M, ZERO_START>(c, wd, so, ss, sold, fb, rr, pp, a));
+    sink(rr * Reg<M>::w + pp, rr, pp, a, fast_value<EXACT, NT, M, ZERO_START>(c, wd, so, ss, sold, fb, rr, pp, a));
   }
   const Strips<M> st(L, T);
   for (int k = threadIdx.x; k < st.count; k += kTT) {
@@ -625,14 +645,17 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
     };
     auto run = [&](auto check) {
       constexpr bool EDGE = decltype(check)::value;
-      for (int e = tid; e < Reg<1>::n; e += kTT) {
-        const int rr = e / Reg<1>::w, pp = e - rr * Reg<1>::w;
+      // edge tiles walk only the rows that hold fast nodes, then the strips
+      const int fa = EDGE ? fast_row0<1>(L, T) : 0;
+      const int na = EDGE ? fast_rows<1>(L, T, fa) * Reg<1>::w : Reg<1>::n;
+      for (int e = tid; e < na; e += kTT) {
+        const int rq = e / Reg<1>::w, pp = e - rq * Reg<1>::w, rr = fa + rq;
         if constexpr (EDGE) {
           int i, j;
           node_of<1>(T, rr, pp, rr & 1, i, j);
           if (!fast_node_c<false>(L, i, j)) continue;
         }
-        red_fast(e, rr, pp);
+        red_fast(rr * Reg<1>::w + pp, rr, pp);
       }
       if constexpr (EDGE) {  // the nodes outside the fast range, in the strips
         const Strips<1> st(L, T);
@@ -647,8 +670,10 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
         }
       }
       __syncthreads();
-      for (int e = tid; e < kTJ * kTP; e += kTT) {
-        const int rr = e / kTP, pp = e - rr * kTP;
+      const int fb0 = EDGE ? fast_row0<0>(L, T) : 0;
+      const int nb = EDGE ? fast_rows<0>(L, T, fb0) * kTP : kTJ * kTP;
+      for (int e = tid; e < nb; e += kTT) {
+        const int rq = e / kTP, pp = e - rq * kTP, rr = fb0 + rq;
         if constexpr (EDGE) {
           int i, j;
           node_of<0>(T, rr, pp, rr & 1, i, j);
