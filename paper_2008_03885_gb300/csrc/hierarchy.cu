@@ -1114,7 +1114,7 @@ mg_status cycle_level(const Ctx& c, int l, T* U, const T* F, bool zero_init, boo
   // that level runs as separate launches (and does not start with a tile presmooth).
   const bool coarse_red = l + 1 != lmax && l + 1 != H.tail_level && h->opt.smoother == MG_SMOOTH_REDBLACK &&
                           !fused_sweeps<T>(h) && h->opt.nu1 >= 1 && !tile_presmooth<T>(h, l + 1);
-  if (tl && cur == U && h->transfer[l] == kRbAxisToRot) {
+  if (tl && cur == U && (h->transfer[l] == kRbAxisToRot || h->transfer[l] == kRbRotToAxis)) {
     Bracket b(h, l, MG_KERNEL_RESIDUAL, c.s);
     LAUNCH(h, 1, launch_tile_res_restrict(*tl, f32(H.L[l]), f32(H.L[l + 1]), c.exact,
                                           (float*)H.f[l + 1], coarse_red ? (float*)H.t[l + 1] : nullptr,

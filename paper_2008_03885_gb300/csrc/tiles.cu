@@ -698,6 +698,360 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
   });
 }
 
+// ---- rotated levels ----------------------------------------------------------------
+// A rotated level's storage row j holds the lattice nodes i = 2q + (j & 1) (q = storage
+// column); its red nodes are the odd rows, its black nodes the even rows. A block owns
+// kRC storage columns x kRR rows (J0 even). Each colour's values live in compact arrays
+// of that colour's rows of a region (M rows and MC columns around the tile, M even).
+// The fast stencil is the first Galerkin 9-point one (Eq. L_G1): terms 0-3 (the +-2
+// lattice axis neighbours) on rows of the node's colour, terms 4-7 (the diagonal
+// neighbours) on the rows of the other colour, term 8 the centre; the host checks this
+// shape, and the storage offsets (sdx by row parity, sdy) come from the level.
+constexpr int kRC = 64;
+constexpr int kRR = 32;
+
+template <int M, int MC>
+struct RReg {
+  static constexpr int w = kRC + 2 * MC;
+  static constexpr int h = kRR / 2 + M;
+  static constexpr int n = w * h;
+};
+
+struct RTile {
+  int J0, C0;
+  __device__ RTile(int bx, int by) : J0(by * kRR), C0(bx * kRC) {}
+};
+
+// Sources of one colour: RComp (compact rows of parity PAR of a region with margins
+// M, MC), RBox (a staged TMA box, both colours, halo HX, HY), RZero (the zero start).
+// step2: index distance from a row to the next row of the same colour.
+template <int M, int MC, int PAR>
+struct RComp {
+  float* p;
+  static constexpr int step2 = RReg<M, MC>::w;
+  __device__ __forceinline__ int idx(const RTile& T, int q, int j) const {
+    return ((j - (T.J0 - M) - PAR) >> 1) * RReg<M, MC>::w + (q - (T.C0 - MC));
+  }
+  __device__ __forceinline__ float at(int k) const { return p[k]; }
+};
+template <int HX, int HY>
+struct RBox {
+  const float* p;
+  static constexpr int W = kRC + 2 * HX;
+  static constexpr int step2 = 2 * W;
+  __device__ __forceinline__ int idx(const RTile& T, int q, int j) const {
+    return (j - (T.J0 - HY)) * W + (q - (T.C0 - HX));
+  }
+  __device__ __forceinline__ float at(int k) const { return p[k]; }
+};
+struct RZero {
+  static constexpr int step2 = 0;
+  __device__ __forceinline__ int idx(const RTile&, int, int) const { return 0; }
+  __device__ __forceinline__ float at(int) const { return 0.f; }
+};
+
+// The fast stencil of a rotated level: coefficients and storage offsets by row parity.
+struct RStencil {
+  float c[9];
+  int sx[2][9], sy[9];
+  __device__ __forceinline__ explicit RStencil(const LevelDev<float>& L) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      c[k] = L.c[k];
+      sx[0][k] = L.sdx[0][k];
+      sx[1][k] = L.sdx[1][k];
+      sy[k] = L.sdy[k];
+    }
+  }
+};
+
+// (L x) at a fast node of parity PAR: same-colour terms from ss (base bs = node), other-
+// colour terms from so (base bo = node's column on row j - 1), in evaluation order.
+template <bool EXACT, int PAR, class SS, class SO>
+__device__ __forceinline__ float rcross(const RStencil& S, const SS& ss, int bs, const SO& so, int bo) {
+  float x[9];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) x[k] = ss.at(bs + (S.sy[k] / 2) * SS::step2 + S.sx[PAR][k]);
+#pragma unroll
+  for (int k = 4; k < 8; ++k) x[k] = so.at(bo + ((S.sy[k] + 1) / 2) * SO::step2 + S.sx[PAR][k]);
+  x[8] = ss.at(bs);
+  if constexpr (EXACT) {
+    const float g0 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x[0], x[1]), x[2]), x[3]);
+    const float g1 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x[4], x[5]), x[6]), x[7]);
+    return Arith<float>::add(Arith<float>::add(Arith<float>::mul(S.c[0], g0), Arith<float>::mul(S.c[4], g1)),
+                             Arith<float>::mul(S.c[8], x[8]));
+  } else {
+    float s = Arith<float>::mul(S.c[0], x[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) s = Arith<float>::fma(S.c[k], x[k], s);
+    return s;
+  }
+}
+
+// Value of lattice node (a, b) in a source.
+template <class SRC>
+__device__ __forceinline__ float rval(const SRC& s, const RTile& T, int a, int b) {
+  return s.at(s.idx(T, a >> 1, b));
+}
+
+// One relaxation phase over the nodes of colour PAR in the region (M, MC): the fast
+// value (relax of the fast stencil, or 0 + f omega / a_pp with ZERO) for nodes of the
+// fast range; with EDGE the other nodes get gen(i, j). sink(e, q, j, v), e = index in
+// the region's compact array.
+template <bool EXACT, int PAR, int M, int MC, bool ZERO, bool EDGE, class SS, class SO, class FB, class SINK, class GEN>
+__device__ __forceinline__ void rphase(const RStencil& S, float wd, const SS& ss, const SO& so, const FB& fb,
+                                       const RTile& T, const LevelDev<float>& L, SINK sink, GEN gen) {
+  using G = RReg<M, MC>;
+  for (int e = threadIdx.x; e < G::n; e += kTT) {
+    const int kr = e / G::w, cq = e - kr * G::w;
+    const int j = T.J0 - M + 2 * kr + PAR, q = T.C0 - MC + cq;
+    if (EDGE && !fast_node_c<false>(L, 2 * q + PAR, j)) {
+      sink(e, q, j, gen(2 * q + PAR, j));
+      continue;
+    }
+    const float f = fb.at(fb.idx(T, q, j));
+    float v;
+    if constexpr (ZERO) {
+      v = relax_from_zero(f, wd);
+    } else {
+      const int bs = ss.idx(T, q, j);
+      v = relax<EXACT>(rcross<EXACT, PAR>(S, ss, bs, so, so.idx(T, q, j - 1)), f, ss.at(bs), wd);
+    }
+    sink(e, q, j, v);
+  }
+}
+
+// Whether every node of the region (M, MC) is in the fast range of the rotated level L.
+template <int M, int MC>
+__device__ __forceinline__ bool rfast_tile(const LevelDev<float>& L, const RTile& T) {
+  return 2 * (T.C0 - MC) >= L.rx && 2 * (T.C0 + kRC + MC - 1) + 1 <= L.fxe && T.J0 - M >= L.ry &&
+         T.J0 + kRR - 1 + M <= L.fye;
+}
+
+template <int NB, class BODY>
+__device__ __forceinline__ void rtile_block(float* box0, int box_floats, const CUtensorMap* const (&maps)[NB], int hx,
+                                            int hy, int* status, BODY body) {
+  __shared__ uint64_t bar;
+  const RTile T(blockIdx.x, blockIdx.y);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar);
+    mbar_expect(&bar, (uint32_t)(NB * (kRC + 2 * hx) * (kRR + 2 * hy) * sizeof(float)));
+#pragma unroll
+    for (int m = 0; m < NB; ++m) tma_load(box0 + m * box_floats, maps[m], T.C0 - hx, T.J0 - hy, &bar);
+  }
+  __syncthreads();
+  if (!wait_tile(&bar, status)) return;
+  body(T, box0);
+}
+
+// Store row j of the tile (values from the compact array src of that row's colour) to
+// the level's storage, bounds-checked.
+template <class SRC>
+__device__ __forceinline__ void rstore_row(float* out, const LevelDev<float>& L, const RTile& T, const SRC& src, int j,
+                                           int cq) {
+  const int q = T.C0 + cq;
+  if (j > L.n || q >= L.cols) return;
+  out[(int64_t)j * L.pitch + q] = src.at(src.idx(T, q, j));
+}
+
+// Box geometry of the rotated kernels (x halo rounded to 4 floats for TMA).
+constexpr int kRHX = 4;
+constexpr int kRPreHY = 6;  // presmooth: f on red rows of the tile plus 6 rows, 3 columns
+constexpr int kRHY = 4;     // sweep, residual + restriction: u, f on the tile plus 4 rows
+
+// ---- rotated presmooth: 2 red-black sweeps from u = 0 ------------------------------
+template <bool EXACT>
+__global__ void __launch_bounds__(kTT, 3) k_rtile_presmooth(const LevelDev<float>* __restrict__ Lp,
+                                                         const __grid_constant__ CUtensorMap mapF,
+                                                         float* __restrict__ out, int* __restrict__ status) {
+  constexpr int FN = (kRC + 2 * kRHX) * (kRR + 2 * kRPreHY);
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float* box0 = smem_base(tile_smem);
+  float* sR0 = box0 + pad32(FN);
+  float* sB1 = sR0 + RReg<6, 3>::n;
+  float* sR2 = sB1 + RReg<4, 2>::n;
+  const LevelDev<float>& L = *Lp;
+  const RStencil S(L);
+  const float wdf = L.wd;
+  const int n = L.n;
+  const CUtensorMap* const maps[1] = {&mapF};
+  rtile_block<1>(box0, pad32(FN), maps, kRHX, kRPreHY, status, [&](const RTile& T, float* sF) {
+    const RBox<kRHX, kRPreHY> fb{sF};
+    const RComp<6, 3, 1> r0{sR0};
+    const RComp<4, 2, 0> b1{sB1};
+    const RComp<2, 1, 1> r2{sR2};
+    auto F = [=](int i, int j) { return rval(fb, T, i, j); };
+    auto run = [&](auto check) {
+      constexpr bool EDGE = decltype(check)::value;
+      // red from zero: 0 + f omega / a_pp
+      rphase<EXACT, 1, 6, 3, true, EDGE>(S, wdf, RZero{}, RZero{}, fb, T, L,
+                                         [=](int e, int, int, float v) { sR0[e] = v; }, [=](int i, int j) {
+                                           return inner(n, i, j) ? relax_from_zero(F(i, j), wd_at(L, wdf, i, j)) : 0.f;
+                                         });
+      __syncthreads();
+      // black of sweep 1 (old values 0)
+      rphase<EXACT, 0, 4, 2, false, EDGE>(S, wdf, RZero{}, r0, fb, T, L, [=](int e, int, int, float v) { sB1[e] = v; },
+                                          [=](int i, int j) {
+                                            if (!inner(n, i, j)) return 0.f;
+                                            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+                                              return (a & 1) ? rval(r0, T, a, b) : 0.f;
+                                            });
+                                            return relax<EXACT>(st, F(i, j), 0.f, wd_at(L, wdf, i, j));
+                                          });
+      __syncthreads();
+      // red of sweep 2
+      rphase<EXACT, 1, 2, 1, false, EDGE>(S, wdf, r0, b1, fb, T, L, [=](int e, int, int, float v) { sR2[e] = v; },
+                                          [=](int i, int j) {
+                                            if (!inner(n, i, j)) return 0.f;
+                                            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+                                              return (a & 1) ? rval(r0, T, a, b) : rval(b1, T, a, b);
+                                            });
+                                            return relax<EXACT>(st, F(i, j), rval(r0, T, i, j), wd_at(L, wdf, i, j));
+                                          });
+      __syncthreads();
+      // black of sweep 2 on the tile, stored; then the red rows of the tile
+      rphase<EXACT, 0, 0, 0, false, EDGE>(
+          S, wdf, b1, r2, fb, T, L,
+          [=](int, int q, int j, float v) {
+            if (EDGE && (j > n || q >= L.cols)) return;
+            out[(int64_t)j * L.pitch + q] = v;
+          },
+          [=](int i, int j) {
+            if (!inner(n, i, j)) return 0.f;
+            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+              return (a & 1) ? rval(r2, T, a, b) : rval(b1, T, a, b);
+            });
+            return relax<EXACT>(st, F(i, j), rval(b1, T, i, j), wd_at(L, wdf, i, j));
+          });
+      for (int e = threadIdx.x; e < (kRR / 2) * kRC; e += kTT) {
+        const int kr = e / kRC, cq = e - kr * kRC;
+        rstore_row(out, L, T, r2, T.J0 + 2 * kr + 1, cq);
+      }
+    };
+    if (rfast_tile<6, 3>(L, T)) run(std::false_type{});
+    else run(std::true_type{});
+  });
+}
+
+// ---- rotated sweep: one red-black sweep, u -> out ------------------------------------
+template <bool EXACT>
+__global__ void __launch_bounds__(kTT, 3) k_rtile_sweep(const LevelDev<float>* __restrict__ Lp,
+                                                     const __grid_constant__ CUtensorMap mapU,
+                                                     const __grid_constant__ CUtensorMap mapF, float* __restrict__ out,
+                                                     int* __restrict__ status) {
+  constexpr int BN = (kRC + 2 * kRHX) * (kRR + 2 * kRHY);
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float* box0 = smem_base(tile_smem);
+  float* sR = box0 + 2 * pad32(BN);
+  const LevelDev<float>& L = *Lp;
+  const RStencil S(L);
+  const float wdf = L.wd;
+  const int n = L.n;
+  const CUtensorMap* const maps[2] = {&mapU, &mapF};
+  rtile_block<2>(box0, pad32(BN), maps, kRHX, kRHY, status, [&](const RTile& T, float* sU) {
+    const RBox<kRHX, kRHY> ub{sU}, fb{sU + pad32(BN)};
+    const RComp<2, 1, 1> rn{sR};
+    auto U = [=](int i, int j) { return rval(ub, T, i, j); };
+    auto F = [=](int i, int j) { return rval(fb, T, i, j); };
+    auto run = [&](auto check) {
+      constexpr bool EDGE = decltype(check)::value;
+      rphase<EXACT, 1, 2, 1, false, EDGE>(S, wdf, ub, ub, fb, T, L, [=](int e, int, int, float v) { sR[e] = v; },
+                                          [=](int i, int j) {
+                                            const float v = U(i, j);
+                                            return inner(n, i, j) ? relax<EXACT>(stencil<EXACT, 9>(L, S.c, i, j, U),
+                                                                                 F(i, j), v, wd_at(L, wdf, i, j))
+                                                                  : v;
+                                          });
+      __syncthreads();
+      rphase<EXACT, 0, 0, 0, false, EDGE>(
+          S, wdf, ub, rn, fb, T, L,
+          [=](int, int q, int j, float v) {
+            if (EDGE && (j > n || q >= L.cols)) return;
+            out[(int64_t)j * L.pitch + q] = v;
+          },
+          [=](int i, int j) {
+            const float v = U(i, j);
+            if (!inner(n, i, j)) return v;
+            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+              return (a & 1) ? rval(rn, T, a, b) : U(a, b);
+            });
+            return relax<EXACT>(st, F(i, j), v, wd_at(L, wdf, i, j));
+          });
+      for (int e = threadIdx.x; e < (kRR / 2) * kRC; e += kTT) {
+        const int kr = e / kRC, cq = e - kr * kRC;
+        rstore_row(out, L, T, rn, T.J0 + 2 * kr + 1, cq);
+      }
+    };
+    if (rfast_tile<2, 1>(L, T)) run(std::false_type{});
+    else run(std::true_type{});
+  });
+}
+
+// ---- rotated residual + red-black restriction (rotated level -> its axis level) ------
+// Coarse nodes = the black (even-row) nodes; R = 1/2 P^T, Eq. (transfer_r2) in the
+// rotated frame: terms (-1,-1), (1,-1), (0,0), (-1,1), (1,1) (lattice offsets).
+template <bool EXACT, bool TC>
+__global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<float>* __restrict__ Lp,
+                                                            const LevelDev<float>* __restrict__ Lcp,
+                                                            const __grid_constant__ CUtensorMap mapU,
+                                                            const __grid_constant__ CUtensorMap mapF,
+                                                            float* __restrict__ fc, float* __restrict__ tc,
+                                                            int* __restrict__ status) {
+  constexpr int BN = (kRC + 2 * kRHX) * (kRR + 2 * kRHY);
+  extern __shared__ __align__(128) unsigned char tile_smem[];
+  float* box0 = smem_base(tile_smem);
+  float* sD = box0 + 2 * pad32(BN);  // residuals of the red nodes, region (2, 1)
+  const LevelDev<float>& L = *Lp;
+  const LevelDev<float>& Lc = *Lcp;
+  const RStencil S(L);
+  const int n = L.n, pc = Lc.pitch;
+  const CUtensorMap* const maps[2] = {&mapU, &mapF};
+  rtile_block<2>(box0, pad32(BN), maps, kRHX, kRHY, status, [&](const RTile& T, float* sU) {
+    const RBox<kRHX, kRHY> ub{sU}, fb{sU + pad32(BN)};
+    const RComp<2, 1, 1> dr{sD};
+    auto U = [=](int i, int j) { return rval(ub, T, i, j); };
+    auto F = [=](int i, int j) { return rval(fb, T, i, j); };
+    auto run = [&](auto check) {
+      constexpr bool EDGE = decltype(check)::value;
+      using G = RReg<2, 1>;
+      for (int e = threadIdx.x; e < G::n; e += kTT) {  // red residuals (0 off the interior)
+        const int kr = e / G::w, cq = e - kr * G::w;
+        const int j = T.J0 - 2 + 2 * kr + 1, q = T.C0 - 1 + cq, i = 2 * q + 1;
+        if (EDGE && !fast_node_c<false>(L, i, j)) {
+          sD[e] = inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U)) : 0.f;
+          continue;
+        }
+        const int b = ub.idx(T, q, j);
+        sD[e] = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT, 1>(S, ub, b, ub, ub.idx(T, q, j - 1)));
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < (kRR / 2) * kRC; e += kTT) {  // black nodes of the tile
+        const int kr = e / kRC, cq = e - kr * kRC;
+        const int j = T.J0 + 2 * kr, q = T.C0 + cq, i = 2 * q;
+        float d;
+        if (EDGE && !fast_node_c<false>(L, i, j)) {
+          if (!inner(n, i, j)) continue;
+          d = Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U));
+        } else {
+          d = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT, 0>(S, ub, ub.idx(T, q, j), ub, ub.idx(T, q, j - 1)));
+        }
+        const int bu = dr.idx(T, q, j - 1);  // red row j - 1, columns q - 1 and q; then row j + 1
+        float w = Arith<float>::mul(0.125f, dr.at(bu - 1));
+        w = madd<float, EXACT>(w, 0.125f, dr.at(bu));
+        w = madd<float, EXACT>(w, 0.5f, d);
+        w = madd<float, EXACT>(w, 0.125f, dr.at(bu + RReg<2, 1>::w - 1));
+        const float v = madd<float, EXACT>(w, 0.125f, dr.at(bu + RReg<2, 1>::w));
+        const int I = q, J = j >> 1;  // the coarse (axis) node
+        const int64_t at = (int64_t)J * pc + I;
+        fc[at] = v;
+        if (TC) tc[at] = ((I + J) & 1) ? relax_from_zero(v, node_wd(Lc, I, J)) : 0.f;
+      }
+    };
+    if (rfast_tile<2, 1>(L, T)) run(std::false_type{});
+    else run(std::true_type{});
+  });
+}
+
 // ---- host side -----------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
@@ -715,13 +1069,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 2D map over a level's (n + 1) x (n + 1) nodes (row stride pitch) with a box of
 // (kTQ + 2 hx) x (kTJ + 2 hy) elements.
-bool make_map(CUtensorMap* m, const float* base, const LevelDev<float>& L, int hx, int hy) {
+bool make_map(CUtensorMap* m, const float* base, const LevelDev<float>& L, int hx, int hy, int tw = kTQ,
+              int th = kTJ) {
   const auto enc = tensor_map_encoder();
   if (!enc) return false;
   std::memset(m, 0, sizeof(*m));
   const cuuint64_t dims[2] = {(cuuint64_t)L.cols, (cuuint64_t)L.rows};
   const cuuint64_t strides[1] = {(cuuint64_t)L.pitch * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)(kTQ + 2 * hx), (cuuint32_t)(kTJ + 2 * hy)};
+  const cuuint32_t box[2] = {(cuuint32_t)(tw + 2 * hx), (cuuint32_t)(th + 2 * hy)};
   const cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -748,6 +1103,14 @@ size_t rr_smem() {
   return (2 * (size_t)pad32((kTQ + 2 * G::HX) * (kTJ + 2 * G::HY)) + Reg<1>::n) * sizeof(float) + 128;
 }
 
+size_t rpre_smem() {
+  return ((size_t)pad32((kRC + 2 * kRHX) * (kRR + 2 * kRPreHY)) + RReg<6, 3>::n + RReg<4, 2>::n + RReg<2, 1>::n) *
+             sizeof(float) + 128;
+}
+size_t rsw_smem() {
+  return (2 * (size_t)pad32((kRC + 2 * kRHX) * (kRR + 2 * kRHY)) + RReg<2, 1>::n) * sizeof(float) + 128;
+}
+
 // Raise a kernel's dynamic shared-memory limit once per process (the sizes are fixed
 // per instantiation).
 template <auto KERNEL>
@@ -758,10 +1121,27 @@ cudaError_t allow_smem(size_t bytes) {
 
 }  // namespace
 
+// Rotated levels: the first Galerkin 9-point stencil in evaluation order (terms 0-3 on
+// rows two apart or the same row, terms 4-7 on the adjacent rows, the centre last), no
+// term more than one storage column or two rows away.
+bool rot_tile_shape(const LevelDev<float>& L) {
+  if (L.nt != 9 || L.gmask[0] != fast_gmask(9)) return false;
+  for (int w = 1; w < kMaxTerms / 32; ++w)
+    if (L.gmask[w]) return false;
+  for (int k = 0; k < 9; ++k) {
+    const int dy = L.sdy[k];
+    if (std::abs(L.sdx[0][k]) > 1 || std::abs(L.sdx[1][k]) > 1 || std::abs(dy) > 2) return false;
+    if ((k < 4 && (dy & 1)) || (k >= 4 && k < 8 && !(dy & 1))) return false;
+  }
+  return L.sdy[8] == 0 && L.sdx[0][8] == 0 && L.sdx[1][8] == 0;
+}
+
 bool tile_eligible(const LevelPair<float>& P) {
   const LevelDev<float>& L = P.h;
-  if (L.kind != kAxis || L.per || L.bf16 || L.rows < kTileMinRows) return false;
+  if (L.per || L.bf16 || L.rows < kTileMinRows) return false;
   if (L.pitch % 4 != 0) return false;  // TMA row stride: 16 bytes
+  if (L.kind == kRot) return rot_tile_shape(L);
+  if (L.kind != kAxis) return false;
   // the fast stencil must be the 5-point or 9-point cross with terms in (dy, dx) order
   // (offsets in evaluation order: groups of equal coefficient, see LevelDev::c)
   static const int x5[5] = {0, -1, 1, 0, 0}, y5[5] = {-1, 0, 0, 1, 0};
@@ -783,9 +1163,22 @@ bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, flo
   const LevelDev<float>& L = P.h;
   T.nt = L.nt;
   T.reach = L.nt == 9 ? 2 : 1;
+  T.rot = L.kind == kRot;
+  bool ok = true;
+  if (T.rot) {  // rotated tiles: presmooth for nu1 = 2 only
+    T.nu1 = nu1 == 2 ? 2 : 0;
+    T.grid = dim3((L.cols + kRC - 1) / kRC, (L.rows + kRR - 1) / kRR);
+    if (T.nu1) ok &= make_map(&T.f_pre, f, L, kRHX, kRPreHY, kRC, kRR);
+    ok &= make_map(&T.u_sw, u, L, kRHX, kRHY, kRC, kRR);
+    ok &= make_map(&T.t_sw, t, L, kRHX, kRHY, kRC, kRR);
+    ok &= make_map(&T.f_sw, f, L, kRHX, kRHY, kRC, kRR);
+    ok &= make_map(&T.u_rr, u, L, kRHX, kRHY, kRC, kRR);
+    ok &= make_map(&T.f_rr, f, L, kRHX, kRHY, kRC, kRR);
+    T.on = ok;
+    return ok;
+  }
   T.nu1 = (nu1 == 1 || nu1 == 2) ? nu1 : 0;
   T.grid = dim3((L.cols + kTQ - 1) / kTQ, (L.rows + kTJ - 1) / kTJ);
-  bool ok = true;
   if (T.reach == 2) {
     if (T.nu1 == 2) ok &= make_map(&T.f_pre, f, L, PreGeo<2, 2>::HX, PreGeo<2, 2>::HY);
     if (T.nu1 == 1) ok &= make_map(&T.f_pre, f, L, PreGeo<2, 1>::HX, PreGeo<2, 1>::HY);
@@ -836,9 +1229,39 @@ cudaError_t rr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair
 }
 }  // namespace
 
+namespace {
+template <bool EXACT>
+cudaError_t rpresmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u, int* status, cudaStream_t s) {
+  const size_t smem = rpre_smem();
+  cudaError_t e = allow_smem<k_rtile_presmooth<EXACT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_rtile_presmooth<EXACT><<<T.grid, kTT, smem, s>>>(L.d, T.f_pre, u, status);
+  return cudaGetLastError();
+}
+template <bool EXACT>
+cudaError_t rsweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t, float* out, int* status,
+                      cudaStream_t s) {
+  const size_t smem = rsw_smem();
+  cudaError_t e = allow_smem<k_rtile_sweep<EXACT>>(smem);
+  if (e != cudaSuccess) return e;
+  k_rtile_sweep<EXACT><<<T.grid, kTT, smem, s>>>(L.d, from_t ? T.t_sw : T.u_sw, T.f_sw, out, status);
+  return cudaGetLastError();
+}
+template <bool EXACT, bool TC>
+cudaError_t rrr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc, float* fc, float* tc,
+                   int* status, cudaStream_t s) {
+  const size_t smem = rsw_smem();
+  cudaError_t e = allow_smem<k_rtile_res_restrict<EXACT, TC>>(smem);
+  if (e != cudaSuccess) return e;
+  k_rtile_res_restrict<EXACT, TC><<<T.grid, kTT, smem, s>>>(L.d, Lc.d, T.u_rr, T.f_rr, fc, tc, status);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L, bool exact, float* u, int* status,
                                   cudaStream_t s) {
   if (!T.on || !T.nu1) return cudaErrorInvalidValue;
+  if (T.rot) return exact ? rpresmooth_as<true>(T, L, u, status, s) : rpresmooth_as<false>(T, L, u, status, s);
   if (T.nt == 9) {
     if (T.nu1 == 2) return exact ? presmooth_as<true, 9, 2>(T, L, u, status, s) : presmooth_as<false, 9, 2>(T, L, u, status, s);
     return exact ? presmooth_as<true, 9, 1>(T, L, u, status, s) : presmooth_as<false, 9, 1>(T, L, u, status, s);
@@ -850,6 +1273,7 @@ cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L,
 cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, bool exact, bool from_t, float* uout,
                               int* status, cudaStream_t s) {
   if (!T.on) return cudaErrorInvalidValue;
+  if (T.rot) return exact ? rsweep_as<true>(T, L, from_t, uout, status, s) : rsweep_as<false>(T, L, from_t, uout, status, s);
   if (T.nt == 9)
     return exact ? sweep_as<true, 9>(T, L, from_t, uout, status, s) : sweep_as<false, 9>(T, L, from_t, uout, status, s);
   return exact ? sweep_as<true, 5>(T, L, from_t, uout, status, s) : sweep_as<false, 5>(T, L, from_t, uout, status, s);
@@ -857,7 +1281,13 @@ cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, boo
 
 cudaError_t launch_tile_res_restrict(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc,
                                      bool exact, float* fc, float* tc, int* status, cudaStream_t s) {
-  if (!T.on || Lc.h.kind != kRot || Lc.h.bf16) return cudaErrorInvalidValue;
+  if (!T.on || Lc.h.bf16) return cudaErrorInvalidValue;
+  if (T.rot) {
+    if (Lc.h.kind != kAxis) return cudaErrorInvalidValue;
+    if (tc) return exact ? rrr_as<true, true>(T, L, Lc, fc, tc, status, s) : rrr_as<false, true>(T, L, Lc, fc, tc, status, s);
+    return exact ? rrr_as<true, false>(T, L, Lc, fc, tc, status, s) : rrr_as<false, false>(T, L, Lc, fc, tc, status, s);
+  }
+  if (Lc.h.kind != kRot) return cudaErrorInvalidValue;
   if (T.nt == 9) {
     if (tc) return exact ? rr_as<true, 9, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, true>(T, L, Lc, fc, tc, status, s);
     return exact ? rr_as<true, 9, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, false>(T, L, Lc, fc, tc, status, s);

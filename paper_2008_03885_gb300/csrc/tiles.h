@@ -23,15 +23,16 @@ struct TileLevel {
   int reach = 0;        // stencil reach (1: 5-point cross, 2: 9-point fourth-order cross)
   int nt = 0;           // 5 or 9
   int nu1 = 0;          // presmooth sweeps (1 or 2); 0: no fused presmooth
+  bool rot = false;     // a rotated level (brick storage, colours by rows)
   dim3 grid;            // tiles
   CUtensorMap f_pre;    // f with the presmooth halo
   CUtensorMap u_sw, t_sw, f_sw;  // u, t and f with the one-sweep halo
   CUtensorMap u_rr, f_rr;        // u and f with the residual + restriction halo
 };
 
-// Whether level L (FP32) can use the tile kernels: an axis level of at least
-// kTileMinRows rows with Dirichlet boundaries, no bfloat16 rounding, and a 5-point or
-// 9-point cross as its interior stencil.
+// Whether level L (FP32) can use the tile kernels: a level of at least kTileMinRows rows
+// with Dirichlet boundaries and no bfloat16 rounding whose interior stencil is a 5-point
+// or 9-point cross (axis levels) or the first Galerkin 9-point stencil (rotated levels).
 bool tile_eligible(const LevelPair<float>& L);
 // Build the tensor maps of level L over its arrays u, t, f. false if the CUDA driver's
 // tensor-map encoder is unavailable or rejects a map.
@@ -44,8 +45,9 @@ cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L,
 // to the other array.
 cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, bool exact, bool from_t, float* uout,
                               int* status, cudaStream_t s);
-// f_coarse = R (f - L u) for red-black coarsening (axis level -> its black points);
-// with tc also the coarse level's first half-sweep from zero (as launch_restrict).
+// f_coarse = R (f - L u) for red-black coarsening (axis level -> its black points, or
+// rotated level -> its axis level); with tc also the coarse level's first half-sweep
+// from zero (as launch_restrict).
 cudaError_t launch_tile_res_restrict(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc,
                                      bool exact, float* fc, float* tc, int* status, cudaStream_t s);
 

@@ -4,7 +4,8 @@ give the same bits as the per-step half-sweep, residual and restriction kernels
 residual histories) over both orders, red-black and standard coarsening, Galerkin and
 non-Galerkin coarse operators, nu1, nu2 in {1, 2}, one and two inner cycles, and both
 rounding modes; sizes from 257^2 (the smallest level the tile kernels take, with ragged
-last tiles in both directions) upward."""
+last tiles in both directions) upward. Red-black Galerkin hierarchies also run the
+rotated tile kernels on level 1 (the first Galerkin 9-point stencil)."""
 import pytest
 
 import synth
@@ -35,6 +36,7 @@ def solve(n, order, co, op, F, steps, **opts):
 CASES = [
     # (n, order, coarsening, coarse op, nu1, nu2, inner cycles, fma)
     (256, 4, "redblack", "galerkin", 2, 1, 1, 1),
+    (256, 2, "redblack", "galerkin", 2, 2, 1, 0),
     (512, 2, "redblack", "galerkin", 1, 1, 1, 1),
     (512, 4, "redblack", "nongalerkin", 2, 1, 1, 1),
     (512, 2, "redblack", "nongalerkin", 2, 2, 1, 0),
