@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
 // lattice axis neighbours) on rows of the node's colour, terms 4-7 (the diagonal
 // neighbours) on the rows of the other colour, term 8 the centre; the host checks this
 // shape, and the storage offsets (sdx by row parity, sdy) come from the level.
-constexpr int kRC = 64;
+constexpr int kRC = 128;
 constexpr int kRR = 32;
 
 template <int M, int MC>
@@ -765,15 +765,31 @@ struct RStencil {
   }
 };
 
-// (L x) at a fast node of parity PAR: same-colour terms from ss (base bs = node), other-
-// colour terms from so (base bo = node's column on row j - 1), in evaluation order.
-template <bool EXACT, int PAR, class SS, class SO>
-__device__ __forceinline__ float rcross(const RStencil& S, const SS& ss, int bs, const SO& so, int bo) {
+// Index offsets of the fast stencil's terms in two sources, for nodes of parity PAR:
+// terms 0-3 in the same-colour source SS (from the node), terms 4-7 in the other-colour
+// source SO (from the node's column on row j - 1).
+struct ROffsets {
+  int s[4], o[4];
+};
+template <int PAR, class SS, class SO>
+__device__ __forceinline__ ROffsets roffsets(const RStencil& S) {
+  ROffsets r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.s[k] = (S.sy[k] / 2) * SS::step2 + S.sx[PAR][k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r.o[k] = ((S.sy[4 + k] + 1) / 2) * SO::step2 + S.sx[PAR][4 + k];
+  return r;
+}
+
+// (L x) at a fast node: same-colour terms from ss (base bs = the node), other-colour
+// terms from so (base bo), in evaluation order.
+template <bool EXACT, class SS, class SO>
+__device__ __forceinline__ float rcross(const RStencil& S, const ROffsets& of, const SS& ss, int bs, const SO& so, int bo) {
   float x[9];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) x[k] = ss.at(bs + (S.sy[k] / 2) * SS::step2 + S.sx[PAR][k]);
+  for (int k = 0; k < 4; ++k) x[k] = ss.at(bs + of.s[k]);
 #pragma unroll
-  for (int k = 4; k < 8; ++k) x[k] = so.at(bo + ((S.sy[k] + 1) / 2) * SO::step2 + S.sx[PAR][k]);
+  for (int k = 0; k < 4; ++k) x[4 + k] = so.at(bo + of.o[k]);
   x[8] = ss.at(bs);
   if constexpr (EXACT) {
     const float g0 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x[0], x[1]), x[2]), x[3]);
@@ -794,30 +810,91 @@ __device__ __forceinline__ float rval(const SRC& s, const RTile& T, int a, int b
   return s.at(s.idx(T, a >> 1, b));
 }
 
+// Strips of the colour-PAR rows of a rotated region (M, MC) that hold its nodes outside
+// the fast range (rx <= i <= fxe, ry <= j <= fye), within rows 0 <= j <= n and storage
+// columns 0 <= q < cols: compact rows [r0, rt) and [rb, r1), and in the rows between them
+// the columns [p0, pl) and [pr, p1). A superset of those nodes, without overlap; nodes
+// beyond are never read (fast stencils stay two rows and one column inside, boundary-
+// class rows drop boundary columns) nor stored. The fast pass walks rows [rt, rb).
+template <int M, int MC, int PAR>
+struct RStrips {
+  int r0, rt, rb, r1, p0, pl, pr, p1, pw, mw, count;
+  __device__ __forceinline__ RStrips(const LevelDev<float>& L, const RTile& T) {
+    using G = RReg<M, MC>;
+    const int jb = T.J0 - M + PAR, qb = T.C0 - MC;  // row of compact row 0, column of element 0
+    // first compact row whose row j = jb + 2 r reaches a bound: (bound - jb) rounded up
+    auto first = [&](int bound) { return min(max(bound - jb + 1, 0) >> 1, G::h); };
+    r0 = first(0);
+    r1 = max(r0, first(L.n + 1));
+    rt = min(max(first(L.ry), r0), r1);
+    rb = min(max(first(L.fye + 1), rt), r1);
+    p0 = min(max(-qb, 0), G::w);
+    p1 = max(p0, min(L.cols - qb, G::w));
+    pl = min(max(L.rx / 2 + 1 - qb, p0), p1);           // i = 2q + PAR < rx only if q <= rx / 2
+    pr = max(pl, min(max((L.fxe - 1) / 2 - qb, p0), p1));  // ... i > fxe only if q >= (fxe - 1) / 2
+    pw = p1 - p0;
+    mw = (pl - p0) + (p1 - pr);
+    count = (rt - r0 + r1 - rb) * pw + (rb - rt) * mw;
+  }
+  __device__ __forceinline__ void at(int k, int& kr, int& cq) const {
+    const int k1 = (rt - r0) * pw, k2 = k1 + (r1 - rb) * pw;
+    if (k < k1) {
+      const int q = k / pw;
+      kr = r0 + q;
+      cq = p0 + (k - q * pw);
+    } else if (k < k2) {
+      const int q = (k - k1) / pw;
+      kr = rb + q;
+      cq = p0 + (k - k1 - q * pw);
+    } else {
+      const int q = (k - k2) / mw, r = k - k2 - q * mw;
+      kr = rt + q;
+      cq = r < pl - p0 ? p0 + r : pr + (r - (pl - p0));
+    }
+  }
+};
+
 // One relaxation phase over the nodes of colour PAR in the region (M, MC): the fast
 // value (relax of the fast stencil, or 0 + f omega / a_pp with ZERO) for nodes of the
-// fast range; with EDGE the other nodes get gen(i, j). sink(e, q, j, v), e = index in
-// the region's compact array.
+// fast range; with EDGE (a tile reaching the boundary strip) only the rows holding fast
+// nodes are walked with the fast stencil, and the strip nodes outside the fast range
+// get gen(i, j) in a second pass. sink(e, q, j, v), e = index in the region's array.
 template <bool EXACT, int PAR, int M, int MC, bool ZERO, bool EDGE, class SS, class SO, class FB, class SINK, class GEN>
 __device__ __forceinline__ void rphase(const RStencil& S, float wd, const SS& ss, const SO& so, const FB& fb,
                                        const RTile& T, const LevelDev<float>& L, SINK sink, GEN gen) {
   using G = RReg<M, MC>;
-  for (int e = threadIdx.x; e < G::n; e += kTT) {
-    const int kr = e / G::w, cq = e - kr * G::w;
+  const ROffsets of = roffsets<PAR, SS, SO>(S);
+  auto fast = [&](int e, int kr, int cq) {
     const int j = T.J0 - M + 2 * kr + PAR, q = T.C0 - MC + cq;
-    if (EDGE && !fast_node_c<false>(L, 2 * q + PAR, j)) {
-      sink(e, q, j, gen(2 * q + PAR, j));
-      continue;
-    }
+    if (EDGE && !fast_node_c<false>(L, 2 * q + PAR, j)) return;
     const float f = fb.at(fb.idx(T, q, j));
     float v;
     if constexpr (ZERO) {
       v = relax_from_zero(f, wd);
     } else {
       const int bs = ss.idx(T, q, j);
-      v = relax<EXACT>(rcross<EXACT, PAR>(S, ss, bs, so, so.idx(T, q, j - 1)), f, ss.at(bs), wd);
+      v = relax<EXACT>(rcross<EXACT>(S, of, ss, bs, so, so.idx(T, q, j - 1)), f, ss.at(bs), wd);
     }
     sink(e, q, j, v);
+  };
+  if constexpr (!EDGE) {
+    for (int e = threadIdx.x; e < G::n; e += kTT) {
+      const int kr = e / G::w;
+      fast(e, kr, e - kr * G::w);
+    }
+  } else {
+    const RStrips<M, MC, PAR> st(L, T);
+    for (int e = threadIdx.x; e < (st.rb - st.rt) * G::w; e += kTT) {
+      const int r = e / G::w, kr = st.rt + r, cq = e - r * G::w;
+      fast(kr * G::w + cq, kr, cq);
+    }
+    for (int k = threadIdx.x; k < st.count; k += kTT) {
+      int kr, cq;
+      st.at(k, kr, cq);
+      const int j = T.J0 - M + 2 * kr + PAR, q = T.C0 - MC + cq;
+      if (fast_node_c<false>(L, 2 * q + PAR, j)) continue;
+      sink(kr * G::w + cq, q, j, gen(2 * q + PAR, j));
+    }
   }
 }
 
@@ -1013,38 +1090,75 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<fl
     auto F = [=](int i, int j) { return rval(fb, T, i, j); };
     auto run = [&](auto check) {
       constexpr bool EDGE = decltype(check)::value;
+      // red residuals on the region (2, 1) (0 off the interior), through the phase walker
+      // with a residual in place of the relaxation
       using G = RReg<2, 1>;
-      for (int e = threadIdx.x; e < G::n; e += kTT) {  // red residuals (0 off the interior)
-        const int kr = e / G::w, cq = e - kr * G::w;
-        const int j = T.J0 - 2 + 2 * kr + 1, q = T.C0 - 1 + cq, i = 2 * q + 1;
-        if (EDGE && !fast_node_c<false>(L, i, j)) {
-          sD[e] = inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U)) : 0.f;
-          continue;
-        }
+      const ROffsets o1 = roffsets<1, RBox<kRHX, kRHY>, RBox<kRHX, kRHY>>(S);
+      const ROffsets o0 = roffsets<0, RBox<kRHX, kRHY>, RBox<kRHX, kRHY>>(S);
+      auto red_fast = [&](int e, int kr, int cq) {
+        const int j = T.J0 - 2 + 2 * kr + 1, q = T.C0 - 1 + cq;
+        if (EDGE && !fast_node_c<false>(L, 2 * q + 1, j)) return;
         const int b = ub.idx(T, q, j);
-        sD[e] = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT, 1>(S, ub, b, ub, ub.idx(T, q, j - 1)));
+        sD[e] = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT>(S, o1, ub, b, ub, ub.idx(T, q, j - 1)));
+      };
+      if constexpr (!EDGE) {
+        for (int e = threadIdx.x; e < G::n; e += kTT) {
+          const int kr = e / G::w;
+          red_fast(e, kr, e - kr * G::w);
+        }
+      } else {
+        const RStrips<2, 1, 1> st(L, T);
+        for (int e = threadIdx.x; e < (st.rb - st.rt) * G::w; e += kTT) {
+          const int r = e / G::w, kr = st.rt + r, cq = e - r * G::w;
+          red_fast(kr * G::w + cq, kr, cq);
+        }
+        for (int k = threadIdx.x; k < st.count; k += kTT) {
+          int kr, cq;
+          st.at(k, kr, cq);
+          const int j = T.J0 - 2 + 2 * kr + 1, q = T.C0 - 1 + cq, i = 2 * q + 1;
+          if (fast_node_c<false>(L, i, j)) continue;
+          sD[kr * G::w + cq] = inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U)) : 0.f;
+        }
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < (kRR / 2) * kRC; e += kTT) {  // black nodes of the tile
-        const int kr = e / kRC, cq = e - kr * kRC;
-        const int j = T.J0 + 2 * kr, q = T.C0 + cq, i = 2 * q;
-        float d;
-        if (EDGE && !fast_node_c<false>(L, i, j)) {
-          if (!inner(n, i, j)) continue;
-          d = Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U));
-        } else {
-          d = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT, 0>(S, ub, ub.idx(T, q, j), ub, ub.idx(T, q, j - 1)));
-        }
+      // black nodes of the tile = coarse nodes
+      auto coarse = [&](int q, int j, float d) {
         const int bu = dr.idx(T, q, j - 1);  // red row j - 1, columns q - 1 and q; then row j + 1
         float w = Arith<float>::mul(0.125f, dr.at(bu - 1));
         w = madd<float, EXACT>(w, 0.125f, dr.at(bu));
         w = madd<float, EXACT>(w, 0.5f, d);
-        w = madd<float, EXACT>(w, 0.125f, dr.at(bu + RReg<2, 1>::w - 1));
-        const float v = madd<float, EXACT>(w, 0.125f, dr.at(bu + RReg<2, 1>::w));
+        w = madd<float, EXACT>(w, 0.125f, dr.at(bu + G::w - 1));
+        const float v = madd<float, EXACT>(w, 0.125f, dr.at(bu + G::w));
         const int I = q, J = j >> 1;  // the coarse (axis) node
         const int64_t at = (int64_t)J * pc + I;
         fc[at] = v;
         if (TC) tc[at] = ((I + J) & 1) ? relax_from_zero(v, node_wd(Lc, I, J)) : 0.f;
+      };
+      auto black_fast = [&](int kr, int cq) {
+        const int j = T.J0 + 2 * kr, q = T.C0 + cq;
+        if (EDGE && !fast_node_c<false>(L, 2 * q, j)) return;
+        coarse(q, j,
+               Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT>(S, o0, ub, ub.idx(T, q, j), ub, ub.idx(T, q, j - 1))));
+      };
+      using G0 = RReg<0, 0>;
+      if constexpr (!EDGE) {
+        for (int e = threadIdx.x; e < G0::n; e += kTT) {
+          const int kr = e / G0::w;
+          black_fast(kr, e - kr * G0::w);
+        }
+      } else {
+        const RStrips<0, 0, 0> st(L, T);
+        for (int e = threadIdx.x; e < (st.rb - st.rt) * G0::w; e += kTT) {
+          const int r = e / G0::w;
+          black_fast(st.rt + r, e - r * G0::w);
+        }
+        for (int k = threadIdx.x; k < st.count; k += kTT) {
+          int kr, cq;
+          st.at(k, kr, cq);
+          const int j = T.J0 + 2 * kr, q = T.C0 + cq, i = 2 * q;
+          if (fast_node_c<false>(L, i, j) || !inner(n, i, j)) continue;
+          coarse(q, j, Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U)));
+        }
       }
     };
     if (rfast_tile<2, 1>(L, T)) run(std::false_type{});
