@@ -732,6 +732,13 @@ struct RComp {
   __device__ __forceinline__ int idx(const RTile& T, int q, int j) const {
     return ((j - (T.J0 - M) - PAR) >> 1) * RReg<M, MC>::w + (q - (T.C0 - MC));
   }
+  // index of the node on row j + DJ (DJ = 0 or -1) above element (kr, cq) of the
+  // colour-PN rows of a region (MN, MCN): all offsets compile-time
+  template <int MN, int MCN, int PN, int DJ>
+  __device__ __forceinline__ int idx_r(int kr, int cq) const {
+    static_assert(((PN + DJ + M - MN - PAR) & 1) == 0, "row of this source's colour");
+    return (kr + (PN + DJ + M - MN - PAR) / 2) * RReg<M, MC>::w + cq + (MC - MCN);
+  }
   __device__ __forceinline__ float at(int k) const { return p[k]; }
 };
 template <int HX, int HY>
@@ -742,11 +749,17 @@ struct RBox {
   __device__ __forceinline__ int idx(const RTile& T, int q, int j) const {
     return (j - (T.J0 - HY)) * W + (q - (T.C0 - HX));
   }
+  template <int MN, int MCN, int PN, int DJ>
+  __device__ __forceinline__ int idx_r(int kr, int cq) const {
+    return (2 * kr + PN + DJ - MN + HY) * W + cq + (HX - MCN);
+  }
   __device__ __forceinline__ float at(int k) const { return p[k]; }
 };
 struct RZero {
   static constexpr int step2 = 0;
   __device__ __forceinline__ int idx(const RTile&, int, int) const { return 0; }
+  template <int MN, int MCN, int PN, int DJ>
+  __device__ __forceinline__ int idx_r(int, int) const { return 0; }
   __device__ __forceinline__ float at(int) const { return 0.f; }
 };
 
@@ -867,13 +880,13 @@ __device__ __forceinline__ void rphase(const RStencil& S, float wd, const SS& ss
   auto fast = [&](int e, int kr, int cq) {
     const int j = T.J0 - M + 2 * kr + PAR, q = T.C0 - MC + cq;
     if (EDGE && !fast_node_c<false>(L, 2 * q + PAR, j)) return;
-    const float f = fb.at(fb.idx(T, q, j));
+    const float f = fb.at(fb.template idx_r<M, MC, PAR, 0>(kr, cq));
     float v;
     if constexpr (ZERO) {
       v = relax_from_zero(f, wd);
     } else {
-      const int bs = ss.idx(T, q, j);
-      v = relax<EXACT>(rcross<EXACT>(S, of, ss, bs, so, so.idx(T, q, j - 1)), f, ss.at(bs), wd);
+      const int bs = ss.template idx_r<M, MC, PAR, 0>(kr, cq);
+      v = relax<EXACT>(rcross<EXACT>(S, of, ss, bs, so, so.template idx_r<M, MC, PAR, -1>(kr, cq)), f, ss.at(bs), wd);
     }
     sink(e, q, j, v);
   };
