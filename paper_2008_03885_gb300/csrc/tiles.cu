@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
+#include <utility>
 
 #include "device.cuh"
 #include "tiles.h"
@@ -104,15 +105,32 @@ __device__ __forceinline__ float relax(float s, float f, float u, float wd) {
   return EXACT ? Arith<float>::add(u, Arith<float>::mul(r, wd)) : Arith<float>::fma(r, wd, u);
 }
 
+// The 21-point stencil of the second red-black Galerkin level (Eq. L_G_l from the
+// 5-point operator; Sec. 4.4) in evaluation order: its groups of equal coefficient are
+// the eight (1, 2) knight neighbours, the four (2, 0) neighbours, the four diagonal and
+// the four (1, 0) neighbours, the centre; each group in (dy, dx) order.
+__host__ __device__ constexpr int g21_dx(int k) {
+  constexpr int x[21] = {-1, 1, -2, 2, -2, 2, -1, 1, 0, -2, 2, 0, -1, 1, -1, 1, 0, -1, 1, 0, 0};
+  return x[k];
+}
+__host__ __device__ constexpr int g21_dy(int k) {
+  constexpr int y[21] = {-2, -2, -1, -1, 1, 1, 2, 2, -2, 0, 0, 2, -1, -1, 1, 1, -1, 0, 0, 1, 0};
+  return y[k];
+}
+constexpr uint32_t kGmask21 = (1u << 0) | (1u << 8) | (1u << 12) | (1u << 16) | (1u << 20);
+
 // (L x)(i, j): the fast cross stencil with coefficients c (in evaluation order) or the
 // node's boundary-class term list. x(i, j) returns the value of lattice node (i, j).
 template <bool EXACT, int NT, class X>
 __device__ __forceinline__ float stencil(const LevelDev<float>& L, const float (&c)[NT], int i, int j, X x) {
   if (fast_node_c<false>(L, i, j)) {
     // terms in evaluation order: 9 points = +-2 neighbours, +-1 neighbours, centre;
-    // 5 points = the four neighbours, the centre
+    // 5 points = the four neighbours, the centre; 21 points as g21_dx / g21_dy
     RowSum<float, EXACT> acc;
-    if (NT == 9) {
+    if (NT == 21) {
+#pragma unroll
+      for (int k = 0; k < 21; ++k) acc.add(c[k], x(i + g21_dx(k), j + g21_dy(k)), (kGmask21 >> k) & 1u);
+    } else if (NT == 9) {
       acc.add(c[0], x(i, j - 2), true);
       acc.add(c[1], x(i - 2, j), false);
       acc.add(c[2], x(i + 2, j), false);
@@ -214,14 +232,40 @@ struct SBox {  // a staged TMA box (both colours), halo (HX, HY)
   }
 };
 
+// Term K of the 21-point stencil: odd offsets read the other colour's source.
+template <int K, class SO, class SS>
+__device__ __forceinline__ float term21(const SO& so, int bo, const SS& ss, int bs, int a) {
+  constexpr int DX = g21_dx(K), DY = g21_dy(K);
+  if constexpr (((DX + DY) & 1) != 0) return so.template get<DX, DY>(bo, a);
+  else return ss.template get<DX, DY>(bs, a);
+}
+template <bool EXACT, class SO, class SS, int... K>
+__device__ __forceinline__ float cross21(const float (&c)[21], const SO& so, int bo, const SS& ss, int bs, int a,
+                                        std::integer_sequence<int, K...>) {
+  const float x[21] = {term21<K>(so, bo, ss, bs, a)...};
+  if constexpr (EXACT) {
+    RowSum<float, true> acc;
+#pragma unroll
+    for (int k = 0; k < 21; ++k) acc.add(c[k], x[k], (kGmask21 >> k) & 1u);
+    return acc.value();
+  } else {
+    float s = Arith<float>::mul(c[0], x[0]);
+#pragma unroll
+    for (int k = 1; k < 21; ++k) s = Arith<float>::fma(c[k], x[k], s);
+    return s;
+  }
+}
+
 // (L x) at a fast node: terms in (dy, dx) order; odd offsets (DX + DY) read the other
 // colour's source `so` (base bo), even ones the node's own colour `ss` (base bs).
 template <bool EXACT, int NT, class SO, class SS>
 __device__ __forceinline__ float cross(const float (&c)[NT], const SO& so, int bo, const SS& ss, int bs, int a) {
   // terms in evaluation order (group-major, see LevelDev::c): 9 points = the four
   // +-2 neighbours, the four +-1 neighbours, the centre; 5 points = the four neighbours,
-  // the centre
-  if constexpr (NT == 9) {
+  // the centre; 21 points: see g21_dx
+  if constexpr (NT == 21) {
+    return cross21<EXACT>(c, so, bo, ss, bs, a, std::make_integer_sequence<int, 21>{});
+  } else if constexpr (NT == 9) {
     const float x0 = ss.template get<0, -2>(bs, a), x1 = ss.template get<-2, 0>(bs, a);
     const float x2 = ss.template get<2, 0>(bs, a), x3 = ss.template get<0, 2>(bs, a);
     const float x4 = so.template get<0, -1>(bo, a), x5 = so.template get<-1, 0>(bo, a);
@@ -439,7 +483,7 @@ template <bool EXACT, int NT, int NS>
 __global__ void __launch_bounds__(kTT, 3) k_tile_presmooth(const LevelDev<float>* __restrict__ Lp,
                                                         const __grid_constant__ CUtensorMap mapF,
                                                         float* __restrict__ out, int* __restrict__ status) {
-  constexpr int R = NT == 9 ? 2 : 1;
+  constexpr int R = NT == 5 ? 1 : 2;
   using G = PreGeo<R, NS>;
   constexpr int M0 = G::M0, M1 = (2 * NS - 2) * R, M2 = NS == 2 ? R : 0;
   constexpr int FN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
@@ -535,7 +579,7 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_sweep(const LevelDev<float>* __
                                                     const __grid_constant__ CUtensorMap mapU,
                                                     const __grid_constant__ CUtensorMap mapF, float* __restrict__ out,
                                                     int* __restrict__ status) {
-  constexpr int R = NT == 9 ? 2 : 1;
+  constexpr int R = NT == 5 ? 1 : 2;
   using G = SweepGeo<R>;
   constexpr int BN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
@@ -596,7 +640,7 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
                                                            const __grid_constant__ CUtensorMap mapF,
                                                            float* __restrict__ fc, float* __restrict__ tc,
                                                            int* __restrict__ status) {
-  constexpr int R = NT == 9 ? 2 : 1;
+  constexpr int R = NT == 5 ? 1 : 2;
   using G = RrGeo<R>;
   constexpr int BN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
@@ -1273,12 +1317,18 @@ bool tile_eligible(const LevelPair<float>& P) {
   // (offsets in evaluation order: groups of equal coefficient, see LevelDev::c)
   static const int x5[5] = {0, -1, 1, 0, 0}, y5[5] = {-1, 0, 0, 1, 0};
   static const int x9[9] = {0, -2, 2, 0, 0, -1, 1, 0, 0}, y9[9] = {-2, 0, 0, 2, -1, 0, 0, 1, 0};
-  const int* xs = L.nt == 5 ? x5 : L.nt == 9 ? x9 : nullptr;
-  const int* ys = L.nt == 5 ? y5 : y9;
-  if (!xs) return false;
-  for (int k = 0; k < L.nt; ++k)
-    if (L.sdx[0][k] != xs[k] || L.sdy[k] != ys[k]) return false;
-  if (L.gmask[0] != fast_gmask(L.nt)) return false;
+  if (L.nt == 21) {  // the second red-black Galerkin level
+    for (int k = 0; k < 21; ++k)
+      if (L.sdx[0][k] != g21_dx(k) || L.sdy[k] != g21_dy(k)) return false;
+    if (L.gmask[0] != kGmask21) return false;
+  } else {
+    const int* xs = L.nt == 5 ? x5 : L.nt == 9 ? x9 : nullptr;
+    const int* ys = L.nt == 5 ? y5 : y9;
+    if (!xs) return false;
+    for (int k = 0; k < L.nt; ++k)
+      if (L.sdx[0][k] != xs[k] || L.sdy[k] != ys[k]) return false;
+    if (L.gmask[0] != fast_gmask(L.nt)) return false;
+  }
   for (int w = 1; w < kMaxTerms / 32; ++w)
     if (L.gmask[w]) return false;
   return true;
@@ -1289,7 +1339,7 @@ bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, flo
   if (!tile_eligible(P)) return false;
   const LevelDev<float>& L = P.h;
   T.nt = L.nt;
-  T.reach = L.nt == 9 ? 2 : 1;
+  T.reach = L.nt == 5 ? 1 : 2;
   T.rot = L.kind == kRot;
   bool ok = true;
   if (T.rot) {  // rotated tiles: presmooth for nu1 = 2 only
@@ -1330,7 +1380,7 @@ bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, flo
 namespace {
 template <bool EXACT, int NT, int NS>
 cudaError_t presmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u, int* status, cudaStream_t s) {
-  const size_t smem = pre_smem<NT == 9 ? 2 : 1, NS>();
+  const size_t smem = pre_smem<NT == 5 ? 1 : 2, NS>();
   cudaError_t e = allow_smem<k_tile_presmooth<EXACT, NT, NS>>(smem);
   if (e != cudaSuccess) return e;
   k_tile_presmooth<EXACT, NT, NS><<<T.grid, kTT, smem, s>>>(L.d, T.f_pre, u, status);
@@ -1339,7 +1389,7 @@ cudaError_t presmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u
 template <bool EXACT, int NT>
 cudaError_t sweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t, float* out, int* status,
                      cudaStream_t s) {
-  const size_t smem = sweep_smem<NT == 9 ? 2 : 1>();
+  const size_t smem = sweep_smem<NT == 5 ? 1 : 2>();
   cudaError_t e = allow_smem<k_tile_sweep<EXACT, NT>>(smem);
   if (e != cudaSuccess) return e;
   k_tile_sweep<EXACT, NT><<<T.grid, kTT, smem, s>>>(L.d, from_t ? T.t_sw : T.u_sw, T.f_sw, out, status);
@@ -1348,7 +1398,7 @@ cudaError_t sweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t,
 template <bool EXACT, int NT, bool TC>
 cudaError_t rr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc, float* fc, float* tc,
                   int* status, cudaStream_t s) {
-  const size_t smem = rr_smem<NT == 9 ? 2 : 1>();
+  const size_t smem = rr_smem<NT == 5 ? 1 : 2>();
   cudaError_t e = allow_smem<k_tile_res_restrict<EXACT, NT, TC>>(smem);
   if (e != cudaSuccess) return e;
   k_tile_res_restrict<EXACT, NT, TC><<<T.grid, kTT, smem, s>>>(L.d, Lc.d, T.u_rr, T.f_rr, fc, tc, status);
@@ -1389,6 +1439,10 @@ cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L,
                                   cudaStream_t s) {
   if (!T.on || !T.nu1) return cudaErrorInvalidValue;
   if (T.rot) return exact ? rpresmooth_as<true>(T, L, u, status, s) : rpresmooth_as<false>(T, L, u, status, s);
+  if (T.nt == 21) {
+    if (T.nu1 == 2) return exact ? presmooth_as<true, 21, 2>(T, L, u, status, s) : presmooth_as<false, 21, 2>(T, L, u, status, s);
+    return exact ? presmooth_as<true, 21, 1>(T, L, u, status, s) : presmooth_as<false, 21, 1>(T, L, u, status, s);
+  }
   if (T.nt == 9) {
     if (T.nu1 == 2) return exact ? presmooth_as<true, 9, 2>(T, L, u, status, s) : presmooth_as<false, 9, 2>(T, L, u, status, s);
     return exact ? presmooth_as<true, 9, 1>(T, L, u, status, s) : presmooth_as<false, 9, 1>(T, L, u, status, s);
@@ -1401,6 +1455,8 @@ cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, boo
                               int* status, cudaStream_t s) {
   if (!T.on) return cudaErrorInvalidValue;
   if (T.rot) return exact ? rsweep_as<true>(T, L, from_t, uout, status, s) : rsweep_as<false>(T, L, from_t, uout, status, s);
+  if (T.nt == 21)
+    return exact ? sweep_as<true, 21>(T, L, from_t, uout, status, s) : sweep_as<false, 21>(T, L, from_t, uout, status, s);
   if (T.nt == 9)
     return exact ? sweep_as<true, 9>(T, L, from_t, uout, status, s) : sweep_as<false, 9>(T, L, from_t, uout, status, s);
   return exact ? sweep_as<true, 5>(T, L, from_t, uout, status, s) : sweep_as<false, 5>(T, L, from_t, uout, status, s);
@@ -1415,6 +1471,10 @@ cudaError_t launch_tile_res_restrict(const TileLevel& T, const LevelPair<float>&
     return exact ? rrr_as<true, false>(T, L, Lc, fc, tc, status, s) : rrr_as<false, false>(T, L, Lc, fc, tc, status, s);
   }
   if (Lc.h.kind != kRot) return cudaErrorInvalidValue;
+  if (T.nt == 21) {
+    if (tc) return exact ? rr_as<true, 21, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 21, true>(T, L, Lc, fc, tc, status, s);
+    return exact ? rr_as<true, 21, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 21, false>(T, L, Lc, fc, tc, status, s);
+  }
   if (T.nt == 9) {
     if (tc) return exact ? rr_as<true, 9, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, true>(T, L, Lc, fc, tc, status, s);
     return exact ? rr_as<true, 9, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, false>(T, L, Lc, fc, tc, status, s);
