@@ -105,19 +105,43 @@ __device__ __forceinline__ float relax(float s, float f, float u, float wd) {
   return EXACT ? Arith<float>::add(u, Arith<float>::mul(r, wd)) : Arith<float>::fma(r, wd, u);
 }
 
-// The 21-point stencil of the second red-black Galerkin level (Eq. L_G_l from the
-// 5-point operator; Sec. 4.4) in evaluation order: its groups of equal coefficient are
-// the eight (1, 2) knight neighbours, the four (2, 0) neighbours, the four diagonal and
-// the four (1, 0) neighbours, the centre; each group in (dy, dx) order.
-__host__ __device__ constexpr int g21_dx(int k) {
-  constexpr int x[21] = {-1, 1, -2, 2, -2, 2, -1, 1, 0, -2, 2, 0, -1, 1, -1, 1, 0, -1, 1, 0, 0};
-  return x[k];
+// The wide stencils of the second and third red-black Galerkin axis levels (Eq. L_G_l
+// from the 5-point operator; Sec. 4.4) in evaluation order. 21 points (reach 2): its
+// groups of equal coefficient are the eight (1, 2) knight neighbours, the four (2, 0)
+// neighbours, the four diagonal and the four (1, 0) neighbours, the centre. 37 points
+// (reach 3): the eight (1, 3), the four (3, 0), the four (2, 2), the eight (1, 2), the
+// four (2, 0), the four diagonal and the four (1, 0) neighbours, the centre. Each group
+// in (dy, dx) order; gstart marks a group's first term.
+template <int NT>
+__host__ __device__ constexpr int wide_dx(int k) {
+  if constexpr (NT == 21) {
+    constexpr int x[21] = {-1, 1, -2, 2, -2, 2, -1, 1, 0, -2, 2, 0, -1, 1, -1, 1, 0, -1, 1, 0, 0};
+    return x[k];
+  } else {
+    constexpr int x[37] = {-1, 1, -3, 3, -3, 3, -1, 1, 0, -3, 3, 0, -2, 2, -2, 2, -1, 1, -2,
+                           2,  -2, 2, -1, 1, 0, -2, 2, 0, -1, 1, -1, 1, 0, -1, 1, 0, 0};
+    return x[k];
+  }
 }
-__host__ __device__ constexpr int g21_dy(int k) {
-  constexpr int y[21] = {-2, -2, -1, -1, 1, 1, 2, 2, -2, 0, 0, 2, -1, -1, 1, 1, -1, 0, 0, 1, 0};
-  return y[k];
+template <int NT>
+__host__ __device__ constexpr int wide_dy(int k) {
+  if constexpr (NT == 21) {
+    constexpr int y[21] = {-2, -2, -1, -1, 1, 1, 2, 2, -2, 0, 0, 2, -1, -1, 1, 1, -1, 0, 0, 1, 0};
+    return y[k];
+  } else {
+    constexpr int y[37] = {-3, -3, -1, -1, 1, 1, 3, 3, -3, 0, 0, 3, -2, -2, 2, 2, -2, -2, -1,
+                           -1, 1,  1,  2,  2, -2, 0, 0, 2, -1, -1, 1, 1, -1, 0, 0, 1, 0};
+    return y[k];
+  }
 }
-constexpr uint32_t kGmask21 = (1u << 0) | (1u << 8) | (1u << 12) | (1u << 16) | (1u << 20);
+template <int NT>
+__host__ __device__ constexpr bool wide_gstart(int k) {
+  if constexpr (NT == 21) return k == 0 || k == 8 || k == 12 || k == 16 || k == 20;
+  else return k == 0 || k == 8 || k == 12 || k == 16 || k == 24 || k == 28 || k == 32 || k == 36;
+}
+__host__ __device__ constexpr bool wide_nt(int nt) { return nt == 21 || nt == 37; }
+// stencil reach of the NT-term fast stencils of the axis tile kernels
+__host__ __device__ constexpr int tile_reach(int nt) { return nt == 5 ? 1 : nt == 37 ? 3 : 2; }
 
 // (L x)(i, j): the fast cross stencil with coefficients c (in evaluation order) or the
 // node's boundary-class term list. x(i, j) returns the value of lattice node (i, j).
@@ -125,11 +149,11 @@ template <bool EXACT, int NT, class X>
 __device__ __forceinline__ float stencil(const LevelDev<float>& L, const float (&c)[NT], int i, int j, X x) {
   if (fast_node_c<false>(L, i, j)) {
     // terms in evaluation order: 9 points = +-2 neighbours, +-1 neighbours, centre;
-    // 5 points = the four neighbours, the centre; 21 points as g21_dx / g21_dy
+    // 5 points = the four neighbours, the centre; 21 and 37 points as wide_dx / wide_dy
     RowSum<float, EXACT> acc;
-    if (NT == 21) {
+    if constexpr (wide_nt(NT)) {
 #pragma unroll
-      for (int k = 0; k < 21; ++k) acc.add(c[k], x(i + g21_dx(k), j + g21_dy(k)), (kGmask21 >> k) & 1u);
+      for (int k = 0; k < NT; ++k) acc.add(c[k], x(i + wide_dx<NT>(k), j + wide_dy<NT>(k)), wide_gstart<NT>(k));
     } else if (NT == 9) {
       acc.add(c[0], x(i, j - 2), true);
       acc.add(c[1], x(i - 2, j), false);
@@ -232,26 +256,26 @@ struct SBox {  // a staged TMA box (both colours), halo (HX, HY)
   }
 };
 
-// Term K of the 21-point stencil: odd offsets read the other colour's source.
-template <int K, class SO, class SS>
-__device__ __forceinline__ float term21(const SO& so, int bo, const SS& ss, int bs, int a) {
-  constexpr int DX = g21_dx(K), DY = g21_dy(K);
+// Term K of a wide stencil: odd offsets read the other colour's source.
+template <int NT, int K, class SO, class SS>
+__device__ __forceinline__ float term_wide(const SO& so, int bo, const SS& ss, int bs, int a) {
+  constexpr int DX = wide_dx<NT>(K), DY = wide_dy<NT>(K);
   if constexpr (((DX + DY) & 1) != 0) return so.template get<DX, DY>(bo, a);
   else return ss.template get<DX, DY>(bs, a);
 }
-template <bool EXACT, class SO, class SS, int... K>
-__device__ __forceinline__ float cross21(const float (&c)[21], const SO& so, int bo, const SS& ss, int bs, int a,
-                                        std::integer_sequence<int, K...>) {
-  const float x[21] = {term21<K>(so, bo, ss, bs, a)...};
+template <bool EXACT, int NT, class SO, class SS, int... K>
+__device__ __forceinline__ float cross_wide(const float (&c)[NT], const SO& so, int bo, const SS& ss, int bs, int a,
+                                           std::integer_sequence<int, K...>) {
+  const float x[NT] = {term_wide<NT, K>(so, bo, ss, bs, a)...};
   if constexpr (EXACT) {
     RowSum<float, true> acc;
 #pragma unroll
-    for (int k = 0; k < 21; ++k) acc.add(c[k], x[k], (kGmask21 >> k) & 1u);
+    for (int k = 0; k < NT; ++k) acc.add(c[k], x[k], wide_gstart<NT>(k));
     return acc.value();
   } else {
     float s = Arith<float>::mul(c[0], x[0]);
 #pragma unroll
-    for (int k = 1; k < 21; ++k) s = Arith<float>::fma(c[k], x[k], s);
+    for (int k = 1; k < NT; ++k) s = Arith<float>::fma(c[k], x[k], s);
     return s;
   }
 }
@@ -262,9 +286,9 @@ template <bool EXACT, int NT, class SO, class SS>
 __device__ __forceinline__ float cross(const float (&c)[NT], const SO& so, int bo, const SS& ss, int bs, int a) {
   // terms in evaluation order (group-major, see LevelDev::c): 9 points = the four
   // +-2 neighbours, the four +-1 neighbours, the centre; 5 points = the four neighbours,
-  // the centre; 21 points: see g21_dx
-  if constexpr (NT == 21) {
-    return cross21<EXACT>(c, so, bo, ss, bs, a, std::make_integer_sequence<int, 21>{});
+  // the centre; 21 and 37 points: see wide_dx
+  if constexpr (wide_nt(NT)) {
+    return cross_wide<EXACT, NT>(c, so, bo, ss, bs, a, std::make_integer_sequence<int, NT>{});
   } else if constexpr (NT == 9) {
     const float x0 = ss.template get<0, -2>(bs, a), x1 = ss.template get<-2, 0>(bs, a);
     const float x2 = ss.template get<2, 0>(bs, a), x3 = ss.template get<0, 2>(bs, a);
@@ -483,7 +507,7 @@ template <bool EXACT, int NT, int NS>
 __global__ void __launch_bounds__(kTT, 3) k_tile_presmooth(const LevelDev<float>* __restrict__ Lp,
                                                         const __grid_constant__ CUtensorMap mapF,
                                                         float* __restrict__ out, int* __restrict__ status) {
-  constexpr int R = NT == 5 ? 1 : 2;
+  constexpr int R = tile_reach(NT);
   using G = PreGeo<R, NS>;
   constexpr int M0 = G::M0, M1 = (2 * NS - 2) * R, M2 = NS == 2 ? R : 0;
   constexpr int FN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
@@ -579,7 +603,7 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_sweep(const LevelDev<float>* __
                                                     const __grid_constant__ CUtensorMap mapU,
                                                     const __grid_constant__ CUtensorMap mapF, float* __restrict__ out,
                                                     int* __restrict__ status) {
-  constexpr int R = NT == 5 ? 1 : 2;
+  constexpr int R = tile_reach(NT);
   using G = SweepGeo<R>;
   constexpr int BN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
@@ -640,7 +664,7 @@ __global__ void __launch_bounds__(kTT, 3) k_tile_res_restrict(const LevelDev<flo
                                                            const __grid_constant__ CUtensorMap mapF,
                                                            float* __restrict__ fc, float* __restrict__ tc,
                                                            int* __restrict__ status) {
-  constexpr int R = NT == 5 ? 1 : 2;
+  constexpr int R = tile_reach(NT);
   using G = RrGeo<R>;
   constexpr int BN = (kTQ + 2 * G::HX) * (kTJ + 2 * G::HY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
@@ -1307,6 +1331,8 @@ bool rot_tile_shape(const LevelDev<float>& L) {
   return L.sdy[8] == 0 && L.sdx[0][8] == 0 && L.sdx[1][8] == 0;
 }
 
+bool gbit_host(const uint32_t* m, int k) { return (m[k >> 5] >> (k & 31)) & 1u; }
+
 bool tile_eligible(const LevelPair<float>& P) {
   const LevelDev<float>& L = P.h;
   if (L.per || L.bf16 || L.rows < kTileMinRows) return false;
@@ -1317,10 +1343,17 @@ bool tile_eligible(const LevelPair<float>& P) {
   // (offsets in evaluation order: groups of equal coefficient, see LevelDev::c)
   static const int x5[5] = {0, -1, 1, 0, 0}, y5[5] = {-1, 0, 0, 1, 0};
   static const int x9[9] = {0, -2, 2, 0, 0, -1, 1, 0, 0}, y9[9] = {-2, 0, 0, 2, -1, 0, 0, 1, 0};
-  if (L.nt == 21) {  // the second red-black Galerkin level
-    for (int k = 0; k < 21; ++k)
-      if (L.sdx[0][k] != g21_dx(k) || L.sdy[k] != g21_dy(k)) return false;
-    if (L.gmask[0] != kGmask21) return false;
+  if (wide_nt(L.nt)) {  // the second and third red-black Galerkin axis levels
+    for (int k = 0; k < L.nt; ++k) {
+      const bool ok = L.nt == 21 ? L.sdx[0][k] == wide_dx<21>(k) && L.sdy[k] == wide_dy<21>(k) &&
+                                       gbit_host(L.gmask, k) == wide_gstart<21>(k)
+                                 : L.sdx[0][k] == wide_dx<37>(k) && L.sdy[k] == wide_dy<37>(k) &&
+                                       gbit_host(L.gmask, k) == wide_gstart<37>(k);
+      if (!ok) return false;
+    }
+    for (int k = L.nt; k < kMaxTerms; ++k)
+      if (gbit_host(L.gmask, k)) return false;
+    return true;
   } else {
     const int* xs = L.nt == 5 ? x5 : L.nt == 9 ? x9 : nullptr;
     const int* ys = L.nt == 5 ? y5 : y9;
@@ -1334,12 +1367,41 @@ bool tile_eligible(const LevelPair<float>& P) {
   return true;
 }
 
+namespace {
+// Tensor maps of an axis level whose fast stencil reaches R nodes.
+template <int R>
+bool axis_maps(TileLevel& T, const LevelDev<float>& L, float* u, float* t, float* f) {
+  bool ok = true;
+  if (T.nu1 == 2) ok &= make_map(&T.f_pre, f, L, PreGeo<R, 2>::HX, PreGeo<R, 2>::HY);
+  if (T.nu1 == 1) ok &= make_map(&T.f_pre, f, L, PreGeo<R, 1>::HX, PreGeo<R, 1>::HY);
+  ok &= make_map(&T.u_sw, u, L, SweepGeo<R>::HX, SweepGeo<R>::HY);
+  ok &= make_map(&T.t_sw, t, L, SweepGeo<R>::HX, SweepGeo<R>::HY);
+  ok &= make_map(&T.f_sw, f, L, SweepGeo<R>::HX, SweepGeo<R>::HY);
+  ok &= make_map(&T.u_rr, u, L, RrGeo<R>::HX, RrGeo<R>::HY);
+  ok &= make_map(&T.f_rr, f, L, RrGeo<R>::HX, RrGeo<R>::HY);
+  return ok;
+}
+}  // namespace
+
+// Multiprocessors of the current device.
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, float* f, int nu1) {
   T.on = false;
   if (!tile_eligible(P)) return false;
   const LevelDev<float>& L = P.h;
+  // The wide stencils' tiles carry several times the work of a cross stencil's: below one
+  // tile per multiprocessor the per-step kernels, which spread a level over every SM,
+  // were faster (measured on GB300: 1025^2 mixed solve 4.04 ms with per-step kernels on
+  // its 21- and 37-point levels, 4.20 ms with 85 and 27 tiles there).
+  if (wide_nt(L.nt) && (long)((L.cols + kTQ - 1) / kTQ) * ((L.rows + kTJ - 1) / kTJ) < device_sms()) return false;
   T.nt = L.nt;
-  T.reach = L.nt == 5 ? 1 : 2;
+  T.reach = tile_reach(L.nt);
   T.rot = L.kind == kRot;
   bool ok = true;
   if (T.rot) {  // rotated tiles: presmooth for nu1 = 2 only
@@ -1356,23 +1418,9 @@ bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, flo
   }
   T.nu1 = (nu1 == 1 || nu1 == 2) ? nu1 : 0;
   T.grid = dim3((L.cols + kTQ - 1) / kTQ, (L.rows + kTJ - 1) / kTJ);
-  if (T.reach == 2) {
-    if (T.nu1 == 2) ok &= make_map(&T.f_pre, f, L, PreGeo<2, 2>::HX, PreGeo<2, 2>::HY);
-    if (T.nu1 == 1) ok &= make_map(&T.f_pre, f, L, PreGeo<2, 1>::HX, PreGeo<2, 1>::HY);
-    ok &= make_map(&T.u_sw, u, L, SweepGeo<2>::HX, SweepGeo<2>::HY);
-    ok &= make_map(&T.t_sw, t, L, SweepGeo<2>::HX, SweepGeo<2>::HY);
-    ok &= make_map(&T.f_sw, f, L, SweepGeo<2>::HX, SweepGeo<2>::HY);
-    ok &= make_map(&T.u_rr, u, L, RrGeo<2>::HX, RrGeo<2>::HY);
-    ok &= make_map(&T.f_rr, f, L, RrGeo<2>::HX, RrGeo<2>::HY);
-  } else {
-    if (T.nu1 == 2) ok &= make_map(&T.f_pre, f, L, PreGeo<1, 2>::HX, PreGeo<1, 2>::HY);
-    if (T.nu1 == 1) ok &= make_map(&T.f_pre, f, L, PreGeo<1, 1>::HX, PreGeo<1, 1>::HY);
-    ok &= make_map(&T.u_sw, u, L, SweepGeo<1>::HX, SweepGeo<1>::HY);
-    ok &= make_map(&T.t_sw, t, L, SweepGeo<1>::HX, SweepGeo<1>::HY);
-    ok &= make_map(&T.f_sw, f, L, SweepGeo<1>::HX, SweepGeo<1>::HY);
-    ok &= make_map(&T.u_rr, u, L, RrGeo<1>::HX, RrGeo<1>::HY);
-    ok &= make_map(&T.f_rr, f, L, RrGeo<1>::HX, RrGeo<1>::HY);
-  }
+  if (T.reach == 3) ok &= axis_maps<3>(T, L, u, t, f);
+  else if (T.reach == 2) ok &= axis_maps<2>(T, L, u, t, f);
+  else ok &= axis_maps<1>(T, L, u, t, f);
   T.on = ok;
   return ok;
 }
@@ -1380,7 +1428,7 @@ bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, flo
 namespace {
 template <bool EXACT, int NT, int NS>
 cudaError_t presmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u, int* status, cudaStream_t s) {
-  const size_t smem = pre_smem<NT == 5 ? 1 : 2, NS>();
+  const size_t smem = pre_smem<tile_reach(NT), NS>();
   cudaError_t e = allow_smem<k_tile_presmooth<EXACT, NT, NS>>(smem);
   if (e != cudaSuccess) return e;
   k_tile_presmooth<EXACT, NT, NS><<<T.grid, kTT, smem, s>>>(L.d, T.f_pre, u, status);
@@ -1389,7 +1437,7 @@ cudaError_t presmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u
 template <bool EXACT, int NT>
 cudaError_t sweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t, float* out, int* status,
                      cudaStream_t s) {
-  const size_t smem = sweep_smem<NT == 5 ? 1 : 2>();
+  const size_t smem = sweep_smem<tile_reach(NT)>();
   cudaError_t e = allow_smem<k_tile_sweep<EXACT, NT>>(smem);
   if (e != cudaSuccess) return e;
   k_tile_sweep<EXACT, NT><<<T.grid, kTT, smem, s>>>(L.d, from_t ? T.t_sw : T.u_sw, T.f_sw, out, status);
@@ -1398,7 +1446,7 @@ cudaError_t sweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t,
 template <bool EXACT, int NT, bool TC>
 cudaError_t rr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc, float* fc, float* tc,
                   int* status, cudaStream_t s) {
-  const size_t smem = rr_smem<NT == 5 ? 1 : 2>();
+  const size_t smem = rr_smem<tile_reach(NT)>();
   cudaError_t e = allow_smem<k_tile_res_restrict<EXACT, NT, TC>>(smem);
   if (e != cudaSuccess) return e;
   k_tile_res_restrict<EXACT, NT, TC><<<T.grid, kTT, smem, s>>>(L.d, Lc.d, T.u_rr, T.f_rr, fc, tc, status);
@@ -1443,6 +1491,10 @@ cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L,
     if (T.nu1 == 2) return exact ? presmooth_as<true, 21, 2>(T, L, u, status, s) : presmooth_as<false, 21, 2>(T, L, u, status, s);
     return exact ? presmooth_as<true, 21, 1>(T, L, u, status, s) : presmooth_as<false, 21, 1>(T, L, u, status, s);
   }
+  if (T.nt == 37) {
+    if (T.nu1 == 2) return exact ? presmooth_as<true, 37, 2>(T, L, u, status, s) : presmooth_as<false, 37, 2>(T, L, u, status, s);
+    return exact ? presmooth_as<true, 37, 1>(T, L, u, status, s) : presmooth_as<false, 37, 1>(T, L, u, status, s);
+  }
   if (T.nt == 9) {
     if (T.nu1 == 2) return exact ? presmooth_as<true, 9, 2>(T, L, u, status, s) : presmooth_as<false, 9, 2>(T, L, u, status, s);
     return exact ? presmooth_as<true, 9, 1>(T, L, u, status, s) : presmooth_as<false, 9, 1>(T, L, u, status, s);
@@ -1457,6 +1509,8 @@ cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, boo
   if (T.rot) return exact ? rsweep_as<true>(T, L, from_t, uout, status, s) : rsweep_as<false>(T, L, from_t, uout, status, s);
   if (T.nt == 21)
     return exact ? sweep_as<true, 21>(T, L, from_t, uout, status, s) : sweep_as<false, 21>(T, L, from_t, uout, status, s);
+  if (T.nt == 37)
+    return exact ? sweep_as<true, 37>(T, L, from_t, uout, status, s) : sweep_as<false, 37>(T, L, from_t, uout, status, s);
   if (T.nt == 9)
     return exact ? sweep_as<true, 9>(T, L, from_t, uout, status, s) : sweep_as<false, 9>(T, L, from_t, uout, status, s);
   return exact ? sweep_as<true, 5>(T, L, from_t, uout, status, s) : sweep_as<false, 5>(T, L, from_t, uout, status, s);
@@ -1474,6 +1528,10 @@ cudaError_t launch_tile_res_restrict(const TileLevel& T, const LevelPair<float>&
   if (T.nt == 21) {
     if (tc) return exact ? rr_as<true, 21, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 21, true>(T, L, Lc, fc, tc, status, s);
     return exact ? rr_as<true, 21, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 21, false>(T, L, Lc, fc, tc, status, s);
+  }
+  if (T.nt == 37) {
+    if (tc) return exact ? rr_as<true, 37, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 37, true>(T, L, Lc, fc, tc, status, s);
+    return exact ? rr_as<true, 37, false>(T, L, Lc, fc, tc, status, s) : rr_as<false, 37, false>(T, L, Lc, fc, tc, status, s);
   }
   if (T.nt == 9) {
     if (tc) return exact ? rr_as<true, 9, true>(T, L, Lc, fc, tc, status, s) : rr_as<false, 9, true>(T, L, Lc, fc, tc, status, s);
