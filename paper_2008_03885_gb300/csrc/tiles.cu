@@ -143,6 +143,20 @@ __host__ __device__ constexpr bool wide_nt(int nt) { return nt == 21 || nt == 37
 // stencil reach of the NT-term fast stencils of the axis tile kernels
 __host__ __device__ constexpr int tile_reach(int nt) { return nt == 5 ? 1 : nt == 37 ? 3 : 2; }
 
+// (L x)(i, j) at a node outside the fast range: its boundary-class term list.
+template <bool EXACT, class X>
+__device__ __forceinline__ float class_stencil(const LevelDev<float>& L, int i, int j, X x) {
+  const int2 e = L.cls[class_of(L, i, j)];
+  const ClassTerm<float>* tt = L.terms + e.x;
+  RowSum<float, EXACT> acc;
+#pragma unroll 4
+  for (int k = 0; k < e.y; ++k) {
+    const Term<float> t = load_term(tt + k);
+    acc.add(t.c, x(i + t.dx, j + t.dy), t.start);
+  }
+  return acc.value();
+}
+
 // (L x)(i, j): the fast cross stencil with coefficients c (in evaluation order) or the
 // node's boundary-class term list. x(i, j) returns the value of lattice node (i, j).
 template <bool EXACT, int NT, class X>
@@ -173,15 +187,7 @@ __device__ __forceinline__ float stencil(const LevelDev<float>& L, const float (
     }
     return acc.value();
   }
-  const int2 e = L.cls[class_of(L, i, j)];
-  const ClassTerm<float>* tt = L.terms + e.x;
-  RowSum<float, EXACT> acc;
-#pragma unroll 4
-  for (int k = 0; k < e.y; ++k) {
-    const Term<float> t = load_term(tt + k);
-    acc.add(t.c, x(i + t.dx, j + t.dy), t.start);
-  }
-  return acc.value();
+  return class_stencil<EXACT>(L, i, j, x);
 }
 
 // Tile origin of the block.
@@ -831,58 +837,81 @@ struct RZero {
   __device__ __forceinline__ float at(int) const { return 0.f; }
 };
 
-// The fast stencil of a rotated level: coefficients and storage offsets by row parity.
-struct RStencil {
-  float c[9];
-  int sx[2][9], sy[9];
-  __device__ __forceinline__ explicit RStencil(const LevelDev<float>& L) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      c[k] = L.c[k];
-      sx[0][k] = L.sdx[0][k];
-      sx[1][k] = L.sdx[1][k];
-      sy[k] = L.sdy[k];
-    }
+// The fast stencils of the rotated tile kernels, in evaluation order (lattice offsets):
+// 9 points = the first Galerkin stencil (Eq. L_G1): the four (2, 0) neighbours, the four
+// diagonal ones, the centre; 25 points = the second rotated Galerkin level of G^(2): the
+// four (4, 0), the eight (1, 3), the four (2, 2), the four (2, 0), the four diagonal
+// neighbours, the centre. Terms on rows of odd offset are the other colour's.
+template <int NT>
+__host__ __device__ constexpr int rot_dx(int k) {
+  if constexpr (NT == 9) {
+    constexpr int x[9] = {0, -2, 2, 0, -1, 1, -1, 1, 0};
+    return x[k];
+  } else {
+    constexpr int x[25] = {0, -4, 4, 0, -1, 1, -3, 3, -3, 3, -1, 1, -2, 2, -2, 2, 0, -2, 2, 0, -1, 1, -1, 1, 0};
+    return x[k];
   }
-};
-
-// Index offsets of the fast stencil's terms in two sources, for nodes of parity PAR:
-// terms 0-3 in the same-colour source SS (from the node), terms 4-7 in the other-colour
-// source SO (from the node's column on row j - 1).
-struct ROffsets {
-  int s[4], o[4];
-};
-template <int PAR, class SS, class SO>
-__device__ __forceinline__ ROffsets roffsets(const RStencil& S) {
-  ROffsets r;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r.s[k] = (S.sy[k] / 2) * SS::step2 + S.sx[PAR][k];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) r.o[k] = ((S.sy[4 + k] + 1) / 2) * SO::step2 + S.sx[PAR][4 + k];
-  return r;
+}
+template <int NT>
+__host__ __device__ constexpr int rot_dy(int k) {
+  if constexpr (NT == 9) {
+    constexpr int y[9] = {-2, 0, 0, 2, -1, -1, 1, 1, 0};
+    return y[k];
+  } else {
+    constexpr int y[25] = {-4, 0, 0, 4, -3, -3, -1, -1, 1, 1, 3, 3, -2, -2, 2, 2, -2, 0, 0, 2, -1, -1, 1, 1, 0};
+    return y[k];
+  }
+}
+template <int NT>
+__host__ __device__ constexpr bool rot_gstart(int k) {
+  if constexpr (NT == 9) return k == 0 || k == 4 || k == 8;
+  else return k == 0 || k == 4 || k == 12 || k == 16 || k == 20 || k == 24;
+}
+// storage column offset of term k for a node on a row of parity par (i = 2q + par)
+template <int NT>
+__host__ __device__ constexpr int rot_sdx(int k, int par) {
+  return (rot_dy<NT>(k) & 1) ? (2 * par + rot_dx<NT>(k) - 1) / 2 : rot_dx<NT>(k) / 2;
 }
 
-// (L x) at a fast node: same-colour terms from ss (base bs = the node), other-colour
-// terms from so (base bo), in evaluation order.
-template <bool EXACT, class SS, class SO>
-__device__ __forceinline__ float rcross(const RStencil& S, const ROffsets& of, const SS& ss, int bs, const SO& so, int bo) {
-  float x[9];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) x[k] = ss.at(bs + of.s[k]);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) x[4 + k] = so.at(bo + of.o[k]);
-  x[8] = ss.at(bs);
+// Region margins and box halos of the rotated kernels for a stencil reaching RY rows and
+// RX storage columns: each phase's region covers what the next one reads.
+template <int NT>
+struct RGeo {
+  static constexpr int RY = NT == 9 ? 2 : 4, RX = NT == 9 ? 1 : 2;
+  static constexpr int M0 = 3 * RY, MC0 = 3 * RX, M1 = 2 * RY, MC1 = 2 * RX, M2 = RY, MC2 = RX;
+  static constexpr int PHX = round4(MC0), PHY = M0;        // presmooth: f box
+  static constexpr int SHX = round4(2 * RX), SHY = 2 * RY;  // sweep: u, f boxes
+  static constexpr int QHX = round4(1 + RX), QHY = 2 + RY;  // residual + restriction
+};
+
+// (L x) at a fast node of parity PAR: same-colour terms from ss (base bs = the node),
+// other-colour terms from so (base bo = the node's column on row j - 1), in evaluation
+// order; every index offset is a compile-time constant.
+template <int NT, int PAR, int K, class SS, class SO>
+__device__ __forceinline__ float rterm(const SS& ss, int bs, const SO& so, int bo) {
+  constexpr int DY = rot_dy<NT>(K), SX = rot_sdx<NT>(K, PAR);
+  if constexpr ((DY & 1) != 0) return so.at(bo + ((DY + 1) / 2) * SO::step2 + SX);
+  else return ss.at(bs + (DY / 2) * SS::step2 + SX);
+}
+template <bool EXACT, int NT, int PAR, class SS, class SO, int... K>
+__device__ __forceinline__ float rcross_seq(const float (&c)[NT], const SS& ss, int bs, const SO& so, int bo,
+                                           std::integer_sequence<int, K...>) {
+  const float x[NT] = {rterm<NT, PAR, K>(ss, bs, so, bo)...};
   if constexpr (EXACT) {
-    const float g0 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x[0], x[1]), x[2]), x[3]);
-    const float g1 = Arith<float>::add(Arith<float>::add(Arith<float>::add(x[4], x[5]), x[6]), x[7]);
-    return Arith<float>::add(Arith<float>::add(Arith<float>::mul(S.c[0], g0), Arith<float>::mul(S.c[4], g1)),
-                             Arith<float>::mul(S.c[8], x[8]));
-  } else {
-    float s = Arith<float>::mul(S.c[0], x[0]);
+    RowSum<float, true> acc;
 #pragma unroll
-    for (int k = 1; k < 9; ++k) s = Arith<float>::fma(S.c[k], x[k], s);
+    for (int k = 0; k < NT; ++k) acc.add(c[k], x[k], rot_gstart<NT>(k));
+    return acc.value();
+  } else {
+    float s = Arith<float>::mul(c[0], x[0]);
+#pragma unroll
+    for (int k = 1; k < NT; ++k) s = Arith<float>::fma(c[k], x[k], s);
     return s;
   }
+}
+template <bool EXACT, int NT, int PAR, class SS, class SO>
+__device__ __forceinline__ float rcross(const float (&c)[NT], const SS& ss, int bs, const SO& so, int bo) {
+  return rcross_seq<EXACT, NT, PAR>(c, ss, bs, so, bo, std::make_integer_sequence<int, NT>{});
 }
 
 // Value of lattice node (a, b) in a source.
@@ -940,11 +969,11 @@ struct RStrips {
 // fast range; with EDGE (a tile reaching the boundary strip) only the rows holding fast
 // nodes are walked with the fast stencil, and the strip nodes outside the fast range
 // get gen(i, j) in a second pass. sink(e, q, j, v), e = index in the region's array.
-template <bool EXACT, int PAR, int M, int MC, bool ZERO, bool EDGE, class SS, class SO, class FB, class SINK, class GEN>
-__device__ __forceinline__ void rphase(const RStencil& S, float wd, const SS& ss, const SO& so, const FB& fb,
+template <bool EXACT, int NT, int PAR, int M, int MC, bool ZERO, bool EDGE, class SS, class SO, class FB, class SINK,
+          class GEN>
+__device__ __forceinline__ void rphase(const float (&c)[NT], float wd, const SS& ss, const SO& so, const FB& fb,
                                        const RTile& T, const LevelDev<float>& L, SINK sink, GEN gen) {
   using G = RReg<M, MC>;
-  const ROffsets of = roffsets<PAR, SS, SO>(S);
   auto fast = [&](int e, int kr, int cq) {
     const int j = T.J0 - M + 2 * kr + PAR, q = T.C0 - MC + cq;
     if (EDGE && !fast_node_c<false>(L, 2 * q + PAR, j)) return;
@@ -954,7 +983,8 @@ __device__ __forceinline__ void rphase(const RStencil& S, float wd, const SS& ss
       v = relax_from_zero(f, wd);
     } else {
       const int bs = ss.template idx_r<M, MC, PAR, 0>(kr, cq);
-      v = relax<EXACT>(rcross<EXACT>(S, of, ss, bs, so, so.template idx_r<M, MC, PAR, -1>(kr, cq)), f, ss.at(bs), wd);
+      v = relax<EXACT>(rcross<EXACT, NT, PAR>(c, ss, bs, so, so.template idx_r<M, MC, PAR, -1>(kr, cq)), f, ss.at(bs),
+                       wd);
     }
     sink(e, q, j, v);
   };
@@ -1012,71 +1042,69 @@ __device__ __forceinline__ void rstore_row(float* out, const LevelDev<float>& L,
   out[(int64_t)j * L.pitch + q] = src.at(src.idx(T, q, j));
 }
 
-// Box geometry of the rotated kernels (x halo rounded to 4 floats for TMA).
-constexpr int kRHX = 4;
-constexpr int kRPreHY = 6;  // presmooth: f on red rows of the tile plus 6 rows, 3 columns
-constexpr int kRHY = 4;     // sweep, residual + restriction: u, f on the tile plus 4 rows
-
 // ---- rotated presmooth: 2 red-black sweeps from u = 0 ------------------------------
-template <bool EXACT>
+template <bool EXACT, int NT>
 __global__ void __launch_bounds__(kTT, 3) k_rtile_presmooth(const LevelDev<float>* __restrict__ Lp,
                                                          const __grid_constant__ CUtensorMap mapF,
                                                          float* __restrict__ out, int* __restrict__ status) {
-  constexpr int FN = (kRC + 2 * kRHX) * (kRR + 2 * kRPreHY);
+  using G = RGeo<NT>;
+  constexpr int FN = (kRC + 2 * G::PHX) * (kRR + 2 * G::PHY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
   float* box0 = smem_base(tile_smem);
   float* sR0 = box0 + pad32(FN);
-  float* sB1 = sR0 + RReg<6, 3>::n;
-  float* sR2 = sB1 + RReg<4, 2>::n;
+  float* sB1 = sR0 + RReg<G::M0, G::MC0>::n;
+  float* sR2 = sB1 + RReg<G::M1, G::MC1>::n;
   const LevelDev<float>& L = *Lp;
-  const RStencil S(L);
+  float c[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) c[k] = L.c[k];
   const float wdf = L.wd;
   const int n = L.n;
   const CUtensorMap* const maps[1] = {&mapF};
-  rtile_block<1>(box0, pad32(FN), maps, kRHX, kRPreHY, status, [&](const RTile& T, float* sF) {
-    const RBox<kRHX, kRPreHY> fb{sF};
-    const RComp<6, 3, 1> r0{sR0};
-    const RComp<4, 2, 0> b1{sB1};
-    const RComp<2, 1, 1> r2{sR2};
+  rtile_block<1>(box0, pad32(FN), maps, G::PHX, G::PHY, status, [&](const RTile& T, float* sF) {
+    const RBox<G::PHX, G::PHY> fb{sF};
+    const RComp<G::M0, G::MC0, 1> r0{sR0};
+    const RComp<G::M1, G::MC1, 0> b1{sB1};
+    const RComp<G::M2, G::MC2, 1> r2{sR2};
     auto F = [=](int i, int j) { return rval(fb, T, i, j); };
     auto run = [&](auto check) {
       constexpr bool EDGE = decltype(check)::value;
       // red from zero: 0 + f omega / a_pp
-      rphase<EXACT, 1, 6, 3, true, EDGE>(S, wdf, RZero{}, RZero{}, fb, T, L,
+      rphase<EXACT, NT, 1, G::M0, G::MC0, true, EDGE>(c, wdf, RZero{}, RZero{}, fb, T, L,
                                          [=](int e, int, int, float v) { sR0[e] = v; }, [=](int i, int j) {
                                            return inner(n, i, j) ? relax_from_zero(F(i, j), wd_at(L, wdf, i, j)) : 0.f;
                                          });
       __syncthreads();
       // black of sweep 1 (old values 0)
-      rphase<EXACT, 0, 4, 2, false, EDGE>(S, wdf, RZero{}, r0, fb, T, L, [=](int e, int, int, float v) { sB1[e] = v; },
+      rphase<EXACT, NT, 0, G::M1, G::MC1, false, EDGE>(c, wdf, RZero{}, r0, fb, T, L, [=](int e, int, int, float v) { sB1[e] = v; },
                                           [=](int i, int j) {
                                             if (!inner(n, i, j)) return 0.f;
-                                            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+                                            const float st = class_stencil<EXACT>(L, i, j, [=](int a, int b) {
                                               return (a & 1) ? rval(r0, T, a, b) : 0.f;
                                             });
                                             return relax<EXACT>(st, F(i, j), 0.f, wd_at(L, wdf, i, j));
                                           });
       __syncthreads();
       // red of sweep 2
-      rphase<EXACT, 1, 2, 1, false, EDGE>(S, wdf, r0, b1, fb, T, L, [=](int e, int, int, float v) { sR2[e] = v; },
+      rphase<EXACT, NT, 1, G::M2, G::MC2, false, EDGE>(c, wdf, r0, b1, fb, T, L, [=](int e, int, int, float v) { sR2[e] = v; },
                                           [=](int i, int j) {
                                             if (!inner(n, i, j)) return 0.f;
-                                            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+                                            const float st = class_stencil<EXACT>(L, i, j, [=](int a, int b) {
                                               return (a & 1) ? rval(r0, T, a, b) : rval(b1, T, a, b);
                                             });
                                             return relax<EXACT>(st, F(i, j), rval(r0, T, i, j), wd_at(L, wdf, i, j));
                                           });
       __syncthreads();
       // black of sweep 2 on the tile, stored; then the red rows of the tile
-      rphase<EXACT, 0, 0, 0, false, EDGE>(
-          S, wdf, b1, r2, fb, T, L,
+      rphase<EXACT, NT, 0, 0, 0, false, EDGE>(
+          c, wdf, b1, r2, fb, T, L,
           [=](int, int q, int j, float v) {
             if (EDGE && (j > n || q >= L.cols)) return;
             out[(int64_t)j * L.pitch + q] = v;
           },
           [=](int i, int j) {
             if (!inner(n, i, j)) return 0.f;
-            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+            const float st = class_stencil<EXACT>(L, i, j, [=](int a, int b) {
               return (a & 1) ? rval(r2, T, a, b) : rval(b1, T, a, b);
             });
             return relax<EXACT>(st, F(i, j), rval(b1, T, i, j), wd_at(L, wdf, i, j));
@@ -1086,43 +1114,46 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_presmooth(const LevelDev<float
         rstore_row(out, L, T, r2, T.J0 + 2 * kr + 1, cq);
       }
     };
-    if (rfast_tile<6, 3>(L, T)) run(std::false_type{});
+    if (rfast_tile<G::M0, G::MC0>(L, T)) run(std::false_type{});
     else run(std::true_type{});
   });
 }
 
 // ---- rotated sweep: one red-black sweep, u -> out ------------------------------------
-template <bool EXACT>
+template <bool EXACT, int NT>
 __global__ void __launch_bounds__(kTT, 3) k_rtile_sweep(const LevelDev<float>* __restrict__ Lp,
                                                      const __grid_constant__ CUtensorMap mapU,
                                                      const __grid_constant__ CUtensorMap mapF, float* __restrict__ out,
                                                      int* __restrict__ status) {
-  constexpr int BN = (kRC + 2 * kRHX) * (kRR + 2 * kRHY);
+  using G = RGeo<NT>;
+  constexpr int BN = (kRC + 2 * G::SHX) * (kRR + 2 * G::SHY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
   float* box0 = smem_base(tile_smem);
   float* sR = box0 + 2 * pad32(BN);
   const LevelDev<float>& L = *Lp;
-  const RStencil S(L);
+  float c[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) c[k] = L.c[k];
   const float wdf = L.wd;
   const int n = L.n;
   const CUtensorMap* const maps[2] = {&mapU, &mapF};
-  rtile_block<2>(box0, pad32(BN), maps, kRHX, kRHY, status, [&](const RTile& T, float* sU) {
-    const RBox<kRHX, kRHY> ub{sU}, fb{sU + pad32(BN)};
-    const RComp<2, 1, 1> rn{sR};
+  rtile_block<2>(box0, pad32(BN), maps, G::SHX, G::SHY, status, [&](const RTile& T, float* sU) {
+    const RBox<G::SHX, G::SHY> ub{sU}, fb{sU + pad32(BN)};
+    const RComp<G::M2, G::MC2, 1> rn{sR};
     auto U = [=](int i, int j) { return rval(ub, T, i, j); };
     auto F = [=](int i, int j) { return rval(fb, T, i, j); };
     auto run = [&](auto check) {
       constexpr bool EDGE = decltype(check)::value;
-      rphase<EXACT, 1, 2, 1, false, EDGE>(S, wdf, ub, ub, fb, T, L, [=](int e, int, int, float v) { sR[e] = v; },
+      rphase<EXACT, NT, 1, G::M2, G::MC2, false, EDGE>(c, wdf, ub, ub, fb, T, L, [=](int e, int, int, float v) { sR[e] = v; },
                                           [=](int i, int j) {
                                             const float v = U(i, j);
-                                            return inner(n, i, j) ? relax<EXACT>(stencil<EXACT, 9>(L, S.c, i, j, U),
+                                            return inner(n, i, j) ? relax<EXACT>(class_stencil<EXACT>(L, i, j, U),
                                                                                  F(i, j), v, wd_at(L, wdf, i, j))
                                                                   : v;
                                           });
       __syncthreads();
-      rphase<EXACT, 0, 0, 0, false, EDGE>(
-          S, wdf, ub, rn, fb, T, L,
+      rphase<EXACT, NT, 0, 0, 0, false, EDGE>(
+          c, wdf, ub, rn, fb, T, L,
           [=](int, int q, int j, float v) {
             if (EDGE && (j > n || q >= L.cols)) return;
             out[(int64_t)j * L.pitch + q] = v;
@@ -1130,7 +1161,7 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_sweep(const LevelDev<float>* _
           [=](int i, int j) {
             const float v = U(i, j);
             if (!inner(n, i, j)) return v;
-            const float st = stencil<EXACT, 9>(L, S.c, i, j, [=](int a, int b) {
+            const float st = class_stencil<EXACT>(L, i, j, [=](int a, int b) {
               return (a & 1) ? rval(rn, T, a, b) : U(a, b);
             });
             return relax<EXACT>(st, F(i, j), v, wd_at(L, wdf, i, j));
@@ -1140,7 +1171,7 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_sweep(const LevelDev<float>* _
         rstore_row(out, L, T, rn, T.J0 + 2 * kr + 1, cq);
       }
     };
-    if (rfast_tile<2, 1>(L, T)) run(std::false_type{});
+    if (rfast_tile<G::M2, G::MC2>(L, T)) run(std::false_type{});
     else run(std::true_type{});
   });
 }
@@ -1148,24 +1179,27 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_sweep(const LevelDev<float>* _
 // ---- rotated residual + red-black restriction (rotated level -> its axis level) ------
 // Coarse nodes = the black (even-row) nodes; R = 1/2 P^T, Eq. (transfer_r2) in the
 // rotated frame: terms (-1,-1), (1,-1), (0,0), (-1,1), (1,1) (lattice offsets).
-template <bool EXACT, bool TC>
+template <bool EXACT, int NT, bool TC>
 __global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<float>* __restrict__ Lp,
                                                             const LevelDev<float>* __restrict__ Lcp,
                                                             const __grid_constant__ CUtensorMap mapU,
                                                             const __grid_constant__ CUtensorMap mapF,
                                                             float* __restrict__ fc, float* __restrict__ tc,
                                                             int* __restrict__ status) {
-  constexpr int BN = (kRC + 2 * kRHX) * (kRR + 2 * kRHY);
+  using G = RGeo<NT>;
+  constexpr int BN = (kRC + 2 * G::QHX) * (kRR + 2 * G::QHY);
   extern __shared__ __align__(128) unsigned char tile_smem[];
   float* box0 = smem_base(tile_smem);
   float* sD = box0 + 2 * pad32(BN);  // residuals of the red nodes, region (2, 1)
   const LevelDev<float>& L = *Lp;
   const LevelDev<float>& Lc = *Lcp;
-  const RStencil S(L);
+  float c[NT];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) c[k] = L.c[k];
   const int n = L.n, pc = Lc.pitch;
   const CUtensorMap* const maps[2] = {&mapU, &mapF};
-  rtile_block<2>(box0, pad32(BN), maps, kRHX, kRHY, status, [&](const RTile& T, float* sU) {
-    const RBox<kRHX, kRHY> ub{sU}, fb{sU + pad32(BN)};
+  rtile_block<2>(box0, pad32(BN), maps, G::QHX, G::QHY, status, [&](const RTile& T, float* sU) {
+    const RBox<G::QHX, G::QHY> ub{sU}, fb{sU + pad32(BN)};
     const RComp<2, 1, 1> dr{sD};
     auto U = [=](int i, int j) { return rval(ub, T, i, j); };
     auto F = [=](int i, int j) { return rval(fb, T, i, j); };
@@ -1174,13 +1208,11 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<fl
       // red residuals on the region (2, 1) (0 off the interior), through the phase walker
       // with a residual in place of the relaxation
       using G = RReg<2, 1>;
-      const ROffsets o1 = roffsets<1, RBox<kRHX, kRHY>, RBox<kRHX, kRHY>>(S);
-      const ROffsets o0 = roffsets<0, RBox<kRHX, kRHY>, RBox<kRHX, kRHY>>(S);
       auto red_fast = [&](int e, int kr, int cq) {
         const int j = T.J0 - 2 + 2 * kr + 1, q = T.C0 - 1 + cq;
         if (EDGE && !fast_node_c<false>(L, 2 * q + 1, j)) return;
         const int b = ub.idx(T, q, j);
-        sD[e] = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT>(S, o1, ub, b, ub, ub.idx(T, q, j - 1)));
+        sD[e] = Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT, NT, 1>(c, ub, b, ub, ub.idx(T, q, j - 1)));
       };
       if constexpr (!EDGE) {
         for (int e = threadIdx.x; e < G::n; e += kTT) {
@@ -1198,7 +1230,7 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<fl
           st.at(k, kr, cq);
           const int j = T.J0 - 2 + 2 * kr + 1, q = T.C0 - 1 + cq, i = 2 * q + 1;
           if (fast_node_c<false>(L, i, j)) continue;
-          sD[kr * G::w + cq] = inner(n, i, j) ? Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U)) : 0.f;
+          sD[kr * G::w + cq] = inner(n, i, j) ? Arith<float>::sub(F(i, j), class_stencil<EXACT>(L, i, j, U)) : 0.f;
         }
       }
       __syncthreads();
@@ -1219,7 +1251,7 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<fl
         const int j = T.J0 + 2 * kr, q = T.C0 + cq;
         if (EDGE && !fast_node_c<false>(L, 2 * q, j)) return;
         coarse(q, j,
-               Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT>(S, o0, ub, ub.idx(T, q, j), ub, ub.idx(T, q, j - 1))));
+               Arith<float>::sub(fb.at(fb.idx(T, q, j)), rcross<EXACT, NT, 0>(c, ub, ub.idx(T, q, j), ub, ub.idx(T, q, j - 1))));
       };
       using G0 = RReg<0, 0>;
       if constexpr (!EDGE) {
@@ -1238,7 +1270,7 @@ __global__ void __launch_bounds__(kTT, 3) k_rtile_res_restrict(const LevelDev<fl
           st.at(k, kr, cq);
           const int j = T.J0 + 2 * kr, q = T.C0 + cq, i = 2 * q;
           if (fast_node_c<false>(L, i, j) || !inner(n, i, j)) continue;
-          coarse(q, j, Arith<float>::sub(F(i, j), stencil<EXACT, 9>(L, S.c, i, j, U)));
+          coarse(q, j, Arith<float>::sub(F(i, j), class_stencil<EXACT>(L, i, j, U)));
         }
       }
     };
@@ -1298,12 +1330,23 @@ size_t rr_smem() {
   return (2 * (size_t)pad32((kTQ + 2 * G::HX) * (kTJ + 2 * G::HY)) + Reg<1>::n) * sizeof(float) + 128;
 }
 
+template <int NT>
 size_t rpre_smem() {
-  return ((size_t)pad32((kRC + 2 * kRHX) * (kRR + 2 * kRPreHY)) + RReg<6, 3>::n + RReg<4, 2>::n + RReg<2, 1>::n) *
-             sizeof(float) + 128;
+  using G = RGeo<NT>;
+  return ((size_t)pad32((kRC + 2 * G::PHX) * (kRR + 2 * G::PHY)) + RReg<G::M0, G::MC0>::n + RReg<G::M1, G::MC1>::n +
+          RReg<G::M2, G::MC2>::n) *
+             sizeof(float) +
+         128;
 }
+template <int NT>
 size_t rsw_smem() {
-  return (2 * (size_t)pad32((kRC + 2 * kRHX) * (kRR + 2 * kRHY)) + RReg<2, 1>::n) * sizeof(float) + 128;
+  using G = RGeo<NT>;
+  return (2 * (size_t)pad32((kRC + 2 * G::SHX) * (kRR + 2 * G::SHY)) + RReg<G::M2, G::MC2>::n) * sizeof(float) + 128;
+}
+template <int NT>
+size_t rrr_smem() {
+  using G = RGeo<NT>;
+  return (2 * (size_t)pad32((kRC + 2 * G::QHX) * (kRR + 2 * G::QHY)) + RReg<2, 1>::n) * sizeof(float) + 128;
 }
 
 // Raise a kernel's dynamic shared-memory limit once per process (the sizes are fixed
@@ -1316,20 +1359,20 @@ cudaError_t allow_smem(size_t bytes) {
 
 }  // namespace
 
-// Rotated levels: the first Galerkin 9-point stencil in evaluation order (terms 0-3 on
-// rows two apart or the same row, terms 4-7 on the adjacent rows, the centre last), no
-// term more than one storage column or two rows away.
-bool rot_tile_shape(const LevelDev<float>& L) {
-  if (L.nt != 9 || L.gmask[0] != fast_gmask(9)) return false;
-  for (int w = 1; w < kMaxTerms / 32; ++w)
-    if (L.gmask[w]) return false;
-  for (int k = 0; k < 9; ++k) {
-    const int dy = L.sdy[k];
-    if (std::abs(L.sdx[0][k]) > 1 || std::abs(L.sdx[1][k]) > 1 || std::abs(dy) > 2) return false;
-    if ((k < 4 && (dy & 1)) || (k >= 4 && k < 8 && !(dy & 1))) return false;
+// Rotated levels: one of the stencils of rot_dx / rot_dy in evaluation order (the first
+// Galerkin 9-point stencil, or the 25-point one of the second rotated Galerkin level).
+template <int NT>
+bool rot_shape_is(const LevelDev<float>& L) {
+  if (L.nt != NT) return false;
+  for (int k = 0; k < kMaxTerms; ++k) {
+    const bool start = (L.gmask[k >> 5] >> (k & 31)) & 1u;
+    if (k >= NT ? start : start != rot_gstart<NT>(k)) return false;
   }
-  return L.sdy[8] == 0 && L.sdx[0][8] == 0 && L.sdx[1][8] == 0;
+  for (int k = 0; k < NT; ++k)
+    if (L.sdy[k] != rot_dy<NT>(k) || L.sdx[0][k] != rot_sdx<NT>(k, 0) || L.sdx[1][k] != rot_sdx<NT>(k, 1)) return false;
+  return true;
 }
+bool rot_tile_shape(const LevelDev<float>& L) { return rot_shape_is<9>(L) || rot_shape_is<25>(L); }
 
 bool gbit_host(const uint32_t* m, int k) { return (m[k >> 5] >> (k & 31)) & 1u; }
 
@@ -1368,6 +1411,20 @@ bool tile_eligible(const LevelPair<float>& P) {
 }
 
 namespace {
+// Tensor maps of a rotated level with the NT-point stencil.
+template <int NT>
+bool rot_maps(TileLevel& T, const LevelDev<float>& L, float* u, float* t, float* f) {
+  using G = RGeo<NT>;
+  bool ok = true;
+  if (T.nu1) ok &= make_map(&T.f_pre, f, L, G::PHX, G::PHY, kRC, kRR);
+  ok &= make_map(&T.u_sw, u, L, G::SHX, G::SHY, kRC, kRR);
+  ok &= make_map(&T.t_sw, t, L, G::SHX, G::SHY, kRC, kRR);
+  ok &= make_map(&T.f_sw, f, L, G::SHX, G::SHY, kRC, kRR);
+  ok &= make_map(&T.u_rr, u, L, G::QHX, G::QHY, kRC, kRR);
+  ok &= make_map(&T.f_rr, f, L, G::QHX, G::QHY, kRC, kRR);
+  return ok;
+}
+
 // Tensor maps of an axis level whose fast stencil reaches R nodes.
 template <int R>
 bool axis_maps(TileLevel& T, const LevelDev<float>& L, float* u, float* t, float* f) {
@@ -1407,12 +1464,8 @@ bool tile_setup(TileLevel& T, const LevelPair<float>& P, float* u, float* t, flo
   if (T.rot) {  // rotated tiles: presmooth for nu1 = 2 only
     T.nu1 = nu1 == 2 ? 2 : 0;
     T.grid = dim3((L.cols + kRC - 1) / kRC, (L.rows + kRR - 1) / kRR);
-    if (T.nu1) ok &= make_map(&T.f_pre, f, L, kRHX, kRPreHY, kRC, kRR);
-    ok &= make_map(&T.u_sw, u, L, kRHX, kRHY, kRC, kRR);
-    ok &= make_map(&T.t_sw, t, L, kRHX, kRHY, kRC, kRR);
-    ok &= make_map(&T.f_sw, f, L, kRHX, kRHY, kRC, kRR);
-    ok &= make_map(&T.u_rr, u, L, kRHX, kRHY, kRC, kRR);
-    ok &= make_map(&T.f_rr, f, L, kRHX, kRHY, kRC, kRR);
+    if (L.nt == 25 && (long)T.grid.x * T.grid.y < device_sms()) return false;  // as for the axis wide stencils
+    ok &= L.nt == 9 ? rot_maps<9>(T, L, u, t, f) : rot_maps<25>(T, L, u, t, f);
     T.on = ok;
     return ok;
   }
@@ -1455,30 +1508,30 @@ cudaError_t rr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair
 }  // namespace
 
 namespace {
-template <bool EXACT>
+template <bool EXACT, int NT>
 cudaError_t rpresmooth_as(const TileLevel& T, const LevelPair<float>& L, float* u, int* status, cudaStream_t s) {
-  const size_t smem = rpre_smem();
-  cudaError_t e = allow_smem<k_rtile_presmooth<EXACT>>(smem);
+  const size_t smem = rpre_smem<NT>();
+  cudaError_t e = allow_smem<k_rtile_presmooth<EXACT, NT>>(smem);
   if (e != cudaSuccess) return e;
-  k_rtile_presmooth<EXACT><<<T.grid, kTT, smem, s>>>(L.d, T.f_pre, u, status);
+  k_rtile_presmooth<EXACT, NT><<<T.grid, kTT, smem, s>>>(L.d, T.f_pre, u, status);
   return cudaGetLastError();
 }
-template <bool EXACT>
+template <bool EXACT, int NT>
 cudaError_t rsweep_as(const TileLevel& T, const LevelPair<float>& L, bool from_t, float* out, int* status,
                       cudaStream_t s) {
-  const size_t smem = rsw_smem();
-  cudaError_t e = allow_smem<k_rtile_sweep<EXACT>>(smem);
+  const size_t smem = rsw_smem<NT>();
+  cudaError_t e = allow_smem<k_rtile_sweep<EXACT, NT>>(smem);
   if (e != cudaSuccess) return e;
-  k_rtile_sweep<EXACT><<<T.grid, kTT, smem, s>>>(L.d, from_t ? T.t_sw : T.u_sw, T.f_sw, out, status);
+  k_rtile_sweep<EXACT, NT><<<T.grid, kTT, smem, s>>>(L.d, from_t ? T.t_sw : T.u_sw, T.f_sw, out, status);
   return cudaGetLastError();
 }
-template <bool EXACT, bool TC>
+template <bool EXACT, int NT, bool TC>
 cudaError_t rrr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPair<float>& Lc, float* fc, float* tc,
                    int* status, cudaStream_t s) {
-  const size_t smem = rsw_smem();
-  cudaError_t e = allow_smem<k_rtile_res_restrict<EXACT, TC>>(smem);
+  const size_t smem = rrr_smem<NT>();
+  cudaError_t e = allow_smem<k_rtile_res_restrict<EXACT, NT, TC>>(smem);
   if (e != cudaSuccess) return e;
-  k_rtile_res_restrict<EXACT, TC><<<T.grid, kTT, smem, s>>>(L.d, Lc.d, T.u_rr, T.f_rr, fc, tc, status);
+  k_rtile_res_restrict<EXACT, NT, TC><<<T.grid, kTT, smem, s>>>(L.d, Lc.d, T.u_rr, T.f_rr, fc, tc, status);
   return cudaGetLastError();
 }
 }  // namespace
@@ -1486,7 +1539,10 @@ cudaError_t rrr_as(const TileLevel& T, const LevelPair<float>& L, const LevelPai
 cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L, bool exact, float* u, int* status,
                                   cudaStream_t s) {
   if (!T.on || !T.nu1) return cudaErrorInvalidValue;
-  if (T.rot) return exact ? rpresmooth_as<true>(T, L, u, status, s) : rpresmooth_as<false>(T, L, u, status, s);
+  if (T.rot) {
+    if (T.nt == 25) return exact ? rpresmooth_as<true, 25>(T, L, u, status, s) : rpresmooth_as<false, 25>(T, L, u, status, s);
+    return exact ? rpresmooth_as<true, 9>(T, L, u, status, s) : rpresmooth_as<false, 9>(T, L, u, status, s);
+  }
   if (T.nt == 21) {
     if (T.nu1 == 2) return exact ? presmooth_as<true, 21, 2>(T, L, u, status, s) : presmooth_as<false, 21, 2>(T, L, u, status, s);
     return exact ? presmooth_as<true, 21, 1>(T, L, u, status, s) : presmooth_as<false, 21, 1>(T, L, u, status, s);
@@ -1506,7 +1562,11 @@ cudaError_t launch_tile_presmooth(const TileLevel& T, const LevelPair<float>& L,
 cudaError_t launch_tile_sweep(const TileLevel& T, const LevelPair<float>& L, bool exact, bool from_t, float* uout,
                               int* status, cudaStream_t s) {
   if (!T.on) return cudaErrorInvalidValue;
-  if (T.rot) return exact ? rsweep_as<true>(T, L, from_t, uout, status, s) : rsweep_as<false>(T, L, from_t, uout, status, s);
+  if (T.rot) {
+    if (T.nt == 25)
+      return exact ? rsweep_as<true, 25>(T, L, from_t, uout, status, s) : rsweep_as<false, 25>(T, L, from_t, uout, status, s);
+    return exact ? rsweep_as<true, 9>(T, L, from_t, uout, status, s) : rsweep_as<false, 9>(T, L, from_t, uout, status, s);
+  }
   if (T.nt == 21)
     return exact ? sweep_as<true, 21>(T, L, from_t, uout, status, s) : sweep_as<false, 21>(T, L, from_t, uout, status, s);
   if (T.nt == 37)
@@ -1521,8 +1581,12 @@ cudaError_t launch_tile_res_restrict(const TileLevel& T, const LevelPair<float>&
   if (!T.on || Lc.h.bf16) return cudaErrorInvalidValue;
   if (T.rot) {
     if (Lc.h.kind != kAxis) return cudaErrorInvalidValue;
-    if (tc) return exact ? rrr_as<true, true>(T, L, Lc, fc, tc, status, s) : rrr_as<false, true>(T, L, Lc, fc, tc, status, s);
-    return exact ? rrr_as<true, false>(T, L, Lc, fc, tc, status, s) : rrr_as<false, false>(T, L, Lc, fc, tc, status, s);
+    if (T.nt == 25) {
+      if (tc) return exact ? rrr_as<true, 25, true>(T, L, Lc, fc, tc, status, s) : rrr_as<false, 25, true>(T, L, Lc, fc, tc, status, s);
+      return exact ? rrr_as<true, 25, false>(T, L, Lc, fc, tc, status, s) : rrr_as<false, 25, false>(T, L, Lc, fc, tc, status, s);
+    }
+    if (tc) return exact ? rrr_as<true, 9, true>(T, L, Lc, fc, tc, status, s) : rrr_as<false, 9, true>(T, L, Lc, fc, tc, status, s);
+    return exact ? rrr_as<true, 9, false>(T, L, Lc, fc, tc, status, s) : rrr_as<false, 9, false>(T, L, Lc, fc, tc, status, s);
   }
   if (Lc.h.kind != kRot) return cudaErrorInvalidValue;
   if (T.nt == 21) {
