@@ -528,8 +528,9 @@ def run_mixed_large(args):
 
 def run_batched(args):
     """Uneven batch: problems with sides 2^k + 1, k uniform in {7..11}, order 2 or 4
-    (50/50), N(0,1) right-hand sides, mixed precision, each to 1e-8; one
-    level-synchronous batched solve vs the same problems solved one after another."""
+    (50/50), N(0,1) right-hand sides, mixed precision, each to 1e-8; the batched
+    solve (hybrid schedule, and level-synchronous alone) vs the same problems solved
+    one after another (median of three timed solves each)."""
     import numpy as np
     import torch
     import paper_2008_03885_gb300 as mg
@@ -547,23 +548,35 @@ def run_batched(args):
     fs = [rhs[n] for n, _ in specs]
     us = [torch.zeros_like(f) for f in fs]
     setup_s = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    b = mg.mg_batch_create(hs)
-    create_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    mg.mg_batch_solve(b, us, fs, rtol=1e-8, max_cycles=40)  # warm-up (graph capture)
-    torch.cuda.synchronize()
-    for u in us:
-        u.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    l0 = mg.mg_batch_get_launches(b)
-    e0.record(stream)
-    cyc, rr = mg.mg_batch_solve(b, us, fs, rtol=1e-8, max_cycles=40)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    batch_ms = e0.elapsed_time(e1)
-    batch_launches = mg.mg_batch_get_launches(b) - l0
-    b.close()
+
+    def timed(solo_min_n):
+        """Create the batch, warm it up (graph capture), then three timed solves from
+        u = 0: the median time, the launches of one solve and the last cycles/residuals."""
+        t0 = time.perf_counter()
+        b = mg.mg_batch_create(hs, solo_min_n=solo_min_n)
+        create_s = time.perf_counter() - t0
+        mg.mg_batch_solve(b, us, fs, rtol=1e-8, max_cycles=40)
+        times = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            for u in us:
+                u.zero_()
+            l0 = mg.mg_batch_get_launches(b)
+            e0.record(stream)
+            cyc, rr = mg.mg_batch_solve(b, us, fs, rtol=1e-8, max_cycles=40)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            launches = mg.mg_batch_get_launches(b) - l0
+        b.close()
+        return sorted(times)[1], times, launches, cyc, rr, create_s
+
+    # hybrid (library default: N >= 1024 solved alone on 8 worker streams) and the
+    # level-synchronous schedule over every problem
+    batch_ms, batch_times, batch_launches, cyc, rr, create_s = timed(0)
+    sync_ms, sync_times, sync_launches, cyc_s, rr_s, _ = timed(1 << 20)
     # the same problems one after another through mg_solve (graphs warmed first)
     for h, u, f in zip(hs, us, fs):
         u.zero_()
@@ -583,8 +596,13 @@ def run_batched(args):
     return {"problems": count, "sides": "2^k+1, k uniform in {7..11}", "unknowns": points,
             "precision": "mixed FP32 inner / FP64 refinement", "rtol": 1e-8,
             "n_min": N_MIN_SMALL, "coarsest": f"dense solve of {(N_MIN_SMALL - 1) ** 2} unknowns",
-            "batch_ms": batch_ms, "sequential_ms": seq_ms, "speedup": seq_ms / batch_ms,
-            "max_cycles": max(cyc), "max_rel_res": max(rr), "batch_kernel_launches": batch_launches,
+            "schedule": "hybrid: N >= 1024 solved alone on 8 worker streams, the rest level-synchronous",
+            "solo_problems": sum(1 for n, _ in specs if n >= 1024),
+            "batch_ms": batch_ms, "batch_ms_runs": batch_times, "sequential_ms": seq_ms,
+            "speedup": seq_ms / batch_ms, "max_cycles": max(cyc), "max_rel_res": max(rr),
+            "batch_kernel_launches": batch_launches,
+            "level_synchronous_ms": sync_ms, "level_synchronous_ms_runs": sync_times,
+            "level_synchronous_launches": sync_launches, "level_synchronous_max_rel_res": max(rr_s),
             "unknowns_per_s": points / (batch_ms * 1e-3), "setup_s": setup_s, "batch_create_s": create_s}
 
 

@@ -278,11 +278,31 @@ mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const do
    results are bitwise those of mg_solve on each handle alone (same operations per
    node, same order). All handles must share precision, nu1, nu2, fma_contract and
    (mixed precision) inner_cycles; gamma must be 1, the smoother red-black and the
-   boundary Dirichlet (MG_ERR_UNSUPPORTED otherwise). mg_batch_create also autotunes, per level, the rows
+   boundary Dirichlet (MG_ERR_UNSUPPORTED otherwise); a handle may appear only once
+   (MG_ERR_INVALID). mg_batch_create also autotunes, per level, the rows
    per thread of the step kernels by timing them (CUDA events), so create the batch
    once and reuse it. The batch keeps pointers to the handles: destroy the batch
-   before them. */
+   before them.
+
+   Hybrid schedule: problems whose grid side N is at least solo_min_n are not in the
+   level-synchronous schedule. Each is solved by mg_solve on its own handle, on one of
+   `workers` internal non-blocking streams, each driven by a host thread that takes the
+   next unsolved problem, largest first. Meanwhile the calling thread runs the
+   level-synchronous schedule of the other problems. A large problem's own mg_solve
+   runs its single-problem kernels (TMA tiles, fused coarse tail); a small problem's
+   levels leave most SMs idle alone, which the level-synchronous steps fill. The
+   caller's stream waits for all of it. Results stay bitwise those of mg_solve alone.
+   mg_batch_options (opt may be NULL: the defaults):
+     solo_min_n  0: default 1024; a value above 16384 puts every problem in the
+                 level-synchronous schedule; negative: MG_ERR_INVALID.
+     workers     0: default 8 (at most the number of solo problems); 1..64. */
 typedef struct mg_batch mg_batch;
+typedef struct {
+  int solo_min_n;
+  int workers;
+} mg_batch_options;
+mg_status mg_batch_create_ex(mg_handle* const* handles, int count, const mg_batch_options* opt, mg_batch** out);
+/* mg_batch_create_ex with the default options. */
 mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out);
 /* Solve problem p: u[p], f[p] device arrays of handle p's finest level. Per problem:
    cycles (refinement steps for mixed precision) in cycles_out[p] and the final
@@ -291,7 +311,8 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out);
 mg_status mg_batch_solve(mg_batch* b, double* const* u, const double* const* f, double rtol, int max_cycles,
                          int* cycles_out, double* rel_res_out, void* stream);
 mg_status mg_batch_destroy(mg_batch* b);
-/* Kernels launched through the batch so far (graph launches count their kernels). */
+/* Kernels launched through the batch so far, solo solves included (graph launches
+   count their kernels). */
 mg_status mg_batch_get_launches(const mg_batch* b, int64_t* launches);
 /* Convenience: create a batch, solve once, destroy it. */
 mg_status mg_solve_batched(mg_handle* const* handles, double* const* u, const double* const* f, int count,

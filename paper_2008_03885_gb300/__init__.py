@@ -357,24 +357,34 @@ def mg_rel_residual_static(h: Handle, u, f, rel_res_dev, stream=None):
 
 # ---- batched solves ---------------------------------------------------------
 _lib.mg_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]
+
+
+class mg_batch_options(ctypes.Structure):
+    _fields_ = [("solo_min_n", ctypes.c_int), ("workers", ctypes.c_int)]
+
+
+_lib.mg_batch_create_ex.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(mg_batch_options),
+                                    ctypes.POINTER(_vp)]
 _lib.mg_batch_solve.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_double, ctypes.c_int,
                                 _ip, _dp, _vp]
 _lib.mg_batch_destroy.argtypes = [_vp]
 _lib.mg_batch_get_launches.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
 _lib.mg_solve_batched.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int,
                                   ctypes.c_double, ctypes.c_int, _ip, _dp, _vp]
-for _name in ("mg_batch_create", "mg_batch_solve", "mg_batch_destroy", "mg_batch_get_launches", "mg_solve_batched"):
+for _name in ("mg_batch_create", "mg_batch_create_ex", "mg_batch_solve", "mg_batch_destroy", "mg_batch_get_launches", "mg_solve_batched"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
 class Batch:
     """Owns an mg_batch over a list of Handles (which must outlive it)."""
 
-    def __init__(self, handles):
+    def __init__(self, handles, solo_min_n: int = 0, workers: int = 0):
         self.handles = list(handles)
         arr = (_vp * len(self.handles))(*[h.ptr for h in self.handles])
         out = _vp()
-        _check(_lib.mg_batch_create(arr, len(self.handles), ctypes.byref(out)), "mg_batch_create")
+        o = mg_batch_options(solo_min_n, workers)
+        _check(_lib.mg_batch_create_ex(arr, len(self.handles), ctypes.byref(o), ctypes.byref(out)),
+               "mg_batch_create_ex")
         self.ptr = out.value
 
     def close(self):
@@ -389,8 +399,10 @@ class Batch:
             pass
 
 
-def mg_batch_create(handles) -> Batch:
-    return Batch(handles)
+def mg_batch_create(handles, solo_min_n: int = 0, workers: int = 0) -> Batch:
+    """solo_min_n / workers: the hybrid schedule's options (0: the library defaults,
+    solo_min_n above 16384: level-synchronous only)."""
+    return Batch(handles, solo_min_n, workers)
 
 
 def mg_batch_solve(b: Batch, us, fs, rtol: float = 1e-8, max_cycles: int = 50, stream=None,

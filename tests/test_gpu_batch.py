@@ -114,3 +114,72 @@ def test_batch_launch_count_is_per_level_not_per_problem():
         b.close()
         for h in hs:
             h.close()
+
+
+@pytest.mark.parametrize("solo_min_n,workers", [(64, 3), (8, 2), (128, 1)])
+@pytest.mark.parametrize("opts", [dict(), dict(precision=mg.MG_PREC_MIXED_FP32, fma_contract=1)])
+def test_hybrid_batch_matches_individual_solves_bitwise(opts, solo_min_n, workers):
+    """The hybrid schedule: problems with N >= solo_min_n solved alone on worker streams
+    (all of them at 8), the rest level-synchronously, concurrently; every result is
+    bitwise that of mg_solve alone, reported in the caller's problem order."""
+    rtol = 1e-10
+    ref = solo(PROBLEMS, rtol, **opts)
+    hs, us, fs = make(PROBLEMS, **opts)
+    b = mg.mg_batch_create(hs, solo_min_n=solo_min_n, workers=workers)
+    try:
+        for rep in range(2):
+            for u in us:
+                u.zero_()
+            before = mg.mg_batch_get_launches(b)
+            cyc, rr = mg.mg_batch_solve(b, us, fs, rtol=rtol, max_cycles=40)
+            torch.cuda.synchronize()
+            assert mg.mg_batch_get_launches(b) - before >= sum(cyc)
+            for p, (k, r, u_ref) in enumerate(ref):
+                assert cyc[p] == k, (p, cyc[p], k)
+                assert abs(rr[p] - r) <= 1e-12 * r
+                assert np.array_equal(us[p].cpu().numpy(), u_ref), p
+    finally:
+        b.close()
+        for h in hs:
+            h.close()
+
+
+def test_hybrid_batch_on_a_side_stream_and_not_converged_status():
+    """The caller's stream waits for the worker streams; a missed tolerance in either
+    part comes back as MG_ERR_NOT_CONVERGED with every problem's count and residual."""
+    problems = [(128, 2, "redblack", "galerkin"), (32, 4, "redblack", "galerkin"), (256, 4, "redblack", "galerkin")]
+    hs, us, fs = make(problems)
+    b = mg.mg_batch_create(hs, solo_min_n=128, workers=2)
+    side = torch.cuda.Stream()
+    try:
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            cyc, rr = mg.mg_batch_solve(b, us, fs, rtol=1e-14, max_cycles=2, stream=side,
+                                        raise_not_converged=False)
+            norms = [torch.linalg.vector_norm(u).item() for u in us]  # ordered after the solve on `side`
+        assert cyc == [2, 2, 2] and all(1e-14 < r < 1 for r in rr) and all(x > 0 for x in norms)
+        for u in us:
+            u.zero_()
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_batch_solve(b, us, fs, rtol=1e-14, max_cycles=2)
+        assert e.value.status == mg.MG_ERR_NOT_CONVERGED
+    finally:
+        b.close()
+        for h in hs:
+            h.close()
+
+
+def test_batch_rejects_a_repeated_handle_and_bad_options():
+    h1 = mg.mg_setup(32, 2)
+    h2 = mg.mg_setup(32, 2)
+    try:
+        with pytest.raises(mg.MGError) as e:
+            mg.mg_batch_create([h1, h2, h1])
+        assert e.value.status == mg.MG_ERR_INVALID
+        for kw in (dict(solo_min_n=-1), dict(workers=-2), dict(workers=65)):
+            with pytest.raises(mg.MGError) as e:
+                mg.mg_batch_create([h1, h2], **kw)
+            assert e.value.status == mg.MG_ERR_INVALID
+    finally:
+        h1.close()
+        h2.close()
