@@ -573,7 +573,7 @@ def run_batched(args):
         b.close()
         return sorted(times)[1], times, launches, cyc, rr, create_s
 
-    # hybrid (library default: N >= 1024 solved alone on 8 worker streams) and the
+    # hybrid (library default: N >= 1024 solved alone on 12 worker streams) and the
     # level-synchronous schedule over every problem
     batch_ms, batch_times, batch_launches, cyc, rr, create_s = timed(0)
     sync_ms, sync_times, sync_launches, cyc_s, rr_s, _ = timed(1 << 20)
@@ -596,7 +596,7 @@ def run_batched(args):
     return {"problems": count, "sides": "2^k+1, k uniform in {7..11}", "unknowns": points,
             "precision": "mixed FP32 inner / FP64 refinement", "rtol": 1e-8,
             "n_min": N_MIN_SMALL, "coarsest": f"dense solve of {(N_MIN_SMALL - 1) ** 2} unknowns",
-            "schedule": "hybrid: N >= 1024 solved alone on 8 worker streams, the rest level-synchronous",
+            "schedule": "hybrid: N >= 1024 solved alone on 12 worker streams, the rest level-synchronous",
             "solo_problems": sum(1 for n, _ in specs if n >= 1024),
             "batch_ms": batch_ms, "batch_ms_runs": batch_times, "sequential_ms": seq_ms,
             "speedup": seq_ms / batch_ms, "max_cycles": max(cyc), "max_rel_res": max(rr),
@@ -667,18 +667,23 @@ def run_profile_case(args):
 
 def run_profile_solves(args, mixed: bool):
     """Two solves of the bench workload (warm-up + one), for ncu: mixed precision
-    (FP32 inner cycles) or the FP64 headline solve."""
+    (FP32 inner cycles) or the FP64 headline solve. With --profile-batch-problem, three
+    solves of one problem of the batch (N(0,1) right-hand side, n_min 16, to 1e-8)."""
     import torch
     import paper_2008_03885_gb300 as mg
     import synth
     n = args.profile_n
-    f = torch.tensor(synth.rhs_sine_modes(n, SEED), dtype=torch.float64, device="cuda")
+    batch = args.profile_batch_problem  # a problem of the batch: N(0,1), n_min 16, 1e-8
+    rhs = synth.rhs_normal(n, 5) if batch else synth.rhs_sine_modes(n, SEED)
+    f = torch.tensor(rhs, dtype=torch.float64, device="cuda")
     u = torch.zeros_like(f)
     extra = dict(precision=mg.MG_PREC_MIXED_FP32, inner_cycles=1, fma_contract=1) if mixed else {}
+    if batch:
+        extra["n_min"] = N_MIN_SMALL
     h = mg.mg_setup(n, ORDER, "redblack", "galerkin", nu1=NU1, nu2=NU2, **extra)
-    for _ in range(2):
+    for _ in range(3 if batch else 2):
         u.zero_()
-        k, hist = mg.mg_solve(h, u, f, rtol=RTOL, max_cycles=60)
+        k, hist = mg.mg_solve(h, u, f, rtol=1e-8 if batch else RTOL, max_cycles=60)
     torch.cuda.synchronize()
     h.close()
     print(json.dumps({"profile_mixed" if mixed else "profile_fp64": n, "cycles": k, "final": hist[-1]}))
@@ -725,6 +730,8 @@ def main():
     ap.add_argument("--serve-count", type=int, default=20000)
     ap.add_argument("--serve-plain-every", type=int, default=10)
     ap.add_argument("--profile-n", type=int, default=4096)
+    ap.add_argument("--profile-batch-problem", action="store_true",
+                    help="profile solves: the batch's settings (N(0,1) right-hand side, n_min 16, 1e-8; three solves)")
     ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")
     ap.add_argument("--profile-fp64", action="store_true", help="two FP64 solves of the bench workload (ncu)")
     args = ap.parse_args()

@@ -295,7 +295,7 @@ mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const do
    mg_batch_options (opt may be NULL: the defaults):
      solo_min_n  0: default 1024; a value above 16384 puts every problem in the
                  level-synchronous schedule; negative: MG_ERR_INVALID.
-     workers     0: default 8 (at most the number of solo problems); 1..64. */
+     workers     0: default 12 (at most the number of solo problems); 1..64. */
 typedef struct mg_batch mg_batch;
 typedef struct {
   int solo_min_n;

@@ -2227,10 +2227,11 @@ mg_status sync_solve(mg_batch* b, double* const* u, const double* const* f, doub
 
 // Problems at least this large (grid side N) are solved alone by default, on this many
 // worker streams. Measured on 512 mixed-precision problems of sides 128..2048 (orders
-// 2 and 4, n_min 16, rtol 1e-8): 312 ms with (1024, 8) against 546 ms for the
-// level-synchronous schedule alone, 323 ms with (512, 8), 370 ms with (1024, 4).
+// 2 and 4, n_min 16, rtol 1e-8) against 546 ms for the level-synchronous schedule
+// alone: (1024, 4) 370 ms, (1024, 8) 310-313, (1024, 12) 306-310, (1024, 16) 305-308,
+// (512, 12) 318-320, (2048, 12) 338-340.
 constexpr int kSoloMinN = 1024;
-constexpr int kSoloWorkers = 8;
+constexpr int kSoloWorkers = 12;
 
 int status_rank(mg_status s) { return s == MG_OK ? 0 : s == MG_ERR_NOT_CONVERGED ? 1 : 2; }
 

@@ -866,12 +866,27 @@ __global__ void k_coarsest(int64_t idx, T a, int zero_mean, const T* __restrict_
 template <typename T, bool EXACT, class IDX, class SYNC>
 __device__ __forceinline__ bool dense_coarse(const DenseCoarse<T>& C, const LevelDev<T>& L, const T* F, T* Y,
                                              T* U, IDX idx, int tid, int nth, SYNC sync) {
+  // The loads of kDU consecutive terms are issued before their products are summed
+  // (in the same k-ascending order), so each row pays one load latency per kDU terms.
+  constexpr int kDU = 8;
   const int m = C.m;
   const int2 q0 = C.ij[0];
   const T f0 = F[idx(L, q0.x, q0.y)];
   for (int i = tid; i < m; i += nth) {
     T s = Arith<T>::mul(C.ga[i], f0);
-    for (int k = 1; k <= i; ++k) {
+    int k = 1;
+    for (; k + kDU - 1 <= i; k += kDU) {
+      T g[kDU], x[kDU];
+#pragma unroll
+      for (int r = 0; r < kDU; ++r) {
+        const int2 q = C.ij[k + r];
+        g[r] = C.ga[(int64_t)(k + r) * m + i];
+        x[r] = F[idx(L, q.x, q.y)];
+      }
+#pragma unroll
+      for (int r = 0; r < kDU; ++r) s = EXACT ? Arith<T>::add(s, Arith<T>::mul(g[r], x[r])) : Arith<T>::fma(g[r], x[r], s);
+    }
+    for (; k <= i; ++k) {
       const int2 q = C.ij[k];
       const T g = C.ga[(int64_t)k * m + i];
       const T x = F[idx(L, q.x, q.y)];
@@ -884,7 +899,19 @@ __device__ __forceinline__ bool dense_coarse(const DenseCoarse<T>& C, const Leve
   for (int i = tid; i < m; i += nth) {
     const int2 p = C.ij[i];
     T s = Arith<T>::mul(C.gb[(int64_t)i * m + i], Y[idx(L, p.x, p.y)]);
-    for (int k = i + 1; k < m; ++k) {
+    int k = i + 1;
+    for (; k + kDU - 1 < m; k += kDU) {
+      T g[kDU], x[kDU];
+#pragma unroll
+      for (int r = 0; r < kDU; ++r) {
+        const int2 q = C.ij[k + r];
+        g[r] = C.gb[(int64_t)(k + r) * m + i];
+        x[r] = Y[idx(L, q.x, q.y)];
+      }
+#pragma unroll
+      for (int r = 0; r < kDU; ++r) s = EXACT ? Arith<T>::add(s, Arith<T>::mul(g[r], x[r])) : Arith<T>::fma(g[r], x[r], s);
+    }
+    for (; k < m; ++k) {
       const int2 q = C.ij[k];
       const T g = C.gb[(int64_t)k * m + i];
       const T x = Y[idx(L, q.x, q.y)];
