@@ -1338,11 +1338,15 @@ mg_status build_tail(mg_handle* h, int64_t max_unknowns, int64_t smem_elems = 0)
 // latency on 16 SMs only wins for the last few levels (measured on GB300).
 constexpr int64_t kTailUnknownsFp64 = 256;
 // FP32 inner hierarchies by default keep their small levels in one block's shared
-// memory (up to 12K elements = 48 KB for u, t, f and d of every tail level). A larger
-// tail leaves too little L1 for the boundary-class term records the small levels read
-// (measured on GB300, 4097^2 mixed solve: 48K elements 19.4 ms, 24K 19.0, 12K 19.0,
-// 6K 19.2; 129^2: 2.79, 2.60, 2.54, 2.70 ms).
-constexpr int64_t kTailSmemElemsFp32 = 12 * 1024;
+// memory (up to 6K elements = 24 KB for u, t, f and d of every tail level). Measured on
+// GB300, mixed solves (order 4, N(0,1) right-hand side; budget 4K / 6K / 8K / 12K / 16K /
+// 24K elements): 257^2 n_min 16 to 1e-8 1.75 / 1.75 / 1.78 / 1.78 / 1.95 / 1.94 ms;
+// 257^2 n_min 2 2.27 / 2.15 / 2.16 / 2.20 / 2.20 / 2.39; 2049^2 n_min 16 4.97 at 4K-12K,
+// 5.15-5.16 above; 4097^2 n_min 16 to 1e-10 11.38-11.43 at 4K-12K, 11.64-11.65 above.
+// A larger tail runs more levels on one SM, and their boundary-class term records no
+// longer fit the L1 left beside the shared memory; no tail at all is slower still
+// (257^2 n_min 2: 2.71 ms).
+constexpr int64_t kTailSmemElemsFp32 = 6 * 1024;
 // FP64 hierarchies by default use a shared-memory tail too, of 3K elements (24 KB);
 // measured on GB300 (FP64 solve, 4097^2 / 513^2 / 129^2): cluster tail 65.8 / 8.45 /
 // 5.55 ms, 3K 65.0 / 7.64 / 4.77, 6K 65.4 / 8.10 / 5.25, 12K 66.6 / 9.42 / 6.33.
