@@ -29,6 +29,13 @@ int main(void) {
   if (mg_workspace_bytes(&bad, 4, MG_COARSEN_REDBLACK, MG_OP_GALERKIN, &o) != 0) return 13;
   mg_handle* h = NULL;
   if (mg_setup(&bad, 4, MG_COARSEN_REDBLACK, MG_OP_GALERKIN, &o, &h) != MG_ERR_INVALID || h) return 14;
+  mg_batch_options bo = {0, 0};
+  mg_batch* b = NULL;
+  if (mg_batch_create_ex(NULL, 1, &bo, &b) != MG_ERR_INVALID || b) return 15;
+  mg_handle* none[1] = {NULL};
+  bo.workers = 65;  /* above the 64 worker streams allowed */
+  if (mg_batch_create_ex(none, 1, &bo, &b) != MG_ERR_INVALID || b) return 16;
+  if (mg_batch_destroy(NULL) != MG_OK) return 17;
   printf("%zu %zu\n", fp64, mixed);
   return 0;
 }
