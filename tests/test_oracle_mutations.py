@@ -2,13 +2,15 @@
 
 Each case plants one mistake in the oracle (on the CPU, through monkeypatch: a
 dropped stencil term, a wrong sign, a wrong transfer weight, a swapped colour order,
-a wrong residual sign, a wrong coarsest solve, a wrong relaxation scaling, ghosts
+a wrong residual sign, a wrong coarsest solve, a wrong relaxation scaling, a Jacobi step
+without its omega, a W cycle visiting its coarse level once, ghosts
 without the odd-reflection sign; for periodic grids a coarsest solution off zero mean or a
 missing wrap-around; for cubic transfers bilinear or wrong taps) and runs a battery of the
 pins of `test_oracle.py`, `test_oracle_periodic.py` or `test_oracle_cubic.py`
 (printed stencils, the paper's symbols, printed Galerkin operators and transfers, the
 two-level direct-solver theorem, the Schur-complement identity, printed rates and LFA
-rates, agreement with a direct solve). At least one pin must fail for every mistake,
+rates, the exact Fourier spectral radius of the Jacobi two-grid cycle, the cycle's
+operator against the error-propagation recursion, agreement with a direct solve). At least one pin must fail for every mistake,
 and none without one.
 """
 import numpy as np
@@ -30,6 +32,9 @@ BATTERY = [
     ("Schur complement", pins.test_red_black_reduction_schur_complement_is_twice_galerkin),
     ("three-level printed rates", pins.test_three_level_rbc_printed_rates),
     ("LFA two-level rate", lambda: pins.test_two_level_rbc_nongalerkin_rate_matches_lfa(1.0)),
+    ("Jacobi two-grid RFA", lambda: pins.test_jacobi_two_grid_spectral_radius_equals_rfa(0.8, 1, 1)),
+    ("cycle operator recursion",
+     lambda: pins.test_cycle_operator_equals_error_propagation_recursion(omg.REDBLACK, 2, 0.97, 1, 1)),
     ("converged = direct solve", pins.test_converged_multilevel_solution_equals_direct_solve),
     ("closed-form sine solution", pins.test_converged_solution_equals_closed_form_for_sine_rhs),
 ]
@@ -131,6 +136,21 @@ def jacobi_scaling(monkeypatch):
     monkeypatch.setattr(omg.Oracle, "half_sweep", bad)
 
 
+def jacobi_without_omega(monkeypatch):
+    def bad(self, l, u, f):
+        if self.opt.smoother != "jacobi":
+            return orig(self, l, u, f)
+        r = f - self._Au(l, u)
+        return u + r * self.wd[l] / self.opt.omega  # 1 / a_pp: omega forgotten
+
+    orig = omg.Oracle.smooth
+    monkeypatch.setattr(omg.Oracle, "smooth", bad)
+
+
+def gamma_ignored(monkeypatch):
+    monkeypatch.setattr(omg.Oracle, "gamma_at", lambda self, l: 1)  # W and Wn run as V
+
+
 def coarsest_diagonal(monkeypatch):
     def bad(self, d):
         return d / np.diag(self._coarse_dense)
@@ -212,6 +232,8 @@ MUTATIONS = {
     "residual sign in the smoother": residual_sign,
     "relaxation scaled by 1/2": jacobi_scaling,
     "coarsest solve by the diagonal": coarsest_diagonal,
+    "Jacobi step without omega": jacobi_without_omega,
+    "W cycle visits the coarse level once": gamma_ignored,
     "restriction without its 1/2, 1/4 factor": restriction_transposed_weight,
 }
 
