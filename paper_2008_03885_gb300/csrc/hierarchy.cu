@@ -2253,7 +2253,13 @@ mg_status hybrid_solve(mg_batch* b, double* const* u, const double* const* f, do
   std::vector<int64_t> launched(nw, 0);
   std::atomic<int> next{0};
   auto work = [&](int t) {
-    std::vector<double> hist(max_cycles + 1);
+    std::vector<double> hist;
+    try {
+      hist.resize(max_cycles + 1);
+    } catch (...) {  // no memory for the history: this thread's problems report MG_ERR_OOM
+      for (int i; (i = next.fetch_add(1)) < ns;) st[i] = MG_ERR_OOM;
+      return;
+    }
     for (int i; (i = next.fetch_add(1)) < ns;) {
       const int p = b->solo[i];
       mg_handle* h = b->hs[p];
