@@ -1341,7 +1341,7 @@ constexpr int64_t kTailUnknownsFp64 = 256;
 // memory (up to 6K elements = 24 KB for u, t, f and d of every tail level). Measured on
 // GB300, mixed solves (order 4, N(0,1) right-hand side; budget 4K / 6K / 8K / 12K / 16K /
 // 24K elements): 257^2 n_min 16 to 1e-8 1.75 / 1.75 / 1.78 / 1.78 / 1.95 / 1.94 ms;
-// 257^2 n_min 2 2.27 / 2.15 / 2.16 / 2.20 / 2.20 / 2.39; 2049^2 n_min 16 4.97 at 4K-12K,
+// 257^2 n_min 2 2.27 / 2.15 / 2.16 / 2.20 / 2.20 / 2.39; 2049^2 n_min 16 4.97-5.03 at 4K-12K,
 // 5.15-5.16 above; 4097^2 n_min 16 to 1e-10 11.38-11.43 at 4K-12K, 11.64-11.65 above.
 // A larger tail runs more levels on one SM, and their boundary-class term records no
 // longer fit the L1 left beside the shared memory; no tail at all is slower still
