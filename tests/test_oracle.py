@@ -220,6 +220,52 @@ def _asymptotic_cr(o, seed=5, cycles=12):
     return rates[-1]
 
 
+def _rfa_two_level_rbc_spectrum(n, omega, nu1, nu2, coarse):
+    """Every eigenvalue of the Dirichlet two-level red-black-coarsening cycle for the
+    5-point operator (Sec. 4.3), by rigorous Fourier analysis. The sine modes m1 = (k, l)
+    and m2 = (n-k, n-l) agree on one colour and differ in sign on the other. So
+    Rd = m1 on the red nodes and B = m1 on the black (coarse) nodes span a space that
+    every step keeps. With mu = (cos t1 + cos t2) / 2, a red half-sweep maps
+    (x, y) -> ((1 - omega) x + omega mu y, y), and a black one the mirror image.
+    Interpolation gives P b = B + mu Rd, and R = P^T / 2 gives R Rd = mu b / 2,
+    R B = b / 2. The coarse operator is R A P = 2 (1 - mu^2) / h^2 (Galerkin) or the
+    rotated 5-point operator 2 (1 - cos t1 cos t2) / h^2 (non-Galerkin). The
+    coarse-grid correction is then (x, y) -> (x - kappa mu y, (1 - kappa) y), where
+    kappa is the ratio of the two (1 for Galerkin). The mode k = l = n/2 lives on the
+    black nodes alone (x = 0)."""
+    pi = np.pi
+    out = []
+    for k in range(1, n):
+        for l in range(1, n):
+            if (k, l) > (n - k, n - l):
+                continue  # each pair once
+            c1, c2 = np.cos(k * pi / n), np.cos(l * pi / n)
+            mu = (c1 + c2) / 2
+            S = np.array([[1, 0], [omega * mu, 1 - omega]]) @ np.array([[1 - omega, omega * mu], [0, 1]])
+            kap = 1.0 if coarse == GALERKIN else (1 - mu * mu) / (1 - c1 * c2)
+            C = np.array([[1, -kap * mu], [0, 1 - kap]])
+            M = np.linalg.matrix_power(S, nu2) @ C @ np.linalg.matrix_power(S, nu1)
+            if (k, l) == (n - k, n - l):
+                M = M[1:, 1:]
+            out.extend(np.linalg.eigvals(M))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("coarse,omega,nu1,nu2", [(NONGALERKIN, 0.9, 1, 1), (NONGALERKIN, 1.0, 2, 1),
+                                                  (GALERKIN, 1.1, 1, 1), (GALERKIN, 0.8, 1, 0)])
+def test_two_level_rbc_spectrum_equals_rfa(coarse, omega, nu1, nu2):
+    """The whole spectrum of the oracle's two-level RBC cycle (the cycle applied to every
+    unit vector with f = 0) equals the rigorous Fourier analysis mode by mode: sorted
+    moduli and sorted real parts agree to 1e-12. The Fourier analysis is the exact,
+    finite-grid form of the LFA of Sec. 4.3."""
+    n = 16
+    o = Oracle(n, 2, REDBLACK, coarse, Options(omega=omega, nu1=nu1, nu2=nu2, max_levels=2))
+    ev = _cycle_spectrum(o)
+    ref = _rfa_two_level_rbc_spectrum(n, omega, nu1, nu2, coarse)
+    assert ev.size == ref.size == (n - 1) ** 2
+    assert _same_spectrum(ev, ref)
+
+
 @pytest.mark.parametrize("omega", [0.9, 1.0, 1.1])
 def test_two_level_rbc_nongalerkin_rate_matches_lfa(omega):
     """Measured asymptotic CR of the two-level RBC nG cycle vs the LFA of Sec. 4.3."""
@@ -252,28 +298,29 @@ def test_jacobi_smoother_two_level_rate_near_smoothing_factor():
 
 
 def _rfa_two_grid_jacobi_standard(n, omega, nu1, nu2):
-    """Rigorous Fourier analysis of the Dirichlet two-grid cycle with omega-Jacobi
-    (Sec. 5.3), standard coarsening, full weighting, bilinear interpolation (Eq.
-    transfer_2d) and the Galerkin coarse operator, for the 5-point operator. The sine
-    modes sin(k pi x) sin(l pi y) are eigenvectors of the operator and of the Jacobi step
-    (factor 1 - omega (sin^2(t1/2) + sin^2(t2/2)), t = k pi / n). Full weighting maps
-    the four harmonics (k, l), (n-k, l), (k, n-l), (n-k, n-l) onto one coarse sine mode
-    with 1D factors (1 + cos t) / 2 and -(1 - cos t) / 2, and bilinear interpolation
-    maps it back into their span with the same factors. So the cycle is block diagonal
-    with 4 x 4 blocks, plus smoothing-only 1 x 1 blocks for k or l = n/2, which vanish
-    on the coarse grid. The largest block spectral radius is the cycle's own: an exact
-    value, worked out here without the oracle's matrices."""
+    """Every eigenvalue of the Dirichlet two-grid cycle with omega-Jacobi (Sec. 5.3),
+    standard coarsening, full weighting, bilinear interpolation (Eq. transfer_2d) and the
+    Galerkin coarse operator, for the 5-point operator, by rigorous Fourier analysis.
+    The sine modes sin(k pi x) sin(l pi y) are eigenvectors of the operator and of the
+    Jacobi step (factor 1 - omega (sin^2(t1/2) + sin^2(t2/2)), t = k pi / n). Full
+    weighting maps the four harmonics (k, l), (n-k, l), (k, n-l), (n-k, n-l) onto one
+    coarse sine mode with 1D factors (1 + cos t) / 2 and -(1 - cos t) / 2, and bilinear
+    interpolation maps it back into their span with the same factors. So the cycle is
+    block diagonal with 4 x 4 blocks, plus smoothing-only 1 x 1 blocks for k or l = n/2,
+    which vanish on the coarse grid. Worked out here without the oracle's matrices."""
     pi = np.pi
 
     def s(a, b):
         return 1.0 - omega * (np.sin(a / 2) ** 2 + np.sin(b / 2) ** 2)
 
-    best = 0.0
-    for k in range(1, n):
-        t = k * pi / n
-        best = max(best, abs(s(t, pi / 2)) ** (nu1 + nu2), abs(s(pi / 2, t)) ** (nu1 + nu2))
-    for k in range(1, n // 2):
-        for l in range(1, n // 2):
+    out = []
+    h = n // 2
+    for k in range(1, n):  # modes (k, n/2) and (n/2, l), (n/2, n/2) once
+        out.append(s(k * pi / n, pi / 2) ** (nu1 + nu2))
+        if k != h:
+            out.append(s(pi / 2, k * pi / n) ** (nu1 + nu2))
+    for k in range(1, h):
+        for l in range(1, h):
             t1, t2 = k * pi / n, l * pi / n
             T1 = np.array([t1, pi - t1, t1, pi - t1])
             T2 = np.array([t2, t2, pi - t2, pi - t2])
@@ -284,25 +331,35 @@ def _rfa_two_grid_jacobi_standard(n, omega, nu1, nu2):
             S = np.diag(s(T1, T2))
             K = np.eye(4) - np.outer(r, r * lh) / (r @ (lh * r))  # I - P L_H^-1 R L_h
             M = np.linalg.matrix_power(S, nu2) @ K @ np.linalg.matrix_power(S, nu1)
-            best = max(best, float(np.max(np.abs(np.linalg.eigvals(M)))))
-    return best
+            out.extend(np.linalg.eigvals(M))
+    return np.array(out)
+
+
+def _cycle_spectrum(o):
+    """Eigenvalues of the oracle's cycle as an operator on the error (f = 0), from its
+    action on every unit vector."""
+    m = o.levels[0].size
+    zero = np.zeros(m)
+    return np.linalg.eigvals(np.column_stack([o.cycle(np.eye(m)[:, j].copy(), zero) for j in range(m)]))
+
+
+def _same_spectrum(ev, ref, tol=1e-12):
+    return (ev.size == ref.size and np.max(np.abs(np.sort(np.abs(ev)) - np.sort(np.abs(ref)))) <= tol
+            and np.max(np.abs(np.sort(ev.real) - np.sort(ref.real))) <= tol)
 
 
 @pytest.mark.parametrize("omega,nu1,nu2", [(0.8, 1, 1), (0.6, 1, 1), (0.8, 2, 1), (1.0, 2, 0)])
-def test_jacobi_two_grid_spectral_radius_equals_rfa(omega, nu1, nu2):
-    """The spectral radius of the oracle's two-level cycle (omega-Jacobi, standard
-    coarsening, Galerkin; the error propagation u -> cycle(u, f = 0), largest
-    eigenvalues by ARPACK) equals the exact Fourier value to rounding. omega = 0.8 is
-    omega* of Sec. 5.3 for factor-2 coarsening."""
-    from scipy.sparse.linalg import LinearOperator, eigs
+def test_jacobi_two_grid_spectrum_equals_rfa(omega, nu1, nu2):
+    """The whole spectrum of the oracle's two-level cycle (omega-Jacobi, standard
+    coarsening, Galerkin) equals the Fourier analysis mode by mode (sorted moduli and
+    real parts to 1e-12); so does its spectral radius. omega = 0.8 is omega* of
+    Sec. 5.3 for factor-2 coarsening."""
     n = 16
     o = Oracle(n, 2, STANDARD, GALERKIN, Options(omega=omega, smoother="jacobi", max_levels=2, nu1=nu1, nu2=nu2))
-    m = o.levels[0].size
-    zero = np.zeros(m)
-    op = LinearOperator((m, m), matvec=lambda e: o.cycle(np.asarray(e, dtype=float).ravel(), zero), dtype=float)
-    vals = eigs(op, k=4, which="LM", return_eigenvectors=False, tol=1e-13, maxiter=5000)
-    rho = _rfa_two_grid_jacobi_standard(n, omega, nu1, nu2)
-    assert abs(float(np.max(np.abs(vals))) - rho) <= 1e-10 * rho, (np.max(np.abs(vals)), rho)
+    ev = _cycle_spectrum(o)
+    ref = _rfa_two_grid_jacobi_standard(n, omega, nu1, nu2)
+    assert ev.size == ref.size == (n - 1) ** 2
+    assert _same_spectrum(ev, ref)
 
 
 def _cycle_matrix(o, l):

@@ -32,7 +32,8 @@ BATTERY = [
     ("Schur complement", pins.test_red_black_reduction_schur_complement_is_twice_galerkin),
     ("three-level printed rates", pins.test_three_level_rbc_printed_rates),
     ("LFA two-level rate", lambda: pins.test_two_level_rbc_nongalerkin_rate_matches_lfa(1.0)),
-    ("Jacobi two-grid RFA", lambda: pins.test_jacobi_two_grid_spectral_radius_equals_rfa(0.8, 1, 1)),
+    ("Jacobi two-grid RFA", lambda: pins.test_jacobi_two_grid_spectrum_equals_rfa(0.8, 1, 1)),
+    ("RBC two-level RFA", lambda: pins.test_two_level_rbc_spectrum_equals_rfa(omg.NONGALERKIN, 0.9, 1, 1)),
     ("cycle operator recursion",
      lambda: pins.test_cycle_operator_equals_error_propagation_recursion(omg.REDBLACK, 2, 0.97, 1, 1)),
     ("converged = direct solve", pins.test_converged_multilevel_solution_equals_direct_solve),
