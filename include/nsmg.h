@@ -270,6 +270,7 @@ mg_status mg_level_prolong_add(mg_handle* h, int level, double* u_fine, const do
                                void* stream);
 
 /* ---- batched solves (many independent problems) -------------------------------
+   Algorithm "MG" (Sec. 2.2) run on many grids at once; the paper has no batched form.
    A batch advances many handles together by a level-synchronous schedule: each step
    of the V-cycle (a half-sweep, residual, restriction, interpolation, ... of level l)
    is ONE kernel launch covering level l of every problem that has it, with blocks
@@ -307,7 +308,11 @@ mg_status mg_batch_create(mg_handle* const* handles, int count, mg_batch** out);
 /* Solve problem p: u[p], f[p] device arrays of handle p's finest level. Per problem:
    cycles (refinement steps for mixed precision) in cycles_out[p] and the final
    relative residual in rel_res_out[p] (either may be NULL). Returns
-   MG_ERR_NOT_CONVERGED if any problem missed rtol within max_cycles. */
+   MG_ERR_NOT_CONVERGED if any problem missed rtol within max_cycles. With solo
+   problems, the call starts up to `workers` host threads and joins them before it
+   returns; the first error wins (the level-synchronous part's, then the solo problems'
+   in index order). After an error other than MG_ERR_NOT_CONVERGED the outputs of the
+   failed problems carry no meaning. One call at a time per batch. */
 mg_status mg_batch_solve(mg_batch* b, double* const* u, const double* const* f, double rtol, int max_cycles,
                          int* cycles_out, double* rel_res_out, void* stream);
 mg_status mg_batch_destroy(mg_batch* b);
