@@ -50,7 +50,61 @@ N_MIN_SMALL = 16
 # beside it. Flops per updated node of a half-sweep: 2 s for the stencil application of
 # s terms plus 3 (f - L u, the multiply by omega / a_pp, the add to u): 21 for s = 9.
 FP64_PEAK_TFLOPS = 1.25
-FP64_DFMA_MEASURED_TFLOPS = 1.1998
+FP64_DFMA_MEASURED_TFLOPS = 1.1998  # python bench.py --fp-pipe-probe (DFMA line x 2 flops)
+
+# Issue-rate probe behind FP64_DFMA_MEASURED_TFLOPS: per thread, 8 independent chains of
+# one instruction kind (no memory traffic); one warm-up launch, then the mean of 5
+# launches timed with CUDA events.
+FP_PIPE_PROBE_CU = r"""// Floating-point pipe throughput probe for the ALU roofline of the FP64 kernels:
+// independent FMA / add / multiply chains per thread, no memory traffic.
+#include <cstdio>
+#include <cuda_runtime.h>
+template <int OP, typename T>
+__global__ void k(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) x[c] = (T)(threadIdx.x + c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (OP == 0) x[c] = fma(x[c], a, b);
+      else if (OP == 1) x[c] = x[c] + b;
+      else x[c] = x[c] * a;
+    }
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+template <int OP, typename T>
+void run(const char* name, T a, T b) {
+  int blocks = 152 * 8, threads = 256, iters = 2048;
+  T* out; cudaMalloc(&out, sizeof(T) * blocks * threads);
+  cudaEvent_t e0, e1; cudaEventCreate(&e0); cudaEventCreate(&e1);
+  k<OP, T><<<blocks, threads>>>(out, iters, a, b);
+  cudaDeviceSynchronize();
+  cudaEventRecord(e0);
+  for (int r = 0; r < 5; ++r) k<OP, T><<<blocks, threads>>>(out, iters, a, b);
+  cudaEventRecord(e1); cudaEventSynchronize(e1);
+  float ms; cudaEventElapsedTime(&ms, e0, e1);
+  double ops = 5.0 * blocks * threads * (double)iters * 8;
+  printf("%s: %.1f Gop/s (%.3f ms per launch) err=%s\n", name, ops / (ms * 1e-3) / 1e9, ms / 5,
+         cudaGetErrorString(cudaGetLastError()));
+  cudaFree(out);
+}
+int main() {
+  int clk; cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
+  int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  printf("SMs %d, clock %d kHz\n", sms, clk);
+  run<0, double>("DFMA", 0.999999, 1e-7);
+  run<1, double>("DADD", 0.999999, 1e-7);
+  run<2, double>("DMUL", 0.999999, 1e-7);
+  run<0, float>("FFMA", 0.999999f, 1e-7f);
+  run<1, float>("FADD", 0.999999f, 1e-7f);
+  return 0;
+}
+"""
 
 
 def load_peaks():
@@ -713,6 +767,17 @@ def solve_throughput(fp64_ms, fp64_cycles, mixed):
     return out
 
 
+def run_fp_pipe_probe():
+    """Compile FP_PIPE_PROBE_CU for sm_103a and run it (prints G operations/s per kind)."""
+    from paper_2008_03885_gb300 import _build
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "fp_pipe_probe.cu"), os.path.join(d, "fp_pipe_probe")
+        with open(src, "w") as fh:
+            fh.write(FP_PIPE_PROBE_CU)
+        subprocess.run([_build.nvcc(), *_build.ARCH, "-O3", "-o", exe, src], check=True)
+        subprocess.run([exe], check=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -734,7 +799,11 @@ def main():
                     help="profile solves: the batch's settings (N(0,1) right-hand side, n_min 16, 1e-8; three solves)")
     ap.add_argument("--profile-mixed", action="store_true", help="two mixed-precision solves (ncu)")
     ap.add_argument("--profile-fp64", action="store_true", help="two FP64 solves of the bench workload (ncu)")
+    ap.add_argument("--fp-pipe-probe", action="store_true", help="FP64/FP32 arithmetic issue rates (microbenchmark)")
     args = ap.parse_args()
+    if args.fp_pipe_probe:
+        run_fp_pipe_probe()
+        return
     if args.profile_case:
         run_profile_case(args)
         return
