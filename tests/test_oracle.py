@@ -386,13 +386,15 @@ def _cycle_matrix(o, l):
     return np.linalg.matrix_power(S, o.opt.nu2) @ C @ np.linalg.matrix_power(S, o.opt.nu1)
 
 
-@pytest.mark.parametrize("co,gamma,omega,nu1,nu2", [(REDBLACK, 2, 0.97, 1, 1), (REDBLACK, 1, 1.03, 2, 1),
-                                                     (REDBLACK, 3, 1.0, 1, 1), (STANDARD, 2, 0.9, 1, 2)])
-def test_cycle_operator_equals_error_propagation_recursion(co, gamma, omega, nu1, nu2):
+@pytest.mark.parametrize("co,gamma,omega,nu1,nu2,levels", [(REDBLACK, 2, 0.97, 1, 1, 3), (REDBLACK, 1, 1.03, 2, 1, 3),
+                                                            (REDBLACK, 3, 1.0, 1, 1, 3), (STANDARD, 2, 0.9, 1, 2, 3),
+                                                            (VARIABLE, 2, 1.0, 1, 1, 4)])
+def test_cycle_operator_equals_error_propagation_recursion(co, gamma, omega, nu1, nu2, levels):
     """The oracle's cycle, applied to every unit vector with f = 0, is the matrix of
-    the error-propagation recursion (three levels, V / W / Wn): the W recursion, the
-    colour order, omega / a_pp and the correction are each fixed by it."""
-    o = Oracle(16, 2, co, GALERKIN, Options(omega=omega, gamma=gamma, nu1=nu1, nu2=nu2, max_levels=3))
+    the error-propagation recursion (three or four levels, V / W / Wn; variable
+    coarsening: two red-black steps, then standard): the W recursion, the colour order,
+    omega / a_pp and the correction are each fixed by it."""
+    o = Oracle(16, 2, co, GALERKIN, Options(omega=omega, gamma=gamma, nu1=nu1, nu2=nu2, max_levels=levels))
     m = o.levels[0].size
     zero = np.zeros(m)
     M = np.column_stack([o.cycle(np.eye(m)[:, k].copy(), zero) for k in range(m)])

@@ -35,7 +35,7 @@ BATTERY = [
     ("Jacobi two-grid RFA", lambda: pins.test_jacobi_two_grid_spectrum_equals_rfa(0.8, 1, 1)),
     ("RBC two-level RFA", lambda: pins.test_two_level_rbc_spectrum_equals_rfa(omg.NONGALERKIN, 0.9, 1, 1)),
     ("cycle operator recursion",
-     lambda: pins.test_cycle_operator_equals_error_propagation_recursion(omg.REDBLACK, 2, 0.97, 1, 1)),
+     lambda: pins.test_cycle_operator_equals_error_propagation_recursion(omg.REDBLACK, 2, 0.97, 1, 1, 3)),
     ("converged = direct solve", pins.test_converged_multilevel_solution_equals_direct_solve),
     ("closed-form sine solution", pins.test_converged_solution_equals_closed_form_for_sine_rhs),
 ]
