@@ -103,3 +103,21 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     with pytest.raises(mg.MGError) as e:
         mg.mg_setup(64, 4, "standard", 6)
     assert e.value.status == mg.MG_ERR_INVALID
+
+
+def test_batch_arguments_are_checked_before_the_gpu(lib):
+    """The batch entry points validate their arguments on the host: an empty list, a
+    NULL handle and out-of-range options are MG_ERR_INVALID without a device; the
+    options struct is two C ints."""
+    import paper_2008_03885_gb300 as mg
+    assert ctypes.sizeof(mg.mg_batch_options) == 2 * ctypes.sizeof(ctypes.c_int)
+    with pytest.raises(mg.MGError) as e:
+        mg.mg_batch_create([])
+    assert e.value.status == mg.MG_ERR_INVALID
+    none = (ctypes.c_void_p * 1)(None)
+    out = ctypes.c_void_p()
+    for solo_min_n, workers in ((0, 0), (-1, 0), (0, -1), (0, 65)):
+        o = mg.mg_batch_options(solo_min_n, workers)
+        assert lib.mg_batch_create_ex(none, 1, ctypes.byref(o), ctypes.byref(out)) == mg.MG_ERR_INVALID
+        assert out.value is None
+    assert lib.mg_batch_destroy(None) == mg.MG_OK
