@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <new>
 #include <thread>
@@ -2329,8 +2330,6 @@ mg_status mg_batch_create_ex(mg_handle* const* handles, int count, const mg_batc
   for (int p = 0; p < count; ++p) {
     const mg_handle* h = handles[p];
     if (!h) return MG_ERR_INVALID;
-    for (int q = 0; q < p; ++q)
-      if (handles[q] == h) return MG_ERR_INVALID;  // each problem owns its handle's arrays
     const mg_options& o = h->opt;
     if (o.precision != o0.precision || o.nu1 != o0.nu1 || o.nu2 != o0.nu2 || o.fma_contract != o0.fma_contract ||
         (o.precision == MG_PREC_MIXED_FP32 && o.inner_cycles != o0.inner_cycles))
@@ -2339,6 +2338,11 @@ mg_status mg_batch_create_ex(mg_handle* const* handles, int count, const mg_batc
         o.boundary != MG_BOUNDARY_DIRICHLET || o.transfer_order != 2)
       return MG_ERR_UNSUPPORTED;
     if ((int)h->host.size() > kTailMaxLevels) return MG_ERR_UNSUPPORTED;
+  }
+  {  // each problem owns its handle's level arrays: a handle may appear once
+    std::vector<const mg_handle*> seen(handles, handles + count);
+    std::sort(seen.begin(), seen.end(), std::less<const mg_handle*>());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return MG_ERR_INVALID;
   }
   std::vector<int> solo, rest;
   for (int p = 0; p < count; ++p) (handles[p]->N >= solo_min_n ? solo : rest).push_back(p);
